@@ -1,0 +1,107 @@
+"""Seeded synthetic workloads shaped like the paper's shear-flow runs (Sec. 6).
+
+Each builder returns plain numpy arrays and numbers; it does none of the
+method's arithmetic. Lattice nodes sit at integer coordinates ``0..n-1``;
+the moving walls sit half a spacing outside the first and last y rows.
+
+Readings of the paper that fix these shapes:
+
+* Sec. 6.1 drives linear shear by moving the x-z planes in -x (bottom) and
+  +x (top) with ``u_wall = H * gamma_dot / 2``; periodic in x and z.
+* Sec. 6.1 defines ``Ca = eta * gamma_dot / mu``. In lattice units
+  ``eta = rho * c_s^2 * (tau - 1/2)`` with ``rho = 1`` and ``gamma_dot =
+  2 u_wall / ny``.
+* Sec. 2 sets ``mu_1 = w mu`` and ``mu_2 = (1 - w) mu``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .mesh import perturb, sphere_tet_mesh
+
+NOISE_SEED = 20030313
+
+
+@dataclass
+class Cell:
+    x_ref: np.ndarray  # [V,3] float64, absolute lattice coordinates
+    tets: np.ndarray  # [T,4] int32
+    y0: np.ndarray  # [V,3] float64, current positions at t = 0
+    mu: float
+    kappa: float
+    w: float
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    u_wall_lo: float  # x velocity of the wall at y = -1/2
+    u_wall_hi: float  # x velocity of the wall at y = ny - 1/2
+    body_force: tuple = (0.0, 0.0, 0.0)
+    cells: list = field(default_factory=list)
+    steps: int = 100
+
+    @property
+    def n_nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_tets(self) -> int:
+        return sum(len(c.tets) for c in self.cells)
+
+    @property
+    def n_verts(self) -> int:
+        return sum(len(c.x_ref) for c in self.cells)
+
+
+def lattice_viscosity(tau: float) -> float:
+    """Kinematic viscosity of the BGK lattice fluid, c_s^2 (tau - 1/2)."""
+    return (tau - 0.5) / 3.0
+
+
+def shear_modulus_for_ca(ca: float, tau: float, u_wall: float, ny: int) -> float:
+    """mu from Ca = eta gamma_dot / mu (Sec. 6.1), rho = 1."""
+    gamma_dot = 2.0 * u_wall / ny
+    return lattice_viscosity(tau) * gamma_dot / ca
+
+
+def sphere_cell(R, h, centre, mu, kappa, w, noise=0.0, seed=NOISE_SEED) -> Cell:
+    x, tets = sphere_tet_mesh(R, h)
+    x = x + np.asarray(centre, np.float64)[None, :]
+    y0 = perturb(x, noise, seed) if noise > 0 else x.copy()
+    return Cell(x_ref=x, tets=tets, y0=y0, mu=mu, kappa=kappa, w=w)
+
+
+def small_shear(steps: int = 100) -> Workload:
+    """32^3 box, R = 8 sphere (~1k vertices, ~4.3k tets), mu = 1e-3,
+    kappa = 0.1, w = 0.5, current positions perturbed by 1 % of R, tau = 1,
+    walls at -/+0.01. Sized for the FP64 oracle."""
+    cell = sphere_cell(8.0, 1.4, (15.5, 15.5, 15.5), 1e-3, 0.1, 0.5, noise=0.08)
+    return Workload("shear_32^3_R8", 32, 32, 32, 1.0, -0.01, 0.01, cells=[cell], steps=steps)
+
+
+def production_shear(ca: float = 0.2, w: float = 1.0, steps: int = 10000, n: int = 128) -> Workload:
+    """128^3 box, R = 16 sphere (~4.2k vertices, ~20k tets) at the centre,
+    walls at -/+0.05, tau = 1; mu from Ca, kappa = 50 mu."""
+    u_wall = 0.05
+    mu = shear_modulus_for_ca(ca, 1.0, u_wall, n)
+    c = (n - 1) / 2.0
+    cell = sphere_cell(16.0, 1.72, (c, c, c), mu, 50.0 * mu, w)
+    return Workload(f"shear_{n}^3_R16_Ca{ca}_w{w}", n, n, n, 1.0, -u_wall, u_wall, cells=[cell], steps=steps)
+
+
+def random_displacements(cell: Cell, amplitude: float, seed: int) -> np.ndarray:
+    """Positions of ``cell`` perturbed by ``amplitude * U(-1, 1)``."""
+    return perturb(cell.x_ref, amplitude, seed)
+
+
+def random_populations_like(shape, scale: float, seed: int) -> np.ndarray:
+    """Seeded uniform noise of the given shape (for lattice initial states)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return scale * rng.uniform(-1.0, 1.0, size=shape)
