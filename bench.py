@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled cell/fluid time step on one GB300 (per rank).
+
+Workload: single cell in linear shear at production size - 128^3 D3Q19
+lattice (tau = 1, walls at -/+0.05), one R = 16 sphere of ~4.2k vertices and
+~20k tets, Mooney-Rivlin mu from Ca = 0.2, kappa = 50 mu, w = 0.5, FP32.
+One benchmark step is one full coupled time step (tet forces, vertex sums +
+spread, stream-collide, interpolate + advect). Populations (2 x 159 MB) are
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (bounded samples per step).
+
+Multi-GPU (``torchrun --nproc-per-node N``): N independent replicas of the
+workload, one per GPU, no data exchange (weak scaling); the timed region is
+bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled LBM-IBM steps/s & MLUPS (% HBM roofline); tet-forces/s; FP16 vs FP32 error"
+POP_BYTES_PER_NODE = 2 * 19 * 4  # read + write of 19 FP32 populations
+FORCE_BYTES_PER_NODE = 12  # FP32 force read where the cell spreads force
+KERNELS = ("k_tet_force", "k_gather_spread", "k_lbm", "k_interp_advect")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=128, help="cubic lattice extent")
+    ap.add_argument("--ca", type=float, default=0.2)
+    ap.add_argument("--w", type=float, default=0.5)
+    ap.add_argument("--profile-steps", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from workloads import configs
+
+    return configs.production_shear(ca=args.ca, w=args.w, n=args.n)
+
+
+def config_of(wl):
+    return {
+        "workload": wl.name,
+        "lattice": [wl.nx, wl.ny, wl.nz],
+        "n_verts": wl.n_verts,
+        "n_tets": wl.n_tets,
+        "tau": wl.tau,
+        "u_wall": [wl.u_wall_lo, wl.u_wall_hi],
+        "parallelism": "replicas",
+        "l2": "no flush: populations 2 x %.0f MB > 129 MB L2" % (19 * 4 * wl.n_nodes / 1e6),
+    }
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def support_nodes(y, dims):
+    """Number of distinct lattice nodes in the trilinear support of y."""
+    nx, ny, nz = dims
+    b = np.floor(y).astype(np.int64)
+    keys = []
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                X = (b[:, 0] + dx) % nx
+                Y = b[:, 1] + dy
+                Z = (b[:, 2] + dz) % nz
+                keys.append(X + nx * (Y + ny * Z))
+    return int(np.unique(np.concatenate(keys)).size)
+
+
+def traffic_record(kernel, n):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current source of that kernel (else None)."""
+    src = os.path.join(ROOT, "paper_2003_03130_gb300", "csrc", "lbm.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{n}cubed.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_b) or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def cpu_baseline(wl, seconds):
+    """Oracle (FP64, single thread, as it stands) on the same workload:
+    whole coupled steps until `seconds` of CPU work have passed."""
+    import oracle
+
+    oracle.build()
+    sim = oracle.Coupled(wl)
+    sim.step(1)  # first touch
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        sim.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= 200:
+            break
+    return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} whole coupled steps of the same {wl.nx}x{wl.ny}x{wl.nz} workload, FP64, 1 thread",
+            "mlups": n * wl.n_nodes / dt / 1e6}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    dev = local
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    import paper_2003_03130_gb300 as P
+    from paper_2003_03130_gb300 import build as cbuild
+
+    cbuild.build()
+    wl = workload(args)
+    stream = torch.cuda.Stream(dev)
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        ctx = P.cf_create(dev, stream.cuda_stream)
+        ids = P.load_workload(ctx, wl)
+        P.cf_step(ctx, W)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(dev)
+        clocks.start()
+        time.sleep(0.3)
+        ev0.record(stream)
+        P.cf_step_async(ctx, K)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        P.cf_synchronize(ctx)
+        ms = ev0.elapsed_time(ev1)
+        barrier()
+        if world > 1:
+            t = torch.tensor([ms], device=f"cuda:{dev}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+
+        # per-kernel durations: CUDA events around every launch, same stream
+        kms = P.cf_step_profiled(ctx, args.profile_steps)
+
+        # end to end through the public API with host buffers: per step the
+        # positions go host -> device (pinned), one step, positions back
+        nv = P.cf_cell_verts(ctx, ids[0])
+        y_in = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
+        y_out = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
+        P.cf_get_positions(ctx, ids[0], out=y_in)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            P.cf_set_positions(ctx, ids[0], y_in)
+            P.cf_step(ctx, 1)
+            P.cf_get_positions(ctx, ids[0], out=y_out)
+            y_in[...] = y_out
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        y_now = P.cf_get_positions(ctx, ids[0])
+        P.cf_destroy(ctx)
+
+    steps_per_s = world * K / (ms / 1e3)
+    n_sup = support_nodes(y_now, (wl.nx, wl.ny, wl.nz))
+    alg_bytes = POP_BYTES_PER_NODE * wl.n_nodes + FORCE_BYTES_PER_NODE * n_sup
+    lbm_s = kms[2] / 1e3
+    achieved = alg_bytes / lbm_s / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = traffic_record("k_lbm", wl.nx) if wl.nx == wl.ny == wl.nz else None
+    step_ms_profiled = float(sum(kms))
+    out = {
+        "metric": METRIC,
+        "value": steps_per_s,
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded sphere mesh, fluid at rest at t=0)",
+        "config": config_of(wl),
+        "mlups": world * wl.n_nodes * K / (ms / 1e3) / 1e6,
+        "tet_forces_per_s": world * wl.n_tets * K / (ms / 1e3),
+        "gpu_launches": 4 * K,
+        "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
+        "kernel_share": dict(zip(KERNELS, [float(x) / step_ms_profiled for x in kms])),
+        "roofline": {
+            "kernel": "k_lbm",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
+        },
+        "e2e": {
+            "value": world * args.e2e_steps / e2e_s,
+            "unit": "steps/s",
+            "h2d_bytes_per_step": int(nv * 3 * 8),
+            "d2h_bytes_per_step": int(nv * 3 * 8),
+            "api": "cf_set_positions + cf_step(1) + cf_get_positions, pinned host buffers",
+        },
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 oracle on the host cores. Each benchmark step processes a
+    bounded sample: the fraction 1/m of one coupled step (a contiguous slice
+    of the tets, of the vertices and of the lattice nodes, cycling through
+    the slices), with m chosen so that the whole run takes about two
+    minutes; the rate is scaled back to whole steps."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import ctypes
+
+    import oracle
+
+    oracle.build()
+    L = oracle.lib()
+    wl = workload(args)
+    sim = oracle.Coupled(wl)
+    mesh, fl = sim.mesh, sim.fluid
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))  # noqa: E731
+    T, V, N = len(mesh.tets), len(mesh.x), wl.n_nodes
+    fc = np.zeros((T, 4, 3))
+    fv = np.zeros((V, 3))
+    vel = np.zeros((V, 3))
+    fout = np.empty_like(fl.f)
+    cell = mesh.cell
+
+    def sample(k, m):
+        t0, t1 = k * T // m, (k + 1) * T // m
+        v0, v1 = k * V // m, (k + 1) * V // m
+        n0, n1 = k * N // m, (k + 1) * N // m
+        u = sim.y - mesh.x
+        L.ora_tet_force(t0, t1, ip(mesh.tets), dp(mesh.B), dp(mesh.V0), dp(u), ip(cell), dp(mesh.mu),
+                        dp(mesh.kappa), dp(mesh.w), dp(fc), None)
+        L.ora_gather(v0, v1, ip(mesh.ptr), ip(mesh.idx), dp(fc), dp(fv))
+        L.ora_spread(v0, v1, dp(sim.y), dp(fv), wl.nx, wl.ny, wl.nz, dp(sim.Fn))
+        L.ora_lbm_step(wl.nx, wl.ny, wl.nz, wl.tau, wl.u_wall_lo, wl.u_wall_hi, dp(fl.g), dp(fl.f), dp(sim.Fn),
+                       dp(fout), dp(fl.rho), dp(fl.u), n0, n1)
+        L.ora_interp(v0, v1, dp(sim.y), dp(fl.u), wl.nx, wl.ny, wl.nz, dp(vel))
+        sim.y[v0:v1] += vel[v0:v1]
+
+    t = time.perf_counter()
+    sample(0, 16)
+    est_full = 16 * (time.perf_counter() - t)
+    budget = 120.0
+    m = max(1, min(1024, int(np.ceil((args.steps + args.warmup) * est_full / budget))))
+    for k in range(args.warmup):
+        sample(k % m, m)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        sample((args.warmup + k) % m, m)
+    dt = time.perf_counter() - t0
+    steps_per_s = args.steps / m / dt
+    desc = (f"each step = 1/{m} of a coupled step of {wl.name} (slices of tets, vertices and nodes); "
+            f"FP64, 1 thread")
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": steps_per_s,
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 / steps_per_s,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded sphere mesh, fluid at rest at t=0)",
+        "config": config_of(wl),
+        "mlups": N * steps_per_s / 1e6,
+        "tet_forces_per_s": T * steps_per_s,
+        "cpu_baseline": {"value": steps_per_s, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": steps_per_s, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * cellfsi.h - C ABI of the GB300 cell/fluid time-step library (libcellfsi.so).
+ *
+ * One time step of a hyperelastic tetrahedral cell immersed in a lattice-
+ * Boltzmann fluid (Mueller et al., "A hyperelastic model for simulating cells
+ * in flow"):
+ *   (a) Mooney-Rivlin nodal forces f_i^a = -V_0 dU/du_i^a on every tet
+ *       (Sec. 2, Sec. 3.1-3.2), summed per vertex;
+ *   (b) immersed-boundary coupling: vertex forces spread onto the lattice and
+ *       fluid velocity interpolated back with a discrete delta kernel (Sec. 6);
+ *   (c) D3Q19 lattice-Boltzmann stream-collide with forcing and moving walls
+ *       (Sec. 6.1: plane Couette flow, walls moving at -/+u_wall in x).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Units are lattice units: nodes at integer coordinates 0..n-1, time step 1.
+ *   The walls sit half a spacing outside rows y = 0 and y = ny-1; x and z are
+ *   periodic.
+ * - All pointer arguments are HOST pointers, row-major, owned by the caller.
+ *   The library copies inputs before returning and writes outputs into
+ *   caller-allocated arrays; it keeps no reference to caller memory.
+ * - Vertex arrays are [nv][3] doubles; tets are [nt][4] int32 vertex indices
+ *   local to the cell, corner 3 being the paper's vertex 4 (the origin of the
+ *   tet's local coordinates, Sec. 3.2).
+ * - Every call returns a cf_status. On failure cf_last_error() describes it;
+ *   the context stays usable unless the status is CF_ECUDA.
+ * - The library owns all device memory of a context and frees it in
+ *   cf_destroy(). Device work runs on the context's stream; calls that return
+ *   data synchronise that stream. No call traps or hangs the GPU: device-side
+ *   faults of the inputs (inverted tets, non-finite values, a delta support
+ *   that crosses a wall) are reported through status codes.
+ * - A context is not thread-safe; use one per host thread.
+ * - Call order: cf_create, then cf_lbm_init and/or cf_mesh_init (any order,
+ *   repeatable), cf_set_material, then cf_step. cf_step needs cf_lbm_init;
+ *   cf_compute_forces needs only meshes. Otherwise CF_ESTATE.
+ */
+#ifndef CELLFSI_H
+#define CELLFSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cf_ctx cf_ctx;
+
+typedef enum {
+    CF_OK = 0,
+    CF_EINVAL = 1,      /* bad argument: size, index range, repeated vertex, parameter range */
+    CF_EDEGENERATE = 2, /* reference tet with |det J| <= 1e-12 (longest edge)^3 */
+    CF_EINVERTED = 3,   /* a tet reached det F <= 0 during the run */
+    CF_ENONFINITE = 4,  /* NaN or Inf in forces, positions or populations */
+    CF_EDOMAIN = 5,     /* a vertex's delta support left 0 <= y <= ny-1 */
+    CF_ESTATE = 6,      /* call out of order */
+    CF_ECUDA = 7,       /* CUDA runtime error; context must be destroyed */
+    CF_ETIMEOUT = 8,    /* device work did not finish within the host timeout */
+    CF_ENOMEM = 9       /* device allocation failed */
+} cf_status;
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+ * the caller owns (for example PyTorch's current stream) or NULL, in which
+ * case the context creates and owns a non-blocking stream. */
+cf_status cf_create(cf_ctx **out, int device, void *cuda_stream);
+
+/* Free all device memory of the context. NULL is ignored. */
+void cf_destroy(cf_ctx *ctx);
+
+/* Lattice-Boltzmann fluid on nx*ny*nz nodes (Sec. 6.1 box), D3Q19 BGK with
+ * relaxation time tau (> 1/2), Guo forcing, halfway bounce-back walls at
+ * y = -1/2 moving at (u_wall_lo_x, 0, 0) and y = ny-1/2 moving at
+ * (u_wall_hi_x, 0, 0) (|u| < 0.1), and a uniform body-force density
+ * body_force[3] (NULL = none), e.g. for a pressure-driven channel. The fluid
+ * starts at rest with density 1. nx, ny, nz >= 1, nx*ny*nz*19 < 2^31.
+ * Re-initialises the fluid if called again. */
+cf_status cf_lbm_init(cf_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double tau,
+                      double u_wall_lo_x, double u_wall_hi_x, const double *body_force);
+
+/* Add one cell (Sec. 3): reference positions x_ref[nv][3] (absolute lattice
+ * coordinates), tets[nt][4] (local vertex indices) and current positions
+ * y0[nv][3] (NULL = x_ref). Computes once per tet the Jacobian
+ * J_ik = x_i^k - x_i^4, B = J^-1 and V_0 = |det J|/6 (Sec. 3.2); tets with
+ * det J < 0 get corners 1 and 2 swapped so that all are positively oriented.
+ * Builds the vertex -> (tet, corner) incidence rows used to sum vertex forces
+ * in a fixed order. Returns the new cell's id (0, 1, ...) in *cell_id_out.
+ * Errors: CF_EINVAL (nv < 4, nt < 1, index out of range, repeated vertex),
+ * CF_EDEGENERATE. Material defaults to mu = kappa = 0 (no force). */
+cf_status cf_mesh_init(cf_ctx *ctx, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets,
+                       const double *y0, int32_t *cell_id_out);
+
+/* Mooney-Rivlin material of one cell (Sec. 2): shear modulus mu >= 0, bulk
+ * modulus kappa >= 0 and ratio w in [0, 1], with mu_1 = w mu and
+ * mu_2 = (1 - w) mu; w = 1 is neo-Hookean. */
+cf_status cf_set_material(cf_ctx *ctx, int32_t cell_id, double mu, double kappa, double w);
+
+/* Advance n >= 0 coupled time steps t -> t+1, each: elastic forces at y^t,
+ * vertex sums, spread onto the lattice, one stream-collide with that force,
+ * interpolation of the fluid velocity u(t) at y^t and y^{t+1} = y^t + u.
+ * Synchronises and returns the first error any step raised. */
+cf_status cf_step(cf_ctx *ctx, int32_t n);
+
+/* Same as cf_step but returns after enqueueing the work on the stream; the
+ * error word is read by the next synchronising call (cf_synchronize or any
+ * cf_get_*). */
+cf_status cf_step_async(cf_ctx *ctx, int32_t n);
+
+/* Wait for the context's stream (polling, with the host timeout) and return
+ * the accumulated device error status. */
+cf_status cf_synchronize(cf_ctx *ctx);
+
+/* Measurement support: advance n >= 1 steps exactly as cf_step does, but
+ * with direct launches (no graph) and a CUDA event around each launch.
+ * kernel_ms[4] receives the mean duration in ms of the four launches of a
+ * step: tet forces, vertex sums + spread, stream-collide, interpolate +
+ * advect. Synchronises; returns the first device error. */
+cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms);
+
+/* Elastic vertex forces at the current positions only (Sec. 3.1 per tet,
+ * summed per vertex), without touching the fluid. */
+cf_status cf_compute_forces(cf_ctx *ctx);
+
+/* Vertex forces [nv][3] of a cell from the last cf_compute_forces or cf_step
+ * (the forces at y^t of the last step). */
+cf_status cf_get_forces(cf_ctx *ctx, int32_t cell_id, double *out);
+
+/* Current positions y = x_ref + u of a cell, [nv][3]. */
+cf_status cf_get_positions(cf_ctx *ctx, int32_t cell_id, double *out);
+
+/* Overwrite the current positions of a cell, [nv][3]. */
+cf_status cf_set_positions(cf_ctx *ctx, int32_t cell_id, const double *y);
+
+/* Fluid velocity u(t) of the last step on every node, [nz][ny][nx][3]:
+ * rho u = sum_i c_i f_i + F/2 with the force F of that step. */
+cf_status cf_get_velocity(cf_ctx *ctx, double *out);
+
+/* Fluid density rho of the last step on every node, [nz][ny][nx]. */
+cf_status cf_get_density(cf_ctx *ctx, double *out);
+
+/* Elastic energy E = sum over the cell's tets of V_0 U (Sec. 2-3.1) at the
+ * current positions, accumulated in double. */
+cf_status cf_get_energy(cf_ctx *ctx, int32_t cell_id, double *out);
+
+/* Incidence rows of a cell: ptr[nv+1], idx[4 nt] with entries 4*t + c (t
+ * local to the cell, ascending within each row). */
+cf_status cf_get_csr(cf_ctx *ctx, int32_t cell_id, int32_t *ptr, int32_t *idx);
+
+/* Oriented tets [nt][4] (local indices), B [nt][3][3] with B[k][j] =
+ * (J^-1)_kj and V0 [nt] as stored on the device (FP32 values widened).
+ * Any output pointer may be NULL. */
+cf_status cf_get_mesh(cf_ctx *ctx, int32_t cell_id, int32_t *tets, double *B, double *V0);
+
+/* Number of vertices / tets of a cell (0 if the id is unknown). */
+int32_t cf_cell_verts(const cf_ctx *ctx, int32_t cell_id);
+int32_t cf_cell_tets(const cf_ctx *ctx, int32_t cell_id);
+
+/* Message of the last failing call on this context ("" if none). */
+const char *cf_last_error(const cf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELLFSI_H */

@@ -1,0 +1,265 @@
+"""GB300 cell/fluid time step: Mooney-Rivlin tet forces, immersed-boundary
+coupling and D3Q19 lattice Boltzmann, all in the CUDA library
+``libcellfsi.so`` (C ABI in ``include/cellfsi.h``).
+
+This module only marshals arguments to that library through ctypes; every
+step of the computation runs in its kernels. There is no CPU fallback: if the
+library has not been built, importing the binding fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcellfsi.so")
+
+STATUS = {
+    0: "CF_OK", 1: "CF_EINVAL", 2: "CF_EDEGENERATE", 3: "CF_EINVERTED", 4: "CF_ENONFINITE",
+    5: "CF_EDOMAIN", 6: "CF_ESTATE", 7: "CF_ECUDA", 8: "CF_ETIMEOUT", 9: "CF_ENOMEM",
+}
+
+
+class CellFSIError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+_lib = None
+_d = ctypes.POINTER(ctypes.c_double)
+_i = ctypes.POINTER(ctypes.c_int32)
+
+
+def lib():
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        sig = {
+            "cf_create": ([ctypes.POINTER(vp), ctypes.c_int, vp], ctypes.c_int),
+            "cf_destroy": ([vp], None),
+            "cf_lbm_init": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, _d], ctypes.c_int),
+            "cf_mesh_init": ([vp, ctypes.c_int32, _d, ctypes.c_int32, _i, _d, _i], ctypes.c_int),
+            "cf_set_material": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+            "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_synchronize": ([vp], ctypes.c_int),
+            "cf_compute_forces": ([vp], ctypes.c_int),
+            "cf_step_profiled": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_get_forces": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_get_positions": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_set_positions": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_get_velocity": ([vp, _d], ctypes.c_int),
+            "cf_get_density": ([vp, _d], ctypes.c_int),
+            "cf_get_energy": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_get_csr": ([vp, ctypes.c_int32, _i, _i], ctypes.c_int),
+            "cf_get_mesh": ([vp, ctypes.c_int32, _i, _d, _d], ctypes.c_int),
+            "cf_cell_verts": ([vp, ctypes.c_int32], ctypes.c_int32),
+            "cf_cell_tets": ([vp, ctypes.c_int32], ctypes.c_int32),
+            "cf_last_error": ([vp], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status: int):
+    if status != 0:
+        msg = lib().cf_last_error(ctx.handle if ctx is not None else None)
+        raise CellFSIError(status, (msg or b"").decode())
+
+
+def _p(a, t=_d):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _out(out, shape, dtype=np.float64):
+    if out is None:
+        return np.empty(shape, dtype)
+    if out.shape != tuple(shape) or out.dtype != dtype or not out.flags.c_contiguous:
+        raise ValueError(f"output must be a C-contiguous {dtype} array of shape {shape}")
+    return out
+
+
+class Context:
+    """Holds a ``cf_ctx*`` and the sizes needed to shape outputs."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+        self.dims = None  # (nx, ny, nz)
+
+    def __del__(self):
+        try:
+            cf_destroy(self)
+        except Exception:
+            pass
+
+
+def _default_stream(device: int):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream or None
+    except ImportError:
+        pass
+    return None
+
+
+def cf_create(device: int = 0, stream=None) -> Context:
+    """``stream``: a cudaStream_t handle (int); default PyTorch's current
+    stream on ``device`` (the library makes its own if that is the legacy
+    default stream)."""
+    h = ctypes.c_void_p()
+    s = _default_stream(device) if stream is None else (stream or None)
+    st = lib().cf_create(ctypes.byref(h), device, s)
+    if st != 0:
+        raise CellFSIError(st, "cf_create failed")
+    return Context(h, device)
+
+
+def cf_destroy(ctx: Context):
+    if ctx.handle:
+        lib().cf_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def cf_last_error(ctx) -> str:
+    return (lib().cf_last_error(ctx.handle) or b"").decode()
+
+
+def cf_lbm_init(ctx, nx, ny, nz, tau, u_wall_lo_x, u_wall_hi_x, body_force=None):
+    g = None if body_force is None else _f64(body_force).reshape(3)
+    _check(ctx, lib().cf_lbm_init(ctx.handle, nx, ny, nz, tau, u_wall_lo_x, u_wall_hi_x, _p(g)))
+    ctx.dims = (nx, ny, nz)
+
+
+def cf_mesh_init(ctx, x_ref, tets, y0=None) -> int:
+    x = _f64(x_ref).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    y = None if y0 is None else _f64(y0).reshape(-1, 3)
+    if y is not None and y.shape != x.shape:
+        raise ValueError("y0 must have the shape of x_ref")
+    cid = ctypes.c_int32(-1)
+    _check(ctx, lib().cf_mesh_init(ctx.handle, len(x), _p(x), len(t), _p(t, _i), _p(y), ctypes.byref(cid)))
+    return cid.value
+
+
+def cf_set_material(ctx, cell_id, mu, kappa, w):
+    _check(ctx, lib().cf_set_material(ctx.handle, cell_id, mu, kappa, w))
+
+
+def cf_step(ctx, n: int = 1):
+    _check(ctx, lib().cf_step(ctx.handle, n))
+
+
+def cf_step_async(ctx, n: int = 1):
+    _check(ctx, lib().cf_step_async(ctx.handle, n))
+
+
+def cf_synchronize(ctx):
+    _check(ctx, lib().cf_synchronize(ctx.handle))
+
+
+def cf_step_profiled(ctx, n: int):
+    """Mean ms per launch of [tet force, gather + spread, stream-collide,
+    interpolate + advect] over n directly launched steps."""
+    ms = np.zeros(4)
+    _check(ctx, lib().cf_step_profiled(ctx.handle, n, _p(ms)))
+    return ms
+
+
+def cf_compute_forces(ctx):
+    _check(ctx, lib().cf_compute_forces(ctx.handle))
+
+
+def cf_cell_verts(ctx, cell_id) -> int:
+    return lib().cf_cell_verts(ctx.handle, cell_id)
+
+
+def cf_cell_tets(ctx, cell_id) -> int:
+    return lib().cf_cell_tets(ctx.handle, cell_id)
+
+
+def cf_get_forces(ctx, cell_id, out=None):
+    o = _out(out, (cf_cell_verts(ctx, cell_id), 3))
+    _check(ctx, lib().cf_get_forces(ctx.handle, cell_id, _p(o)))
+    return o
+
+
+def cf_get_positions(ctx, cell_id, out=None):
+    o = _out(out, (cf_cell_verts(ctx, cell_id), 3))
+    _check(ctx, lib().cf_get_positions(ctx.handle, cell_id, _p(o)))
+    return o
+
+
+def cf_set_positions(ctx, cell_id, y):
+    y = _f64(y)
+    if y.shape != (cf_cell_verts(ctx, cell_id), 3):
+        raise ValueError("positions must be [nv, 3]")
+    _check(ctx, lib().cf_set_positions(ctx.handle, cell_id, _p(y)))
+
+
+def cf_get_velocity(ctx, out=None):
+    nx, ny, nz = ctx.dims
+    o = _out(out, (nz, ny, nx, 3))
+    _check(ctx, lib().cf_get_velocity(ctx.handle, _p(o)))
+    return o
+
+
+def cf_get_density(ctx, out=None):
+    nx, ny, nz = ctx.dims
+    o = _out(out, (nz, ny, nx))
+    _check(ctx, lib().cf_get_density(ctx.handle, _p(o)))
+    return o
+
+
+def cf_get_energy(ctx, cell_id) -> float:
+    e = ctypes.c_double()
+    _check(ctx, lib().cf_get_energy(ctx.handle, cell_id, ctypes.byref(e)))
+    return e.value
+
+
+def cf_get_csr(ctx, cell_id):
+    nv, nt = cf_cell_verts(ctx, cell_id), cf_cell_tets(ctx, cell_id)
+    ptr = np.empty(nv + 1, np.int32)
+    idx = np.empty(4 * nt, np.int32)
+    _check(ctx, lib().cf_get_csr(ctx.handle, cell_id, _p(ptr, _i), _p(idx, _i)))
+    return ptr, idx
+
+
+def cf_get_mesh(ctx, cell_id):
+    nt = cf_cell_tets(ctx, cell_id)
+    tets = np.empty((nt, 4), np.int32)
+    B = np.empty((nt, 3, 3))
+    V0 = np.empty(nt)
+    _check(ctx, lib().cf_get_mesh(ctx.handle, cell_id, _p(tets, _i), _p(B), _p(V0)))
+    return tets, B, V0
+
+
+def load_workload(ctx, wl):
+    """Set up a :class:`workloads.configs.Workload` on the device: fluid, then
+    every cell with its material. Returns the cell ids."""
+    cf_lbm_init(ctx, wl.nx, wl.ny, wl.nz, wl.tau, wl.u_wall_lo, wl.u_wall_hi, wl.body_force)
+    ids = []
+    for c in wl.cells:
+        cid = cf_mesh_init(ctx, c.x_ref, c.tets, c.y0)
+        cf_set_material(ctx, cid, c.mu, c.kappa, c.w)
+        ids.append(cid)
+    return ids

@@ -1,0 +1,691 @@
+// C ABI of libcellfsi.so (declared in include/cellfsi.h): context, device
+// buffers, once-per-cell set-up and the coupled time step.
+//
+// One time step t -> t+1 is four launches on the context's stream:
+//   K1  tet forces at y^t (+ zero F on the support of y^{t-1})
+//   K23 vertex sums over incidence rows + spread onto F
+//   K4  stream + collide with F, populations f[p] -> f[1-p]
+//   K5  interpolate u(t) at y^t, y^{t+1} = y^t + u  (u[p] -> u[1-p])
+// Populations and displacements are double-buffered with one shared parity
+// p; the four launches of each parity are captured once into a CUDA graph
+// and replayed per step. F keeps the last step's force until the next step
+// begins, so the velocity of the last step can still be read.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/cellfsi.h"
+#include "internal.cuh"
+
+using namespace cf;
+
+namespace {
+
+struct CellInfo {
+    int v_off, nv, t_off, nt;
+    int origin[3];
+    float4 mat;
+};
+
+}  // namespace
+
+struct cf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    double timeout_s = 600.0;
+
+    unsigned *d_err = nullptr;
+    unsigned long long *d_status = nullptr;
+
+    // fluid
+    bool lbm_ready = false;
+    LbmParams lp{};
+    float *f[2] = {nullptr, nullptr};
+    float *F = nullptr;
+
+    // cells
+    int V = 0, T = 0;
+    std::vector<CellInfo> cells;
+    float4 *xr = nullptr, *u[2] = {nullptr, nullptr}, *fv = nullptr, *fc = nullptr;
+    double *xref64 = nullptr;
+    int4 *tet = nullptr;
+    float *B = nullptr, *V0 = nullptr;
+    int *tcell = nullptr, *origin = nullptr;
+    float4 *mat = nullptr;
+    int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
+    double *energy_partial = nullptr, *energy_out = nullptr;
+    double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
+
+    int cur = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+cf_status fail(cf_ctx *c, cf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CUDA_TRY(c, expr)                                                                              \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void drop_graphs(cf_ctx *c) {
+    for (auto &g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+MeshView view(const cf_ctx *c) {
+    MeshView m;
+    m.V = c->V;
+    m.T = c->T;
+    m.xr = c->xr;
+    m.origin = c->origin;
+    m.tet = c->tet;
+    m.B = c->B;
+    m.V0 = c->V0;
+    m.tcell = c->tcell;
+    m.mat = c->mat;
+    m.csr_ptr = c->csr_ptr;
+    m.csr_idx = c->csr_idx;
+    m.fc = c->fc;
+    m.fv = c->fv;
+    return m;
+}
+
+// Wait for the stream by polling, giving up after the context's timeout.
+cf_status wait_stream(cf_ctx *c) {
+    auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) return CF_OK;
+        if (e != cudaErrorNotReady) return fail(c, CF_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > c->timeout_s) return fail(c, CF_ETIMEOUT, "device work did not finish within %.0f s", c->timeout_s);
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// Read and clear the device error word.
+cf_status consume_errors(cf_ctx *c) {
+    unsigned h = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+    cf_status s = wait_stream(c);
+    if (s != CF_OK) return s;
+    if (h & ERR_INVERTED) return fail(c, CF_EINVERTED, "a tet reached det F <= 0");
+    if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
+    if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
+    return CF_OK;
+}
+
+cf_status enqueue_step(cf_ctx *c, int p, cudaStream_t s) {
+    const MeshView m = view(c);
+    const bool cells = c->T > 0;
+    if (cells) {
+        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s));
+        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s));
+    }
+    CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], cells ? c->F : nullptr, c->lp, s));
+    if (cells) CUDA_TRY(c, launch_interp_advect(m, c->f[1 - p], c->F, c->lp, c->u[p], c->u[1 - p], c->d_err, s));
+    return CF_OK;
+}
+
+cf_status build_graphs(cf_ctx *c) {
+    cudaStream_t cap;
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return fail(c, CF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        cf_status st = enqueue_step(c, p, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        if (st != CF_OK || e != cudaSuccess) {
+            if (e == cudaSuccess) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            return st != CF_OK ? st : fail(c, CF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&c->graph[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return fail(c, CF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaStreamDestroy(cap);
+    return CF_OK;
+}
+
+const CellInfo *cell_of(cf_ctx *c, int id) {
+    if (!c || id < 0 || id >= (int)c->cells.size()) return nullptr;
+    return &c->cells[id];
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
+    if (!out) return CF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CF_EINVAL;
+    cf_ctx *c = new cf_ctx();
+    c->device = device;
+    DeviceGuard g(device);
+    if (const char *t = getenv("CELLFSI_TIMEOUT_S")) c->timeout_s = atof(t);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return CF_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
+        dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+        cf_destroy(c);
+        return CF_ENOMEM;
+    }
+    *out = c;
+    return CF_OK;
+}
+
+void cf_destroy(cf_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    dfree(c->d_err);
+    dfree(c->d_status);
+    dfree(c->f[0]);
+    dfree(c->f[1]);
+    dfree(c->F);
+    dfree(c->xr);
+    dfree(c->u[0]);
+    dfree(c->u[1]);
+    dfree(c->fv);
+    dfree(c->fc);
+    dfree(c->xref64);
+    dfree(c->tet);
+    dfree(c->B);
+    dfree(c->V0);
+    dfree(c->tcell);
+    dfree(c->origin);
+    dfree(c->mat);
+    dfree(c->csr_ptr);
+    dfree(c->csr_idx);
+    dfree(c->csr_cursor);
+    dfree(c->energy_partial);
+    dfree(c->energy_out);
+    dfree(c->stage);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *cf_last_error(const cf_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau, double u_lo, double u_hi,
+                      const double *g) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (nx < 1 || ny < 1 || nz < 1) return fail(c, CF_EINVAL, "lattice extents must be >= 1");
+    const long long N = (long long)nx * ny * nz;
+    if (N * 19 >= (1LL << 31)) return fail(c, CF_EINVAL, "lattice too large: 19 * nx*ny*nz must be < 2^31");
+    if (!(tau > 0.5)) return fail(c, CF_EINVAL, "tau must be > 1/2");
+    if (!(std::fabs(u_lo) < 0.1 && std::fabs(u_hi) < 0.1)) return fail(c, CF_EINVAL, "|u_wall| must be < 0.1");
+    if (g && !(std::isfinite(g[0]) && std::isfinite(g[1]) && std::isfinite(g[2])))
+        return fail(c, CF_EINVAL, "body force must be finite");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    dfree(c->f[0]);
+    dfree(c->f[1]);
+    dfree(c->F);
+    c->lbm_ready = false;
+    LbmParams p{};
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.N = N;
+    p.omega = (float)(1.0 / tau);
+    p.guo = (float)(1.0 - 0.5 / tau);
+    p.uw_lo = (float)u_lo;
+    p.uw_hi = (float)u_hi;
+    p.gx = g ? (float)g[0] : 0.f;
+    p.gy = g ? (float)g[1] : 0.f;
+    p.gz = g ? (float)g[2] : 0.f;
+    CUDA_TRY(c, dalloc(&c->f[0], 19 * (size_t)N));
+    CUDA_TRY(c, dalloc(&c->f[1], 19 * (size_t)N));
+    CUDA_TRY(c, dalloc(&c->F, 3 * (size_t)N));
+    CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
+    CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float) * 3 * (size_t)N, c->stream));
+    c->lp = p;
+    // both displacement buffers must agree: the first step clears F on the
+    // support of the "previous" positions
+    if (c->V > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->u[1 - c->cur], c->u[c->cur], sizeof(float4) * c->V, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    c->lbm_ready = true;
+    return wait_stream(c);
+}
+
+cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets, const double *y0,
+                       int32_t *cell_id_out) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (nv < 4 || nt < 1 || !x_ref || !tets) return fail(c, CF_EINVAL, "need nv >= 4, nt >= 1 and non-null arrays");
+    if ((long long)c->T + nt > INT_MAX / 4 || (long long)c->V + nv > INT_MAX / 4)
+        return fail(c, CF_EINVAL, "mesh too large");
+    double mean[3] = {0, 0, 0};
+    for (int v = 0; v < nv; ++v)
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(x_ref[3 * v + a]) || (y0 && !std::isfinite(y0[3 * v + a])))
+                return fail(c, CF_EINVAL, "non-finite coordinate at vertex %d", v);
+            mean[a] += x_ref[3 * v + a];
+        }
+    CellInfo ci;
+    ci.v_off = c->V;
+    ci.nv = nv;
+    ci.t_off = c->T;
+    ci.nt = nt;
+    for (int a = 0; a < 3; ++a) ci.origin[a] = (int)std::lround(mean[a] / nv);
+    ci.mat = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int V1 = c->V + nv, T1 = c->T + nt, cell = (int)c->cells.size();
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+
+    // new arrays; the old ones are freed only on success
+    cf_ctx n;  // holder for the new buffers (never destroyed as a context)
+    double *x64 = nullptr, *y64 = nullptr;
+    int *tin = nullptr;
+    auto cleanup = [&]() {
+        dfree(n.xr); dfree(n.u[0]); dfree(n.u[1]); dfree(n.fv); dfree(n.fc); dfree(n.xref64); dfree(n.tet);
+        dfree(n.B); dfree(n.V0); dfree(n.tcell); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
+        dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(x64); dfree(y64);
+        dfree(tin);
+    };
+#define TRY_N(expr)                                                                                    \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            cleanup();                                                                                 \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA, "%s: %s", #expr,   \
+                        cudaGetErrorString(e_));                                                       \
+        }                                                                                              \
+    } while (0)
+    TRY_N(dalloc(&n.xr, V1));
+    TRY_N(dalloc(&n.u[0], V1));
+    TRY_N(dalloc(&n.u[1], V1));
+    TRY_N(dalloc(&n.fv, V1));
+    TRY_N(dalloc(&n.fc, 4 * (size_t)T1));
+    TRY_N(dalloc(&n.xref64, 3 * (size_t)V1));
+    TRY_N(dalloc(&n.tet, T1));
+    TRY_N(dalloc(&n.B, 9 * (size_t)T1));
+    TRY_N(dalloc(&n.V0, T1));
+    TRY_N(dalloc(&n.tcell, T1));
+    TRY_N(dalloc(&n.origin, 3 * (cell + 1)));
+    TRY_N(dalloc(&n.mat, cell + 1));
+    TRY_N(dalloc(&n.csr_ptr, V1 + 1));
+    TRY_N(dalloc(&n.csr_idx, 4 * (size_t)T1));
+    TRY_N(dalloc(&n.csr_cursor, V1));
+    TRY_N(dalloc(&n.energy_partial, (T1 + 255) / 256 + 1));
+    TRY_N(dalloc(&n.stage, 3 * (size_t)V1));
+    TRY_N(dalloc(&x64, 3 * (size_t)nv));
+    TRY_N(dalloc(&tin, 4 * (size_t)nt));
+    if (y0) TRY_N(dalloc(&y64, 3 * (size_t)nv));
+    cudaStream_t s = c->stream;
+    if (c->V > 0) {
+        TRY_N(cudaMemcpyAsync(n.xr, c->xr, sizeof(float4) * c->V, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.u[0], c->u[0], sizeof(float4) * c->V, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.u[1], c->u[1], sizeof(float4) * c->V, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.xref64, c->xref64, sizeof(double) * 3 * c->V, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.tet, c->tet, sizeof(int4) * c->T, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpy2DAsync(n.B, sizeof(float) * T1, c->B, sizeof(float) * c->T, sizeof(float) * c->T, 9,
+                                cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.V0, c->V0, sizeof(float) * c->T, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.tcell, c->tcell, sizeof(int) * c->T, cudaMemcpyDeviceToDevice, s));
+    }
+    std::vector<int> orig(3 * (cell + 1));
+    std::vector<float4> mats(cell + 1);
+    for (int i = 0; i < cell; ++i) {
+        for (int a = 0; a < 3; ++a) orig[3 * i + a] = c->cells[i].origin[a];
+        mats[i] = c->cells[i].mat;
+    }
+    for (int a = 0; a < 3; ++a) orig[3 * cell + a] = ci.origin[a];
+    mats[cell] = ci.mat;
+    TRY_N(cudaMemcpyAsync(n.origin, orig.data(), sizeof(int) * orig.size(), cudaMemcpyHostToDevice, s));
+    TRY_N(cudaMemcpyAsync(n.mat, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, s));
+    TRY_N(cudaMemcpyAsync(x64, x_ref, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s));
+    TRY_N(cudaMemcpyAsync(tin, tets, sizeof(int) * 4 * nt, cudaMemcpyHostToDevice, s));
+    if (y0) TRY_N(cudaMemcpyAsync(y64, y0, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s));
+    TRY_N(cudaMemsetAsync(c->d_status, 0xff, sizeof(unsigned long long), s));
+    TRY_N(launch_mesh_prepare(x64, nv, tin, nt, c->V, c->T, T1, cell, n.tet, n.B, n.V0, n.tcell, c->d_status, s));
+    unsigned long long st = 0;
+    TRY_N(cudaMemcpyAsync(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
+    TRY_N(cudaStreamSynchronize(s));
+    if (st != ~0ULL) {
+        cleanup();
+        const int code = (int)(st & 0xff), bad = (int)(st >> 8);
+        if (code == 3) return fail(c, CF_EDEGENERATE, "tet %d is degenerate (|det J| <= 1e-12 l^3)", bad);
+        return fail(c, CF_EINVAL, "tet %d: %s", bad, code == 1 ? "vertex index out of range" : "repeated vertex");
+    }
+    TRY_N(launch_vertex_prepare(x64, y64, nv, c->V, cell, ci.origin, n.xr, n.u[0], n.u[1], n.xref64, s));
+    // both parities of the new cell start at y0
+    TRY_N(launch_csr_build(n.tet, T1, V1, n.csr_ptr, n.csr_idx, n.csr_cursor, s));
+    TRY_N(cudaStreamSynchronize(s));
+#undef TRY_N
+    dfree(x64);
+    dfree(y64);
+    dfree(tin);
+    drop_graphs(c);
+    std::swap(c->xr, n.xr);
+    std::swap(c->u[0], n.u[0]);
+    std::swap(c->u[1], n.u[1]);
+    std::swap(c->fv, n.fv);
+    std::swap(c->fc, n.fc);
+    std::swap(c->xref64, n.xref64);
+    std::swap(c->tet, n.tet);
+    std::swap(c->B, n.B);
+    std::swap(c->V0, n.V0);
+    std::swap(c->tcell, n.tcell);
+    std::swap(c->origin, n.origin);
+    std::swap(c->mat, n.mat);
+    std::swap(c->csr_ptr, n.csr_ptr);
+    std::swap(c->csr_idx, n.csr_idx);
+    std::swap(c->csr_cursor, n.csr_cursor);
+    std::swap(c->energy_partial, n.energy_partial);
+    std::swap(c->stage, n.stage);
+    cleanup();  // frees the old buffers now held by n
+    c->V = V1;
+    c->T = T1;
+    c->cells.push_back(ci);
+    if (cell_id_out) *cell_id_out = cell;
+    return CF_OK;
+}
+
+cf_status cf_set_material(cf_ctx *c, int32_t id, double mu, double kappa, double w) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (id < 0 || id >= (int)c->cells.size()) return fail(c, CF_EINVAL, "unknown cell %d", id);
+    if (!(mu >= 0.0 && kappa >= 0.0 && w >= 0.0 && w <= 1.0 && std::isfinite(mu) && std::isfinite(kappa)))
+        return fail(c, CF_EINVAL, "need mu >= 0, kappa >= 0, 0 <= w <= 1");
+    CellInfo &ci = c->cells[id];
+    ci.mat = make_float4((float)(w * mu), (float)((1.0 - w) * mu), (float)kappa, 0.f);
+    CUDA_TRY(c, cudaMemcpyAsync(c->mat + id, &ci.mat, sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+    return wait_stream(c);
+}
+
+cf_status cf_step_async(cf_ctx *c, int32_t n) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
+    if (!c->graph[0]) {
+        cf_status s = build_graphs(c);
+        if (s != CF_OK) return s;
+    }
+    for (int i = 0; i < n; ++i) {
+        CUDA_TRY(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+        c->cur ^= 1;
+    }
+    return CF_OK;
+}
+
+cf_status cf_synchronize(cf_ctx *c) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    return consume_errors(c);
+}
+
+cf_status cf_step(cf_ctx *c, int32_t n) {
+    cf_status s = cf_step_async(c, n);
+    if (s != CF_OK) return s;
+    return cf_synchronize(c);
+}
+
+cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms) {
+    if (!c || !kernel_ms) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (n < 1) return fail(c, CF_EINVAL, "n must be >= 1");
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
+    const int BATCH = 32;
+    std::vector<cudaEvent_t> ev(5 * BATCH);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(c, CF_ECUDA, "event create failed");
+    double acc[4] = {0, 0, 0, 0};
+    cf_status st = CF_OK;
+    const MeshView m = view(c);
+    const bool cells = c->T > 0;
+    cudaStream_t s = c->stream;
+    for (int done = 0; done < n && st == CF_OK;) {
+        const int b = std::min(BATCH, n - done);
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < b && e == cudaSuccess; ++i) {
+            const int p = c->cur;
+            cudaEvent_t *E = &ev[5 * i];
+            cudaEventRecord(E[0], s);
+            if (cells) e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s);
+            cudaEventRecord(E[1], s);
+            if (cells && e == cudaSuccess) e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s);
+            cudaEventRecord(E[2], s);
+            if (e == cudaSuccess) e = launch_lbm(c->f[p], c->f[1 - p], cells ? c->F : nullptr, c->lp, s);
+            cudaEventRecord(E[3], s);
+            if (cells && e == cudaSuccess)
+                e = launch_interp_advect(m, c->f[1 - p], c->F, c->lp, c->u[p], c->u[1 - p], c->d_err, s);
+            cudaEventRecord(E[4], s);
+            c->cur ^= 1;
+        }
+        if (e != cudaSuccess) {
+            st = fail(c, CF_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        st = wait_stream(c);
+        for (int i = 0; i < b && st == CF_OK; ++i)
+            for (int k = 0; k < 4; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[5 * i + k], ev[5 * i + k + 1]);
+                acc[k] += ms;
+            }
+        done += b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != CF_OK) return st;
+    for (int k = 0; k < 4; ++k) kernel_ms[k] = acc[k] / n;
+    return consume_errors(c);
+}
+
+cf_status cf_compute_forces(cf_ctx *c) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (c->T == 0) return fail(c, CF_ESTATE, "no cells");
+    const MeshView m = view(c);
+    CUDA_TRY(c, launch_tet_force(m, c->u[c->cur], c->d_err, nullptr, nullptr, nullptr, c->stream));
+    CUDA_TRY(c, launch_gather_spread(m, c->u[c->cur], nullptr, nullptr, c->d_err, c->stream));
+    return consume_errors(c);
+}
+
+cf_status cf_get_forces(cf_ctx *c, int32_t id, double *out) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    DeviceGuard dg(c->device);
+    CUDA_TRY(c, launch_get_forces(c->fv, ci->v_off, ci->nv, c->stage, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, sizeof(double) * 3 * ci->nv, cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c);
+}
+
+cf_status cf_get_positions(cf_ctx *c, int32_t id, double *out) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    DeviceGuard dg(c->device);
+    CUDA_TRY(c, launch_get_positions(c->u[c->cur], c->xref64, ci->v_off, ci->nv, c->stage, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, sizeof(double) * 3 * ci->nv, cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c);
+}
+
+cf_status cf_set_positions(cf_ctx *c, int32_t id, const double *y) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !y) return fail(c, CF_EINVAL, "unknown cell or null input");
+    DeviceGuard dg(c->device);
+    for (int i = 0; i < 3 * ci->nv; ++i)
+        if (!std::isfinite(y[i])) return fail(c, CF_EINVAL, "non-finite position");
+    CUDA_TRY(c, cudaMemcpyAsync(c->stage, y, sizeof(double) * 3 * ci->nv, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_set_positions(c->stage, ci->v_off, ci->nv, c->xref64, c->u[c->cur], c->stream));
+    return wait_stream(c);
+}
+
+static cf_status get_macro(cf_ctx *c, double *rho_out, double *u_out) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "no fluid: call cf_lbm_init");
+    const size_t N = (size_t)c->lp.N;
+    double *d;
+    CUDA_TRY(c, dalloc(&d, u_out ? 3 * N : N));
+    cudaError_t e = launch_lbm_macro(c->f[c->cur], c->F, c->lp, u_out ? nullptr : d, u_out ? d : nullptr, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(u_out ? u_out : rho_out, d, sizeof(double) * (u_out ? 3 * N : N), cudaMemcpyDeviceToHost,
+                            c->stream);
+    cf_status s = e == cudaSuccess ? wait_stream(c) : fail(c, CF_ECUDA, "%s", cudaGetErrorString(e));
+    cudaFree(d);
+    return s;
+}
+
+cf_status cf_get_velocity(cf_ctx *c, double *out) {
+    if (!out) return fail(c, CF_EINVAL, "null output");
+    return get_macro(c, nullptr, out);
+}
+
+cf_status cf_get_density(cf_ctx *c, double *out) {
+    if (!out) return fail(c, CF_EINVAL, "null output");
+    return get_macro(c, out, nullptr);
+}
+
+cf_status cf_get_energy(cf_ctx *c, int32_t id, double *out) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    DeviceGuard dg(c->device);
+    CUDA_TRY(c, launch_energy(view(c), c->u[c->cur], ci->t_off, ci->t_off + ci->nt, c->energy_partial, c->energy_out,
+                              c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->energy_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c);
+}
+
+cf_status cf_get_csr(cf_ctx *c, int32_t id, int32_t *ptr, int32_t *idx) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !ptr || !idx) return fail(c, CF_EINVAL, "unknown cell or null output");
+    DeviceGuard dg(c->device);
+    std::vector<int> p(ci->nv + 1);
+    CUDA_TRY(c, cudaMemcpyAsync(p.data(), c->csr_ptr + ci->v_off, sizeof(int) * (ci->nv + 1), cudaMemcpyDeviceToHost,
+                                c->stream));
+    cf_status s = wait_stream(c);
+    if (s != CF_OK) return s;
+    const int base = p[0], len = p[ci->nv] - p[0];
+    if (len != 4 * ci->nt) return fail(c, CF_ECUDA, "incidence rows inconsistent");
+    CUDA_TRY(c, cudaMemcpyAsync(idx, c->csr_idx + base, sizeof(int) * len, cudaMemcpyDeviceToHost, c->stream));
+    s = wait_stream(c);
+    if (s != CF_OK) return s;
+    for (int v = 0; v <= ci->nv; ++v) ptr[v] = p[v] - base;
+    for (int e = 0; e < len; ++e) idx[e] -= 4 * ci->t_off;
+    return CF_OK;
+}
+
+cf_status cf_get_mesh(cf_ctx *c, int32_t id, int32_t *tets, double *B, double *V0) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci) return fail(c, CF_EINVAL, "unknown cell");
+    DeviceGuard dg(c->device);
+    const int nt = ci->nt, T = c->T;
+    if (tets) {
+        std::vector<int4> t(nt);
+        CUDA_TRY(c, cudaMemcpyAsync(t.data(), c->tet + ci->t_off, sizeof(int4) * nt, cudaMemcpyDeviceToHost, c->stream));
+        cf_status s = wait_stream(c);
+        if (s != CF_OK) return s;
+        for (int i = 0; i < nt; ++i) {
+            tets[4 * i] = t[i].x - ci->v_off;
+            tets[4 * i + 1] = t[i].y - ci->v_off;
+            tets[4 * i + 2] = t[i].z - ci->v_off;
+            tets[4 * i + 3] = t[i].w - ci->v_off;
+        }
+    }
+    if (B) {
+        std::vector<float> b(9 * (size_t)nt);
+        CUDA_TRY(c, cudaMemcpy2DAsync(b.data(), sizeof(float) * nt, c->B + ci->t_off, sizeof(float) * T,
+                                      sizeof(float) * nt, 9, cudaMemcpyDeviceToHost, c->stream));
+        cf_status s = wait_stream(c);
+        if (s != CF_OK) return s;
+        for (int i = 0; i < nt; ++i)
+            for (int k = 0; k < 9; ++k) B[9 * i + k] = b[(size_t)k * nt + i];
+    }
+    if (V0) {
+        std::vector<float> v(nt);
+        CUDA_TRY(c, cudaMemcpyAsync(v.data(), c->V0 + ci->t_off, sizeof(float) * nt, cudaMemcpyDeviceToHost, c->stream));
+        cf_status s = wait_stream(c);
+        if (s != CF_OK) return s;
+        for (int i = 0; i < nt; ++i) V0[i] = v[i];
+    }
+    return CF_OK;
+}
+
+int32_t cf_cell_verts(const cf_ctx *c, int32_t id) {
+    return (c && id >= 0 && id < (int)c->cells.size()) ? c->cells[id].nv : 0;
+}
+
+int32_t cf_cell_tets(const cf_ctx *c, int32_t id) {
+    return (c && id >= 0 && id < (int)c->cells.size()) ? c->cells[id].nt : 0;
+}
+
+}  // extern "C"

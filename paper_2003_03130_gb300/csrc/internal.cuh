@@ -1,0 +1,148 @@
+// Internal declarations of the GB300 cell/fluid library: device layouts,
+// kernel launchers and the D3Q19 lattice as compile-time constants.
+//
+// Device layout (structure of arrays throughout, so that consecutive threads
+// touch consecutive words):
+//   populations  f[q * N + n], q = 0..18, n = x + nx*(y + ny*z), stored as the
+//                deviation f_q - w_q from the rest equilibrium (keeps FP32
+//                rounding relative to the O(u) signal, not to O(w_q));
+//   force field  F[a * N + n], a = 0..2;
+//   vertices     float4 per vertex (one 16-byte load in the tet gathers):
+//                xr (FP32 x_ref relative to the cell's integer origin, .w =
+//                cell id), u (FP32 displacement y - x_ref), fv (force);
+//                xref64 [V][3] FP64 for exact host round trips;
+//   tets         int4 tet[t], B[(3k + j) * T + t], V0[t], tcell[t];
+//   corner force float4 fc[c * T + t].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cf {
+
+// Error bits of the device error word (never trapped; read by the host).
+enum : unsigned {
+    ERR_INVERTED = 1u << 0,   // det F <= 0 in some tet
+    ERR_NONFINITE = 1u << 1,  // NaN / Inf in a force or a displacement
+    ERR_DOMAIN = 1u << 2,     // delta support outside 0 <= y <= ny-1
+};
+
+// ---------------------------------------------------------------- D3Q19
+// Velocity set: q = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = the twelve
+// vectors with two nonzero components in lexicographic order of (cx,cy,cz).
+// Opposite of q: axis pairs swap within (1,2), (3,4), (5,6); diagonal q <-> 25-q.
+__host__ __device__ constexpr int cx(int q) {
+    return q == 1 ? 1 : q == 2 ? -1 : (q >= 7 && q <= 10) ? -1 : (q >= 15) ? 1 : 0;
+}
+__host__ __device__ constexpr int cy(int q) {
+    return q == 3 ? 1 : q == 4 ? -1
+         : (q == 7 || q == 11 || q == 12 || q == 15) ? -1
+         : (q == 10 || q == 13 || q == 14 || q == 18) ? 1 : 0;
+}
+__host__ __device__ constexpr int cz(int q) {
+    return q == 5 ? 1 : q == 6 ? -1
+         : (q == 8 || q == 11 || q == 13 || q == 16) ? -1
+         : (q == 9 || q == 12 || q == 14 || q == 17) ? 1 : 0;
+}
+__host__ __device__ constexpr int opp(int q) {
+    return q == 0 ? 0 : q <= 6 ? (q % 2 ? q + 1 : q - 1) : 25 - q;
+}
+__host__ __device__ constexpr float wq(int q) {
+    return q == 0 ? 1.0f / 3.0f : q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f;
+}
+
+struct LbmParams {
+    int nx, ny, nz;
+    long long N;
+    float omega;        // 1/tau
+    float guo;          // 1 - 1/(2 tau)
+    float uw_lo, uw_hi; // wall x velocities at y = -1/2 and y = ny - 1/2
+    float gx, gy, gz;   // uniform body-force density
+};
+
+struct MeshView {
+    int V, T;
+    const float4 *xr;      // [V]: x_ref - origin (FP32), .w = cell id (int bits)
+    const int *origin;     // [3 * ncells], integer origin of each cell
+    const int4 *tet;       // [T]: global vertex indices, corner 3 = vertex 4
+    const float *B;        // [9][T]: B[(3k + j) * T + t] = (J^-1)_kj
+    const float *V0;       // [T]
+    const int *tcell;      // [T]
+    const float4 *mat;     // [ncells]: mu1, mu2, kappa, 0
+    const int *csr_ptr;    // [V+1]
+    const int *csr_idx;    // [4T]: entries 4 t + c, ascending per row
+    float4 *fc;            // [4][T]: corner force fc[c * T + t]
+    float4 *fv;            // [V]: vertex force
+};
+
+// Trilinear delta support of a vertex at x + u: lower corner (absolute node,
+// x and z not yet wrapped) and fractional offsets. False if the position is
+// not finite, absurdly far away, or the support leaves 0 <= y <= ny-1. Shared
+// by the spread, the interpolation and the clearing of F so that all three
+// see exactly the same node set.
+struct Support {
+    int bx, by, bz;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ bool support_of(const int *__restrict__ origin, float4 xr, float4 u, int ny,
+                                           Support &s) {
+    const int c = __float_as_int(xr.w);
+    const float px = xr.x + u.x, py = xr.y + u.y, pz = xr.z + u.z;
+    if (!(fabsf(px) < 1e6f && fabsf(py) < 1e6f && fabsf(pz) < 1e6f)) return false;  // also NaN
+    const float lx = floorf(px), ly = floorf(py), lz = floorf(pz);
+    s.fx = px - lx;
+    s.fy = py - ly;
+    s.fz = pz - lz;
+    s.bx = (int)lx + __ldg(origin + 3 * c + 0);
+    s.by = (int)ly + __ldg(origin + 3 * c + 1);
+    s.bz = (int)lz + __ldg(origin + 3 * c + 2);
+    return s.by >= 0 && s.by + 1 <= ny - 1;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `s` and return the launch status.
+// Once per cell (Sec. 3.2): validate, orient, B = J^-1 and V_0 in FP64;
+// *status receives min over failing tets of (t << 8 | code), code 1 = index
+// out of range, 2 = repeated vertex, 3 = degenerate.
+cudaError_t launch_mesh_prepare(const double *x64, int nv, const int *tets_in, int nt, int v_off, int t_off,
+                                int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
+                                unsigned long long *status, cudaStream_t s);
+cudaError_t launch_vertex_prepare(const double *x64, const double *y64, int nv, int v_off, int cell,
+                                  const int *origin_host3, float4 *xr, float4 *u0, float4 *u1, double *xref64,
+                                  cudaStream_t s);
+cudaError_t launch_csr_build(const int4 *tet, int T, int V, int *ptr, int *idx, int *cursor, cudaStream_t s);
+cudaError_t launch_set_positions(const double *y64, int v0, int nv, const double *xref64, float4 *u,
+                                 cudaStream_t s);
+cudaError_t launch_get_positions(const float4 *u, const double *xref64, int v0, int nv, double *y64,
+                                 cudaStream_t s);
+cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cudaStream_t s);
+
+// K1: elastic corner forces of all tets at displacements u; when `u_prev` is
+// non-null the same launch also zeroes the force field on the delta support
+// of the positions x + u_prev (where the previous step spread its forces).
+cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
+                             const LbmParams *lp, cudaStream_t s);
+// Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
+cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
+                          cudaStream_t s);
+// K2 (+K3): vertex force sums over the incidence rows; with F != null the
+// same threads spread their vertex force onto the lattice.
+cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
+                                 cudaStream_t s);
+// K4: pull stream + BGK collide with Guo forcing, fin -> fout.
+cudaError_t launch_lbm(const float *fin, float *fout, const float *F, const LbmParams &p, cudaStream_t s);
+// K5: velocity u(t) interpolated at x + u_cur from post-collision populations
+// and F; u_next = u_cur + velocity.
+cudaError_t launch_interp_advect(const MeshView &m, const float *f, const float *F, const LbmParams &p,
+                                 const float4 *u_cur, float4 *u_next, unsigned *err, cudaStream_t s);
+cudaError_t launch_lbm_init(float *f, const LbmParams &p, cudaStream_t s);
+cudaError_t launch_lbm_macro(const float *f, const float *F, const LbmParams &p, double *rho, double *u,
+                             cudaStream_t s);
+
+}  // namespace cf

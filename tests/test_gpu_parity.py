@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances: norm-wise relative error ||x_gpu - x_oracle|| / ||x_oracle||
+<= 1e-5 on forces, fluid velocities and displacements (FP32 path against
+FP64); bit-exact on tet orientation and incidence rows. Element-wise errors
+are not used because forces near the rest state are ~0.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import configs
+from workloads.configs import Cell, Workload
+from workloads.mesh import perturb, sphere_tet_mesh
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2003_03130_gb300 import build
+
+    build.build()
+    import paper_2003_03130_gb300 as P
+
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def small_cell(R=4.0, h=1.3, centre=(10.0, 10.0, 10.0), mu=1e-3, kappa=0.1, w=0.5, noise=0.1, seed=1):
+    x, t = sphere_tet_mesh(R, h)
+    x = x + np.asarray(centre)
+    y0 = perturb(x, noise, seed) if noise else x.copy()
+    return Cell(x, t, y0, mu, kappa, w)
+
+
+# ---------------------------------------------------------------- mesh set-up
+
+def test_mesh_setup_matches_oracle_bit_exact(P):
+    cell = configs.small_shear().cells[0]
+    ctx = P.cf_create(0)
+    cid = P.cf_mesh_init(ctx, cell.x_ref, cell.tets, cell.y0)
+    tets, B, V0 = P.cf_get_mesh(ctx, cid)
+    ot, oB, oV0 = oracle.mesh_prepare(cell.x_ref, cell.tets)
+    assert np.array_equal(tets, ot)
+    ptr, idx = P.cf_get_csr(ctx, cid)
+    optr, oidx = oracle.csr(len(cell.x_ref), ot)
+    assert np.array_equal(ptr, optr) and np.array_equal(idx, oidx)
+    assert np.allclose(B, oB, rtol=1e-6, atol=1e-7 * np.abs(oB).max())
+    assert np.allclose(V0, oV0, rtol=1e-6)
+    assert np.allclose(P.cf_get_positions(ctx, cid), cell.y0, rtol=0, atol=1e-6)
+
+
+# ---------------------------------------------------------------- forces
+
+@pytest.mark.parametrize("mat", [(1e-3, 0.1, 0.5), (1e-3, 0.1, 1.0), (2e-3, 0.1, 0.0), (6.5e-4, 50 * 6.5e-4, 1.0)])
+@pytest.mark.parametrize("amp", [0.02, 0.08, 0.2])
+def test_forces_match_oracle(P, mat, amp):
+    cell = configs.small_shear().cells[0]
+    y = perturb(cell.x_ref, amp, 17)
+    ctx = P.cf_create(0)
+    cid = P.cf_mesh_init(ctx, cell.x_ref, cell.tets, y)
+    P.cf_set_material(ctx, cid, *mat)
+    P.cf_compute_forces(ctx)
+    got = P.cf_get_forces(ctx, cid)
+    ref = oracle.Mesh([Cell(cell.x_ref, cell.tets, y, *mat)]).forces(y)
+    assert rel(got, ref) <= TOL
+    # same inputs, same bits: the vertex sums use fixed incidence-row order
+    P.cf_compute_forces(ctx)
+    assert np.array_equal(P.cf_get_forces(ctx, cid), got)
+
+
+def test_rest_state_forces_are_exactly_zero(P):
+    cell = configs.small_shear().cells[0]
+    ctx = P.cf_create(0)
+    cid = P.cf_mesh_init(ctx, cell.x_ref, cell.tets, None)
+    P.cf_set_material(ctx, cid, 1e-3, 0.1, 0.5)
+    P.cf_compute_forces(ctx)
+    assert np.abs(P.cf_get_forces(ctx, cid)).max() == 0.0
+    assert P.cf_get_energy(ctx, cid) == 0.0
+
+
+def test_energy_matches_oracle(P):
+    cell = configs.small_shear().cells[0]
+    ctx = P.cf_create(0)
+    cid = P.cf_mesh_init(ctx, cell.x_ref, cell.tets, cell.y0)
+    P.cf_set_material(ctx, cid, cell.mu, cell.kappa, cell.w)
+    e = P.cf_get_energy(ctx, cid)
+    ref = oracle.Mesh([cell]).energy(cell.y0)
+    assert abs(e - ref) <= TOL * abs(ref)
+
+
+def test_several_cells_with_own_materials(P):
+    cells = [small_cell(centre=(8.0, 9.0, 8.0), mu=1e-3, kappa=0.1, w=0.3, seed=2),
+             small_cell(R=3.0, h=1.1, centre=(22.0, 12.0, 14.0), mu=3e-3, kappa=0.05, w=1.0, seed=3),
+             small_cell(R=5.0, h=1.4, centre=(15.0, 20.0, 25.0), mu=5e-4, kappa=0.2, w=0.0, seed=4)]
+    ctx = P.cf_create(0)
+    ids = []
+    for c in cells:
+        ids.append(P.cf_mesh_init(ctx, c.x_ref, c.tets, c.y0))
+        P.cf_set_material(ctx, ids[-1], c.mu, c.kappa, c.w)
+    P.cf_compute_forces(ctx)
+    ref = oracle.Mesh(cells).forces(np.concatenate([c.y0 for c in cells]))
+    got = np.concatenate([P.cf_get_forces(ctx, i) for i in ids])
+    assert rel(got, ref) <= TOL
+    for i, c in zip(ids, cells):
+        assert abs(P.cf_get_energy(ctx, i) - oracle.Mesh([c]).energy(c.y0)) <= TOL * oracle.Mesh([c]).energy(c.y0)
+
+
+# ---------------------------------------------------------------- fluid
+
+def _fluid_pair(P, nx, ny, nz, tau, lo, hi, g, steps):
+    ctx = P.cf_create(0)
+    P.cf_lbm_init(ctx, nx, ny, nz, tau, lo, hi, g)
+    P.cf_step(ctx, steps)
+    fl = oracle.Fluid(nx, ny, nz, tau, lo, hi, g)
+    for _ in range(steps):
+        fl.step()
+    return ctx, fl
+
+
+def test_couette_start_up_matches_oracle(P):
+    ctx, fl = _fluid_pair(P, 16, 16, 8, 0.8, -0.02, 0.02, (0.0, 0.0, 0.0), 300)
+    assert rel(P.cf_get_velocity(ctx), fl.u) <= TOL
+    rho = P.cf_get_density(ctx)
+    assert np.abs(rho - fl.rho).max() <= 1e-6
+
+
+def test_ragged_box_with_body_force_matches_oracle(P):
+    ctx, fl = _fluid_pair(P, 37, 21, 13, 1.0, -0.01, 0.03, (1e-5, 0.0, 2e-6), 200)
+    assert rel(P.cf_get_velocity(ctx), fl.u) <= TOL
+    rho = P.cf_get_density(ctx)
+    assert abs((rho - 1.0).sum()) <= 1e-6 * rho.size ** 0.5  # mass
+    assert np.abs(rho - fl.rho).max() <= 1e-6
+
+
+def test_single_node_planes(P):
+    """nz = 1 and nx = 1: periodic directions of extent one."""
+    ctx, fl = _fluid_pair(P, 1, 9, 1, 0.9, -0.01, 0.01, (0.0, 0.0, 0.0), 100)
+    assert rel(P.cf_get_velocity(ctx), fl.u) <= TOL
+
+
+# ---------------------------------------------------------------- coupled
+
+def _coupled_pair(P, wl, steps):
+    ctx = P.cf_create(0)
+    ids = P.load_workload(ctx, wl)
+    sim = oracle.Coupled(wl)
+    P.cf_step(ctx, steps)
+    sim.step(steps)
+    y = np.concatenate([P.cf_get_positions(ctx, i) for i in ids])
+    f = np.concatenate([P.cf_get_forces(ctx, i) for i in ids])
+    return ctx, sim, y, f
+
+
+def test_coupled_small_shear_100_steps(P):
+    wl = configs.small_shear()
+    y0 = np.concatenate([c.y0 for c in wl.cells])
+    ctx, sim, y, f = _coupled_pair(P, wl, 100)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_coupled_ragged_box_two_cells_body_force(P):
+    cells = [small_cell(centre=(9.3, 8.7, 10.1), mu=2e-3, kappa=0.1, w=0.7, seed=5),
+             small_cell(R=3.5, h=1.2, centre=(28.2, 17.4, 7.9), mu=1e-3, kappa=0.3, w=0.2, seed=6)]
+    wl = Workload("ragged", 41, 27, 19, 0.9, -0.015, 0.02, body_force=(2e-6, 0.0, -1e-6), cells=cells)
+    y0 = np.concatenate([c.y0 for c in wl.cells])
+    ctx, sim, y, f = _coupled_pair(P, wl, 40)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_production_shear_full_size(P):
+    """128^3 lattice, R = 16 cell (~4.2k vertices, ~20k tets), in the launch
+    configuration the benchmark times (graph replay of cf_step): full-field
+    comparison after 3 steps, and the forces of a perturbed cell."""
+    wl = configs.production_shear(ca=0.2, w=0.5)
+    cell = wl.cells[0]
+    cell.y0 = perturb(cell.x_ref, 0.08, 20030313)  # min det F = 0.28 (0.16 inverts tets)
+    y0 = cell.y0.copy()
+    ctx, sim, y, f = _coupled_pair(P, wl, 3)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_step_then_set_positions_round_trip(P):
+    wl = configs.small_shear()
+    ctx = P.cf_create(0)
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 5)
+    y = P.cf_get_positions(ctx, cid)
+    P.cf_set_positions(ctx, cid, y + 0.25)
+    assert np.allclose(P.cf_get_positions(ctx, cid), y + 0.25, rtol=0, atol=2e-6)
+
+
+# ---------------------------------------------------------------- errors
+
+def test_errors_are_status_codes(P):
+    from paper_2003_03130_gb300 import CellFSIError
+
+    cell = small_cell(noise=0.0)
+    ctx = P.cf_create(0)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_step(ctx, 1)
+    assert e.value.name == "CF_ESTATE"
+    bad = cell.tets.copy()
+    bad[3, 2] = len(cell.x_ref) + 5
+    with pytest.raises(CellFSIError) as e:
+        P.cf_mesh_init(ctx, cell.x_ref, bad)
+    assert e.value.name == "CF_EINVAL"
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], float)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_mesh_init(ctx, flat, np.array([[0, 1, 2, 3]]))
+    assert e.value.name == "CF_EDEGENERATE"
+    with pytest.raises(CellFSIError) as e:
+        P.cf_lbm_init(ctx, 8, 8, 8, 0.4, 0.0, 0.0)
+    assert e.value.name == "CF_EINVAL"
+
+    cid = P.cf_mesh_init(ctx, cell.x_ref, cell.tets)
+    P.cf_set_material(ctx, cid, 1e-3, 0.1, 0.5)
+    y = cell.x_ref.copy()
+    t0 = cell.tets[0]
+    # push corner 0 of tet 0 through the opposite face: det F < 0
+    face = y[t0[1:]].mean(0)
+    y[t0[0]] = face + 1.5 * (face - y[t0[0]])
+    P.cf_set_positions(ctx, cid, y)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_compute_forces(ctx)
+    assert e.value.name == "CF_EINVERTED"
+    # the context stays usable
+    P.cf_set_positions(ctx, cid, cell.x_ref)
+    P.cf_compute_forces(ctx)
+
+    # a cell whose delta support crosses the wall
+    P.cf_lbm_init(ctx, 24, 24, 24, 1.0, 0.0, 0.0)
+    y = cell.x_ref.copy()
+    y[:, 1] += -10.0 + 3.5  # lowest vertices end below y = 0
+    P.cf_set_positions(ctx, cid, y)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_step(ctx, 1)
+    assert e.value.name == "CF_EDOMAIN"
