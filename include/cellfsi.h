@@ -156,6 +156,53 @@ int32_t cf_cell_tets(const cf_ctx *ctx, int32_t cell_id);
 /* Message of the last failing call on this context ("" if none). */
 const char *cf_last_error(const cf_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Vertex forces for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a service of the library. It is for
+ * code that is not allowed to call cudaMalloc or any allocating library
+ * routine - for example a solver running as a plugin inside a host
+ * application that owns all device memory, or a real-time loop whose memory
+ * is fixed before it starts. It computes the same elastic vertex forces as
+ * cf_compute_forces (Sec. 3.1-3.2 per tet, summed per vertex in incidence-row
+ * order) for one cell with one material, without a context, and allocates
+ * nothing: the per-corner forces between the two kernels live in a static
+ * device array of CF_STATIC_MAX_TETS * 64 bytes (4 MiB), plus 256 KiB of
+ * zeros, reserved on every GPU that loads the library until the process
+ * exits.
+ *
+ * All array pointers are DEVICE pointers owned by the caller; the layouts are
+ * those the library uses internally (cf_get_mesh and cf_get_csr return the
+ * same data on the host):
+ *   tets    [nt][4] int32, positively oriented, corner 3 = the paper's
+ *           vertex 4, 16-byte aligned;
+ *   B       [9][nt] float, B[(3k + j) * nt + t] = (J^-1)_kj of tet t;
+ *   V0      [nt] float, reference tet volumes;
+ *   u       [nv][4] float, displacement y - x_ref in the first three, 16-byte
+ *           aligned;
+ *   csr_ptr [nv+1], csr_idx [4 nt] int32: incidence rows, entries 4 t + c
+ *           ascending within each row;
+ *   f       [nv][4] float output, vertex force in the first three, 16-byte
+ *           aligned.
+ * mu, kappa, w: the material as in cf_set_material. cuda_stream: the stream
+ * to run on (NULL = legacy default stream); the call synchronises it.
+ *
+ * Returns CF_EINVAL for nt > CF_STATIC_MAX_TETS (the scratch would not fit),
+ * nv < 1, nt < 1, a null or misaligned pointer, or a material out of range;
+ * CF_EINVERTED / CF_ENONFINITE as cf_compute_forces; CF_ECUDA on a runtime
+ * error. Indices are not validated here (cf_mesh_init validates them).
+ *
+ * The first call on each device looks up the static array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Every call shares the one array: calls that
+ * overlap on the GPU (several streams or host threads at once) race and
+ * must be serialised by the caller. Each call overwrites the scratch it reads.
+ * ------------------------------------------------------------------------ */
+#define CF_STATIC_MAX_TETS 65536
+cf_status cf_vertex_forces_static(int32_t nv, int32_t nt, const int32_t *tets, const float *B, const float *V0,
+                                  const float *u, const int32_t *csr_ptr, const int32_t *csr_idx, double mu,
+                                  double kappa, double w, float *f, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

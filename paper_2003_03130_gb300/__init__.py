@@ -65,6 +65,8 @@ def lib():
             "cf_cell_verts": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_cell_tets": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_last_error": ([vp], ctypes.c_char_p),
+            "cf_vertex_forces_static": ([ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -251,6 +253,16 @@ def cf_get_mesh(ctx, cell_id):
     V0 = np.empty(nt)
     _check(ctx, lib().cf_get_mesh(ctx.handle, cell_id, _p(tets, _i), _p(B), _p(V0)))
     return tets, B, V0
+
+
+def cf_vertex_forces_static(nv, nt, tets, B, V0, u, csr_ptr, csr_idx, mu, kappa, w, f, stream=None):
+    """Vertex forces of one cell without a context and without any device
+    allocation. Every array argument is a DEVICE address (int) in the
+    layouts of ``cf_vertex_forces_static`` in include/cellfsi.h; ``stream``
+    is a cudaStream_t handle (int) or None."""
+    st = lib().cf_vertex_forces_static(nv, nt, tets, B, V0, u, csr_ptr, csr_idx, mu, kappa, w, f, stream or None)
+    if st != 0:
+        raise CellFSIError(st, "cf_vertex_forces_static failed")
 
 
 def load_workload(ctx, wl):
