@@ -55,7 +55,8 @@ typedef enum {
     CF_ESTATE = 6,      /* call out of order */
     CF_ECUDA = 7,       /* CUDA runtime error; context must be destroyed */
     CF_ETIMEOUT = 8,    /* device work did not finish within the host timeout */
-    CF_ENOMEM = 9       /* device allocation failed */
+    CF_ENOMEM = 9,      /* device allocation failed */
+    CF_EUNSTABLE = 10   /* a vertex moved a lattice spacing or more in one step */
 } cf_status;
 
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
@@ -108,12 +109,15 @@ cf_status cf_step_async(cf_ctx *ctx, int32_t n);
  * the accumulated device error status. */
 cf_status cf_synchronize(cf_ctx *ctx);
 
-/* Measurement support: advance n >= 1 steps exactly as cf_step does, but
- * with direct launches (no graph) and a CUDA event around each launch.
- * kernel_ms[4] receives the mean duration in ms of the four launches of a
- * step: tet forces, vertex sums + spread, stream-collide, interpolate +
- * advect. Synchronises; returns the first device error. */
-cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms);
+/* Measurement support: advance n >= 1 steps with the same kernels as
+ * cf_step, but launched one after another on the context's stream (no
+ * graph, no overlap) with a CUDA event around each launch. kernel_ms[5]
+ * receives the mean duration in ms per step of: tet forces, vertex sums +
+ * spread, far-field stream-collide (the whole lattice when there are no
+ * cells), near-field stream-collide, interpolate + advect. *near_nodes (may
+ * be NULL) receives the number of nodes in the last step's force region.
+ * Synchronises; returns the first device error. */
+cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *near_nodes);
 
 /* Elastic vertex forces at the current positions only (Sec. 3.1 per tet,
  * summed per vertex), without touching the fluid. */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcellfsi.so")
 
 STATUS = {
     0: "CF_OK", 1: "CF_EINVAL", 2: "CF_EDEGENERATE", 3: "CF_EINVERTED", 4: "CF_ENONFINITE",
-    5: "CF_EDOMAIN", 6: "CF_ESTATE", 7: "CF_ECUDA", 8: "CF_ETIMEOUT", 9: "CF_ENOMEM",
+    5: "CF_EDOMAIN", 6: "CF_ESTATE", 7: "CF_ECUDA", 8: "CF_ETIMEOUT", 9: "CF_ENOMEM", 10: "CF_EUNSTABLE",
 }
 
 
@@ -53,7 +53,7 @@ def lib():
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_synchronize": ([vp], ctypes.c_int),
             "cf_compute_forces": ([vp], ctypes.c_int),
-            "cf_step_profiled": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_step_profiled": ([vp, ctypes.c_int32, _d, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
             "cf_get_forces": ([vp, ctypes.c_int32, _d], ctypes.c_int),
             "cf_get_positions": ([vp, ctypes.c_int32, _d], ctypes.c_int),
             "cf_set_positions": ([vp, ctypes.c_int32, _d], ctypes.c_int),
@@ -180,11 +180,13 @@ def cf_synchronize(ctx):
 
 
 def cf_step_profiled(ctx, n: int):
-    """Mean ms per launch of [tet force, gather + spread, stream-collide,
-    interpolate + advect] over n directly launched steps."""
-    ms = np.zeros(4)
-    _check(ctx, lib().cf_step_profiled(ctx.handle, n, _p(ms)))
-    return ms
+    """Mean ms per step of [tet force, gather + spread, far-field LBM,
+    near-field LBM, interpolate + advect] over n directly launched steps,
+    and the number of nodes in the force region."""
+    ms = np.zeros(5)
+    near = ctypes.c_int64(0)
+    _check(ctx, lib().cf_step_profiled(ctx.handle, n, _p(ms), ctypes.byref(near)))
+    return ms, near.value
 
 
 def cf_compute_forces(ctx):

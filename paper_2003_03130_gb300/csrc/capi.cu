@@ -1,15 +1,23 @@
 // C ABI of libcellfsi.so (declared in include/cellfsi.h): context, device
 // buffers, once-per-cell set-up and the coupled time step.
 //
-// One time step t -> t+1 is four launches on the context's stream:
+// One time step t -> t+1 (parity p) is, on the context's stream:
 //   K1  tet forces at y^t (+ zero F on the support of y^{t-1})
 //   K23 vertex sums over incidence rows + spread onto F
 //   K4  stream + collide with F, populations f[p] -> f[1-p]
 //   K5  interpolate u(t) at y^t, y^{t+1} = y^t + u  (u[p] -> u[1-p])
-// Populations and displacements are double-buffered with one shared parity
-// p; the four launches of each parity are captured once into a CUDA graph
-// and replayed per step. F keeps the last step's force until the next step
-// begins, so the velocity of the last step can still be read.
+// With cells present, K4 is split by a force region around the cells: the
+// far part (every node outside the region, ~all of the lattice, no force
+// read) runs on a second stream concurrently with the cell chain
+// K5(t-1) -> K1(t) -> K23(t); after the join the near part updates the
+// region with the force field. The region of step t is the support box of
+// y^{t-1} grown by one node (a vertex moves less than one spacing per step;
+// K23 checks this and raises CF_EUNSTABLE otherwise). A cf_step call is a
+// "first" step graph (region from the current positions, no K5 before it),
+// n - 1 pipelined step graphs and a final K5. Populations and displacements
+// are double-buffered with one shared parity; each graph is captured once per
+// parity. F keeps the last step's force until the next step begins, so the
+// velocity of the last step can still be read.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -54,6 +62,7 @@ struct cf_ctx {
     LbmParams lp{};
     float *f[2] = {nullptr, nullptr};
     float *F = nullptr;
+    float *vel = nullptr;  // u(t) on the force region, [3][N]
 
     // cells
     int V = 0, T = 0;
@@ -68,8 +77,10 @@ struct cf_ctx {
     double *energy_partial = nullptr, *energy_out = nullptr;
     double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
 
+    int *box = nullptr;  // two force-region slots of 8 ints (see NodeBox)
+
     int cur = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t g_first[2] = {nullptr, nullptr}, g_mid[2] = {nullptr, nullptr}, g_tail[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -106,11 +117,12 @@ void dfree(T *&p) {
 }
 
 void drop_graphs(cf_ctx *c) {
-    for (auto &g : c->graph)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (auto *gs : {c->g_first, c->g_mid, c->g_tail})
+        for (int p = 0; p < 2; ++p)
+            if (gs[p]) {
+                cudaGraphExecDestroy(gs[p]);
+                gs[p] = nullptr;
+            }
 }
 
 MeshView view(const cf_ctx *c) {
@@ -155,46 +167,85 @@ cf_status consume_errors(cf_ctx *c) {
     if (h & ERR_INVERTED) return fail(c, CF_EINVERTED, "a tet reached det F <= 0");
     if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
     if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
+    if (h & ERR_MOVED) return fail(c, CF_EUNSTABLE, "a vertex moved a lattice spacing or more in one step");
     return CF_OK;
 }
 
-cf_status enqueue_step(cf_ctx *c, int p, cudaStream_t s) {
+enum class StepKind { First, Mid, Tail };
+
+// Enqueue one graph's worth of work for parity p. s2 and the two events carry
+// the fork/join of the cell branch.
+cf_status enqueue(cf_ctx *c, StepKind kind, int p, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork,
+                  cudaEvent_t join) {
     const MeshView m = view(c);
     const bool cells = c->T > 0;
-    if (cells) {
-        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s));
-        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s));
+    if (kind == StepKind::Tail) {  // K5 of the last step (parity p)
+        if (cells) CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s));
+        return CF_OK;
     }
-    CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], cells ? c->F : nullptr, c->lp, s));
-    if (cells) CUDA_TRY(c, launch_interp_advect(m, c->f[1 - p], c->F, c->lp, c->u[p], c->u[1 - p], c->d_err, s));
+    if (!cells) {
+        CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], nullptr, c->lp, s));
+        return CF_OK;
+    }
+    int *use = c->box + 8 * (1 - p);  // force region of this step
+    int *acc = c->box + 8 * p;        // support box of y^t, region of the next step
+    if (kind == StepKind::First) {
+        CUDA_TRY(c, cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), s));
+        CUDA_TRY(c, launch_support_box(m, c->u[p], c->lp, use, s));
+    }
+    CUDA_TRY(c, cudaEventRecord(fork, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(s2, fork, 0));
+    CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, s));
+    if (kind == StepKind::Mid)  // K5 of the previous step (parity 1-p)
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s2));
+    CUDA_TRY(c, cudaMemsetAsync(acc, 0x7f, 6 * sizeof(int), s2));
+    CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s2));
+    CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s2, acc, use));
+    CUDA_TRY(c, cudaEventRecord(join, s2));
+    CUDA_TRY(c, cudaStreamWaitEvent(s, join, 0));
+    CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s));
+    return CF_OK;
+}
+
+cf_status capture(cf_ctx *c, StepKind kind, int p, cudaGraphExec_t *out) {
+    cudaStream_t s = nullptr, s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cf_status st = CF_OK;
+    cudaGraph_t g = nullptr;
+    // the cell branch runs at the highest stream priority so that its small
+    // kernels get SMs as soon as far-field blocks retire
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = enqueue(c, kind, p, s, s2, fork, join);
+        e = cudaStreamEndCapture(s, &g);
+    }
+    if (e == cudaSuccess && st == CF_OK) e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (g) cudaGraphDestroy(g);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (s2) cudaStreamDestroy(s2);
+    if (s) cudaStreamDestroy(s);
+    if (st != CF_OK) return st;
+    if (e != cudaSuccess) return fail(c, CF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     return CF_OK;
 }
 
 cf_status build_graphs(cf_ctx *c) {
-    cudaStream_t cap;
-    CUDA_TRY(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     for (int p = 0; p < 2; ++p) {
-        cudaGraph_t g;
-        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) {
-            cudaStreamDestroy(cap);
-            return fail(c, CF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        }
-        cf_status st = enqueue_step(c, p, cap);
-        e = cudaStreamEndCapture(cap, &g);
-        if (st != CF_OK || e != cudaSuccess) {
-            if (e == cudaSuccess) cudaGraphDestroy(g);
-            cudaStreamDestroy(cap);
-            return st != CF_OK ? st : fail(c, CF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        }
-        e = cudaGraphInstantiate(&c->graph[p], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            cudaStreamDestroy(cap);
-            return fail(c, CF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        cf_status st = capture(c, StepKind::First, p, &c->g_first[p]);
+        if (st == CF_OK) st = capture(c, StepKind::Mid, p, &c->g_mid[p]);
+        if (st == CF_OK) st = capture(c, StepKind::Tail, p, &c->g_tail[p]);
+        if (st != CF_OK) {
+            drop_graphs(c);
+            return st;
         }
     }
-    cudaStreamDestroy(cap);
     return CF_OK;
 }
 
@@ -239,6 +290,7 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         c->own_stream = true;
     }
     if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
+        dalloc(&c->box, 16) != cudaSuccess ||
         dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
@@ -254,9 +306,11 @@ void cf_destroy(cf_ctx *c) {
     drop_graphs(c);
     dfree(c->d_err);
     dfree(c->d_status);
+    dfree(c->box);
     dfree(c->f[0]);
     dfree(c->f[1]);
     dfree(c->F);
+    dfree(c->vel);
     dfree(c->xr);
     dfree(c->u[0]);
     dfree(c->u[1]);
@@ -297,6 +351,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     dfree(c->f[0]);
     dfree(c->f[1]);
     dfree(c->F);
+    dfree(c->vel);
     c->lbm_ready = false;
     LbmParams p{};
     p.nx = nx;
@@ -313,9 +368,11 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     CUDA_TRY(c, dalloc(&c->f[0], 19 * (size_t)N));
     CUDA_TRY(c, dalloc(&c->f[1], 19 * (size_t)N));
     CUDA_TRY(c, dalloc(&c->F, 3 * (size_t)N));
+    CUDA_TRY(c, dalloc(&c->vel, 3 * (size_t)N));
     CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float) * 3 * (size_t)N, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->vel, 0, sizeof(float) * 3 * (size_t)N, c->stream));
     c->lp = p;
     // both displacement buffers must agree: the first step clears F on the
     // support of the "previous" positions
@@ -476,14 +533,16 @@ cf_status cf_step_async(cf_ctx *c, int32_t n) {
     DeviceGuard dg(c->device);
     if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
-    if (!c->graph[0]) {
+    if (!c->g_first[0]) {
         cf_status s = build_graphs(c);
         if (s != CF_OK) return s;
     }
+    if (n == 0) return CF_OK;
     for (int i = 0; i < n; ++i) {
-        CUDA_TRY(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+        CUDA_TRY(c, cudaGraphLaunch(i == 0 ? c->g_first[c->cur] : c->g_mid[c->cur], c->stream));
         c->cur ^= 1;
     }
+    CUDA_TRY(c, cudaGraphLaunch(c->g_tail[c->cur ^ 1], c->stream));
     return CF_OK;
 }
 
@@ -499,16 +558,18 @@ cf_status cf_step(cf_ctx *c, int32_t n) {
     return cf_synchronize(c);
 }
 
-cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms) {
+cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *near_nodes) {
     if (!c || !kernel_ms) return CF_EINVAL;
     DeviceGuard dg(c->device);
     if (n < 1) return fail(c, CF_EINVAL, "n must be >= 1");
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
-    const int BATCH = 32;
-    std::vector<cudaEvent_t> ev(5 * BATCH);
+    // per step: [K5 of the previous step], K1, K23, far, near (or the whole
+    // lattice without cells); the final K5 is timed with the interpolations
+    const int BATCH = 32, NE = 6;
+    std::vector<cudaEvent_t> ev(NE * BATCH + 2);
     for (auto &e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(c, CF_ECUDA, "event create failed");
-    double acc[4] = {0, 0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
     cf_status st = CF_OK;
     const MeshView m = view(c);
     const bool cells = c->T > 0;
@@ -517,18 +578,30 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms) {
         const int b = std::min(BATCH, n - done);
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < b && e == cudaSuccess; ++i) {
-            const int p = c->cur;
-            cudaEvent_t *E = &ev[5 * i];
+            const int p = c->cur, t = done + i;
+            int *use = c->box + 8 * (1 - p), *accb = c->box + 8 * p;
+            cudaEvent_t *E = &ev[NE * i];
             cudaEventRecord(E[0], s);
-            if (cells) e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s);
+            if (cells && t > 0) e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s);
+            if (cells && t == 0 && e == cudaSuccess) {
+                e = cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), s);
+                if (e == cudaSuccess) e = launch_support_box(m, c->u[p], c->lp, use, s);
+            }
             cudaEventRecord(E[1], s);
-            if (cells && e == cudaSuccess) e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s);
+            if (cells && e == cudaSuccess) {
+                e = cudaMemsetAsync(accb, 0x7f, 6 * sizeof(int), s);
+                if (e == cudaSuccess) e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s);
+            }
             cudaEventRecord(E[2], s);
-            if (e == cudaSuccess) e = launch_lbm(c->f[p], c->f[1 - p], cells ? c->F : nullptr, c->lp, s);
-            cudaEventRecord(E[3], s);
             if (cells && e == cudaSuccess)
-                e = launch_interp_advect(m, c->f[1 - p], c->F, c->lp, c->u[p], c->u[1 - p], c->d_err, s);
+                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, accb, use);
+            cudaEventRecord(E[3], s);
+            if (e == cudaSuccess)
+                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, s)
+                          : launch_lbm(c->f[p], c->f[1 - p], nullptr, c->lp, s);
             cudaEventRecord(E[4], s);
+            if (cells && e == cudaSuccess) e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s);
+            cudaEventRecord(E[5], s);
             c->cur ^= 1;
         }
         if (e != cudaSuccess) {
@@ -536,17 +609,49 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms) {
             break;
         }
         st = wait_stream(c);
+        // event pairs -> [interp, tet, gather+spread, far, near]
+        const int slot[5] = {0, 1, 2, 3, 4};
         for (int i = 0; i < b && st == CF_OK; ++i)
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 5; ++k) {
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[5 * i + k], ev[5 * i + k + 1]);
-                acc[k] += ms;
+                cudaEventElapsedTime(&ms, ev[NE * i + k], ev[NE * i + k + 1]);
+                acc[slot[k]] += ms;
             }
         done += b;
     }
+    if (st == CF_OK && cells) {  // final K5
+        const int p = c->cur ^ 1;
+        cudaEventRecord(ev[NE * BATCH], s);
+        cudaError_t e = launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s);
+        cudaEventRecord(ev[NE * BATCH + 1], s);
+        st = e == cudaSuccess ? wait_stream(c) : fail(c, CF_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+        float ms = 0.f;
+        if (st == CF_OK) cudaEventElapsedTime(&ms, ev[NE * BATCH], ev[NE * BATCH + 1]);
+        acc[0] += ms;
+    }
+    if (st == CF_OK && near_nodes) {
+        *near_nodes = 0;
+        if (cells) {  // size of the region the last step used
+            int h[6];
+            CUDA_TRY(c, cudaMemcpyAsync(h, c->box + 8 * c->cur, sizeof h, cudaMemcpyDeviceToHost, s));
+            st = wait_stream(c);
+            const LbmParams &p = c->lp;
+            if (st == CF_OK && h[0] <= -h[3]) {
+                const long long lx = std::min<long long>(p.nx, -h[3] - h[0] + 3);
+                const long long lz = std::min<long long>(p.nz, -h[5] - h[2] + 3);
+                const long long ly = std::min(p.ny - 1, -h[4] + 1) - std::max(0, h[1] - 1) + 1;
+                *near_nodes = lx * ly * lz;
+            }
+        }
+    }
     for (auto &e : ev) cudaEventDestroy(e);
     if (st != CF_OK) return st;
-    for (int k = 0; k < 4; ++k) kernel_ms[k] = acc[k] / n;
+    // report order: tet force, gather + spread, far LBM, near LBM, interpolation
+    kernel_ms[0] = acc[1] / n;
+    kernel_ms[1] = acc[2] / n;
+    kernel_ms[2] = acc[3] / n;
+    kernel_ms[3] = acc[4] / n;
+    kernel_ms[4] = acc[0] / n;
     return consume_errors(c);
 }
 

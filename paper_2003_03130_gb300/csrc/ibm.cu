@@ -11,113 +11,169 @@
 //         is their sum);
 //   F(x) += f_v delta_h(x - y_v) on the 8 support nodes (float atomics:
 //         the spread field is exact up to the order of those additions).
-// K5 (k_interp_advect), one thread per vertex:
-//   u(t) on each support node from the post-collision populations through
-//   rho u = sum_q c_q f*_q - F/2 (the collision adds exactly F to the
-//   momentum, and rho u = sum_q c_q f_q + F/2 before it), then
-//   y^{t+1} = y^t + sum_x u(x) delta_h(x - y^t).
+// K5 (k_interp_advect), eight threads per vertex:
+//   y^{t+1} = y^t + sum_x u(x) delta_h(x - y^t), with u(t) as stored by the
+//   near-field stream-collide on every node of the force region (which holds
+//   the support of y^t).
+#include <climits>
+
 #include "internal.cuh"
 
 namespace cf {
 
-__global__ void __launch_bounds__(256) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
-                                                       int do_spread, unsigned *err) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= m.V) return;
-    const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int e = e0; e < e1; ++e) {
-        const int id = __ldg(m.csr_idx + e);
-        const float4 c = m.fc[(id & 3) * m.T + (id >> 2)];
-        fx += c.x;
-        fy += c.y;
-        fz += c.z;
-    }
-    m.fv[v] = make_float4(fx, fy, fz, 0.f);
-    if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
-    if (!do_spread) return;
-    Support s;
-    if (!support_of(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
-        atomicOr(err, ERR_DOMAIN);
-        return;
-    }
-    const int N = (int)p.N;
-    const float wx[2] = {1.f - s.fx, s.fx}, wy[2] = {1.f - s.fy, s.fy}, wz[2] = {1.f - s.fz, s.fz};
+// Block-wide minimum of 6 ints folded into a box slot with one atomicMin
+// per value per block. Every thread of the block must call it.
+__device__ __forceinline__ void box_accumulate(int (&v)[6], int *slot) {
+    __shared__ int red[32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
-        const int Z = wrapi(s.bz + dz, p.nz);
+    for (int k = 0; k < 6; ++k)
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
+        for (int o = 16; o > 0; o >>= 1) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    if (lane == 0)
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
-                const float w = wx[dx] * wy[dy] * wz[dz];
-                atomicAdd(F + n, w * fx);
-                atomicAdd(F + N + n, w * fy);
-                atomicAdd(F + 2 * N + n, w * fz);
-            }
+        for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int m = INT_MAX;
+        for (int w = 0; w < nwarps; ++w) m = min(m, red[w][threadIdx.x]);
+        if (m != INT_MAX) atomicMin(slot + threadIdx.x, m);
     }
 }
 
-cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s) {
+// Support nodes of one vertex as a box: wrapped x/z pairs, y pair.
+__device__ __forceinline__ void support_box(const Support &s, const LbmParams &p, int (&v)[6]) {
+    const int X0 = wrapi(s.bx, p.nx), X1 = wrapi(s.bx + 1, p.nx);
+    const int Z0 = wrapi(s.bz, p.nz), Z1 = wrapi(s.bz + 1, p.nz);
+    v[0] = min(X0, X1);
+    v[1] = s.by;
+    v[2] = min(Z0, Z1);
+    v[3] = -max(X0, X1);
+    v[4] = -(s.by + 1);
+    v[5] = -max(Z0, Z1);
+}
+
+__global__ void __launch_bounds__(256) k_support_box(MeshView m, const float4 *__restrict__ u, LbmParams p,
+                                                     int *box_out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+    Support s;
+    if (v < m.V && support_of(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) support_box(s, p, b);
+    box_accumulate(b, box_out);
+}
+
+cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmParams &p, int *box_out,
+                               cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
-    LbmParams p{};
-    if (lp) p = *lp;
-    k_gather_spread<<<(m.V + 255) / 256, 256, 0, s>>>(m, u, F, p, (F && lp) ? 1 : 0, err);
+    k_support_box<<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, box_out);
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *__restrict__ f,
-                                                       const float *__restrict__ F, LbmParams p,
+__global__ void __launch_bounds__(256) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
+                                                       int do_spread, unsigned *err, int *box_out,
+                                                       const int *__restrict__ box_in) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+    if (v < m.V) {
+        const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int e = e0; e < e1; ++e) {
+            const int id = __ldg(m.csr_idx + e);
+            const float4 c = m.fc[(id & 3) * m.T + (id >> 2)];
+            fx += c.x;
+            fy += c.y;
+            fz += c.z;
+        }
+        m.fv[v] = make_float4(fx, fy, fz, 0.f);
+        if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
+        Support s;
+        if (!do_spread) {
+        } else if (!support_of(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+            atomicOr(err, ERR_DOMAIN);
+        } else {
+            support_box(s, p, b);
+            if (box_in) {
+                const NodeBox r = region_of(box_in, p.nx, p.ny, p.nz);
+                if (!(in_region(r, -b[3], -b[4], -b[5], p.nx, p.nz) && in_region(r, b[0], b[1], b[2], p.nx, p.nz)))
+                    atomicOr(err, ERR_MOVED);
+            }
+            const int N = (int)p.N;
+            const float wx[2] = {1.f - s.fx, s.fx}, wy[2] = {1.f - s.fy, s.fy}, wz[2] = {1.f - s.fz, s.fz};
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const int Z = wrapi(s.bz + dz, p.nz);
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
+                        const float w = wx[dx] * wy[dy] * wz[dz];
+                        atomicAdd(F + n, w * fx);
+                        atomicAdd(F + N + n, w * fy);
+                        atomicAdd(F + 2 * N + n, w * fz);
+                    }
+            }
+        }
+    }
+    if (box_out) box_accumulate(b, box_out);
+}
+
+cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
+                                 cudaStream_t s, int *box_out, const int *box_in) {
+    if (m.V == 0) return cudaSuccess;
+    LbmParams p{};
+    if (lp) p = *lp;
+    k_gather_spread<<<(m.V + 63) / 64, 64, 0, s>>>(m, u, F, p, (F && lp) ? 1 : 0, err, box_out, box_in);
+    return cudaGetLastError();
+}
+
+// Eight threads per vertex, one per support node; the group of eight sums
+// its contributions with shuffles.
+__global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
                                                        unsigned *err) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= m.V) return;
-    const float4 uc = __ldg(u_cur + v);
-    Support s;
-    if (!support_of(m.origin, __ldg(m.xr + v), uc, p.ny, s)) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = g >> 3, corner = g & 7;
+    const bool live = v < m.V;
+    float4 uc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    bool ok = false;
+    if (live) {
+        uc = __ldg(u_cur + v);
+        Support s;
+        ok = support_of(m.origin, __ldg(m.xr + v), uc, p.ny, s);
+        if (ok) {
+            const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+            const int N = (int)p.N;
+            const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * wrapi(s.bz + dz, p.nz));
+            const float w = (dx ? s.fx : 1.f - s.fx) * (dy ? s.fy : 1.f - s.fy) * (dz ? s.fz : 1.f - s.fz);
+            vx = w * __ldg(vel + n);
+            vy = w * __ldg(vel + N + n);
+            vz = w * __ldg(vel + 2 * N + n);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        vx += __shfl_xor_sync(0xffffffffu, vx, o);
+        vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        vz += __shfl_xor_sync(0xffffffffu, vz, o);
+    }
+    if (!live || corner != 0) return;
+    if (!ok) {
         atomicOr(err, ERR_DOMAIN);
         u_next[v] = uc;
         return;
-    }
-    const int N = (int)p.N;
-    const float wx[2] = {1.f - s.fx, s.fx}, wy[2] = {1.f - s.fy, s.fy}, wz[2] = {1.f - s.fz, s.fz};
-    float vx = 0.f, vy = 0.f, vz = 0.f;
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
-        const int Z = wrapi(s.bz + dz, p.nz);
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
-                float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-                for (int q = 0; q < 19; ++q) {
-                    const float d = __ldg(f + q * N + n);
-                    drho += d;
-                    if (cx(q)) jx += cx(q) * d;
-                    if (cy(q)) jy += cy(q) * d;
-                    if (cz(q)) jz += cz(q) * d;
-                }
-                const float Fx = __ldg(F + n) + p.gx, Fy = __ldg(F + N + n) + p.gy, Fz = __ldg(F + 2 * N + n) + p.gz;
-                const float ir = 1.f / (1.f + drho);
-                const float w = wx[dx] * wy[dy] * wz[dz];
-                vx += w * ((jx - 0.5f * Fx) * ir);
-                vy += w * ((jy - 0.5f * Fy) * ir);
-                vz += w * ((jz - 0.5f * Fz) * ir);
-            }
     }
     const float4 un = make_float4(uc.x + vx, uc.y + vy, uc.z + vz, 0.f);
     if (!isfinite(un.x + un.y + un.z)) atomicOr(err, ERR_NONFINITE);
     u_next[v] = un;
 }
 
-cudaError_t launch_interp_advect(const MeshView &m, const float *f, const float *F, const LbmParams &p,
-                                 const float4 *u_cur, float4 *u_next, unsigned *err, cudaStream_t s) {
+cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
+                                 float4 *u_next, unsigned *err, cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
-    k_interp_advect<<<(m.V + 127) / 128, 128, 0, s>>>(m, f, F, p, u_cur, u_next, err);
+    const long long threads = 8LL * m.V;
+    k_interp_advect<<<(int)((threads + 127) / 128), 128, 0, s>>>(m, vel, p, u_cur, u_next, err);
     return cudaGetLastError();
 }
 

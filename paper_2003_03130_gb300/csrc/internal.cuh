@@ -25,6 +25,7 @@ enum : unsigned {
     ERR_INVERTED = 1u << 0,   // det F <= 0 in some tet
     ERR_NONFINITE = 1u << 1,  // NaN / Inf in a force or a displacement
     ERR_DOMAIN = 1u << 2,     // delta support outside 0 <= y <= ny-1
+    ERR_MOVED = 1u << 3,      // a support node fell outside the step's force region
 };
 
 // ---------------------------------------------------------------- D3Q19
@@ -105,6 +106,45 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
+// Force region of a step. A box slot holds the bounding box of the delta
+// support nodes of all vertices as 6 ints {min x, min y, min z, -max x,
+// -max y, -max z} (x and z wrapped into the lattice), all accumulated with
+// atomicMin from INT_MAX. The region a step uses is that box grown by one
+// node in every direction (x, z periodic as start + length; y clamped).
+struct NodeBox {
+    int x0, lx, y0, y1, z0, lz;
+};
+
+__device__ __forceinline__ NodeBox region_of(const int *__restrict__ slot, int nx, int ny, int nz) {
+    NodeBox b;
+    const int xmin = slot[0], ymin = slot[1], zmin = slot[2];
+    const int xmax = -slot[3], ymax = -slot[4], zmax = -slot[5];
+    if (xmin > xmax) {  // empty: no vertex spread anything
+        b.x0 = 0; b.lx = 0; b.y0 = 1; b.y1 = 0; b.z0 = 0; b.lz = 0;
+        return b;
+    }
+    b.lx = xmax - xmin + 3;
+    b.x0 = xmin - 1;
+    if (b.lx >= nx) { b.x0 = 0; b.lx = nx; }
+    b.lz = zmax - zmin + 3;
+    b.z0 = zmin - 1;
+    if (b.lz >= nz) { b.z0 = 0; b.lz = nz; }
+    b.y0 = ymin - 1 < 0 ? 0 : ymin - 1;
+    b.y1 = ymax + 1 > ny - 1 ? ny - 1 : ymax + 1;
+    return b;
+}
+
+// offset of a periodic coordinate from the region start, in [0, n)
+__device__ __forceinline__ int region_off(int c, int c0, int n) {
+    int d = c - c0;
+    d %= n;
+    return d < 0 ? d + n : d;
+}
+
+__device__ __forceinline__ bool in_region(const NodeBox &b, int x, int y, int z, int nx, int nz) {
+    return y >= b.y0 && y <= b.y1 && region_off(x, b.x0, nx) < b.lx && region_off(z, b.z0, nz) < b.lz;
+}
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch status.
 // Once per cell (Sec. 3.2): validate, orient, B = J^-1 and V_0 in FP64;
@@ -132,15 +172,26 @@ cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, 
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
-// same threads spread their vertex force onto the lattice.
+// same threads spread their vertex force onto the lattice. With box_out the
+// bounding box of the support nodes is accumulated into that slot; with
+// box_in every support node must lie in the region of that slot (else
+// ERR_MOVED).
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s);
-// K4: pull stream + BGK collide with Guo forcing, fin -> fout.
+                                 cudaStream_t s, int *box_out = nullptr, const int *box_in = nullptr);
+// Bounding box of the support nodes of x + u into a slot (reset by the caller).
+cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmParams &p, int *box_out,
+                               cudaStream_t s);
+// K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node.
 cudaError_t launch_lbm(const float *fin, float *fout, const float *F, const LbmParams &p, cudaStream_t s);
-// K5: velocity u(t) interpolated at x + u_cur from post-collision populations
-// and F; u_next = u_cur + velocity.
-cudaError_t launch_interp_advect(const MeshView &m, const float *f, const float *F, const LbmParams &p,
-                                 const float4 *u_cur, float4 *u_next, unsigned *err, cudaStream_t s);
+// K4 split by the force region of a slot: far = every node outside it, with
+// no force-field read; near = the nodes inside it, with the force field.
+cudaError_t launch_lbm_far(const float *fin, float *fout, const LbmParams &p, const int *box, cudaStream_t s);
+cudaError_t launch_lbm_near(const float *fin, float *fout, const float *F, const LbmParams &p, const int *box,
+                            float *vel, cudaStream_t s);
+// K5: velocity u(t) (stored by the near-field stream-collide) interpolated at
+// x + u_cur; u_next = u_cur + velocity.
+cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
+                                 float4 *u_next, unsigned *err, cudaStream_t s);
 cudaError_t launch_lbm_init(float *f, const LbmParams &p, cudaStream_t s);
 cudaError_t launch_lbm_macro(const float *f, const float *F, const LbmParams &p, double *rho, double *u,
                              cudaStream_t s);

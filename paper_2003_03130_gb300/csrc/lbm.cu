@@ -19,12 +19,72 @@
 
 namespace cf {
 
-template <bool HAS_F>
-__global__ void __launch_bounds__(128) k_lbm(const float *__restrict__ fin, float *__restrict__ fout,
-                                             const float *__restrict__ F, LbmParams p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
+// c . v for a compile-time lattice vector (a, b, c): only the nonzero
+// components enter (0.0f * v cannot be folded away under IEEE rules).
+template <int a, int b, int c>
+__device__ __forceinline__ float cdot(float x, float y, float z) {
+    float s = 0.f;
+    if constexpr (a != 0 && b != 0) {
+        s = (a > 0 ? x : -x) + (b > 0 ? y : -y);
+    } else if constexpr (a != 0 && c != 0) {
+        s = (a > 0 ? x : -x) + (c > 0 ? z : -z);
+    } else if constexpr (b != 0 && c != 0) {
+        s = (b > 0 ? y : -y) + (c > 0 ? z : -z);
+    } else if constexpr (a != 0) {
+        s = a > 0 ? x : -x;
+    } else if constexpr (b != 0) {
+        s = b > 0 ? y : -y;
+    } else if constexpr (c != 0) {
+        s = c > 0 ? z : -z;
+    }
+    return s;
+}
+
+// Per weight class w: constants of the collision that do not depend on the
+// direction within the class.
+struct WClass {
+    float c0;   // omega (w drho - w rho 3/2 u.u) - 3 g w (u.F): direction-free part
+    float e45;  // 9/2 omega w rho
+    float o3;   // 3 omega w rho
+    float g9;   // 9 g w
+    float g3;   // 3 g w
+};
+
+__device__ __forceinline__ WClass wclass(float w, float drho, float rho, float usq15, float uF, float om, float g) {
+    WClass k;
+    const float wr = w * rho;
+    k.c0 = om * (w * drho - wr * usq15) - 3.f * g * w * uF;
+    k.e45 = 4.5f * om * wr;
+    k.o3 = 3.f * om * wr;
+    k.g9 = 9.f * g * w;
+    k.g3 = 3.f * g * w;
+    return k;
+}
+
+// Collide the opposite pair (A, opp(A)). With cu = c_A.u and cF = c_A.F the
+// equilibrium and source split into a part even in c (P) and a part odd in
+// c (Q): d*_A = (1-omega) d_A + P + Q, d*_opp = (1-omega) d_opp + P - Q, with
+//   P = omega w [drho + rho (9/2 cu^2 - 3/2 u.u)] + g w [9 cu cF - 3 u.F],
+//   Q = 3 omega w rho cu + 3 g w cF.
+template <int A>
+__device__ __forceinline__ void collide_pair(const float (&d)[19], float *__restrict__ fout, int n, int N,
+                                             const WClass &k, float om1, float ux, float uy, float uz, float Fx,
+                                             float Fy, float Fz) {
+    constexpr int B = opp(A);
+    const float cu = cdot<cx(A), cy(A), cz(A)>(ux, uy, uz);
+    const float cF = cdot<cx(A), cy(A), cz(A)>(Fx, Fy, Fz);
+    const float P = fmaf(cu, fmaf(k.g9, cF, k.e45 * cu), k.c0);
+    const float Q = fmaf(k.o3, cu, k.g3 * cF);
+    fout[A * N + n] = fmaf(om1, d[A], P + Q);
+    fout[B * N + n] = fmaf(om1, d[B], P - Q);
+}
+
+// One node. WALL: the row touches a wall (y = 0 or y = ny-1), so pulls from
+// beyond it are bounced back; interior rows skip those tests.
+template <bool WALL, bool HAS_F>
+__device__ __forceinline__ void lbm_node(const float *__restrict__ fin, float *__restrict__ fout,
+                                         const float *__restrict__ F, const LbmParams &p, int x, int y, int z,
+                                         float *__restrict__ vel = nullptr) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -35,24 +95,27 @@ __global__ void __launch_bounds__(128) k_lbm(const float *__restrict__ fin, floa
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
-        const int sy = y - cy(q);
         const int sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z);
-        if (cy(q) != 0 && (sy < 0 || sy >= ny)) {
-            const float uw = sy < 0 ? p.uw_lo : p.uw_hi;
-            d[q] = __ldg(fin + opp(q) * N + n) + (6.f * wq(q) * cx(q)) * uw;
+        const int sy = y - cy(q);
+        if (WALL && ((cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1))) {
+            const float uw = cy(q) == 1 ? p.uw_lo : p.uw_hi;
+            d[q] = __ldg(fin + opp(q) * N + n);
+            if (cx(q) != 0) d[q] += (6.f * wq(q) * cx(q)) * uw;
         } else {
             d[q] = __ldg(fin + q * N + sx + nx * (sy + ny * sz));
         }
     }
 
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        drho += d[q];
-        if (cx(q)) jx += cx(q) * d[q];
-        if (cy(q)) jy += cy(q) * d[q];
-        if (cz(q)) jz += cz(q) * d[q];
-    }
+    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) +
+                       ((d[8] + d[9]) + (d[10] + d[11])) + ((d[12] + d[13]) + (d[14] + d[15])) +
+                       ((d[16] + d[17]) + d[18]);
+    // x: +1 at 1, 15..18; -1 at 2, 7..10
+    const float jx = ((d[1] - d[2]) + (d[15] - d[7])) + ((d[16] - d[8]) + (d[17] - d[9])) + (d[18] - d[10]);
+    // y: +1 at 3, 10, 13, 14, 18; -1 at 4, 7, 11, 12, 15
+    const float jy = ((d[3] - d[4]) + (d[10] - d[7])) + ((d[13] - d[11]) + (d[14] - d[12])) + (d[18] - d[15]);
+    // z: +1 at 5, 9, 12, 14, 17; -1 at 6, 8, 11, 13, 16
+    const float jz = ((d[5] - d[6]) + (d[9] - d[8])) + ((d[12] - d[11]) + (d[14] - d[13])) + (d[17] - d[16]);
+
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
     if (HAS_F) {
         Fx += __ldg(F + n);
@@ -60,19 +123,98 @@ __global__ void __launch_bounds__(128) k_lbm(const float *__restrict__ fin, floa
         Fz += __ldg(F + 2 * N + n);
     }
     const float rho = 1.f + drho;
-    const float ir = 1.f / rho;
-    const float ux = (jx + 0.5f * Fx) * ir, uy = (jy + 0.5f * Fy) * ir, uz = (jz + 0.5f * Fz) * ir;
-    const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float uF = ux * Fx + uy * Fy + uz * Fz;
-    const float om = p.omega, g = p.guo;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-        const float cF = cx(q) * Fx + cy(q) * Fy + cz(q) * Fz;
-        const float deq = wq(q) * (drho + rho * (3.f * cu + 4.5f * cu * cu - usq));
-        const float src = (g * wq(q)) * (3.f * (cF - uF) + 9.f * cu * cF);
-        fout[q * N + n] = d[q] + om * (deq - d[q]) + src;
+    const float ir = __frcp_rn(rho);
+    const float ux = fmaf(0.5f, Fx, jx) * ir, uy = fmaf(0.5f, Fy, jy) * ir, uz = fmaf(0.5f, Fz, jz) * ir;
+    if (vel) {  // u(t) of this step, for the interpolation at the vertices
+        vel[n] = ux;
+        vel[N + n] = uy;
+        vel[2 * N + n] = uz;
     }
+    const float usq15 = 1.5f * fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
+    const float om = p.omega, g = p.guo, om1 = 1.f - om;
+
+    const WClass k0 = wclass(1.f / 3.f, drho, rho, usq15, uF, om, g);
+    const WClass k1 = wclass(1.f / 18.f, drho, rho, usq15, uF, om, g);
+    const WClass k2 = wclass(1.f / 36.f, drho, rho, usq15, uF, om, g);
+    fout[n] = fmaf(om1, d[0], k0.c0);
+    collide_pair<1>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<3>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<5>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<7>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<8>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<9>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<10>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<11>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<12>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+}
+
+template <bool HAS_F>
+__global__ void __launch_bounds__(128) k_lbm(const float *__restrict__ fin, float *__restrict__ fout,
+                                             const float *__restrict__ F, LbmParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (y > 0 && y < p.ny - 1)
+        lbm_node<false, HAS_F>(fin, fout, F, p, x, y, z);
+    else
+        lbm_node<true, HAS_F>(fin, fout, F, p, x, y, z);
+}
+
+// Every node outside the force region (F is zero there: no force-field read).
+__global__ void __launch_bounds__(128) k_lbm_far(const float *__restrict__ fin, float *__restrict__ fout, LbmParams p,
+                                                 const int *__restrict__ box) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
+    if (in_region(b, x, y, z, p.nx, p.nz)) return;
+    if (y > 0 && y < p.ny - 1)
+        lbm_node<false, false>(fin, fout, nullptr, p, x, y, z);
+    else
+        lbm_node<true, false>(fin, fout, nullptr, p, x, y, z);
+}
+
+// The nodes inside the force region, with the force field; also stores u(t)
+// there. The grid is fixed when a step is captured while the region moves
+// with the cells, so threads stride over the region's nodes.
+__global__ void __launch_bounds__(128) k_lbm_near(const float *__restrict__ fin, float *__restrict__ fout,
+                                                  const float *__restrict__ F, LbmParams p,
+                                                  const int *__restrict__ box, float *__restrict__ vel) {
+    const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
+    const int ly = b.y1 - b.y0 + 1;
+    if (ly <= 0 || b.lx <= 0 || b.lz <= 0) return;
+    const int plane = b.lx * ly, total = plane * b.lz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int k = i / plane, r = i - k * plane;
+        const int j = r / b.lx, xi = r - j * b.lx;
+        int x = b.x0 + xi, z = b.z0 + k;
+        x -= x >= p.nx ? p.nx : 0;
+        x += x < 0 ? p.nx : 0;
+        z -= z >= p.nz ? p.nz : 0;
+        z += z < 0 ? p.nz : 0;
+        const int y = b.y0 + j;
+        if (y > 0 && y < p.ny - 1)
+            lbm_node<false, true>(fin, fout, F, p, x, y, z, vel);
+        else
+            lbm_node<true, true>(fin, fout, F, p, x, y, z, vel);
+    }
+}
+
+cudaError_t launch_lbm_far(const float *fin, float *fout, const LbmParams &p, const int *box, cudaStream_t s) {
+    const int bx = p.nx < 128 ? p.nx : 128;
+    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+    k_lbm_far<<<grid, bx, 0, s>>>(fin, fout, p, box);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_near(const float *fin, float *fout, const float *F, const LbmParams &p, const int *box,
+                            float *vel, cudaStream_t s) {
+    // one pass over regions up to ~155k nodes (8 blocks of 128 per SM)
+    const long long cap = (p.N + 127) / 128;
+    const int blocks = (int)(cap < 1216 ? cap : 1216);
+    k_lbm_near<<<blocks, 128, 0, s>>>(fin, fout, F, p, box, vel);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lbm(const float *fin, float *fout, const float *F, const LbmParams &p, cudaStream_t s) {

@@ -249,3 +249,64 @@ def test_errors_are_status_codes(P):
     with pytest.raises(CellFSIError) as e:
         P.cf_step(ctx, 1)
     assert e.value.name == "CF_EDOMAIN"
+
+
+# ---------------------------------------------------------------- orchestration
+
+def test_pipelined_steps_equal_single_steps_and_profiled_path(P):
+    """cf_step(n) overlaps the far-field stream-collide with the cell chain of
+    the next step; n calls of cf_step(1) and the sequential profiled path
+    (cf_step_profiled) must give the same state, and all three the oracle's."""
+    wl = configs.small_shear()
+    y0 = wl.cells[0].y0
+    runs = []
+    for mode in ("pipelined", "single", "profiled"):
+        ctx = P.cf_create(0)
+        (cid,) = P.load_workload(ctx, wl)
+        if mode == "pipelined":
+            P.cf_step(ctx, 30)
+        elif mode == "single":
+            for _ in range(30):
+                P.cf_step(ctx, 1)
+        else:
+            ms, near = P.cf_step_profiled(ctx, 30)
+            assert near > 0 and (ms > 0).all()
+        runs.append((P.cf_get_positions(ctx, cid), P.cf_get_velocity(ctx)))
+    sim = oracle.Coupled(wl)
+    sim.step(30)
+    for y, u in runs:
+        assert rel(y - y0, sim.y - y0) <= TOL
+        assert rel(u, sim.fluid.u) <= TOL
+
+
+def test_cells_near_the_periodic_seam(P):
+    """A cell straddling the periodic x and z boundaries: its force region
+    wraps around."""
+    x, t = sphere_tet_mesh(4.0, 1.3)
+    x = x + np.array([0.3, 12.0, 23.6])
+    cell = Cell(x, t, perturb(x, 0.1, 8), 2e-3, 0.2, 0.6)
+    wl = Workload("seam", 24, 24, 24, 1.0, -0.02, 0.02, cells=[cell])
+    ctx, sim, y, f = _coupled_pair(P, wl, 25)
+    assert rel(y - cell.y0, sim.y - cell.y0) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_unstable_run_reports_an_error_status(P):
+    """A far too stiff, strongly perturbed cell blows up within a few steps;
+    the run must end in an error status (never a GPU fault), and the
+    context must stay usable."""
+    from paper_2003_03130_gb300 import CellFSIError
+
+    x, t = sphere_tet_mesh(4.0, 1.3)
+    x = x + 12.0
+    ctx = P.cf_create(0)
+    P.cf_lbm_init(ctx, 24, 24, 24, 1.0, 0.0, 0.0)
+    cid = P.cf_mesh_init(ctx, x, t, perturb(x, 0.3, 4))
+    P.cf_set_material(ctx, cid, 20.0, 200.0, 0.5)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_step(ctx, 60)
+    assert e.value.name in ("CF_EINVERTED", "CF_ENONFINITE", "CF_EDOMAIN", "CF_EUNSTABLE")
+    P.cf_lbm_init(ctx, 24, 24, 24, 1.0, 0.0, 0.0)
+    P.cf_set_positions(ctx, cid, x)
+    P.cf_set_material(ctx, cid, 1e-3, 0.1, 0.5)
+    P.cf_step(ctx, 3)
