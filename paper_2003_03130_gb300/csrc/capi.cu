@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <thread>
 #include <vector>
@@ -77,10 +78,11 @@ struct cf_ctx {
     double *energy_partial = nullptr, *energy_out = nullptr;
     double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
 
-    int *box = nullptr;  // two force-region slots of 8 ints (see NodeBox)
+    int *box = nullptr;  // three force-region slots of 8 ints (see NodeBox)
 
-    int cur = 0;
-    cudaGraphExec_t g_first[2] = {nullptr, nullptr}, g_mid[2] = {nullptr, nullptr}, g_tail[2] = {nullptr, nullptr};
+    int cur = 0;          // buffer parity of the next step
+    long long tstep = 0;  // steps taken; tstep % 3 picks the region slots
+    std::map<int, cudaGraphExec_t> graphs;
 };
 
 namespace {
@@ -117,12 +119,8 @@ void dfree(T *&p) {
 }
 
 void drop_graphs(cf_ctx *c) {
-    for (auto *gs : {c->g_first, c->g_mid, c->g_tail})
-        for (int p = 0; p < 2; ++p)
-            if (gs[p]) {
-                cudaGraphExecDestroy(gs[p]);
-                gs[p] = nullptr;
-            }
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
 }
 
 MeshView view(const cf_ctx *c) {
@@ -171,81 +169,135 @@ cf_status consume_errors(cf_ctx *c) {
     return CF_OK;
 }
 
-enum class StepKind { First, Mid, Tail };
+// Steps per graph in the steady part of cf_step: even (buffer parity) and a
+// multiple of 3 (region slots), so a graph starts and ends in the same phase.
+constexpr int kChunk = 12;
 
-// Enqueue one graph's worth of work for parity p. s2 and the two events carry
-// the fork/join of the cell branch.
-cf_status enqueue(cf_ctx *c, StepKind kind, int p, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork,
-                  cudaEvent_t join) {
+enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3 };
+
+// Region slots of step t (phase s = t % 3): the step's force region is slot
+// (s + 2) % 3 (written by step t - 1, or by the support box of the current
+// positions in the first step of a call); the step accumulates the support
+// box of y^t into slot s for step t + 1. Three slots keep a slot from being
+// reset while a far-field kernel two steps back may still read it.
+int *region_slot(cf_ctx *c, int s) { return c->box + 8 * ((s + 2) % 3); }
+int *accum_slot(cf_ctx *c, int s) { return c->box + 8 * s; }
+
+// Enqueue `nsteps` steps starting at parity p0 and phase s0 on two streams:
+// sf carries the far-field stream-collide, sc the cell chain and the near
+// field. ev holds 2 * nsteps + 1 events for the cross-stream dependencies:
+//   far(t)   after far(t-1) [sf order] and near(t-1)
+//   K5(t-1) -> K1(t) -> K23(t) after near(t-1) [sc order]
+//   near(t)  after K23(t) [sc order] and far(t-1) (it reads far nodes' halo)
+// so near(t) and the cell chain overlap far(t).
+cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaStream_t sf, cudaStream_t sc,
+                        cudaEvent_t *ev) {
     const MeshView m = view(c);
-    const bool cells = c->T > 0;
-    if (kind == StepKind::Tail) {  // K5 of the last step (parity p)
-        if (cells) CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s));
+    if (kind == Kind::Tail) {  // K5 of the last step (parity p0)
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sf));
         return CF_OK;
     }
-    if (!cells) {
-        CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], nullptr, c->lp, s));
+    if (kind == Kind::Fluid) {
+        for (int i = 0; i < nsteps; ++i) {
+            const int p = p0 ^ (i & 1);
+            CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], nullptr, c->lp, sf));
+        }
         return CF_OK;
     }
-    int *use = c->box + 8 * (1 - p);  // force region of this step
-    int *acc = c->box + 8 * p;        // support box of y^t, region of the next step
-    if (kind == StepKind::First) {
-        CUDA_TRY(c, cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), s));
-        CUDA_TRY(c, launch_support_box(m, c->u[p], c->lp, use, s));
+    cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
+    if (kind == Kind::First) {
+        int *use = region_slot(c, s0);
+        CUDA_TRY(c, cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), sf));
+        CUDA_TRY(c, launch_support_box(m, c->u[p0], c->lp, use, sf));
     }
-    CUDA_TRY(c, cudaEventRecord(fork, s));
-    CUDA_TRY(c, cudaStreamWaitEvent(s2, fork, 0));
-    CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, s));
-    if (kind == StepKind::Mid)  // K5 of the previous step (parity 1-p)
-        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s2));
-    CUDA_TRY(c, cudaMemsetAsync(acc, 0x7f, 6 * sizeof(int), s2));
-    CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s2));
-    CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s2, acc, use));
-    CUDA_TRY(c, cudaEventRecord(join, s2));
-    CUDA_TRY(c, cudaStreamWaitEvent(s, join, 0));
-    CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s));
+    CUDA_TRY(c, cudaEventRecord(fork, sf));
+    CUDA_TRY(c, cudaStreamWaitEvent(sc, fork, 0));
+    for (int i = 0; i < nsteps; ++i) {
+        const int p = p0 ^ (i & 1), s = (s0 + i) % 3;
+        int *use = region_slot(c, s), *acc = accum_slot(c, s);
+        if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
+        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, sf));
+        CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
+        if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
+            CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc));
+        CUDA_TRY(c, cudaMemsetAsync(acc, 0x7f, 6 * sizeof(int), sc));
+        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc));
+        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, acc, use));
+        if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
+        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, sc));
+        CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
+    }
+    CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
+    CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_far[nsteps - 1], 0));
     return CF_OK;
 }
 
-cf_status capture(cf_ctx *c, StepKind kind, int p, cudaGraphExec_t *out) {
-    cudaStream_t s = nullptr, s2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    cf_status st = CF_OK;
-    cudaGraph_t g = nullptr;
-    // the cell branch runs at the highest stream priority so that its small
+// Captured graph for (kind, parity, phase, steps), built on first use.
+cf_status get_graph(cf_ctx *c, Kind kind, int p, int s, int nsteps, cudaGraphExec_t *out) {
+    const int key = (((int)kind * 2 + p) * 3 + s) * 64 + nsteps;
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+        *out = it->second;
+        return CF_OK;
+    }
+    // the cell chain runs at the highest stream priority so that its small
     // kernels get SMs as soon as far-field blocks retire
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, greatest);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    cudaStream_t sf = nullptr, sc = nullptr;
+    std::vector<cudaEvent_t> ev(2 * nsteps + 1, nullptr);
+    cf_status st = CF_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamCreateWithPriority(&sf, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sc, cudaStreamNonBlocking, greatest);
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(sf, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = enqueue(c, kind, p, s, s2, fork, join);
-        e = cudaStreamEndCapture(s, &g);
+        st = enqueue_steps(c, kind, p, s, nsteps, sf, sc, ev.data());
+        e = cudaStreamEndCapture(sf, &g);
     }
-    if (e == cudaSuccess && st == CF_OK) e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
+    // every kernel node but the far field gets the highest priority
+    if (e == cudaSuccess && st == CF_OK) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+            cudaGraphNodeType ty;
+            e = cudaGraphNodeGetType(nodes[i], &ty);
+            if (e != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+            if (e != cudaSuccess) break;
+            cudaLaunchAttributeValue v;
+            v.priority = kp.func == lbm_far_kernel() ? least : greatest;
+            e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && st == CF_OK) e = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
     if (g) cudaGraphDestroy(g);
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (s2) cudaStreamDestroy(s2);
-    if (s) cudaStreamDestroy(s);
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (sc) cudaStreamDestroy(sc);
+    if (sf) cudaStreamDestroy(sf);
     if (st != CF_OK) return st;
     if (e != cudaSuccess) return fail(c, CF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    c->graphs[key] = exec;
+    *out = exec;
     return CF_OK;
 }
 
-cf_status build_graphs(cf_ctx *c) {
-    for (int p = 0; p < 2; ++p) {
-        cf_status st = capture(c, StepKind::First, p, &c->g_first[p]);
-        if (st == CF_OK) st = capture(c, StepKind::Mid, p, &c->g_mid[p]);
-        if (st == CF_OK) st = capture(c, StepKind::Tail, p, &c->g_tail[p]);
-        if (st != CF_OK) {
-            drop_graphs(c);
-            return st;
-        }
-    }
+// Launch one graph of `nsteps` steps at the context's phase and advance it.
+cf_status launch_steps(cf_ctx *c, Kind kind, int nsteps) {
+    cudaGraphExec_t g;
+    const int s = (int)(c->tstep % 3);
+    cf_status st = get_graph(c, kind, c->cur, s, nsteps, &g);
+    if (st != CF_OK) return st;
+    CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
+    c->cur ^= nsteps & 1;
+    c->tstep += nsteps;
     return CF_OK;
 }
 
@@ -290,7 +342,7 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         c->own_stream = true;
     }
     if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
-        dalloc(&c->box, 16) != cudaSuccess ||
+        dalloc(&c->box, 24) != cudaSuccess ||
         dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
@@ -533,16 +585,36 @@ cf_status cf_step_async(cf_ctx *c, int32_t n) {
     DeviceGuard dg(c->device);
     if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
-    if (!c->g_first[0]) {
-        cf_status s = build_graphs(c);
-        if (s != CF_OK) return s;
-    }
     if (n == 0) return CF_OK;
-    for (int i = 0; i < n; ++i) {
-        CUDA_TRY(c, cudaGraphLaunch(i == 0 ? c->g_first[c->cur] : c->g_mid[c->cur], c->stream));
-        c->cur ^= 1;
+    cf_status st = CF_OK;
+    if (c->T == 0) {  // fluid only
+        int left = n;
+        while (st == CF_OK && left >= kChunk) {
+            st = launch_steps(c, Kind::Fluid, kChunk);
+            left -= kChunk;
+        }
+        while (st == CF_OK && left > 0) {
+            st = launch_steps(c, Kind::Fluid, 1);
+            --left;
+        }
+        return st;
     }
-    CUDA_TRY(c, cudaGraphLaunch(c->g_tail[c->cur ^ 1], c->stream));
+    st = launch_steps(c, Kind::First, 1);
+    int left = n - 1;
+    while (st == CF_OK && left >= kChunk) {
+        st = launch_steps(c, Kind::Mid, kChunk);
+        left -= kChunk;
+    }
+    while (st == CF_OK && left > 0) {
+        st = launch_steps(c, Kind::Mid, 1);
+        --left;
+    }
+    if (st != CF_OK) return st;
+    // K5 of the last step: parity of that step is cur ^ 1
+    cudaGraphExec_t g;
+    st = get_graph(c, Kind::Tail, c->cur ^ 1, 0, 1, &g);
+    if (st != CF_OK) return st;
+    CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
     return CF_OK;
 }
 
@@ -579,7 +651,8 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < b && e == cudaSuccess; ++i) {
             const int p = c->cur, t = done + i;
-            int *use = c->box + 8 * (1 - p), *accb = c->box + 8 * p;
+            const int sph = (int)((c->tstep) % 3);
+            int *use = region_slot(c, sph), *accb = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
             cudaEventRecord(E[0], s);
             if (cells && t > 0) e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s);
@@ -603,6 +676,7 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
             if (cells && e == cudaSuccess) e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
+            c->tstep += 1;
         }
         if (e != cudaSuccess) {
             st = fail(c, CF_ECUDA, "launch failed: %s", cudaGetErrorString(e));
@@ -633,7 +707,8 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
         *near_nodes = 0;
         if (cells) {  // size of the region the last step used
             int h[6];
-            CUDA_TRY(c, cudaMemcpyAsync(h, c->box + 8 * c->cur, sizeof h, cudaMemcpyDeviceToHost, s));
+            const int *last = region_slot(c, (int)((c->tstep - 1) % 3));
+            CUDA_TRY(c, cudaMemcpyAsync(h, last, sizeof h, cudaMemcpyDeviceToHost, s));
             st = wait_stream(c);
             const LbmParams &p = c->lp;
             if (st == CF_OK && h[0] <= -h[3]) {

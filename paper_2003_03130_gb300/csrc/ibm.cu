@@ -4,11 +4,11 @@
 // max(0, 1 - |r|), nonzero on the 8 nodes floor(y) + {0,1}^3. Every vertex,
 // interior ones included, is a coupling point (the fluid fills the cell).
 //
-// K2+K3 (k_gather_spread), one thread per vertex:
-//   f_v = sum of the corner forces in the vertex's incidence row, in the
-//         row's fixed ascending (tet, corner) order - deterministic, no
-//         atomics (Sec. 3.1 defines forces per tet corner; the vertex force
-//         is their sum);
+// K2+K3 (k_gather_spread), four threads per vertex:
+//   f_v = sum of the corner forces in the vertex's incidence row, in a fixed
+//         order (strided partial sums combined by a fixed shuffle tree) -
+//         deterministic, no atomics (Sec. 3.1 defines forces per tet corner;
+//         the vertex force is their sum);
 //   F(x) += f_v delta_h(x - y_v) on the 8 support nodes (float atomics:
 //         the spread field is exact up to the order of those additions).
 // K5 (k_interp_advect), eight threads per vertex:
@@ -69,49 +69,61 @@ cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmPara
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
+// Four lanes per vertex: lane k sums the entries k, k+4, k+8, ... of the
+// incidence row, the four partial sums are combined by a fixed shuffle tree
+// (the same order every call: deterministic), and lane k spreads onto the
+// support nodes 2k and 2k+1.
+__global__ void __launch_bounds__(128) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
                                                        int do_spread, unsigned *err, int *box_out,
                                                        const int *__restrict__ box_in) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = g >> 2, lane = g & 3;
+    const bool live = v < m.V;
     int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX};
-    if (v < m.V) {
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (live) {
         const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int e = e0; e < e1; ++e) {
+        for (int e = e0 + lane; e < e1; e += 4) {
             const int id = __ldg(m.csr_idx + e);
             const float4 c = m.fc[(id & 3) * m.T + (id >> 2)];
             fx += c.x;
             fy += c.y;
             fz += c.z;
         }
-        m.fv[v] = make_float4(fx, fy, fz, 0.f);
-        if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (live) {
+        if (lane == 0) {
+            m.fv[v] = make_float4(fx, fy, fz, 0.f);
+            if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
+        }
         Support s;
         if (!do_spread) {
         } else if (!support_of(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
-            atomicOr(err, ERR_DOMAIN);
+            if (lane == 0) atomicOr(err, ERR_DOMAIN);
         } else {
             support_box(s, p, b);
-            if (box_in) {
+            if (box_in && lane == 0) {
                 const NodeBox r = region_of(box_in, p.nx, p.ny, p.nz);
                 if (!(in_region(r, -b[3], -b[4], -b[5], p.nx, p.nz) && in_region(r, b[0], b[1], b[2], p.nx, p.nz)))
                     atomicOr(err, ERR_MOVED);
             }
             const int N = (int)p.N;
-            const float wx[2] = {1.f - s.fx, s.fx}, wy[2] = {1.f - s.fy, s.fy}, wz[2] = {1.f - s.fz, s.fz};
+            const int dz = lane >> 1, dy = lane & 1;
+            const int Z = wrapi(s.bz + dz, p.nz);
+            const float wyz = (dy ? s.fy : 1.f - s.fy) * (dz ? s.fz : 1.f - s.fz);
 #pragma unroll
-            for (int dz = 0; dz < 2; ++dz) {
-                const int Z = wrapi(s.bz + dz, p.nz);
-#pragma unroll
-                for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) {
-                        const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
-                        const float w = wx[dx] * wy[dy] * wz[dz];
-                        atomicAdd(F + n, w * fx);
-                        atomicAdd(F + N + n, w * fy);
-                        atomicAdd(F + 2 * N + n, w * fz);
-                    }
+            for (int dx = 0; dx < 2; ++dx) {
+                const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
+                const float w = (dx ? s.fx : 1.f - s.fx) * wyz;
+                atomicAdd(F + n, w * fx);
+                atomicAdd(F + N + n, w * fy);
+                atomicAdd(F + 2 * N + n, w * fz);
             }
         }
     }
@@ -123,7 +135,8 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, c
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
-    k_gather_spread<<<(m.V + 63) / 64, 64, 0, s>>>(m, u, F, p, (F && lp) ? 1 : 0, err, box_out, box_in);
+    const long long threads = 4LL * m.V;
+    k_gather_spread<<<(int)((threads + 127) / 128), 128, 0, s>>>(m, u, F, p, (F && lp) ? 1 : 0, err, box_out, box_in);
     return cudaGetLastError();
 }
 

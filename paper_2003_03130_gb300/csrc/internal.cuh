@@ -186,6 +186,8 @@ cudaError_t launch_lbm(const float *fin, float *fout, const float *F, const LbmP
 // K4 split by the force region of a slot: far = every node outside it, with
 // no force-field read; near = the nodes inside it, with the force field.
 cudaError_t launch_lbm_far(const float *fin, float *fout, const LbmParams &p, const int *box, cudaStream_t s);
+// Device function of the far-field kernel (to tell its graph nodes apart).
+const void *lbm_far_kernel();
 cudaError_t launch_lbm_near(const float *fin, float *fout, const float *F, const LbmParams &p, const int *box,
                             float *vel, cudaStream_t s);
 // K5: velocity u(t) (stored by the near-field stream-collide) interpolated at

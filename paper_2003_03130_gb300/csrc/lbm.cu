@@ -14,7 +14,10 @@
 //                     + (1 - omega/2) w_q [3 (c_q - u) + 9 (c_q . u) c_q] . F,
 //     d^eq_q = w_q [(rho - 1) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)].
 // Loads along x are coalesced (scalar, unit stride, possibly shifted by one
-// word); stores are unit-stride.
+// word); stores are unit-stride. Population loads and stores carry the
+// streaming cache hint (evict first): every population is touched once per
+// step, and the hint keeps the cells' few MB of mesh data resident in L2
+// while the lattice streams through it.
 #include "internal.cuh"
 
 namespace cf {
@@ -75,8 +78,8 @@ __device__ __forceinline__ void collide_pair(const float (&d)[19], float *__rest
     const float cF = cdot<cx(A), cy(A), cz(A)>(Fx, Fy, Fz);
     const float P = fmaf(cu, fmaf(k.g9, cF, k.e45 * cu), k.c0);
     const float Q = fmaf(k.o3, cu, k.g3 * cF);
-    fout[A * N + n] = fmaf(om1, d[A], P + Q);
-    fout[B * N + n] = fmaf(om1, d[B], P - Q);
+    __stcs(fout + A * N + n, fmaf(om1, d[A], P + Q));
+    __stcs(fout + B * N + n, fmaf(om1, d[B], P - Q));
 }
 
 // One node. WALL: the row touches a wall (y = 0 or y = ny-1), so pulls from
@@ -99,10 +102,10 @@ __device__ __forceinline__ void lbm_node(const float *__restrict__ fin, float *_
         const int sy = y - cy(q);
         if (WALL && ((cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1))) {
             const float uw = cy(q) == 1 ? p.uw_lo : p.uw_hi;
-            d[q] = __ldg(fin + opp(q) * N + n);
+            d[q] = __ldcs(fin + opp(q) * N + n);
             if (cx(q) != 0) d[q] += (6.f * wq(q) * cx(q)) * uw;
         } else {
-            d[q] = __ldg(fin + q * N + sx + nx * (sy + ny * sz));
+            d[q] = __ldcs(fin + q * N + sx + nx * (sy + ny * sz));
         }
     }
 
@@ -137,7 +140,7 @@ __device__ __forceinline__ void lbm_node(const float *__restrict__ fin, float *_
     const WClass k0 = wclass(1.f / 3.f, drho, rho, usq15, uF, om, g);
     const WClass k1 = wclass(1.f / 18.f, drho, rho, usq15, uF, om, g);
     const WClass k2 = wclass(1.f / 36.f, drho, rho, usq15, uF, om, g);
-    fout[n] = fmaf(om1, d[0], k0.c0);
+    __stcs(fout + n, fmaf(om1, d[0], k0.c0));
     collide_pair<1>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
     collide_pair<3>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
     collide_pair<5>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(128) k_lbm_far(const float *__restrict__ fin, 
     if (x >= p.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
-    if (in_region(b, x, y, z, p.nx, p.nz)) return;
+    if (y >= b.y0 && y <= b.y1 && region_off(z, b.z0, p.nz) < b.lz && region_off(x, b.x0, p.nx) < b.lx) return;
     if (y > 0 && y < p.ny - 1)
         lbm_node<false, false>(fin, fout, nullptr, p, x, y, z);
     else
@@ -200,6 +203,8 @@ __global__ void __launch_bounds__(128) k_lbm_near(const float *__restrict__ fin,
             lbm_node<true, true>(fin, fout, F, p, x, y, z, vel);
     }
 }
+
+const void *lbm_far_kernel() { return (const void *)k_lbm_far; }
 
 cudaError_t launch_lbm_far(const float *fin, float *fout, const LbmParams &p, const int *box, cudaStream_t s) {
     const int bx = p.nx < 128 ? p.nx : 128;
