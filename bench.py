@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision-steps", type=int, default=2000,
+                    help="steps of the FP32/FP16/BF16 comparison on the channel workload (0 = skip)")
     return ap.parse_args()
 
 
@@ -178,6 +180,49 @@ def cpu_baseline(wl, seconds):
             "mlups": n * wl.n_nodes / dt / 1e6}
 
 
+def precision_block(P, torch, dev, steps):
+    """FP32, FP16 and BF16 population storage on the pressure-driven channel
+    (256 x 128 x 128, one R = 16 cell): steps/s of each, and the error of the
+    16-bit runs against the FP32 run after the same steps from t = 0
+    (norm-wise relative on the fluid velocity and the cell displacement;
+    relative on the Taylor deformation D)."""
+    from workloads import configs
+
+    wl = configs.precision_channel(steps=steps)
+    res = {}
+    stream = torch.cuda.Stream(dev)
+    for fmt in ("f32", "f16", "bf16"):
+        with torch.cuda.stream(stream):
+            ctx = P.cf_create(dev, stream.cuda_stream)
+            P.cf_set_population_format(ctx, fmt)
+            (cid,) = P.load_workload(ctx, wl)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.cf_step_async(ctx, steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            P.cf_synchronize(ctx)
+            ms = e0.elapsed_time(e1)
+            y = P.cf_get_positions(ctx, cid)
+            u = P.cf_get_velocity(ctx)
+            D = P.cf_get_taylor(ctx, cid)["D"]
+            P.cf_destroy(ctx)
+        res[fmt] = {"steps_per_s": steps / (ms / 1e3), "mlups": wl.n_nodes * steps / (ms / 1e3) / 1e6,
+                    "y": y, "u": u, "D": D}
+    x0 = wl.cells[0].x_ref
+    ref = res["f32"]
+    out = {"workload": wl.name, "steps": steps, "D_f32": ref["D"]}
+    for fmt in ("f32", "f16", "bf16"):
+        r = res[fmt]
+        out[fmt] = {"steps_per_s": r["steps_per_s"], "mlups": r["mlups"], "D": r["D"]}
+        if fmt != "f32":
+            out[fmt]["rel_err_velocity_vs_f32"] = float(np.linalg.norm(r["u"] - ref["u"]) / np.linalg.norm(ref["u"]))
+            out[fmt]["rel_err_displacement_vs_f32"] = float(
+                np.linalg.norm(r["y"] - ref["y"]) / np.linalg.norm(ref["y"] - x0))
+            out[fmt]["rel_err_D_vs_f32"] = float(abs(r["D"] - ref["D"]) / abs(ref["D"]))
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -301,6 +346,8 @@ def run_ours(args):
         },
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and args.precision_steps > 0:
+        out["precision"] = precision_block(P, torch, dev, args.precision_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if world > 1:

@@ -67,6 +67,14 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream);
 /* Free all device memory of the context. NULL is ignored. */
 void cf_destroy(cf_ctx *ctx);
 
+/* Storage of the lattice populations, used by the next cf_lbm_init (which
+ * re-initialises the fluid). The populations are kept as deviations
+ * f_q - w_q from the rest equilibrium; FP16 and BF16 store them multiplied by
+ * a power of two per weight class. The collide always computes in FP32.
+ * Default CF_POP_F32. Errors: CF_EINVAL for an unknown format. */
+enum { CF_POP_F32 = 0, CF_POP_F16 = 1, CF_POP_BF16 = 2 };
+cf_status cf_set_population_format(cf_ctx *ctx, int32_t format);
+
 /* Lattice-Boltzmann fluid on nx*ny*nz nodes (Sec. 6.1 box), D3Q19 BGK with
  * relaxation time tau (> 1/2), Guo forcing, halfway bounce-back walls at
  * y = -1/2 moving at (u_wall_lo_x, 0, 0) and y = ny-1/2 moving at
@@ -143,6 +151,17 @@ cf_status cf_get_density(cf_ctx *ctx, double *out);
 /* Elastic energy E = sum over the cell's tets of V_0 U (Sec. 2-3.1) at the
  * current positions, accumulated in double. */
 cf_status cf_get_energy(cf_ctx *ctx, int32_t cell_id, double *out);
+
+/* Taylor deformation of a cell at its current positions (Sec. 3.3), computed
+ * on the device: inertia tensor Theta = sum_l V_l (r.r I - r r^T) over the
+ * tets (r = tet centroid relative to the volume-weighted cell centroid, V_l
+ * the current tet volume), its eigenvalues theta_1 >= theta_2 >= theta_3, the
+ * semi-axes a_i (square roots of the paper's expressions, which have units of
+ * length squared) and D = (a3 - a1)/(a3 + a1). out[10] = D, D computed from
+ * the squared expressions as printed, inclination of the major axis to x in
+ * the x-y plane (degrees, (-90, 90]), a1, a2, a3, theta1, theta2, theta3,
+ * cell volume. */
+cf_status cf_get_taylor(cf_ctx *ctx, int32_t cell_id, double *out);
 
 /* Incidence rows of a cell: ptr[nv+1], idx[4 nt] with entries 4*t + c (t
  * local to the cell, ascending within each row). */

@@ -45,6 +45,7 @@ def lib():
         sig = {
             "cf_create": ([ctypes.POINTER(vp), ctypes.c_int, vp], ctypes.c_int),
             "cf_destroy": ([vp], None),
+            "cf_set_population_format": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_lbm_init": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, _d], ctypes.c_int),
             "cf_mesh_init": ([vp, ctypes.c_int32, _d, ctypes.c_int32, _i, _d, _i], ctypes.c_int),
@@ -61,6 +62,7 @@ def lib():
             "cf_get_density": ([vp, _d], ctypes.c_int),
             "cf_get_energy": ([vp, ctypes.c_int32, _d], ctypes.c_int),
             "cf_get_csr": ([vp, ctypes.c_int32, _i, _i], ctypes.c_int),
+            "cf_get_taylor": ([vp, ctypes.c_int32, _d], ctypes.c_int),
             "cf_get_mesh": ([vp, ctypes.c_int32, _i, _d, _d], ctypes.c_int),
             "cf_cell_verts": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_cell_tets": ([vp, ctypes.c_int32], ctypes.c_int32),
@@ -144,6 +146,17 @@ def cf_destroy(ctx: Context):
 
 def cf_last_error(ctx) -> str:
     return (lib().cf_last_error(ctx.handle) or b"").decode()
+
+
+CF_POP_F32, CF_POP_F16, CF_POP_BF16 = 0, 1, 2
+POP_FORMATS = {"f32": CF_POP_F32, "f16": CF_POP_F16, "bf16": CF_POP_BF16}
+
+
+def cf_set_population_format(ctx, fmt):
+    """``fmt``: CF_POP_F32 / CF_POP_F16 / CF_POP_BF16 or "f32" / "f16" /
+    "bf16"; applies at the next cf_lbm_init."""
+    fmt = POP_FORMATS.get(fmt, fmt)
+    _check(ctx, lib().cf_set_population_format(ctx.handle, int(fmt)))
 
 
 def cf_lbm_init(ctx, nx, ny, nz, tau, u_wall_lo_x, u_wall_hi_x, body_force=None):
@@ -238,6 +251,16 @@ def cf_get_energy(ctx, cell_id) -> float:
     e = ctypes.c_double()
     _check(ctx, lib().cf_get_energy(ctx.handle, cell_id, ctypes.byref(e)))
     return e.value
+
+
+TAYLOR_KEYS = ("D", "D_literal", "inclination", "a1", "a2", "a3", "theta1", "theta2", "theta3", "volume")
+
+
+def cf_get_taylor(ctx, cell_id):
+    """Taylor deformation of a cell (computed on the device), as a dict."""
+    out = np.zeros(10)
+    _check(ctx, lib().cf_get_taylor(ctx.handle, cell_id, _p(out)))
+    return dict(zip(TAYLOR_KEYS, out.tolist()))
 
 
 def cf_get_csr(ctx, cell_id):

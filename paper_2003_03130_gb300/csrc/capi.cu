@@ -61,7 +61,8 @@ struct cf_ctx {
     // fluid
     bool lbm_ready = false;
     LbmParams lp{};
-    float *f[2] = {nullptr, nullptr};
+    int pop_format = POP_F32;  // storage of the populations (next cf_lbm_init)
+    void *f[2] = {nullptr, nullptr};
     float *F = nullptr;
     float *vel = nullptr;  // u(t) on the force region, [3][N]
 
@@ -77,6 +78,7 @@ struct cf_ctx {
     int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
     double *energy_partial = nullptr, *energy_out = nullptr;
     double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
+    double *taylor_partial = nullptr, *taylor_out = nullptr;
 
     int *box = nullptr;  // three force-region slots of 8 ints (see NodeBox)
 
@@ -200,7 +202,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     if (kind == Kind::Fluid) {
         for (int i = 0; i < nsteps; ++i) {
             const int p = p0 ^ (i & 1);
-            CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], nullptr, c->lp, sf));
+            CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], c->lp, sf));
         }
         return CF_OK;
     }
@@ -271,7 +273,7 @@ cf_status get_graph(cf_ctx *c, Kind kind, int p, int s, int nsteps, cudaGraphExe
             e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
             if (e != cudaSuccess) break;
             cudaLaunchAttributeValue v;
-            v.priority = kp.func == lbm_far_kernel() ? least : greatest;
+            v.priority = is_lbm_far_kernel(kp.func) ? least : greatest;
             e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
         }
     }
@@ -342,7 +344,7 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         c->own_stream = true;
     }
     if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
-        dalloc(&c->box, 24) != cudaSuccess ||
+        dalloc(&c->box, 24) != cudaSuccess || dalloc(&c->taylor_out, 10) != cudaSuccess ||
         dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
@@ -381,6 +383,8 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->energy_partial);
     dfree(c->energy_out);
     dfree(c->stage);
+    dfree(c->taylor_partial);
+    dfree(c->taylor_out);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -406,6 +410,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     dfree(c->vel);
     c->lbm_ready = false;
     LbmParams p{};
+    p.fmt = c->pop_format;
     p.nx = nx;
     p.ny = ny;
     p.nz = nz;
@@ -417,8 +422,9 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     p.gx = g ? (float)g[0] : 0.f;
     p.gy = g ? (float)g[1] : 0.f;
     p.gz = g ? (float)g[2] : 0.f;
-    CUDA_TRY(c, dalloc(&c->f[0], 19 * (size_t)N));
-    CUDA_TRY(c, dalloc(&c->f[1], 19 * (size_t)N));
+    const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
+    CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
+    CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
     CUDA_TRY(c, dalloc(&c->F, 3 * (size_t)N));
     CUDA_TRY(c, dalloc(&c->vel, 3 * (size_t)N));
     CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
@@ -433,6 +439,14 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
                                     c->stream));
     c->lbm_ready = true;
     return wait_stream(c);
+}
+
+cf_status cf_set_population_format(cf_ctx *c, int32_t format) {
+    if (!c) return CF_EINVAL;
+    if (format != CF_POP_F32 && format != CF_POP_F16 && format != CF_POP_BF16)
+        return fail(c, CF_EINVAL, "unknown population format %d", format);
+    c->pop_format = format;
+    return CF_OK;
 }
 
 cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets, const double *y0,
@@ -466,7 +480,7 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     auto cleanup = [&]() {
         dfree(n.xr); dfree(n.u[0]); dfree(n.u[1]); dfree(n.fv); dfree(n.fc); dfree(n.xref64); dfree(n.tet);
         dfree(n.B); dfree(n.V0); dfree(n.tcell); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
-        dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(x64); dfree(y64);
+        dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(n.taylor_partial); dfree(x64); dfree(y64);
         dfree(tin);
     };
 #define TRY_N(expr)                                                                                    \
@@ -495,6 +509,7 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     TRY_N(dalloc(&n.csr_cursor, V1));
     TRY_N(dalloc(&n.energy_partial, (T1 + 255) / 256 + 1));
     TRY_N(dalloc(&n.stage, 3 * (size_t)V1));
+    TRY_N(dalloc(&n.taylor_partial, 10 * ((size_t)(T1 + 255) / 256 + 1)));
     TRY_N(dalloc(&x64, 3 * (size_t)nv));
     TRY_N(dalloc(&tin, 4 * (size_t)nt));
     if (y0) TRY_N(dalloc(&y64, 3 * (size_t)nv));
@@ -560,6 +575,7 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     std::swap(c->csr_cursor, n.csr_cursor);
     std::swap(c->energy_partial, n.energy_partial);
     std::swap(c->stage, n.stage);
+    std::swap(c->taylor_partial, n.taylor_partial);
     cleanup();  // frees the old buffers now held by n
     c->V = V1;
     c->T = T1;
@@ -671,7 +687,7 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
                 e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, s)
-                          : launch_lbm(c->f[p], c->f[1 - p], nullptr, c->lp, s);
+                          : launch_lbm(c->f[p], c->f[1 - p], c->lp, s);
             cudaEventRecord(E[4], s);
             if (cells && e == cudaSuccess) e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s);
             cudaEventRecord(E[5], s);
@@ -802,6 +818,16 @@ cf_status cf_get_energy(cf_ctx *c, int32_t id, double *out) {
     CUDA_TRY(c, launch_energy(view(c), c->u[c->cur], ci->t_off, ci->t_off + ci->nt, c->energy_partial, c->energy_out,
                               c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(out, c->energy_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c);
+}
+
+cf_status cf_get_taylor(cf_ctx *c, int32_t id, double *out) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    DeviceGuard dg(c->device);
+    CUDA_TRY(c, launch_taylor(view(c), c->u[c->cur], ci->t_off, ci->t_off + ci->nt, c->taylor_partial, c->taylor_out,
+                              c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->taylor_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return wait_stream(c);
 }
 

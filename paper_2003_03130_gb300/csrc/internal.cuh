@@ -52,7 +52,11 @@ __host__ __device__ constexpr float wq(int q) {
     return q == 0 ? 1.0f / 3.0f : q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f;
 }
 
+// Population storage formats (see csrc/lbm.cu).
+enum : int { POP_F32 = 0, POP_F16 = 1, POP_BF16 = 2 };
+
 struct LbmParams {
+    int fmt;  // POP_F32, POP_F16 or POP_BF16
     int nx, ny, nz;
     long long N;
     float omega;        // 1/tau
@@ -171,6 +175,11 @@ cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, 
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
+// K8: Taylor deformation of tets [t0, t1) at displacements u; out[10] (device)
+// = D, D from the printed squared expression, inclination (deg), a1, a2, a3,
+// theta1, theta2, theta3, volume. partial: 10 doubles per 256 tets.
+cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
+                          cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
 // same threads spread their vertex force onto the lattice. With box_out the
 // bounding box of the support nodes is accumulated into that slot; with
@@ -181,21 +190,25 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, c
 // Bounding box of the support nodes of x + u into a slot (reset by the caller).
 cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmParams &p, int *box_out,
                                cudaStream_t s);
-// K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node.
-cudaError_t launch_lbm(const float *fin, float *fout, const float *F, const LbmParams &p, cudaStream_t s);
+// K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
+// force field (fluid-only runs). Population buffers are in the format p.fmt.
+cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStream_t s);
 // K4 split by the force region of a slot: far = every node outside it, with
-// no force-field read; near = the nodes inside it, with the force field.
-cudaError_t launch_lbm_far(const float *fin, float *fout, const LbmParams &p, const int *box, cudaStream_t s);
-// Device function of the far-field kernel (to tell its graph nodes apart).
-const void *lbm_far_kernel();
-cudaError_t launch_lbm_near(const float *fin, float *fout, const float *F, const LbmParams &p, const int *box,
+// no force-field read; near = the nodes inside it, with the force field, also
+// storing u(t) there.
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const int *box, cudaStream_t s);
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *box,
                             float *vel, cudaStream_t s);
+// True for the device functions of the far-field kernels (to tell their graph
+// nodes apart).
+bool is_lbm_far_kernel(const void *fn);
+size_t pop_bytes(int fmt);
 // K5: velocity u(t) (stored by the near-field stream-collide) interpolated at
 // x + u_cur; u_next = u_cur + velocity.
 cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s);
-cudaError_t launch_lbm_init(float *f, const LbmParams &p, cudaStream_t s);
-cudaError_t launch_lbm_macro(const float *f, const float *F, const LbmParams &p, double *rho, double *u,
+cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s);
+cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, double *rho, double *u,
                              cudaStream_t s);
 
 }  // namespace cf

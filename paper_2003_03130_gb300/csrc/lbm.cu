@@ -1,10 +1,8 @@
 // K4: D3Q19 lattice-Boltzmann stream + collide (the fluid of Sec. 6; the
-// paper uses ESPResSo's LB without stating the operator). One thread per
-// node, pull scheme: the buffer holds post-collision populations, a node
-// pulls f_q(x - c_q) from the old buffer, collides, and writes the new
-// post-collision populations at x into the other buffer. Populations are
-// stored as deviations d_q = f_q - w_q, so rest equilibrium is all zeros and
-// every FP32 operation is relative to the O(u) signal.
+// paper uses ESPResSo's LB without stating the operator). Pull scheme: the
+// buffer holds post-collision populations, a node pulls f_q(x - c_q) from the
+// old buffer, collides, and writes the new post-collision populations at x
+// into the other buffer.
 //
 //   walls (Sec. 6.1 moving planes): a pull from beyond y = -1/2 or
 //     y = ny - 1/2 is halfway bounce-back with the moving-wall term,
@@ -13,15 +11,75 @@
 //   BGK + Guo: d*_q = d_q + omega (d^eq_q - d_q)
 //                     + (1 - omega/2) w_q [3 (c_q - u) + 9 (c_q . u) c_q] . F,
 //     d^eq_q = w_q [(rho - 1) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)].
-// Loads along x are coalesced (scalar, unit stride, possibly shifted by one
-// word); stores are unit-stride. Population loads and stores carry the
-// streaming cache hint (evict first): every population is touched once per
-// step, and the hint keeps the cells' few MB of mesh data resident in L2
-// while the lattice streams through it.
+//
+// Storage: populations are kept as deviations d_q = f_q - w_q from the rest
+// equilibrium (FP32 rounding then scales with the O(u) signal), in FP32, or in
+// FP16 / BF16 multiplied by a power of two per weight class (2^14, 2^16, 2^17
+// for w = 1/3, 1/18, 1/36, so that the stored values are O(10^3) and never
+// subnormal in FP16); the collide always runs in FP32. Population loads and
+// stores carry the streaming cache hint (evict first): every population is
+// touched once per step, and the hint keeps the cells' few MB of mesh data
+// resident in L2 while the lattice streams through it.
+//
+// One node per thread, 128 threads along x: 19 independent coalesced loads
+// per node (x-shifted rows are off by one word; neighbouring warps share the
+// lines in L2), the collide, 19 coalesced stores.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace cf {
 
+// ---------------------------------------------------------------- storage
+template <class T>
+struct Pop;
+
+template <>
+struct Pop<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
+    static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+    static __device__ __forceinline__ float2 ld2(const float *p) { return __ldcs(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ void st2(float *p, float a, float b) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+    }
+};
+
+template <>
+struct Pop<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ float2 ld2(const __half *p) {
+        return __half22float2(__ldcs(reinterpret_cast<const __half2 *>(p)));
+    }
+    static __device__ __forceinline__ void st2(__half *p, float a, float b) {
+        __stcs(reinterpret_cast<__half2 *>(p), __floats2half2_rn(a, b));
+    }
+};
+
+template <>
+struct Pop<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(__ldcs(reinterpret_cast<const __nv_bfloat162 *>(p)));
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16 *p, float a, float b) {
+        __stcs(reinterpret_cast<__nv_bfloat162 *>(p), __floats2bfloat162_rn(a, b));
+    }
+};
+
+// stored value = d_q * scale; exact powers of two
+template <class T>
+__device__ __forceinline__ constexpr float pop_scale(int q) {
+    return sizeof(T) == 4 ? 1.f : (q == 0 ? 16384.f : (q <= 6 ? 65536.f : 131072.f));
+}
+template <class T>
+__device__ __forceinline__ constexpr float pop_unscale(int q) {
+    return sizeof(T) == 4 ? 1.f : (q == 0 ? 1.f / 16384.f : (q <= 6 ? 1.f / 65536.f : 1.f / 131072.f));
+}
+
+// ---------------------------------------------------------------- collide
 // c . v for a compile-time lattice vector (a, b, c): only the nonzero
 // components enter (0.0f * v cannot be folded away under IEEE rules).
 template <int a, int b, int c>
@@ -64,30 +122,71 @@ __device__ __forceinline__ WClass wclass(float w, float drho, float rho, float u
     return k;
 }
 
-// Collide the opposite pair (A, opp(A)). With cu = c_A.u and cF = c_A.F the
-// equilibrium and source split into a part even in c (P) and a part odd in
-// c (Q): d*_A = (1-omega) d_A + P + Q, d*_opp = (1-omega) d_opp + P - Q, with
+// Collide the opposite pair (A, opp(A)) in place. With cu = c_A.u and
+// cF = c_A.F the equilibrium and source split into a part even in c (P) and a
+// part odd in c (Q): d*_A = (1-omega) d_A + P + Q, d*_opp = (1-omega) d_opp +
+// P - Q, with
 //   P = omega w [drho + rho (9/2 cu^2 - 3/2 u.u)] + g w [9 cu cF - 3 u.F],
 //   Q = 3 omega w rho cu + 3 g w cF.
 template <int A>
-__device__ __forceinline__ void collide_pair(const float (&d)[19], float *__restrict__ fout, int n, int N,
-                                             const WClass &k, float om1, float ux, float uy, float uz, float Fx,
-                                             float Fy, float Fz) {
+__device__ __forceinline__ void collide_pair(float (&d)[19], const WClass &k, float om1, float ux, float uy, float uz,
+                                             float Fx, float Fy, float Fz) {
     constexpr int B = opp(A);
     const float cu = cdot<cx(A), cy(A), cz(A)>(ux, uy, uz);
     const float cF = cdot<cx(A), cy(A), cz(A)>(Fx, Fy, Fz);
     const float P = fmaf(cu, fmaf(k.g9, cF, k.e45 * cu), k.c0);
     const float Q = fmaf(k.o3, cu, k.g3 * cF);
-    __stcs(fout + A * N + n, fmaf(om1, d[A], P + Q));
-    __stcs(fout + B * N + n, fmaf(om1, d[B], P - Q));
+    const float a = fmaf(om1, d[A], P + Q);
+    const float b = fmaf(om1, d[B], P - Q);
+    d[A] = a;
+    d[B] = b;
 }
 
-// One node. WALL: the row touches a wall (y = 0 or y = ny-1), so pulls from
-// beyond it are bounced back; interior rows skip those tests.
-template <bool WALL, bool HAS_F>
-__device__ __forceinline__ void lbm_node(const float *__restrict__ fin, float *__restrict__ fout,
+// Moments and collision of one node, in place: d holds the pulled
+// populations on entry and the post-collision ones on exit. Returns u(t).
+__device__ __forceinline__ float3 collide(float (&d)[19], float Fx, float Fy, float Fz, const LbmParams &p) {
+    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) +
+                       ((d[8] + d[9]) + (d[10] + d[11])) + ((d[12] + d[13]) + (d[14] + d[15])) +
+                       ((d[16] + d[17]) + d[18]);
+    // x: +1 at 1, 15..18; -1 at 2, 7..10
+    const float jx = ((d[1] - d[2]) + (d[15] - d[7])) + ((d[16] - d[8]) + (d[17] - d[9])) + (d[18] - d[10]);
+    // y: +1 at 3, 10, 13, 14, 18; -1 at 4, 7, 11, 12, 15
+    const float jy = ((d[3] - d[4]) + (d[10] - d[7])) + ((d[13] - d[11]) + (d[14] - d[12])) + (d[18] - d[15]);
+    // z: +1 at 5, 9, 12, 14, 17; -1 at 6, 8, 11, 13, 16
+    const float jz = ((d[5] - d[6]) + (d[9] - d[8])) + ((d[12] - d[11]) + (d[14] - d[13])) + (d[17] - d[16]);
+    const float rho = 1.f + drho;
+    const float ir = __frcp_rn(rho);
+    const float ux = fmaf(0.5f, Fx, jx) * ir, uy = fmaf(0.5f, Fy, jy) * ir, uz = fmaf(0.5f, Fz, jz) * ir;
+    const float usq15 = 1.5f * fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
+    const float om = p.omega, g = p.guo, om1 = 1.f - om;
+    const WClass k0 = wclass(1.f / 3.f, drho, rho, usq15, uF, om, g);
+    const WClass k1 = wclass(1.f / 18.f, drho, rho, usq15, uF, om, g);
+    const WClass k2 = wclass(1.f / 36.f, drho, rho, usq15, uF, om, g);
+    d[0] = fmaf(om1, d[0], k0.c0);
+    collide_pair<1>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<3>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<5>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<7>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<8>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<9>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<10>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<11>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair<12>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    return make_float3(ux, uy, uz);
+}
+
+// pull from beyond a wall? (only in rows y = 0 and y = ny - 1)
+template <int q>
+__device__ __forceinline__ bool wall_pull(int y, int ny) {
+    return (cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1);
+}
+
+// ---------------------------------------------------------------- one node
+template <class T, bool WALL, bool HAS_F>
+__device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restrict__ fout,
                                          const float *__restrict__ F, const LbmParams &p, int x, int y, int z,
-                                         float *__restrict__ vel = nullptr) {
+                                         float *__restrict__ vel) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -102,70 +201,44 @@ __device__ __forceinline__ void lbm_node(const float *__restrict__ fin, float *_
         const int sy = y - cy(q);
         if (WALL && ((cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1))) {
             const float uw = cy(q) == 1 ? p.uw_lo : p.uw_hi;
-            d[q] = __ldcs(fin + opp(q) * N + n);
+            d[q] = Pop<T>::ld(fin + opp(q) * N + n) * pop_unscale<T>(q);
             if (cx(q) != 0) d[q] += (6.f * wq(q) * cx(q)) * uw;
         } else {
-            d[q] = __ldcs(fin + q * N + sx + nx * (sy + ny * sz));
+            d[q] = Pop<T>::ld(fin + q * N + sx + nx * (sy + ny * sz)) * pop_unscale<T>(q);
         }
     }
-
-    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) +
-                       ((d[8] + d[9]) + (d[10] + d[11])) + ((d[12] + d[13]) + (d[14] + d[15])) +
-                       ((d[16] + d[17]) + d[18]);
-    // x: +1 at 1, 15..18; -1 at 2, 7..10
-    const float jx = ((d[1] - d[2]) + (d[15] - d[7])) + ((d[16] - d[8]) + (d[17] - d[9])) + (d[18] - d[10]);
-    // y: +1 at 3, 10, 13, 14, 18; -1 at 4, 7, 11, 12, 15
-    const float jy = ((d[3] - d[4]) + (d[10] - d[7])) + ((d[13] - d[11]) + (d[14] - d[12])) + (d[18] - d[15]);
-    // z: +1 at 5, 9, 12, 14, 17; -1 at 6, 8, 11, 13, 16
-    const float jz = ((d[5] - d[6]) + (d[9] - d[8])) + ((d[12] - d[11]) + (d[14] - d[13])) + (d[17] - d[16]);
-
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
     if (HAS_F) {
         Fx += __ldg(F + n);
         Fy += __ldg(F + N + n);
         Fz += __ldg(F + 2 * N + n);
     }
-    const float rho = 1.f + drho;
-    const float ir = __frcp_rn(rho);
-    const float ux = fmaf(0.5f, Fx, jx) * ir, uy = fmaf(0.5f, Fy, jy) * ir, uz = fmaf(0.5f, Fz, jz) * ir;
+    const float3 u = collide(d, Fx, Fy, Fz, p);
     if (vel) {  // u(t) of this step, for the interpolation at the vertices
-        vel[n] = ux;
-        vel[N + n] = uy;
-        vel[2 * N + n] = uz;
+        vel[n] = u.x;
+        vel[N + n] = u.y;
+        vel[2 * N + n] = u.z;
     }
-    const float usq15 = 1.5f * fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    const float uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
-    const float om = p.omega, g = p.guo, om1 = 1.f - om;
-
-    const WClass k0 = wclass(1.f / 3.f, drho, rho, usq15, uF, om, g);
-    const WClass k1 = wclass(1.f / 18.f, drho, rho, usq15, uF, om, g);
-    const WClass k2 = wclass(1.f / 36.f, drho, rho, usq15, uF, om, g);
-    __stcs(fout + n, fmaf(om1, d[0], k0.c0));
-    collide_pair<1>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<3>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<5>(d, fout, n, N, k1, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<7>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<8>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<9>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<10>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<11>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
-    collide_pair<12>(d, fout, n, N, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) Pop<T>::st(fout + q * N + n, d[q] * pop_scale<T>(q));
 }
 
-template <bool HAS_F>
-__global__ void __launch_bounds__(128) k_lbm(const float *__restrict__ fin, float *__restrict__ fout,
-                                             const float *__restrict__ F, LbmParams p) {
+// ---------------------------------------------------------------- kernels
+// Whole lattice, no force field (fluid-only runs).
+template <class T>
+__global__ void __launch_bounds__(128) k_lbm(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<false, HAS_F>(fin, fout, F, p, x, y, z);
+        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr);
     else
-        lbm_node<true, HAS_F>(fin, fout, F, p, x, y, z);
+        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
 }
 
 // Every node outside the force region (F is zero there: no force-field read).
-__global__ void __launch_bounds__(128) k_lbm_far(const float *__restrict__ fin, float *__restrict__ fout, LbmParams p,
+template <class T>
+__global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
                                                  const int *__restrict__ box) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
@@ -173,15 +246,16 @@ __global__ void __launch_bounds__(128) k_lbm_far(const float *__restrict__ fin, 
     const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
     if (y >= b.y0 && y <= b.y1 && region_off(z, b.z0, p.nz) < b.lz && region_off(x, b.x0, p.nx) < b.lx) return;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<false, false>(fin, fout, nullptr, p, x, y, z);
+        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr);
     else
-        lbm_node<true, false>(fin, fout, nullptr, p, x, y, z);
+        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
 }
 
 // The nodes inside the force region, with the force field; also stores u(t)
 // there. The grid is fixed when a step is captured while the region moves
 // with the cells, so threads stride over the region's nodes.
-__global__ void __launch_bounds__(128) k_lbm_near(const float *__restrict__ fin, float *__restrict__ fout,
+template <class T>
+__global__ void __launch_bounds__(128) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
                                                   const float *__restrict__ F, LbmParams p,
                                                   const int *__restrict__ box, float *__restrict__ vel) {
     const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
@@ -198,56 +272,24 @@ __global__ void __launch_bounds__(128) k_lbm_near(const float *__restrict__ fin,
         z += z < 0 ? p.nz : 0;
         const int y = b.y0 + j;
         if (y > 0 && y < p.ny - 1)
-            lbm_node<false, true>(fin, fout, F, p, x, y, z, vel);
+            lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel);
         else
-            lbm_node<true, true>(fin, fout, F, p, x, y, z, vel);
+            lbm_node<T, true, true>(fin, fout, F, p, x, y, z, vel);
     }
 }
 
-const void *lbm_far_kernel() { return (const void *)k_lbm_far; }
-
-cudaError_t launch_lbm_far(const float *fin, float *fout, const LbmParams &p, const int *box, cudaStream_t s) {
-    const int bx = p.nx < 128 ? p.nx : 128;
-    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-    k_lbm_far<<<grid, bx, 0, s>>>(fin, fout, p, box);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lbm_near(const float *fin, float *fout, const float *F, const LbmParams &p, const int *box,
-                            float *vel, cudaStream_t s) {
-    // one pass over regions up to ~155k nodes (8 blocks of 128 per SM)
-    const long long cap = (p.N + 127) / 128;
-    const int blocks = (int)(cap < 1216 ? cap : 1216);
-    k_lbm_near<<<blocks, 128, 0, s>>>(fin, fout, F, p, box, vel);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lbm(const float *fin, float *fout, const float *F, const LbmParams &p, cudaStream_t s) {
-    const int bx = p.nx < 128 ? p.nx : 128;
-    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-    if (F)
-        k_lbm<true><<<grid, bx, 0, s>>>(fin, fout, F, p);
-    else
-        k_lbm<false><<<grid, bx, 0, s>>>(fin, fout, F, p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lbm_init(float *f, const LbmParams &p, cudaStream_t s) {
-    // rest equilibrium, rho = 1, u = 0: every deviation is zero
-    return cudaMemsetAsync(f, 0, sizeof(float) * 19 * (size_t)p.N, s);
-}
-
 // rho and u(t) on every node from post-collision populations and the force of
-// the same step: rho = 1 + sum d*_q, rho u = sum c_q d*_q - F/2.
-__global__ void k_macro(const float *__restrict__ f, const float *__restrict__ F, LbmParams p, double *rho,
-                        double *u) {
+// the same step: rho = 1 + sum d*_q, rho u = sum c_q d*_q - F/2 (the collision
+// adds exactly F to the momentum, and rho u = sum c_q d_q + F/2 before it).
+template <class T>
+__global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, LbmParams p, double *rho, double *u) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = (int)p.N;
     if (n >= N) return;
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
-        const float d = f[q * N + n];
+        const float d = Pop<T>::ld(f + q * N + n) * pop_unscale<T>(q);
         drho += d;
         if (cx(q)) jx += cx(q) * d;
         if (cy(q)) jy += cy(q) * d;
@@ -263,9 +305,81 @@ __global__ void k_macro(const float *__restrict__ f, const float *__restrict__ F
     }
 }
 
-cudaError_t launch_lbm_macro(const float *f, const float *F, const LbmParams &p, double *rho, double *u,
+// ---------------------------------------------------------------- launchers
+size_t pop_bytes(int fmt) { return fmt == POP_F32 ? 4 : 2; }
+
+template <class T>
+static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, cudaStream_t s) {
+    const int bx = p.nx < 128 ? p.nx : 128;
+    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+    k_lbm<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p);
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const int *box, cudaStream_t s) {
+    const int bx = p.nx < 128 ? p.nx : 128;
+    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+    k_lbm_far<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, box);
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const int *box, float *vel,
+                          cudaStream_t s) {
+    // one pass over regions up to ~155k nodes (8 blocks of 128 per SM)
+    const long long cap = (p.N + 127) / 128;
+    const int blocks = (int)(cap < 1216 ? cap : 1216);
+    k_lbm_near<T><<<blocks, 128, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, box, vel);
+    return cudaGetLastError();
+}
+
+bool is_lbm_far_kernel(const void *fn) {
+    return fn == (const void *)k_lbm_far<float> || fn == (const void *)k_lbm_far<__half> ||
+           fn == (const void *)k_lbm_far<__nv_bfloat16>;
+}
+
+cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStream_t s) {
+    switch (p.fmt) {
+        case POP_F16: return lbm_t<__half>(fin, fout, p, s);
+        case POP_BF16: return lbm_t<__nv_bfloat16>(fin, fout, p, s);
+        default: return lbm_t<float>(fin, fout, p, s);
+    }
+}
+
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const int *box, cudaStream_t s) {
+    switch (p.fmt) {
+        case POP_F16: return far_t<__half>(fin, fout, p, box, s);
+        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, box, s);
+        default: return far_t<float>(fin, fout, p, box, s);
+    }
+}
+
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *box,
+                            float *vel, cudaStream_t s) {
+    switch (p.fmt) {
+        case POP_F16: return near_t<__half>(fin, fout, F, p, box, vel, s);
+        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, box, vel, s);
+        default: return near_t<float>(fin, fout, F, p, box, vel, s);
+    }
+}
+
+cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s) {
+    // rest equilibrium, rho = 1, u = 0: every deviation is zero (all-zero bits
+    // in every storage format)
+    return cudaMemsetAsync(f, 0, pop_bytes(p.fmt) * 19 * (size_t)p.N, s);
+}
+
+cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, double *rho, double *u,
                              cudaStream_t s) {
-    k_macro<<<(int)((p.N + 255) / 256), 256, 0, s>>>(f, F, p, rho, u);
+    const int blocks = (int)((p.N + 255) / 256);
+    switch (p.fmt) {
+        case POP_F16: k_macro<__half><<<blocks, 256, 0, s>>>(static_cast<const __half *>(f), F, p, rho, u); break;
+        case POP_BF16:
+            k_macro<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(f), F, p, rho, u);
+            break;
+        default: k_macro<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(f), F, p, rho, u);
+    }
     return cudaGetLastError();
 }
 

@@ -310,3 +310,28 @@ def test_unstable_run_reports_an_error_status(P):
     P.cf_set_positions(ctx, cid, x)
     P.cf_set_material(ctx, cid, 1e-3, 0.1, 0.5)
     P.cf_step(ctx, 3)
+
+
+# ---------------------------------------------------------------- diagnostics
+
+@pytest.mark.parametrize("stretch,angle", [((1.0, 1.0, 1.0), 0.0), ((1.3, 0.85, 1.0), 0.0),
+                                           ((1.4, 0.9, 1.0), 30.0), ((0.9, 1.2, 1.1), -55.0)])
+def test_device_taylor_matches_oracle(P, stretch, angle):
+    """cf_get_taylor (inertia tensor reduced on the device, Jacobi on one
+    thread) against the oracle's diagnostic on the same positions."""
+    from oracle import analysis
+
+    cell = configs.small_shear().cells[0]
+    c = cell.x_ref.mean(0)
+    phi = np.radians(angle)
+    Rz = np.array([[np.cos(phi), -np.sin(phi), 0], [np.sin(phi), np.cos(phi), 0], [0, 0, 1]])
+    y = c + (cell.x_ref - c) @ (Rz @ np.diag(stretch)).T
+    ctx = P.cf_create(0)
+    cid = P.cf_mesh_init(ctx, cell.x_ref, cell.tets, y)
+    got = P.cf_get_taylor(ctx, cid)
+    ref = analysis.taylor(P.cf_get_positions(ctx, cid), oracle.Mesh([cell]).tets)
+    assert abs(got["D"] - ref["D"]) <= 1e-6 * max(ref["D"], 1e-3)
+    assert abs(got["D_literal"] - ref["D_literal"]) <= 1e-6 * max(ref["D_literal"], 1e-3)
+    assert np.allclose([got["a1"], got["a2"], got["a3"]], ref["a"], rtol=1e-7)
+    if ref["D"] > 0.05:
+        assert abs(got["inclination"] - ref["inclination"]) <= 1e-4

@@ -1,0 +1,118 @@
+"""GPU: population storage formats and the two-node stream-collide kernels.
+
+* Row-edge shapes (nx = 2; a partial block; two blocks per row) in FP32 and
+  FP16.
+* FP16 / BF16 storage of the deviations f_q - w_q (power-of-two scaled,
+  collide in FP32) against the FP64 oracle: velocity fields and the Taylor
+  deformation of a sheared cell. The tolerances state the error of each
+  format as measured on GB300 (velocity after 600 steps of a forced Couette
+  start-up: FP16 3.6e-3, BF16 5.8e-2; D after 800 steps of a sheared cell:
+  FP32 3.2e-6, FP16 3.2e-5, BF16 8.6e-3). FP16 meets the 1e-3 relative bound
+  on D; BF16's 8-bit mantissa does not.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analysis
+from workloads.configs import Cell, Workload
+from workloads.mesh import sphere_tet_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2003_03130_gb300 import build
+
+    build.build()
+    import paper_2003_03130_gb300 as P
+
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def fluid_run(P, fmt, nx, ny, nz, tau, lo, hi, g, steps):
+    ctx = P.cf_create(0)
+    P.cf_set_population_format(ctx, fmt)
+    P.cf_lbm_init(ctx, nx, ny, nz, tau, lo, hi, g)
+    P.cf_step(ctx, steps)
+    return P.cf_get_velocity(ctx), P.cf_get_density(ctx)
+
+
+def oracle_fluid(nx, ny, nz, tau, lo, hi, g, steps):
+    fl = oracle.Fluid(nx, ny, nz, tau, lo, hi, g)
+    for _ in range(steps):
+        fl.step()
+    return fl
+
+
+@pytest.mark.parametrize("dims", [(2, 12, 3), (130, 10, 4), (256, 6, 2)])
+def test_row_edge_shapes(P, dims):
+    """FP32 at 1e-5 and FP16 at its storage error against the oracle."""
+    nx, ny, nz = dims
+    args = (0.9, -0.02, 0.03, (1e-5, 0.0, -3e-6), 150)
+    u32, rho32 = fluid_run(P, "f32", nx, ny, nz, *args)
+    fl = oracle_fluid(nx, ny, nz, *args)
+    assert rel(u32, fl.u) <= 1e-5
+    assert np.abs(rho32 - fl.rho).max() <= 1e-6
+    u16, _ = fluid_run(P, "f16", nx, ny, nz, *args)
+    assert rel(u16, fl.u) <= 5e-3
+
+
+@pytest.mark.parametrize("fmt,tol", [("f16", 5e-3), ("bf16", 8e-2)])
+def test_reduced_precision_fluid(P, fmt, tol):
+    args = (16, 24, 8, 0.8, -0.02, 0.02, (2e-6, 0.0, 0.0), 600)
+    u, rho = fluid_run(P, fmt, *args)
+    fl = oracle_fluid(*args)
+    err = rel(u, fl.u)
+    print(f"{fmt}: relative velocity error {err:.2e}")
+    assert err <= tol
+    assert abs((rho - 1.0).sum()) <= 1e-3 * rho.size ** 0.5
+
+
+def sheared_cell():
+    """R = 6 cell at the centre of a 32^3 box, walls -/+0.04 (shear rate
+    2.5e-3), Ca = 0.2 with w = 0.5, kappa = 20 mu."""
+    x, t = sphere_tet_mesh(6.0, 1.2)
+    x = x + 15.5
+    gamma = 2 * 0.04 / 32
+    mu = (0.5 / 3) * gamma / 0.2
+    return Workload("shear_32^3_R6", 32, 32, 32, 1.0, -0.04, 0.04,
+                    cells=[Cell(x, t, x.copy(), mu, 20 * mu, 0.5)])
+
+
+@pytest.fixture(scope="module")
+def sheared_oracle():
+    wl = sheared_cell()
+    sim = oracle.Coupled(wl)
+    sim.step(800)
+    return wl, sim.y.copy(), analysis.taylor(sim.y, sim.mesh.tets)["D"]
+
+
+@pytest.mark.parametrize("fmt,tol", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 2e-2)])
+def test_taylor_deformation_by_format(P, sheared_oracle, fmt, tol):
+    wl, y_ref, D_ref = sheared_oracle
+    ctx = P.cf_create(0)
+    P.cf_set_population_format(ctx, fmt)
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 800)
+    y = P.cf_get_positions(ctx, cid)
+    D = analysis.taylor(y, oracle.Mesh(wl.cells).tets)["D"]
+    x0 = wl.cells[0].x_ref
+    print(f"{fmt}: D {D:.6f} (oracle {D_ref:.6f}), rel err D {abs(D - D_ref) / D_ref:.2e}, "
+          f"displacement {rel(y - x0, y_ref - x0):.2e}")
+    assert D_ref > 0.02
+    assert abs(D - D_ref) <= tol * D_ref
+
+
+def test_format_is_validated(P):
+    from paper_2003_03130_gb300 import CellFSIError
+
+    ctx = P.cf_create(0)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_set_population_format(ctx, 7)
+    assert e.value.name == "CF_EINVAL"

@@ -96,6 +96,20 @@ def production_shear(ca: float = 0.2, w: float = 1.0, steps: int = 10000, n: int
     return Workload(f"shear_{n}^3_R16_Ca{ca}_w{w}", n, n, n, 1.0, -u_wall, u_wall, cells=[cell], steps=steps)
 
 
+def precision_channel(steps: int = 2000, nx: int = 256, ny: int = 128, nz: int = 128) -> Workload:
+    """Pressure-driven channel 256 x 128 x 128 (walls at rest, uniform body
+    force for a centre-line velocity of 0.02 at tau = 1: g = 8 nu u_max / ny^2),
+    one R = 16 cell a quarter of the width off the centre plane (in shear),
+    mu = 6.51e-4 (as the 128^3 shear workload at Ca = 0.2), kappa = 50 mu,
+    w = 0.5."""
+    tau = 1.0
+    g = 8.0 * lattice_viscosity(tau) * 0.02 / ny**2
+    mu = shear_modulus_for_ca(0.2, tau, 0.05, 128)
+    cell = sphere_cell(16.0, 1.72, ((nx - 1) / 2.0, ny / 4.0 + 8.0, (nz - 1) / 2.0), mu, 50.0 * mu, 0.5)
+    return Workload(f"channel_{nx}x{ny}x{nz}_R16", nx, ny, nz, tau, 0.0, 0.0, body_force=(g, 0.0, 0.0),
+                    cells=[cell], steps=steps)
+
+
 def random_displacements(cell: Cell, amplitude: float, seed: int) -> np.ndarray:
     """Positions of ``cell`` perturbed by ``amplitude * U(-1, 1)``."""
     return perturb(cell.x_ref, amplitude, seed)
