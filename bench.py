@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=128, help="cubic lattice extent")
+    ap.add_argument("--workload", choices=("shear", "suspension"), default="shear",
+                    help="shear: one R = 16 cell in a 128^3 Couette box; suspension: 400 cells in a "
+                         "512 x 256 x 256 channel")
     ap.add_argument("--ca", type=float, default=0.2)
     ap.add_argument("--w", type=float, default=0.5)
     ap.add_argument("--profile-steps", type=int, default=2000)
@@ -59,6 +62,8 @@ def parse():
 def workload(args):
     from workloads import configs
 
+    if args.workload == "suspension":
+        return configs.batched_channel()
     return configs.production_shear(ca=args.ca, w=args.w, n=args.n)
 
 
@@ -275,20 +280,20 @@ def run_ours(args):
 
         # end to end through the public API with host buffers: per step the
         # positions go host -> device (pinned), one step, positions back
-        nv = P.cf_cell_verts(ctx, ids[0])
+        nv = P.cf_cell_verts(ctx, P.CF_ALL_CELLS)
         y_in = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
         y_out = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
-        P.cf_get_positions(ctx, ids[0], out=y_in)
+        P.cf_get_positions(ctx, P.CF_ALL_CELLS, out=y_in)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            P.cf_set_positions(ctx, ids[0], y_in)
+            P.cf_set_positions(ctx, P.CF_ALL_CELLS, y_in)
             P.cf_step(ctx, 1)
-            P.cf_get_positions(ctx, ids[0], out=y_out)
+            P.cf_get_positions(ctx, P.CF_ALL_CELLS, out=y_out)
             y_in[...] = y_out
         e2e_s = time.perf_counter() - t0
         barrier()
-        y_now = P.cf_get_positions(ctx, ids[0])
+        y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
         P.cf_destroy(ctx)
 
     steps_per_s = world * K / (ms / 1e3)
@@ -301,7 +306,7 @@ def run_ours(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = traffic_record("k_lbm_far", wl.nx) if wl.nx == wl.ny == wl.nz else None
+    traffic = traffic_record("k_lbm_far", wl.nx) if args.workload == "shear" and wl.nx == wl.ny == wl.nz else None
     step_ms_profiled = float(sum(kms))
     out = {
         "metric": METRIC,
@@ -342,13 +347,13 @@ def run_ours(args):
             "unit": "steps/s",
             "h2d_bytes_per_step": int(nv * 3 * 8),
             "d2h_bytes_per_step": int(nv * 3 * 8),
-            "api": "cf_set_positions + cf_step(1) + cf_get_positions, pinned host buffers",
+            "api": "cf_set_positions + cf_step(1) + cf_get_positions (all cells), pinned host buffers",
         },
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and args.precision_steps > 0:
+    if rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear":
         out["precision"] = precision_block(P, torch, dev, args.precision_steps)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "shear":
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if world > 1:
         torch.distributed.destroy_process_group()

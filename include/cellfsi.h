@@ -97,10 +97,25 @@ cf_status cf_lbm_init(cf_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double ta
 cf_status cf_mesh_init(cf_ctx *ctx, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets,
                        const double *y0, int32_t *cell_id_out);
 
+/* Add ncells cells at once (one reallocation and one incidence-row build
+ * for all of them; for suspensions of hundreds of cells). nv[ncells],
+ * nt[ncells]: sizes; x_ref [sum nv][3], tets [sum nt][4] (indices local to
+ * each cell), y0 [sum nv][3] or NULL: the cells' arrays concatenated in
+ * order. cell_ids_out[ncells] receives the ids. Same per-cell set-up and
+ * errors as cf_mesh_init (the message names the cell); on error no cell is
+ * added. */
+cf_status cf_mesh_init_batch(cf_ctx *ctx, int32_t ncells, const int32_t *nv, const double *x_ref, const int32_t *nt,
+                             const int32_t *tets, const double *y0, int32_t *cell_ids_out);
+
 /* Mooney-Rivlin material of one cell (Sec. 2): shear modulus mu >= 0, bulk
  * modulus kappa >= 0 and ratio w in [0, 1], with mu_1 = w mu and
  * mu_2 = (1 - w) mu; w = 1 is neo-Hookean. */
 cf_status cf_set_material(cf_ctx *ctx, int32_t cell_id, double mu, double kappa, double w);
+
+/* Materials of several cells at once: ids[ncells], mu, kappa, w as in
+ * cf_set_material (all validated before any is applied). */
+cf_status cf_set_materials(cf_ctx *ctx, int32_t ncells, const int32_t *ids, const double *mu, const double *kappa,
+                           const double *w);
 
 /* Advance n >= 0 coupled time steps t -> t+1, each: elastic forces at y^t,
  * vertex sums, spread onto the lattice, one stream-collide with that force,
@@ -130,6 +145,11 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
 /* Elastic vertex forces at the current positions only (Sec. 3.1 per tet,
  * summed per vertex), without touching the fluid. */
 cf_status cf_compute_forces(cf_ctx *ctx);
+
+/* cell_id value that addresses every vertex of every cell, in cell order
+ * (cf_get_forces, cf_get_positions, cf_set_positions, cf_cell_verts,
+ * cf_cell_tets). */
+#define CF_ALL_CELLS (-1)
 
 /* Vertex forces [nv][3] of a cell from the last cf_compute_forces or cf_step
  * (the forces at y^t of the last step). */

@@ -49,6 +49,8 @@ def lib():
             "cf_lbm_init": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, _d], ctypes.c_int),
             "cf_mesh_init": ([vp, ctypes.c_int32, _d, ctypes.c_int32, _i, _d, _i], ctypes.c_int),
+            "cf_mesh_init_batch": ([vp, ctypes.c_int32, _i, _d, _i, _i, _d, _i], ctypes.c_int),
+            "cf_set_materials": ([vp, ctypes.c_int32, _i, _d, _d, _d], ctypes.c_int),
             "cf_set_material": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
             "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
@@ -149,6 +151,7 @@ def cf_last_error(ctx) -> str:
 
 
 CF_POP_F32, CF_POP_F16, CF_POP_BF16 = 0, 1, 2
+CF_ALL_CELLS = -1
 POP_FORMATS = {"f32": CF_POP_F32, "f16": CF_POP_F16, "bf16": CF_POP_BF16}
 
 
@@ -174,6 +177,28 @@ def cf_mesh_init(ctx, x_ref, tets, y0=None) -> int:
     cid = ctypes.c_int32(-1)
     _check(ctx, lib().cf_mesh_init(ctx.handle, len(x), _p(x), len(t), _p(t, _i), _p(y), ctypes.byref(cid)))
     return cid.value
+
+
+def cf_mesh_init_batch(ctx, cells_x_ref, cells_tets, cells_y0=None):
+    """Add several cells at once: lists of per-cell ``x_ref [nv,3]``,
+    ``tets [nt,4]`` (local indices) and optionally ``y0``. Returns the ids."""
+    xs = [_f64(x).reshape(-1, 3) for x in cells_x_ref]
+    ts = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1, 4) for t in cells_tets]
+    nv = np.array([len(x) for x in xs], np.int32)
+    nt = np.array([len(t) for t in ts], np.int32)
+    x = np.ascontiguousarray(np.concatenate(xs))
+    t = np.ascontiguousarray(np.concatenate(ts))
+    y = None if cells_y0 is None else np.ascontiguousarray(np.concatenate([_f64(v).reshape(-1, 3) for v in cells_y0]))
+    ids = np.zeros(len(xs), np.int32)
+    _check(ctx, lib().cf_mesh_init_batch(ctx.handle, len(xs), _p(nv, _i), _p(x), _p(nt, _i), _p(t, _i), _p(y),
+                                         _p(ids, _i)))
+    return ids.tolist()
+
+
+def cf_set_materials(ctx, ids, mu, kappa, w):
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    mu, kappa, w = _f64(mu), _f64(kappa), _f64(w)
+    _check(ctx, lib().cf_set_materials(ctx.handle, len(ids), _p(ids, _i), _p(mu), _p(kappa), _p(w)))
 
 
 def cf_set_material(ctx, cell_id, mu, kappa, w):
@@ -294,9 +319,8 @@ def load_workload(ctx, wl):
     """Set up a :class:`workloads.configs.Workload` on the device: fluid, then
     every cell with its material. Returns the cell ids."""
     cf_lbm_init(ctx, wl.nx, wl.ny, wl.nz, wl.tau, wl.u_wall_lo, wl.u_wall_hi, wl.body_force)
-    ids = []
-    for c in wl.cells:
-        cid = cf_mesh_init(ctx, c.x_ref, c.tets, c.y0)
-        cf_set_material(ctx, cid, c.mu, c.kappa, c.w)
-        ids.append(cid)
+    if not wl.cells:
+        return []
+    ids = cf_mesh_init_batch(ctx, [c.x_ref for c in wl.cells], [c.tets for c in wl.cells], [c.y0 for c in wl.cells])
+    cf_set_materials(ctx, ids, [c.mu for c in wl.cells], [c.kappa for c in wl.cells], [c.w for c in wl.cells])
     return ids

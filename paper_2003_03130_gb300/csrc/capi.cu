@@ -308,6 +308,22 @@ const CellInfo *cell_of(cf_ctx *c, int id) {
     return &c->cells[id];
 }
 
+// Vertex range of a cell, or of all cells for CF_ALL_CELLS.
+bool vertex_range(cf_ctx *c, int id, int *v0, int *nv) {
+    if (!c) return false;
+    if (id == CF_ALL_CELLS) {
+        if (c->V == 0) return false;
+        *v0 = 0;
+        *nv = c->V;
+        return true;
+    }
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci) return false;
+    *v0 = ci->v_off;
+    *nv = ci->nv;
+    return true;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -449,28 +465,39 @@ cf_status cf_set_population_format(cf_ctx *c, int32_t format) {
     return CF_OK;
 }
 
-cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets, const double *y0,
-                       int32_t *cell_id_out) {
+cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const double *x_ref, const int32_t *nt,
+                             const int32_t *tets, const double *y0, int32_t *cell_ids_out) {
     if (!c) return CF_EINVAL;
     DeviceGuard dg(c->device);
-    if (nv < 4 || nt < 1 || !x_ref || !tets) return fail(c, CF_EINVAL, "need nv >= 4, nt >= 1 and non-null arrays");
-    if ((long long)c->T + nt > INT_MAX / 4 || (long long)c->V + nv > INT_MAX / 4)
+    if (ncells < 1 || !nv || !nt || !x_ref || !tets) return fail(c, CF_EINVAL, "need ncells >= 1 and non-null arrays");
+    // per-cell offsets into the concatenated inputs, origins, validation
+    std::vector<long long> voff(ncells + 1, 0), toff(ncells + 1, 0);
+    std::vector<CellInfo> add(ncells);
+    for (int k = 0; k < ncells; ++k) {
+        if (nv[k] < 4 || nt[k] < 1) return fail(c, CF_EINVAL, "cell %d: need nv >= 4 and nt >= 1", k);
+        voff[k + 1] = voff[k] + nv[k];
+        toff[k + 1] = toff[k] + nt[k];
+    }
+    if (c->T + toff[ncells] > INT_MAX / 4 || c->V + voff[ncells] > INT_MAX / 4)
         return fail(c, CF_EINVAL, "mesh too large");
-    double mean[3] = {0, 0, 0};
-    for (int v = 0; v < nv; ++v)
-        for (int a = 0; a < 3; ++a) {
-            if (!std::isfinite(x_ref[3 * v + a]) || (y0 && !std::isfinite(y0[3 * v + a])))
-                return fail(c, CF_EINVAL, "non-finite coordinate at vertex %d", v);
-            mean[a] += x_ref[3 * v + a];
-        }
-    CellInfo ci;
-    ci.v_off = c->V;
-    ci.nv = nv;
-    ci.t_off = c->T;
-    ci.nt = nt;
-    for (int a = 0; a < 3; ++a) ci.origin[a] = (int)std::lround(mean[a] / nv);
-    ci.mat = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int V1 = c->V + nv, T1 = c->T + nt, cell = (int)c->cells.size();
+    for (int k = 0; k < ncells; ++k) {
+        double mean[3] = {0, 0, 0};
+        for (long long v = voff[k]; v < voff[k + 1]; ++v)
+            for (int a = 0; a < 3; ++a) {
+                if (!std::isfinite(x_ref[3 * v + a]) || (y0 && !std::isfinite(y0[3 * v + a])))
+                    return fail(c, CF_EINVAL, "cell %d: non-finite coordinate at vertex %lld", k, v - voff[k]);
+                mean[a] += x_ref[3 * v + a];
+            }
+        CellInfo &ci = add[k];
+        ci.v_off = c->V + (int)voff[k];
+        ci.nv = nv[k];
+        ci.t_off = c->T + (int)toff[k];
+        ci.nt = nt[k];
+        for (int a = 0; a < 3; ++a) ci.origin[a] = (int)std::lround(mean[a] / nv[k]);
+        ci.mat = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int Vadd = (int)voff[ncells], Tadd = (int)toff[ncells];
+    const int V1 = c->V + Vadd, T1 = c->T + Tadd, cell0 = (int)c->cells.size(), C1 = cell0 + ncells;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
 
     // new arrays; the old ones are freed only on success
@@ -480,8 +507,8 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     auto cleanup = [&]() {
         dfree(n.xr); dfree(n.u[0]); dfree(n.u[1]); dfree(n.fv); dfree(n.fc); dfree(n.xref64); dfree(n.tet);
         dfree(n.B); dfree(n.V0); dfree(n.tcell); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
-        dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(n.taylor_partial); dfree(x64); dfree(y64);
-        dfree(tin);
+        dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(n.taylor_partial);
+        dfree(x64); dfree(y64); dfree(tin);
     };
 #define TRY_N(expr)                                                                                    \
     do {                                                                                               \
@@ -502,17 +529,17 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     TRY_N(dalloc(&n.B, 9 * (size_t)T1));
     TRY_N(dalloc(&n.V0, T1));
     TRY_N(dalloc(&n.tcell, T1));
-    TRY_N(dalloc(&n.origin, 3 * (cell + 1)));
-    TRY_N(dalloc(&n.mat, cell + 1));
+    TRY_N(dalloc(&n.origin, 3 * (size_t)C1));
+    TRY_N(dalloc(&n.mat, C1));
     TRY_N(dalloc(&n.csr_ptr, V1 + 1));
     TRY_N(dalloc(&n.csr_idx, 4 * (size_t)T1));
     TRY_N(dalloc(&n.csr_cursor, V1));
     TRY_N(dalloc(&n.energy_partial, (T1 + 255) / 256 + 1));
     TRY_N(dalloc(&n.stage, 3 * (size_t)V1));
     TRY_N(dalloc(&n.taylor_partial, 10 * ((size_t)(T1 + 255) / 256 + 1)));
-    TRY_N(dalloc(&x64, 3 * (size_t)nv));
-    TRY_N(dalloc(&tin, 4 * (size_t)nt));
-    if (y0) TRY_N(dalloc(&y64, 3 * (size_t)nv));
+    TRY_N(dalloc(&x64, 3 * (size_t)Vadd));
+    TRY_N(dalloc(&tin, 4 * (size_t)Tadd));
+    if (y0) TRY_N(dalloc(&y64, 3 * (size_t)Vadd));
     cudaStream_t s = c->stream;
     if (c->V > 0) {
         TRY_N(cudaMemcpyAsync(n.xr, c->xr, sizeof(float4) * c->V, cudaMemcpyDeviceToDevice, s));
@@ -525,32 +552,42 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
         TRY_N(cudaMemcpyAsync(n.V0, c->V0, sizeof(float) * c->T, cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpyAsync(n.tcell, c->tcell, sizeof(int) * c->T, cudaMemcpyDeviceToDevice, s));
     }
-    std::vector<int> orig(3 * (cell + 1));
-    std::vector<float4> mats(cell + 1);
-    for (int i = 0; i < cell; ++i) {
+    std::vector<int> orig(3 * (size_t)C1);
+    std::vector<float4> mats(C1);
+    for (int i = 0; i < cell0; ++i) {
         for (int a = 0; a < 3; ++a) orig[3 * i + a] = c->cells[i].origin[a];
         mats[i] = c->cells[i].mat;
     }
-    for (int a = 0; a < 3; ++a) orig[3 * cell + a] = ci.origin[a];
-    mats[cell] = ci.mat;
+    for (int k = 0; k < ncells; ++k) {
+        for (int a = 0; a < 3; ++a) orig[3 * (cell0 + k) + a] = add[k].origin[a];
+        mats[cell0 + k] = add[k].mat;
+    }
     TRY_N(cudaMemcpyAsync(n.origin, orig.data(), sizeof(int) * orig.size(), cudaMemcpyHostToDevice, s));
     TRY_N(cudaMemcpyAsync(n.mat, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, s));
-    TRY_N(cudaMemcpyAsync(x64, x_ref, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s));
-    TRY_N(cudaMemcpyAsync(tin, tets, sizeof(int) * 4 * nt, cudaMemcpyHostToDevice, s));
-    if (y0) TRY_N(cudaMemcpyAsync(y64, y0, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s));
+    TRY_N(cudaMemcpyAsync(x64, x_ref, sizeof(double) * 3 * Vadd, cudaMemcpyHostToDevice, s));
+    TRY_N(cudaMemcpyAsync(tin, tets, sizeof(int) * 4 * (size_t)Tadd, cudaMemcpyHostToDevice, s));
+    if (y0) TRY_N(cudaMemcpyAsync(y64, y0, sizeof(double) * 3 * Vadd, cudaMemcpyHostToDevice, s));
     TRY_N(cudaMemsetAsync(c->d_status, 0xff, sizeof(unsigned long long), s));
-    TRY_N(launch_mesh_prepare(x64, nv, tin, nt, c->V, c->T, T1, cell, n.tet, n.B, n.V0, n.tcell, c->d_status, s));
+    for (int k = 0; k < ncells; ++k)
+        TRY_N(launch_mesh_prepare(x64 + 3 * voff[k], nv[k], tin + 4 * toff[k], nt[k], add[k].v_off, add[k].t_off,
+                                  (int)toff[k], T1, cell0 + k, n.tet, n.B, n.V0, n.tcell, c->d_status, s));
     unsigned long long st = 0;
     TRY_N(cudaMemcpyAsync(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
     TRY_N(cudaStreamSynchronize(s));
     if (st != ~0ULL) {
         cleanup();
-        const int code = (int)(st & 0xff), bad = (int)(st >> 8);
-        if (code == 3) return fail(c, CF_EDEGENERATE, "tet %d is degenerate (|det J| <= 1e-12 l^3)", bad);
-        return fail(c, CF_EINVAL, "tet %d: %s", bad, code == 1 ? "vertex index out of range" : "repeated vertex");
+        const int code = (int)(st & 0xff);
+        const long long bad = (long long)(st >> 8);  // tet index within the batch
+        int k = 0;
+        while (k + 1 < ncells && toff[k + 1] <= bad) ++k;
+        const int local = (int)(bad - toff[k]);
+        if (code == 3) return fail(c, CF_EDEGENERATE, "cell %d, tet %d is degenerate (|det J| <= 1e-12 l^3)", k, local);
+        return fail(c, CF_EINVAL, "cell %d, tet %d: %s", k, local,
+                    code == 1 ? "vertex index out of range" : "repeated vertex");
     }
-    TRY_N(launch_vertex_prepare(x64, y64, nv, c->V, cell, ci.origin, n.xr, n.u[0], n.u[1], n.xref64, s));
-    // both parities of the new cell start at y0
+    for (int k = 0; k < ncells; ++k)
+        TRY_N(launch_vertex_prepare(x64 + 3 * voff[k], y64 ? y64 + 3 * voff[k] : nullptr, nv[k], add[k].v_off,
+                                    cell0 + k, add[k].origin, n.xr, n.u[0], n.u[1], n.xref64, s));
     TRY_N(launch_csr_build(n.tet, T1, V1, n.csr_ptr, n.csr_idx, n.csr_cursor, s));
     TRY_N(cudaStreamSynchronize(s));
 #undef TRY_N
@@ -579,9 +616,39 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     cleanup();  // frees the old buffers now held by n
     c->V = V1;
     c->T = T1;
-    c->cells.push_back(ci);
-    if (cell_id_out) *cell_id_out = cell;
+    for (int k = 0; k < ncells; ++k) {
+        c->cells.push_back(add[k]);
+        if (cell_ids_out) cell_ids_out[k] = cell0 + k;
+    }
     return CF_OK;
+}
+
+cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets, const double *y0,
+                       int32_t *cell_id_out) {
+    return cf_mesh_init_batch(c, 1, &nv, x_ref, &nt, tets, y0, cell_id_out);
+}
+
+cf_status cf_set_materials(cf_ctx *c, int32_t ncells, const int32_t *ids, const double *mu, const double *kappa,
+                           const double *w) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (ncells < 0 || (ncells > 0 && (!ids || !mu || !kappa || !w))) return fail(c, CF_EINVAL, "null arrays");
+    for (int k = 0; k < ncells; ++k) {
+        if (ids[k] < 0 || ids[k] >= (int)c->cells.size()) return fail(c, CF_EINVAL, "unknown cell %d", ids[k]);
+        if (!(mu[k] >= 0.0 && kappa[k] >= 0.0 && w[k] >= 0.0 && w[k] <= 1.0 && std::isfinite(mu[k]) &&
+              std::isfinite(kappa[k])))
+            return fail(c, CF_EINVAL, "cell %d: need mu >= 0, kappa >= 0, 0 <= w <= 1", ids[k]);
+    }
+    std::vector<float4> mats(c->cells.size());
+    for (int k = 0; k < ncells; ++k) {
+        CellInfo &ci = c->cells[ids[k]];
+        ci.mat = make_float4((float)(w[k] * mu[k]), (float)((1.0 - w[k]) * mu[k]), (float)kappa[k], 0.f);
+    }
+    for (size_t i = 0; i < c->cells.size(); ++i) mats[i] = c->cells[i].mat;
+    if (!mats.empty())
+        CUDA_TRY(c, cudaMemcpyAsync(c->mat, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice,
+                                    c->stream));
+    return wait_stream(c);
 }
 
 cf_status cf_set_material(cf_ctx *c, int32_t id, double mu, double kappa, double w) {
@@ -757,31 +824,31 @@ cf_status cf_compute_forces(cf_ctx *c) {
 }
 
 cf_status cf_get_forces(cf_ctx *c, int32_t id, double *out) {
-    const CellInfo *ci = cell_of(c, id);
-    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    int v0, nv;
+    if (!vertex_range(c, id, &v0, &nv) || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
     DeviceGuard dg(c->device);
-    CUDA_TRY(c, launch_get_forces(c->fv, ci->v_off, ci->nv, c->stage, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, sizeof(double) * 3 * ci->nv, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, launch_get_forces(c->fv, v0, nv, c->stage, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, sizeof(double) * 3 * nv, cudaMemcpyDeviceToHost, c->stream));
     return wait_stream(c);
 }
 
 cf_status cf_get_positions(cf_ctx *c, int32_t id, double *out) {
-    const CellInfo *ci = cell_of(c, id);
-    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    int v0, nv;
+    if (!vertex_range(c, id, &v0, &nv) || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
     DeviceGuard dg(c->device);
-    CUDA_TRY(c, launch_get_positions(c->u[c->cur], c->xref64, ci->v_off, ci->nv, c->stage, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, sizeof(double) * 3 * ci->nv, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, launch_get_positions(c->u[c->cur], c->xref64, v0, nv, c->stage, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, sizeof(double) * 3 * nv, cudaMemcpyDeviceToHost, c->stream));
     return wait_stream(c);
 }
 
 cf_status cf_set_positions(cf_ctx *c, int32_t id, const double *y) {
-    const CellInfo *ci = cell_of(c, id);
-    if (!ci || !y) return fail(c, CF_EINVAL, "unknown cell or null input");
+    int v0, nv;
+    if (!vertex_range(c, id, &v0, &nv) || !y) return fail(c, CF_EINVAL, "unknown cell or null input");
     DeviceGuard dg(c->device);
-    for (int i = 0; i < 3 * ci->nv; ++i)
+    for (long long i = 0; i < 3LL * nv; ++i)
         if (!std::isfinite(y[i])) return fail(c, CF_EINVAL, "non-finite position");
-    CUDA_TRY(c, cudaMemcpyAsync(c->stage, y, sizeof(double) * 3 * ci->nv, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, launch_set_positions(c->stage, ci->v_off, ci->nv, c->xref64, c->u[c->cur], c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->stage, y, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_set_positions(c->stage, v0, nv, c->xref64, c->u[c->cur], c->stream));
     return wait_stream(c);
 }
 
@@ -887,10 +954,12 @@ cf_status cf_get_mesh(cf_ctx *c, int32_t id, int32_t *tets, double *B, double *V
 }
 
 int32_t cf_cell_verts(const cf_ctx *c, int32_t id) {
+    if (c && id == CF_ALL_CELLS) return c->V;
     return (c && id >= 0 && id < (int)c->cells.size()) ? c->cells[id].nv : 0;
 }
 
 int32_t cf_cell_tets(const cf_ctx *c, int32_t id) {
+    if (c && id == CF_ALL_CELLS) return c->T;
     return (c && id >= 0 && id < (int)c->cells.size()) ? c->cells[id].nt : 0;
 }
 

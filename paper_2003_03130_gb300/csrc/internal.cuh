@@ -152,10 +152,10 @@ __device__ __forceinline__ bool in_region(const NodeBox &b, int x, int y, int z,
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch status.
 // Once per cell (Sec. 3.2): validate, orient, B = J^-1 and V_0 in FP64;
-// *status receives min over failing tets of (t << 8 | code), code 1 = index
-// out of range, 2 = repeated vertex, 3 = degenerate.
+// *status receives min over failing tets of ((t_report + t) << 8 | code),
+// code 1 = index out of range, 2 = repeated vertex, 3 = degenerate.
 cudaError_t launch_mesh_prepare(const double *x64, int nv, const int *tets_in, int nt, int v_off, int t_off,
-                                int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
+                                int t_report, int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
                                 unsigned long long *status, cudaStream_t s);
 cudaError_t launch_vertex_prepare(const double *x64, const double *y64, int nv, int v_off, int cell,
                                   const int *origin_host3, float4 *xr, float4 *u0, float4 *u1, double *xref64,

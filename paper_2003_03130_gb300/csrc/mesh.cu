@@ -9,8 +9,8 @@ namespace cf {
 
 // One thread per tet of the new cell.
 __global__ void k_mesh_prepare(const double *__restrict__ x64, int nv, const int *__restrict__ tets_in, int nt,
-                               int v_off, int t_off, int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
-                               unsigned long long *status) {
+                               int v_off, int t_off, int t_report, int T, int cell, int4 *tet, float *B, float *V0,
+                               int *tcell, unsigned long long *status) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     int a[4];
@@ -25,7 +25,7 @@ __global__ void k_mesh_prepare(const double *__restrict__ x64, int nv, const int
             for (int e = c + 1; e < 4; ++e)
                 if (a[c] == a[e]) code = 2;
     if (code) {
-        atomicMin(status, ((unsigned long long)t << 8) | code);
+        atomicMin(status, ((unsigned long long)(t_report + t) << 8) | code);
         return;
     }
     double Jm[3][3];  // J_ik = x_i^k - x_i^4
@@ -46,7 +46,7 @@ __global__ void k_mesh_prepare(const double *__restrict__ x64, int nv, const int
         }
     const double lmax = sqrt(l2);
     if (fabs(det) <= 1e-12 * lmax * lmax * lmax) {
-        atomicMin(status, ((unsigned long long)t << 8) | 3u);
+        atomicMin(status, ((unsigned long long)(t_report + t) << 8) | 3u);
         return;
     }
     if (det < 0.0) {  // swap corners 1 and 2: positively oriented
@@ -79,11 +79,11 @@ __global__ void k_mesh_prepare(const double *__restrict__ x64, int nv, const int
     tcell[tg] = cell;
 }
 
-cudaError_t launch_mesh_prepare(const double *x64, int nv, const int *tets_in, int nt, int v_off, int t_off, int T,
-                                int cell, int4 *tet, float *B, float *V0, int *tcell, unsigned long long *status,
-                                cudaStream_t s) {
-    k_mesh_prepare<<<(nt + 127) / 128, 128, 0, s>>>(x64, nv, tets_in, nt, v_off, t_off, T, cell, tet, B, V0, tcell,
-                                                    status);
+cudaError_t launch_mesh_prepare(const double *x64, int nv, const int *tets_in, int nt, int v_off, int t_off,
+                                int t_report, int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
+                                unsigned long long *status, cudaStream_t s) {
+    k_mesh_prepare<<<(nt + 127) / 128, 128, 0, s>>>(x64, nv, tets_in, nt, v_off, t_off, t_report, T, cell, tet, B, V0,
+                                                    tcell, status);
     return cudaGetLastError();
 }
 

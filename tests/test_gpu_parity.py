@@ -335,3 +335,46 @@ def test_device_taylor_matches_oracle(P, stretch, angle):
     assert np.allclose([got["a1"], got["a2"], got["a3"]], ref["a"], rtol=1e-7)
     if ref["D"] > 0.05:
         assert abs(got["inclination"] - ref["inclination"]) <= 1e-4
+
+
+# ---------------------------------------------------------------- batches
+
+def test_batch_init_matches_single_inits_and_oracle(P):
+    """cf_mesh_init_batch gives the same device mesh as one cf_mesh_init per
+    cell, and a suspension set up by it steps like the oracle."""
+    wl = configs.batched_channel(ncells=10, nx=64, ny=48, nz=48, r_min=3.0, r_max=6.0, h=1.3, seed=7)
+    for c, s in zip(wl.cells, range(len(wl.cells))):
+        c.y0 = perturb(c.x_ref, 0.05, 100 + s)
+    ctx_b = P.cf_create(0)
+    ids = P.load_workload(ctx_b, wl)
+    ctx_s = P.cf_create(0)
+    for c in wl.cells:
+        cid = P.cf_mesh_init(ctx_s, c.x_ref, c.tets, c.y0)
+        P.cf_set_material(ctx_s, cid, c.mu, c.kappa, c.w)
+    for i in ids:
+        tb, Bb, Vb = P.cf_get_mesh(ctx_b, i)
+        ts, Bs, Vs = P.cf_get_mesh(ctx_s, i)
+        assert np.array_equal(tb, ts) and np.array_equal(Bb, Bs) and np.array_equal(Vb, Vs)
+        pb, ib = P.cf_get_csr(ctx_b, i)
+        ps, is_ = P.cf_get_csr(ctx_s, i)
+        assert np.array_equal(pb, ps) and np.array_equal(ib, is_)
+    P.cf_step(ctx_b, 30)
+    sim = oracle.Coupled(wl)
+    sim.step(30)
+    y0 = np.concatenate([c.y0 for c in wl.cells])
+    y = np.concatenate([P.cf_get_positions(ctx_b, i) for i in ids])
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(P.cf_get_velocity(ctx_b), sim.fluid.u) <= TOL
+
+
+def test_batch_init_names_the_failing_cell(P):
+    from paper_2003_03130_gb300 import CellFSIError
+
+    cells = [small_cell(seed=k, centre=(10.0 + 12 * k, 10.0, 10.0)) for k in range(4)]
+    tets = [c.tets.copy() for c in cells]
+    tets[2][5, 1] = tets[2][5, 0]  # repeated vertex in cell 2, tet 5
+    ctx = P.cf_create(0)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_mesh_init_batch(ctx, [c.x_ref for c in cells], tets)
+    assert e.value.name == "CF_EINVAL" and "cell 2, tet 5" in str(e.value)
+    assert P.cf_cell_verts(ctx, 0) == 0  # nothing was added

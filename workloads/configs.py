@@ -110,6 +110,56 @@ def precision_channel(steps: int = 2000, nx: int = 256, ny: int = 128, nz: int =
                     cells=[cell], steps=steps)
 
 
+def batched_channel(ncells: int = 400, nx: int = 512, ny: int = 256, nz: int = 256, r_min: float = 6.0,
+                    r_max: float = 20.0, seed: int = 400, steps: int = 100, h: float = 1.64) -> Workload:
+    """Suspension in a pressure-driven channel: ``ncells`` spheres with radii
+    drawn uniformly from [r_min, r_max] (rounded to 0.5 so meshes can be
+    shared), placed without overlap (gap >= 2 lattice units, periodic in x and
+    z, at least R + 2 from the walls) by seeded rejection sampling; per-cell
+    mu log-uniform in [2.6e-4, 1.3e-3] (Ca 0.1-0.5 at the 128^3 shear rate),
+    kappa = 50 mu, w uniform in [0, 1]; centre-line velocity 0.02 at tau = 1.
+    Meshes use spacing h (tets grow as R^3; ~6M tets in all for 400 cells)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    radii = np.round(rng.uniform(r_min, r_max, ncells) * 2.0) / 2.0
+    order = np.argsort(-radii, kind="stable")  # place large cells first
+    centres = np.zeros((ncells, 3))
+    placed = []
+    L = np.array([nx, ny, nz], np.float64)
+    for i in order:
+        R = radii[i]
+        for _ in range(200000):
+            c = np.array([rng.uniform(0, nx), rng.uniform(R + 2.0, ny - 3.0 - R), rng.uniform(0, nz)])
+            ok = True
+            for j in placed:
+                d = np.abs(c - centres[j])
+                d[[0, 2]] = np.minimum(d[[0, 2]], L[[0, 2]] - d[[0, 2]])
+                if np.sqrt((d * d).sum()) < R + radii[j] + 2.0:
+                    ok = False
+                    break
+            if ok:
+                break
+        else:
+            raise RuntimeError("could not place all cells")
+        centres[i] = c
+        placed.append(i)
+    mus = np.exp(rng.uniform(np.log(2.6e-4), np.log(1.3e-3), ncells))
+    ws = rng.uniform(0.0, 1.0, ncells)
+    cache = {}
+    cells = []
+    for i in range(ncells):
+        R = float(radii[i])
+        if R not in cache:
+            cache[R] = sphere_tet_mesh(R, h)
+        x, tets = cache[R]
+        xc = x + centres[i][None, :]
+        cells.append(Cell(x_ref=xc, tets=tets, y0=xc.copy(), mu=float(mus[i]), kappa=50.0 * float(mus[i]),
+                          w=float(ws[i])))
+    tau = 1.0
+    g = 8.0 * lattice_viscosity(tau) * 0.02 / ny**2
+    return Workload(f"suspension_{nx}x{ny}x{nz}_{ncells}cells", nx, ny, nz, tau, 0.0, 0.0, body_force=(g, 0.0, 0.0),
+                    cells=cells, steps=steps)
+
+
 def random_displacements(cell: Cell, amplitude: float, seed: int) -> np.ndarray:
     """Positions of ``cell`` perturbed by ``amplitude * U(-1, 1)``."""
     return perturb(cell.x_ref, amplitude, seed)
