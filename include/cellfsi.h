@@ -192,6 +192,60 @@ cf_status cf_get_csr(cf_ctx *ctx, int32_t cell_id, int32_t *ptr, int32_t *idx);
  * Any output pointer may be NULL. */
 cf_status cf_get_mesh(cf_ctx *ctx, int32_t cell_id, int32_t *tets, double *B, double *V0);
 
+/* ------------------------------------------------------------------------
+ * Compression between plates and the adjoint (fitting the moduli).
+ *
+ * The paper compresses a cell between a resting plate and a moving one, with
+ * a repulsive force keeping the vertices out of the plates (Sec. 4.2), and
+ * fits E and w to force-deformation curves (Sec. 4.3). Here: cells without
+ * fluid, a one-sided harmonic plate penalty f_z = k (z_lo - z)_+ -
+ * k (z - z_hi)_+ per vertex, quasi-static relaxation by damped steps
+ * y <- y + dt (f_el(y) + f_plate(y)), and the top plate's force
+ * F = sum_v k (z_v - z_hi)_+ per cell. The adjoint gives dL/d(mu, kappa, w)
+ * per cell for any loss L of the plate forces at the ends of recorded
+ * relaxation calls.
+ * ------------------------------------------------------------------------ */
+
+/* Plate stiffness k >= 0 and plate heights z_lo[c] < z_hi[c] per cell
+ * (absolute lattice coordinates). Takes effect for the following calls. */
+cf_status cf_plates_set(cf_ctx *ctx, double k_plate, const double *z_lo, const double *z_hi);
+
+/* n >= 1 damped steps of all cells with step dt > 0 (the fluid, if any, is
+ * not advanced). record != 0 appends the call to the context's tape, keeping
+ * device checkpoints of the positions every 50 steps and at the end (memory:
+ * 16 bytes per vertex per checkpoint). Errors: CF_ESTATE without cells or
+ * plates, CF_ENONFINITE if a position blows up (dt too large for the
+ * stiffness). */
+cf_status cf_relax(cf_ctx *ctx, int32_t n, double dt, int32_t record);
+
+/* Top-plate force per cell at the current positions, out[ncells]. */
+cf_status cf_plate_force(cf_ctx *ctx, double *out);
+
+/* Drop the tape and zero the adjoint state (dL/dy and the accumulated
+ * parameter gradients). */
+cf_status cf_tape_clear(cf_ctx *ctx);
+
+/* Reverse the most recent recorded cf_relax call not yet reversed: dF[ncells]
+ * is dL/dF for the plate forces at the end of that call. Adds the call's
+ * contribution to dL/d(mu, kappa, w) per cell (accumulated in double) and
+ * carries dL/dy back to its start (recomputing positions from the
+ * checkpoints). Reverse the calls last to first. CF_ESTATE if the tape is
+ * empty. */
+cf_status cf_relax_adjoint(cf_ctx *ctx, const double *dF);
+
+/* Accumulated dL/d(mu, kappa, w) per cell, out[ncells][3]. */
+cf_status cf_adjoint_gradients(cf_ctx *ctx, double *out);
+
+/* Directional derivative of the elastic vertex forces along v[V][3] at the
+ * current positions (all cells): out = J v, J = df/dy = -(Hessian of the
+ * elastic energy), so J is symmetric and this is also the vector-Jacobian
+ * product. */
+cf_status cf_force_jvp(cf_ctx *ctx, const double *v, double *out);
+
+/* lambda . df/d(mu, kappa, w) per cell for lambda[V][3] at the current
+ * positions, out[ncells][3] (double). */
+cf_status cf_force_param_vjp(cf_ctx *ctx, const double *lambda, double *out);
+
 /* Number of vertices / tets of a cell (0 if the id is unknown). */
 int32_t cf_cell_verts(const cf_ctx *ctx, int32_t cell_id);
 int32_t cf_cell_tets(const cf_ctx *ctx, int32_t cell_id);

@@ -1,0 +1,59 @@
+"""Compression between plates, FP64 (test infrastructure only).
+
+The paper compresses a cell between a resting plate and a moving one with a
+repulsive force that keeps vertices out of the plates (Sec. 4.2; the form of
+that force is given only in the supplement). Reading used here: a one-sided
+harmonic penalty per vertex, E_plate = k/2 [(z_lo - z)_+^2 + (z - z_hi)_+^2],
+so f_plate,z = k (z_lo - z)_+ - k (z - z_hi)_+, and quasi-static relaxation
+by damped (gradient-flow) steps y <- y + dt (f_el(y) + f_plate(y)). The
+measured force is the top plate's, F = sum_v k (z_v - z_hi)_+.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def plate_forces(y, k, z_lo, z_hi):
+    """Per-vertex plate force [V,3]; z_lo, z_hi per vertex."""
+    f = np.zeros_like(y)
+    z = y[:, 2]
+    f[:, 2] = k * np.maximum(z_lo - z, 0.0) - k * np.maximum(z - z_hi, 0.0)
+    return f
+
+
+def plate_energy(y, k, z_lo, z_hi):
+    z = y[:, 2]
+    return 0.5 * k * float((np.maximum(z_lo - z, 0.0) ** 2).sum() + (np.maximum(z - z_hi, 0.0) ** 2).sum())
+
+
+def top_force(y, k, z_hi, ranges):
+    """F per cell: sum over its vertices of k (z - z_hi)_+."""
+    pen = k * np.maximum(y[:, 2] - z_hi, 0.0)
+    return np.array([pen[a:b].sum() for a, b in ranges])
+
+
+def per_vertex(values, ranges):
+    out = np.zeros(ranges[-1][1])
+    for (a, b), v in zip(ranges, values):
+        out[a:b] = v
+    return out
+
+
+def relax(mesh, y, n, dt, k, z_lo, z_hi):
+    """n damped steps of all cells; z_lo, z_hi per cell."""
+    zl = per_vertex(z_lo, mesh.vert_ranges)
+    zh = per_vertex(z_hi, mesh.vert_ranges)
+    for _ in range(n):
+        y = y + dt * (mesh.forces(y) + plate_forces(y, k, zl, zh))
+    return y
+
+
+def protocol(mesh, y0, z_lo, radius, strains, steps, dt, k):
+    """Top-plate force per cell at the end of each strain level [ncells, nlevels]."""
+    y = np.array(y0, dtype=np.float64)
+    out = []
+    for s in strains:
+        z_hi = np.asarray(z_lo) + 2.0 * np.asarray(radius) * (1.0 - s)
+        y = relax(mesh, y, steps, dt, k, z_lo, z_hi)
+        out.append(top_force(y, k, per_vertex(z_hi, mesh.vert_ranges), mesh.vert_ranges))
+    return np.stack(out, axis=1), y

@@ -69,6 +69,14 @@ def lib():
             "cf_cell_verts": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_cell_tets": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_last_error": ([vp], ctypes.c_char_p),
+            "cf_plates_set": ([vp, ctypes.c_double, _d, _d], ctypes.c_int),
+            "cf_relax": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
+            "cf_plate_force": ([vp, _d], ctypes.c_int),
+            "cf_tape_clear": ([vp], ctypes.c_int),
+            "cf_relax_adjoint": ([vp, _d], ctypes.c_int),
+            "cf_adjoint_gradients": ([vp, _d], ctypes.c_int),
+            "cf_force_jvp": ([vp, _d, _d], ctypes.c_int),
+            "cf_force_param_vjp": ([vp, _d, _d], ctypes.c_int),
             "cf_vertex_forces_static": ([ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         }
@@ -313,6 +321,57 @@ def cf_vertex_forces_static(nv, nt, tets, B, V0, u, csr_ptr, csr_idx, mu, kappa,
     st = lib().cf_vertex_forces_static(nv, nt, tets, B, V0, u, csr_ptr, csr_idx, mu, kappa, w, f, stream or None)
     if st != 0:
         raise CellFSIError(st, "cf_vertex_forces_static failed")
+
+
+def _ncells(ctx):
+    n = 0
+    while cf_cell_verts(ctx, n) > 0:
+        n += 1
+    return n
+
+
+def cf_plates_set(ctx, k_plate, z_lo, z_hi):
+    zlo, zhi = _f64(z_lo).reshape(-1), _f64(z_hi).reshape(-1)
+    _check(ctx, lib().cf_plates_set(ctx.handle, k_plate, _p(zlo), _p(zhi)))
+
+
+def cf_relax(ctx, n, dt, record=False):
+    _check(ctx, lib().cf_relax(ctx.handle, n, dt, 1 if record else 0))
+
+
+def cf_plate_force(ctx):
+    out = np.zeros(_ncells(ctx))
+    _check(ctx, lib().cf_plate_force(ctx.handle, _p(out)))
+    return out
+
+
+def cf_tape_clear(ctx):
+    _check(ctx, lib().cf_tape_clear(ctx.handle))
+
+
+def cf_relax_adjoint(ctx, dF):
+    dF = _f64(dF).reshape(-1)
+    _check(ctx, lib().cf_relax_adjoint(ctx.handle, _p(dF)))
+
+
+def cf_adjoint_gradients(ctx):
+    out = np.zeros((_ncells(ctx), 3))
+    _check(ctx, lib().cf_adjoint_gradients(ctx.handle, _p(out)))
+    return out
+
+
+def cf_force_jvp(ctx, v):
+    v = _f64(v).reshape(-1, 3)
+    out = np.zeros_like(v)
+    _check(ctx, lib().cf_force_jvp(ctx.handle, _p(v), _p(out)))
+    return out
+
+
+def cf_force_param_vjp(ctx, lam):
+    lam = _f64(lam).reshape(-1, 3)
+    out = np.zeros((_ncells(ctx), 3))
+    _check(ctx, lib().cf_force_param_vjp(ctx.handle, _p(lam), _p(out)))
+    return out
 
 
 def load_workload(ctx, wl):

@@ -1,0 +1,60 @@
+"""Differentiable compression experiment (PyTorch autograd over the C ABI).
+
+``CompressionCurve.apply(mu, kappa, w, run)`` returns the top-plate force of
+every cell at the end of each strain level of a quasi-static compression
+protocol (``run``: a :class:`Compression`), as a ``[ncells, nlevels]``
+tensor; its backward pass reverses the recorded relaxation calls with
+``cf_relax_adjoint`` (hand-written adjoint in the CUDA library, positions
+recomputed from checkpoints) and returns dL/d(mu, kappa, w) per cell. All
+numerics run in the library; this module only orders the calls.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (CF_ALL_CELLS, cf_adjoint_gradients, cf_plate_force, cf_plates_set, cf_relax, cf_relax_adjoint,
+               cf_set_materials, cf_set_positions, cf_tape_clear)
+
+
+class Compression:
+    """Protocol: cells start at y0 on the lower plate z_lo; for each strain
+    s in ``strains`` the upper plate sits at z_lo + 2 R (1 - s) and the
+    cells relax for ``steps`` damped steps of size ``dt``."""
+
+    def __init__(self, ctx, ids, y0, z_lo, radius, strains, steps, dt, k_plate):
+        self.ctx, self.ids = ctx, list(ids)
+        self.y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        self.z_lo = np.asarray(z_lo, np.float64)
+        self.radius = np.asarray(radius, np.float64)
+        self.strains = list(strains)
+        self.steps, self.dt, self.k_plate = steps, dt, k_plate
+
+    def run(self, mu, kappa, w, record):
+        c = self.ctx
+        cf_set_materials(c, self.ids, mu, kappa, w)
+        cf_set_positions(c, CF_ALL_CELLS, self.y0)
+        cf_tape_clear(c)
+        forces = []
+        for s in self.strains:
+            cf_plates_set(c, self.k_plate, self.z_lo, self.z_lo + 2.0 * self.radius * (1.0 - s))
+            cf_relax(c, self.steps, self.dt, record=record)
+            forces.append(cf_plate_force(c))
+        return np.stack(forces, axis=1)
+
+
+class CompressionCurve(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, mu, kappa, w, run: Compression):
+        F = run.run(mu.detach().cpu().numpy(), kappa.detach().cpu().numpy(), w.detach().cpu().numpy(), record=True)
+        fctx.run = run
+        return torch.as_tensor(F, dtype=torch.float64)
+
+    @staticmethod
+    def backward(fctx, dF):
+        run = fctx.run
+        dF = dF.detach().cpu().numpy()
+        for level in reversed(range(len(run.strains))):  # each level is one recorded cf_relax call
+            cf_relax_adjoint(run.ctx, np.ascontiguousarray(dF[:, level]))
+        g = torch.as_tensor(cf_adjoint_gradients(run.ctx), dtype=torch.float64)
+        return g[:, 0], g[:, 1], g[:, 2], None

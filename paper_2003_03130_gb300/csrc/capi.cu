@@ -33,143 +33,11 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/cellfsi.h"
-#include "internal.cuh"
+#include "ctx.h"
 
 using namespace cf;
 
 namespace {
-
-struct CellInfo {
-    int v_off, nv, t_off, nt;
-    int origin[3];
-    float4 mat;
-};
-
-}  // namespace
-
-struct cf_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::string err;
-    double timeout_s = 600.0;
-
-    unsigned *d_err = nullptr;
-    unsigned long long *d_status = nullptr;
-
-    // fluid
-    bool lbm_ready = false;
-    LbmParams lp{};
-    int pop_format = POP_F32;  // storage of the populations (next cf_lbm_init)
-    void *f[2] = {nullptr, nullptr};
-    float *F = nullptr;
-    float *vel = nullptr;  // u(t) on the force region, [3][N]
-
-    // cells
-    int V = 0, T = 0;
-    std::vector<CellInfo> cells;
-    float4 *xr = nullptr, *u[2] = {nullptr, nullptr}, *fv = nullptr, *fc = nullptr;
-    double *xref64 = nullptr;
-    int4 *tet = nullptr;
-    float *B = nullptr, *V0 = nullptr;
-    int *tcell = nullptr, *origin = nullptr;
-    float4 *mat = nullptr;
-    int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
-    double *energy_partial = nullptr, *energy_out = nullptr;
-    double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
-    double *taylor_partial = nullptr, *taylor_out = nullptr;
-
-    int *box = nullptr;  // three force-region slots of 8 ints (see NodeBox)
-
-    int cur = 0;          // buffer parity of the next step
-    long long tstep = 0;  // steps taken; tstep % 3 picks the region slots
-    std::map<int, cudaGraphExec_t> graphs;
-};
-
-namespace {
-
-cf_status fail(cf_ctx *c, cf_status s, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    if (c) c->err = buf;
-    return s;
-}
-
-#define CUDA_TRY(c, expr)                                                                              \
-    do {                                                                                               \
-        cudaError_t e_ = (expr);                                                                       \
-        if (e_ != cudaSuccess)                                                                         \
-            return fail((c), e_ == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA, "%s: %s (%s:%d)", \
-                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
-    } while (0)
-
-template <class T>
-cudaError_t dalloc(T **p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    return cudaMalloc((void **)p, sizeof(T) * count);
-}
-
-template <class T>
-void dfree(T *&p) {
-    if (p) cudaFree(p);
-    p = nullptr;
-}
-
-void drop_graphs(cf_ctx *c) {
-    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
-}
-
-MeshView view(const cf_ctx *c) {
-    MeshView m;
-    m.V = c->V;
-    m.T = c->T;
-    m.xr = c->xr;
-    m.origin = c->origin;
-    m.tet = c->tet;
-    m.B = c->B;
-    m.V0 = c->V0;
-    m.tcell = c->tcell;
-    m.mat = c->mat;
-    m.csr_ptr = c->csr_ptr;
-    m.csr_idx = c->csr_idx;
-    m.fc = c->fc;
-    m.fv = c->fv;
-    return m;
-}
-
-// Wait for the stream by polling, giving up after the context's timeout.
-cf_status wait_stream(cf_ctx *c) {
-    auto t0 = std::chrono::steady_clock::now();
-    int spins = 0;
-    for (;;) {
-        cudaError_t e = cudaStreamQuery(c->stream);
-        if (e == cudaSuccess) return CF_OK;
-        if (e != cudaErrorNotReady) return fail(c, CF_ECUDA, "device work failed: %s", cudaGetErrorString(e));
-        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (dt > c->timeout_s) return fail(c, CF_ETIMEOUT, "device work did not finish within %.0f s", c->timeout_s);
-        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
-}
-
-// Read and clear the device error word.
-cf_status consume_errors(cf_ctx *c) {
-    unsigned h = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
-    cf_status s = wait_stream(c);
-    if (s != CF_OK) return s;
-    if (h & ERR_INVERTED) return fail(c, CF_EINVERTED, "a tet reached det F <= 0");
-    if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
-    if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
-    if (h & ERR_MOVED) return fail(c, CF_EUNSTABLE, "a vertex moved a lattice spacing or more in one step");
-    return CF_OK;
-}
 
 // Steps per graph in the steady part of cf_step: even (buffer parity) and a
 // multiple of 3 (region slots), so a graph starts and ends in the same phase.
@@ -303,40 +171,6 @@ cf_status launch_steps(cf_ctx *c, Kind kind, int nsteps) {
     return CF_OK;
 }
 
-const CellInfo *cell_of(cf_ctx *c, int id) {
-    if (!c || id < 0 || id >= (int)c->cells.size()) return nullptr;
-    return &c->cells[id];
-}
-
-// Vertex range of a cell, or of all cells for CF_ALL_CELLS.
-bool vertex_range(cf_ctx *c, int id, int *v0, int *nv) {
-    if (!c) return false;
-    if (id == CF_ALL_CELLS) {
-        if (c->V == 0) return false;
-        *v0 = 0;
-        *nv = c->V;
-        return true;
-    }
-    const CellInfo *ci = cell_of(c, id);
-    if (!ci) return false;
-    *v0 = ci->v_off;
-    *nv = ci->nv;
-    return true;
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int now;
-        cudaGetDevice(&now);
-        if (prev >= 0 && now != prev) cudaSetDevice(prev);
-    }
-};
-
 }  // namespace
 
 extern "C" {
@@ -401,6 +235,7 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->stage);
     dfree(c->taylor_partial);
     dfree(c->taylor_out);
+    cf_free_adjoint(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -642,7 +477,7 @@ cf_status cf_set_materials(cf_ctx *c, int32_t ncells, const int32_t *ids, const 
     std::vector<float4> mats(c->cells.size());
     for (int k = 0; k < ncells; ++k) {
         CellInfo &ci = c->cells[ids[k]];
-        ci.mat = make_float4((float)(w[k] * mu[k]), (float)((1.0 - w[k]) * mu[k]), (float)kappa[k], 0.f);
+        ci.mat = make_float4((float)(w[k] * mu[k]), (float)((1.0 - w[k]) * mu[k]), (float)kappa[k], (float)w[k]);
     }
     for (size_t i = 0; i < c->cells.size(); ++i) mats[i] = c->cells[i].mat;
     if (!mats.empty())
@@ -658,7 +493,7 @@ cf_status cf_set_material(cf_ctx *c, int32_t id, double mu, double kappa, double
     if (!(mu >= 0.0 && kappa >= 0.0 && w >= 0.0 && w <= 1.0 && std::isfinite(mu) && std::isfinite(kappa)))
         return fail(c, CF_EINVAL, "need mu >= 0, kappa >= 0, 0 <= w <= 1");
     CellInfo &ci = c->cells[id];
-    ci.mat = make_float4((float)(w * mu), (float)((1.0 - w) * mu), (float)kappa, 0.f);
+    ci.mat = make_float4((float)(w * mu), (float)((1.0 - w) * mu), (float)kappa, (float)w);
     CUDA_TRY(c, cudaMemcpyAsync(c->mat + id, &ci.mat, sizeof(float4), cudaMemcpyHostToDevice, c->stream));
     return wait_stream(c);
 }

@@ -1,0 +1,212 @@
+// Private to the library: the context behind the C ABI's opaque cf_ctx and
+// the helpers shared by the translation units that implement the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/cellfsi.h"
+#include "internal.cuh"
+
+namespace cf {
+
+struct CellInfo {
+    int v_off, nv, t_off, nt;
+    int origin[3];
+    float4 mat;
+};
+
+}  // namespace cf
+
+using namespace cf;
+
+struct cf_ctx;
+// Frees the compression/adjoint buffers and the tape (csrc/plates.cu).
+void cf_free_adjoint(cf_ctx *c);
+
+struct cf_ctx {
+    using CellInfo = cf::CellInfo;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    double timeout_s = 600.0;
+
+    unsigned *d_err = nullptr;
+    unsigned long long *d_status = nullptr;
+
+    // fluid
+    bool lbm_ready = false;
+    LbmParams lp{};
+    int pop_format = POP_F32;  // storage of the populations (next cf_lbm_init)
+    void *f[2] = {nullptr, nullptr};
+    float *F = nullptr;
+    float *vel = nullptr;  // u(t) on the force region, [3][N]
+
+    // cells
+    int V = 0, T = 0;
+    std::vector<CellInfo> cells;
+    float4 *xr = nullptr, *u[2] = {nullptr, nullptr}, *fv = nullptr, *fc = nullptr;
+    double *xref64 = nullptr;
+    int4 *tet = nullptr;
+    float *B = nullptr, *V0 = nullptr;
+    int *tcell = nullptr, *origin = nullptr;
+    float4 *mat = nullptr;
+    int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
+    double *energy_partial = nullptr, *energy_out = nullptr;
+    double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
+    double *taylor_partial = nullptr, *taylor_out = nullptr;
+
+    int *box = nullptr;  // three force-region slots of 8 ints (see NodeBox)
+
+    // compression between plates and its adjoint (csrc/plates.cu)
+    struct TapeEntry {
+        int n;
+        float dt, kp;
+        std::vector<float> zlo, zhi;
+        int ck0, nck;  // checkpoints ck0 .. ck0 + nck - 1: steps 0, S, 2S, ..., and the end state
+    };
+    float k_plate = 0.f;
+    std::vector<float> zlo_h, zhi_h;   // current plates per cell
+    float *zlo = nullptr, *zhi = nullptr;
+    std::vector<TapeEntry> tape;
+    std::vector<float4 *> ckpt;        // device checkpoints of V vertices each
+    int ck_used = 0;
+    float4 *lam = nullptr, *jv = nullptr, *vtmp = nullptr, *seg = nullptr;
+    double *grad = nullptr, *gtmp = nullptr, *pforce = nullptr, *dF = nullptr;
+    int adj_V = 0, adj_C = 0;
+
+    int cur = 0;          // buffer parity of the next step
+    long long tstep = 0;  // steps taken; tstep % 3 picks the region slots
+    std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+cf_status fail(cf_ctx *c, cf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CUDA_TRY(c, expr)                                                                              \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void drop_graphs(cf_ctx *c) {
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+MeshView view(const cf_ctx *c) {
+    MeshView m;
+    m.V = c->V;
+    m.T = c->T;
+    m.xr = c->xr;
+    m.origin = c->origin;
+    m.tet = c->tet;
+    m.B = c->B;
+    m.V0 = c->V0;
+    m.tcell = c->tcell;
+    m.mat = c->mat;
+    m.csr_ptr = c->csr_ptr;
+    m.csr_idx = c->csr_idx;
+    m.fc = c->fc;
+    m.fv = c->fv;
+    return m;
+}
+
+// Wait for the stream by polling, giving up after the context's timeout.
+cf_status wait_stream(cf_ctx *c) {
+    auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) return CF_OK;
+        if (e != cudaErrorNotReady) return fail(c, CF_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > c->timeout_s) return fail(c, CF_ETIMEOUT, "device work did not finish within %.0f s", c->timeout_s);
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// Read and clear the device error word.
+cf_status consume_errors(cf_ctx *c) {
+    unsigned h = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+    cf_status s = wait_stream(c);
+    if (s != CF_OK) return s;
+    if (h & ERR_INVERTED) return fail(c, CF_EINVERTED, "a tet reached det F <= 0");
+    if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
+    if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
+    if (h & ERR_MOVED) return fail(c, CF_EUNSTABLE, "a vertex moved a lattice spacing or more in one step");
+    return CF_OK;
+}
+
+const CellInfo *cell_of(cf_ctx *c, int id) {
+    if (!c || id < 0 || id >= (int)c->cells.size()) return nullptr;
+    return &c->cells[id];
+}
+
+// Vertex range of a cell, or of all cells for CF_ALL_CELLS.
+bool vertex_range(cf_ctx *c, int id, int *v0, int *nv) {
+    if (!c) return false;
+    if (id == CF_ALL_CELLS) {
+        if (c->V == 0) return false;
+        *v0 = 0;
+        *nv = c->V;
+        return true;
+    }
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci) return false;
+    *v0 = ci->v_off;
+    *nv = ci->nv;
+    return true;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace

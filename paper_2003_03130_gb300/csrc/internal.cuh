@@ -73,7 +73,7 @@ struct MeshView {
     const float *B;        // [9][T]: B[(3k + j) * T + t] = (J^-1)_kj
     const float *V0;       // [T]
     const int *tcell;      // [T]
-    const float4 *mat;     // [ncells]: mu1, mu2, kappa, 0
+    const float4 *mat;     // [ncells]: mu1, mu2, kappa, w
     const int *csr_ptr;    // [V+1]
     const int *csr_idx;    // [4T]: entries 4 t + c, ascending per row
     float4 *fc;            // [4][T]: corner force fc[c * T + t]
@@ -207,6 +207,23 @@ size_t pop_bytes(int fmt);
 // x + u_cur; u_next = u_cur + velocity.
 cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s);
+// Compression between plates and the adjoint (csrc/adjoint.cu).
+// out = J_el v at displacements u (vertex sums of the corner tangents; uses m.fc).
+cudaError_t launch_force_jvp(const MeshView &m, const float4 *u, const float4 *v, float4 *out, unsigned *err,
+                             cudaStream_t s);
+// grad[3 c + (0, 1, 2)] += scale * lambda . df/d(mu, kappa, w) per cell (double).
+cudaError_t launch_param_vjp(const MeshView &m, const float4 *u, const float4 *lam, double scale, double *grad,
+                             cudaStream_t s);
+cudaError_t launch_plate_step(const MeshView &m, const float4 *u_in, const float4 *fel, float4 *u_out, float dt,
+                              float kp, const float *zlo, const float *zhi, unsigned *err, cudaStream_t s);
+cudaError_t launch_plate_force(const MeshView &m, const float4 *u, float kp, const float *zlo, const float *zhi,
+                               double *out, cudaStream_t s);
+cudaError_t launch_adj_seed(const MeshView &m, const float4 *u, float kp, const float *zlo, const float *zhi,
+                            const double *dF, float4 *lam, cudaStream_t s);
+cudaError_t launch_adj_step(const MeshView &m, const float4 *u, const float4 *jv, float4 *lam, float dt, float kp,
+                            const float *zlo, const float *zhi, cudaStream_t s);
+cudaError_t launch_pack3(const double *in, int n, float4 *out, cudaStream_t s);
+
 cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s);
 cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, double *rho, double *u,
                              cudaStream_t s);
