@@ -210,19 +210,22 @@ cf_status cf_get_mesh(cf_ctx *ctx, int32_t cell_id, int32_t *tets, double *B, do
  * (absolute lattice coordinates). Takes effect for the following calls. */
 cf_status cf_plates_set(cf_ctx *ctx, double k_plate, const double *z_lo, const double *z_hi);
 
-/* n >= 1 damped steps of all cells with step dt > 0 (the fluid, if any, is
- * not advanced). record != 0 appends the call to the context's tape, keeping
- * device checkpoints of the positions every 50 steps and at the end (memory:
- * 16 bytes per vertex per checkpoint). Errors: CF_ESTATE without cells or
+/* n >= 1 damped relaxation steps of all cells (unit-mass vertices; the fluid,
+ * if any, is not advanced): v <- damping v + dt (f_el + f_plate),
+ * y <- y + dt v, with 0 <= damping < 1 (damping = 0: first-order gradient
+ * flow y <- y + dt^2 f). Velocities start at zero after cf_tape_clear.
+ * record != 0 appends the call to the context's tape, keeping device
+ * checkpoints of positions and velocities every 50 steps and at the end
+ * (32 bytes per vertex per checkpoint). Errors: CF_ESTATE without cells or
  * plates, CF_ENONFINITE if a position blows up (dt too large for the
- * stiffness). */
-cf_status cf_relax(cf_ctx *ctx, int32_t n, double dt, int32_t record);
+ * stiffness), CF_EINVERTED if a tet inverts. */
+cf_status cf_relax(cf_ctx *ctx, int32_t n, double dt, double damping, int32_t record);
 
 /* Top-plate force per cell at the current positions, out[ncells]. */
 cf_status cf_plate_force(cf_ctx *ctx, double *out);
 
-/* Drop the tape and zero the adjoint state (dL/dy and the accumulated
- * parameter gradients). */
+/* Drop the tape, zero the relaxation velocities and the adjoint state
+ * (dL/dy, dL/dv and the accumulated parameter gradients). */
 cf_status cf_tape_clear(cf_ctx *ctx);
 
 /* Reverse the most recent recorded cf_relax call not yet reversed: dF[ncells]

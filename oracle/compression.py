@@ -39,21 +39,45 @@ def per_vertex(values, ranges):
     return out
 
 
-def relax(mesh, y, n, dt, k, z_lo, z_hi):
-    """n damped steps of all cells; z_lo, z_hi per cell."""
+def relax(mesh, y, n, dt, k, z_lo, z_hi, v=None, c=0.0):
+    """n damped steps of unit-mass vertices, v <- c v + dt f, y <- y + dt v
+    (c = 0: gradient flow with step dt^2); z_lo, z_hi per cell. Returns
+    (y, v)."""
     zl = per_vertex(z_lo, mesh.vert_ranges)
     zh = per_vertex(z_hi, mesh.vert_ranges)
+    v = np.zeros_like(y) if v is None else v
     for _ in range(n):
-        y = y + dt * (mesh.forces(y) + plate_forces(y, k, zl, zh))
-    return y
+        v = c * v + dt * (mesh.forces(y) + plate_forces(y, k, zl, zh))
+        y = y + dt * v
+    return y, v
 
 
-def protocol(mesh, y0, z_lo, radius, strains, steps, dt, k):
+def plate_schedule(z_lo, radius, strains, steps, ramp):
+    """Per strain level: the top plate moves from its previous height to
+    z_lo + 2 R (1 - s) in ``ramp`` equal moves of ``steps // (2 ramp)`` steps
+    each (a quasi-static approach), then holds for the remaining steps. Yields
+    (z_hi per cell, number of steps, measured) with measured True at the end
+    of a level; ramp = 0 jumps to the new height."""
+    z_lo, radius = np.asarray(z_lo, np.float64), np.asarray(radius, np.float64)
+    prev = z_lo + 2.0 * radius
+    for s in strains:
+        new = z_lo + 2.0 * radius * (1.0 - s)
+        n_move = steps // (2 * ramp) if ramp > 0 else 0
+        for r in range(1, ramp + 1):
+            yield prev + (new - prev) * (r / ramp), n_move, False
+        yield new, steps - ramp * n_move, True
+        prev = new
+
+
+def protocol(mesh, y0, z_lo, radius, strains, steps, dt, k, ramp=0, c=0.0):
     """Top-plate force per cell at the end of each strain level [ncells, nlevels]."""
     y = np.array(y0, dtype=np.float64)
+    v = np.zeros_like(y)
     out = []
-    for s in strains:
-        z_hi = np.asarray(z_lo) + 2.0 * np.asarray(radius) * (1.0 - s)
-        y = relax(mesh, y, steps, dt, k, z_lo, z_hi)
-        out.append(top_force(y, k, per_vertex(z_hi, mesh.vert_ranges), mesh.vert_ranges))
+    for z_hi, n, measured in plate_schedule(z_lo, radius, strains, steps, ramp):
+        if n == 0:
+            continue
+        y, v = relax(mesh, y, n, dt, k, z_lo, z_hi, v, c)
+        if measured:
+            out.append(top_force(y, k, per_vertex(z_hi, mesh.vert_ranges), mesh.vert_ranges))
     return np.stack(out, axis=1), y

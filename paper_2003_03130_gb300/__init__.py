@@ -70,7 +70,7 @@ def lib():
             "cf_cell_tets": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_last_error": ([vp], ctypes.c_char_p),
             "cf_plates_set": ([vp, ctypes.c_double, _d, _d], ctypes.c_int),
-            "cf_relax": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
+            "cf_relax": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
             "cf_plate_force": ([vp, _d], ctypes.c_int),
             "cf_tape_clear": ([vp], ctypes.c_int),
             "cf_relax_adjoint": ([vp, _d], ctypes.c_int),
@@ -335,8 +335,8 @@ def cf_plates_set(ctx, k_plate, z_lo, z_hi):
     _check(ctx, lib().cf_plates_set(ctx.handle, k_plate, _p(zlo), _p(zhi)))
 
 
-def cf_relax(ctx, n, dt, record=False):
-    _check(ctx, lib().cf_relax(ctx.handle, n, dt, 1 if record else 0))
+def cf_relax(ctx, n, dt, damping=0.0, record=False):
+    _check(ctx, lib().cf_relax(ctx.handle, n, dt, damping, 1 if record else 0))
 
 
 def cf_plate_force(ctx):

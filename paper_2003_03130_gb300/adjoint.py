@@ -17,29 +17,52 @@ from . import (CF_ALL_CELLS, cf_adjoint_gradients, cf_plate_force, cf_plates_set
                cf_set_materials, cf_set_positions, cf_tape_clear)
 
 
+def plate_schedule(z_lo, radius, strains, steps, ramp):
+    """Per strain level: the top plate moves from its previous height to
+    z_lo + 2 R (1 - s) in ``ramp`` equal moves of ``steps // (2 ramp)`` steps
+    each (a quasi-static approach), then holds for the remaining steps. Yields
+    (z_hi per cell, number of steps, measured) with measured True at the end
+    of a level; ramp = 0 jumps to the new height."""
+    prev = z_lo + 2.0 * radius
+    for s in strains:
+        new = z_lo + 2.0 * radius * (1.0 - s)
+        n_move = steps // (2 * ramp) if ramp > 0 else 0
+        for r in range(1, ramp + 1):
+            yield prev + (new - prev) * (r / ramp), n_move, False
+        yield new, steps - ramp * n_move, True
+        prev = new
+
+
 class Compression:
     """Protocol: cells start at y0 on the lower plate z_lo; for each strain
-    s in ``strains`` the upper plate sits at z_lo + 2 R (1 - s) and the
-    cells relax for ``steps`` damped steps of size ``dt``."""
+    s in ``strains`` the upper plate approaches z_lo + 2 R (1 - s) (see
+    plate_schedule) while the cells relax with damped steps (size ``dt``,
+    velocity retention ``damping``); the top-plate force is measured at the
+    end of each level."""
 
-    def __init__(self, ctx, ids, y0, z_lo, radius, strains, steps, dt, k_plate):
+    def __init__(self, ctx, ids, y0, z_lo, radius, strains, steps, dt, k_plate, ramp=0, damping=0.0):
         self.ctx, self.ids = ctx, list(ids)
         self.y0 = np.ascontiguousarray(y0, dtype=np.float64)
         self.z_lo = np.asarray(z_lo, np.float64)
         self.radius = np.asarray(radius, np.float64)
         self.strains = list(strains)
-        self.steps, self.dt, self.k_plate = steps, dt, k_plate
+        self.steps, self.dt, self.k_plate, self.ramp, self.damping = steps, dt, k_plate, ramp, damping
+        self.measured = []  # per recorded cf_relax call: True at the end of a level
 
     def run(self, mu, kappa, w, record):
         c = self.ctx
         cf_set_materials(c, self.ids, mu, kappa, w)
         cf_set_positions(c, CF_ALL_CELLS, self.y0)
         cf_tape_clear(c)
-        forces = []
-        for s in self.strains:
-            cf_plates_set(c, self.k_plate, self.z_lo, self.z_lo + 2.0 * self.radius * (1.0 - s))
-            cf_relax(c, self.steps, self.dt, record=record)
-            forces.append(cf_plate_force(c))
+        forces, self.measured = [], []
+        for z_hi, n, measured in plate_schedule(self.z_lo, self.radius, self.strains, self.steps, self.ramp):
+            if n == 0:
+                continue
+            cf_plates_set(c, self.k_plate, self.z_lo, z_hi)
+            cf_relax(c, n, self.dt, self.damping, record=record)
+            self.measured.append(measured)
+            if measured:
+                forces.append(cf_plate_force(c))
         return np.stack(forces, axis=1)
 
 
@@ -54,7 +77,13 @@ class CompressionCurve(torch.autograd.Function):
     def backward(fctx, dF):
         run = fctx.run
         dF = dF.detach().cpu().numpy()
-        for level in reversed(range(len(run.strains))):  # each level is one recorded cf_relax call
-            cf_relax_adjoint(run.ctx, np.ascontiguousarray(dF[:, level]))
+        level = dF.shape[1]
+        zero = np.zeros(dF.shape[0])
+        for measured in reversed(run.measured):  # recorded cf_relax calls, last first
+            if measured:
+                level -= 1
+                cf_relax_adjoint(run.ctx, np.ascontiguousarray(dF[:, level]))
+            else:
+                cf_relax_adjoint(run.ctx, zero)
         g = torch.as_tensor(cf_adjoint_gradients(run.ctx), dtype=torch.float64)
         return g[:, 0], g[:, 1], g[:, 2], None

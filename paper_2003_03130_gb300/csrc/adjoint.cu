@@ -5,15 +5,20 @@
 // a repulsive force keeping vertices out of the plates (Sec. 4.2; the form of
 // that force is in the supplement): here a one-sided harmonic penalty per
 // vertex, f_z = k (z_lo - z)_+ - k (z - z_hi)_+, and quasi-static relaxation
-// by damped steps y <- y + dt (f_el(y) + f_plate(y)). The measured force is
-// the top plate's, F = sum_v k (z_v - z_hi)_+.
+// by damped steps of unit-mass vertices,
+//   v <- c v + dt (f_el(y) + f_plate(y)),  y <- y + dt v   (0 <= c < 1;
+// c = 0 is the first-order gradient flow y <- y + dt^2 f). The measured force
+// is the top plate's, F = sum_v k (z_v - z_hi)_+.
 //
-// Adjoint of one step (lambda = dL/dy): lambda_k = lambda_{k+1} + dt (J_el +
-// J_plate)^T lambda_{k+1}. J_el = -Hessian of the elastic energy is symmetric,
-// so J_el^T lambda is the directional derivative of the forces along lambda:
-// k_tet_jvp runs the force evaluation of mr.cuh on dual numbers. The forces
-// are linear in (mu_1, mu_2, kappa), so lambda . df/d(mu, kappa, w) comes from
-// the forces at unit moduli (k_param_vjp), reduced in double.
+// Adjoint of one step with (lambda_y, lambda_v) = dL/d(y, v) after it and
+// m = dt lambda_y + lambda_v (the sensitivity to the new velocity):
+//   lambda_y <- lambda_y + dt (J_el + J_plate) m,  lambda_v <- c m,
+//   dL/dtheta += dt m . df/dtheta.
+// J_el = -Hessian of the elastic energy is symmetric, so J_el m is the
+// directional derivative of the forces along m: k_tet_jvp runs the force
+// evaluation of mr.cuh on dual numbers. The forces are linear in
+// (mu_1, mu_2, kappa), so m . df/d(mu, kappa, w) comes from the forces at unit
+// moduli (k_param_vjp), reduced in double.
 #include "mr.cuh"
 
 namespace cf {
@@ -130,25 +135,30 @@ __device__ __forceinline__ PlateZ plates_of(const MeshView &m, int c, const floa
     return {__ldg(zlo + c) - oz, __ldg(zhi + c) - oz};
 }
 
-// u_out = u_in + dt (f_el + f_plate); u_out may alias u_in.
-__global__ void k_plate_step(MeshView m, const float4 *u_in, const float4 *__restrict__ fel, float4 *u_out, float dt,
-                             float kp, const float *__restrict__ zlo, const float *__restrict__ zhi, unsigned *err) {
+// v <- c v + dt (f_el + f_plate), y <- y + dt v from (u_in, v_in) into
+// (u_out, v_out); outputs may alias inputs.
+__global__ void k_plate_step(MeshView m, const float4 *u_in, const float4 *v_in, const float4 *__restrict__ fel,
+                             float4 *u_out, float4 *v_out, float dt, float c, float kp, const float *__restrict__ zlo,
+                             const float *__restrict__ zhi, unsigned *err) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= m.V) return;
     const float4 xr = __ldg(m.xr + v);
     const PlateZ pz = plates_of(m, __float_as_int(xr.w), zlo, zhi);
-    const float4 uu = u_in[v], f = fel[v];
+    const float4 uu = u_in[v], vv = v_in[v], f = fel[v];
     const float z = xr.z + uu.z;
     const float fz = f.z + kp * fmaxf(pz.lo - z, 0.f) - kp * fmaxf(z - pz.hi, 0.f);
-    const float4 un = make_float4(uu.x + dt * f.x, uu.y + dt * f.y, uu.z + dt * fz, 0.f);
+    const float4 vn = make_float4(c * vv.x + dt * f.x, c * vv.y + dt * f.y, c * vv.z + dt * fz, 0.f);
+    const float4 un = make_float4(uu.x + dt * vn.x, uu.y + dt * vn.y, uu.z + dt * vn.z, 0.f);
     if (!isfinite(un.x + un.y + un.z)) atomicOr(err, ERR_NONFINITE);
     u_out[v] = un;
+    v_out[v] = vn;
 }
 
-cudaError_t launch_plate_step(const MeshView &m, const float4 *u_in, const float4 *fel, float4 *u_out, float dt,
-                              float kp, const float *zlo, const float *zhi, unsigned *err, cudaStream_t s) {
+cudaError_t launch_plate_step(const MeshView &m, const float4 *u_in, const float4 *v_in, const float4 *fel,
+                              float4 *u_out, float4 *v_out, float dt, float c, float kp, const float *zlo,
+                              const float *zhi, unsigned *err, cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
-    k_plate_step<<<(m.V + 255) / 256, 256, 0, s>>>(m, u_in, fel, u_out, dt, kp, zlo, zhi, err);
+    k_plate_step<<<(m.V + 255) / 256, 256, 0, s>>>(m, u_in, v_in, fel, u_out, v_out, dt, c, kp, zlo, zhi, err);
     return cudaGetLastError();
 }
 
@@ -185,18 +195,29 @@ __global__ void k_adj_seed(MeshView m, const float4 *__restrict__ u, float kp, c
     if (xr.z + __ldg(u + v).z > pz.hi) lam[v].z += (float)(__ldg(dF + c) * (double)kp);
 }
 
-// lambda <- lambda + dt (J_el lambda + J_plate lambda) at positions u, with
-// J_el lambda given (jv) and J_plate = diag(0, 0, -k) on penetrating vertices.
-__global__ void k_adj_step(MeshView m, const float4 *__restrict__ u, const float4 *__restrict__ jv, float4 *lam,
-                           float dt, float kp, const float *__restrict__ zlo, const float *__restrict__ zhi) {
+// m = dt lambda_y + lambda_v
+__global__ void k_adj_m(int n, const float4 *__restrict__ ly, const float4 *__restrict__ lv, float dt, float4 *mvec) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const float4 a = __ldg(ly + v), b = __ldg(lv + v);
+    mvec[v] = make_float4(fmaf(dt, a.x, b.x), fmaf(dt, a.y, b.y), fmaf(dt, a.z, b.z), 0.f);
+}
+
+// lambda_y <- lambda_y + dt (J_el m + J_plate m), lambda_v <- c m at positions
+// u, with J_el m given (jv) and J_plate = diag(0, 0, -k) on penetrating
+// vertices.
+__global__ void k_adj_step(MeshView m, const float4 *__restrict__ u, const float4 *__restrict__ jv,
+                           const float4 *__restrict__ mvec, float4 *ly, float4 *lv, float dt, float c, float kp,
+                           const float *__restrict__ zlo, const float *__restrict__ zhi) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= m.V) return;
     const float4 xr = __ldg(m.xr + v);
     const PlateZ pz = plates_of(m, __float_as_int(xr.w), zlo, zhi);
     const float z = xr.z + __ldg(u + v).z;
-    const float4 l = lam[v], j = __ldg(jv + v);
-    const float jz = (z < pz.lo || z > pz.hi) ? -kp * l.z : 0.f;
-    lam[v] = make_float4(l.x + dt * j.x, l.y + dt * j.y, l.z + dt * (j.z + jz), 0.f);
+    const float4 l = ly[v], j = __ldg(jv + v), mm = __ldg(mvec + v);
+    const float jz = (z < pz.lo || z > pz.hi) ? -kp * mm.z : 0.f;
+    ly[v] = make_float4(l.x + dt * j.x, l.y + dt * j.y, l.z + dt * (j.z + jz), 0.f);
+    lv[v] = make_float4(c * mm.x, c * mm.y, c * mm.z, 0.f);
 }
 
 cudaError_t launch_adj_seed(const MeshView &m, const float4 *u, float kp, const float *zlo, const float *zhi,
@@ -206,10 +227,16 @@ cudaError_t launch_adj_seed(const MeshView &m, const float4 *u, float kp, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_step(const MeshView &m, const float4 *u, const float4 *jv, float4 *lam, float dt, float kp,
-                            const float *zlo, const float *zhi, cudaStream_t s) {
+cudaError_t launch_adj_m(int n, const float4 *ly, const float4 *lv, float dt, float4 *mvec, cudaStream_t s) {
+    if (n > 0) k_adj_m<<<(n + 255) / 256, 256, 0, s>>>(n, ly, lv, dt, mvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const MeshView &m, const float4 *u, const float4 *jv, const float4 *mvec, float4 *ly,
+                            float4 *lv, float dt, float c, float kp, const float *zlo, const float *zhi,
+                            cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
-    k_adj_step<<<(m.V + 255) / 256, 256, 0, s>>>(m, u, jv, lam, dt, kp, zlo, zhi);
+    k_adj_step<<<(m.V + 255) / 256, 256, 0, s>>>(m, u, jv, mvec, ly, lv, dt, c, kp, zlo, zhi);
     return cudaGetLastError();
 }
 

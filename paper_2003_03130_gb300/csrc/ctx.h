@@ -72,7 +72,7 @@ struct cf_ctx {
     // compression between plates and its adjoint (csrc/plates.cu)
     struct TapeEntry {
         int n;
-        float dt, kp;
+        float dt, c, kp;
         std::vector<float> zlo, zhi;
         int ck0, nck;  // checkpoints ck0 .. ck0 + nck - 1: steps 0, S, 2S, ..., and the end state
     };
@@ -80,9 +80,11 @@ struct cf_ctx {
     std::vector<float> zlo_h, zhi_h;   // current plates per cell
     float *zlo = nullptr, *zhi = nullptr;
     std::vector<TapeEntry> tape;
-    std::vector<float4 *> ckpt;        // device checkpoints of V vertices each
+    std::vector<float4 *> ckpt;        // device checkpoints: positions then velocities, 2 V float4 each
     int ck_used = 0;
-    float4 *lam = nullptr, *jv = nullptr, *vtmp = nullptr, *seg = nullptr;
+    float4 *vel_r = nullptr;           // relaxation velocities [V]
+    float4 *lam = nullptr, *lamv = nullptr, *mvec = nullptr, *jv = nullptr, *vtmp = nullptr;
+    float4 *seg = nullptr, *segv = nullptr;  // positions / velocities of one segment, (stride + 1) x V
     double *grad = nullptr, *gtmp = nullptr, *pforce = nullptr, *dF = nullptr;
     int adj_V = 0, adj_C = 0;
 

@@ -214,14 +214,17 @@ cudaError_t launch_force_jvp(const MeshView &m, const float4 *u, const float4 *v
 // grad[3 c + (0, 1, 2)] += scale * lambda . df/d(mu, kappa, w) per cell (double).
 cudaError_t launch_param_vjp(const MeshView &m, const float4 *u, const float4 *lam, double scale, double *grad,
                              cudaStream_t s);
-cudaError_t launch_plate_step(const MeshView &m, const float4 *u_in, const float4 *fel, float4 *u_out, float dt,
-                              float kp, const float *zlo, const float *zhi, unsigned *err, cudaStream_t s);
+cudaError_t launch_plate_step(const MeshView &m, const float4 *u_in, const float4 *v_in, const float4 *fel,
+                              float4 *u_out, float4 *v_out, float dt, float c, float kp, const float *zlo,
+                              const float *zhi, unsigned *err, cudaStream_t s);
 cudaError_t launch_plate_force(const MeshView &m, const float4 *u, float kp, const float *zlo, const float *zhi,
                                double *out, cudaStream_t s);
 cudaError_t launch_adj_seed(const MeshView &m, const float4 *u, float kp, const float *zlo, const float *zhi,
                             const double *dF, float4 *lam, cudaStream_t s);
-cudaError_t launch_adj_step(const MeshView &m, const float4 *u, const float4 *jv, float4 *lam, float dt, float kp,
-                            const float *zlo, const float *zhi, cudaStream_t s);
+cudaError_t launch_adj_m(int n, const float4 *ly, const float4 *lv, float dt, float4 *mvec, cudaStream_t s);
+cudaError_t launch_adj_step(const MeshView &m, const float4 *u, const float4 *jv, const float4 *mvec, float4 *ly,
+                            float4 *lv, float dt, float c, float kp, const float *zlo, const float *zhi,
+                            cudaStream_t s);
 cudaError_t launch_pack3(const double *in, int n, float4 *out, cudaStream_t s);
 
 cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s);

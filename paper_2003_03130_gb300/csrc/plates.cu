@@ -2,13 +2,15 @@
 // of its adjoint: cf_plates_set, cf_relax, cf_plate_force, cf_tape_clear,
 // cf_relax_adjoint, cf_adjoint_gradients, cf_force_jvp, cf_force_param_vjp.
 //
-// A recorded cf_relax call appends a tape entry and keeps device checkpoints
-// of the positions every kTapeStride steps and at its end. cf_relax_adjoint
-// reverses the last entry: it seeds lambda = dL/dy with dL/dF (F = top-plate
-// force at the end of that call), then, segment by segment from the last,
-// restores the checkpoint, recomputes the segment's positions, and walks it
-// backwards: lambda <- lambda + dt (J_el + J_plate)^T lambda, accumulating
-// dt lambda . df/d(mu, kappa, w) per cell in double.
+// Relaxation steps (unit-mass vertices): v <- c v + dt (f_el + f_plate),
+// y <- y + dt v. A recorded cf_relax call appends a tape entry and keeps
+// device checkpoints of (y, v) every kTapeStride steps and at its end.
+// cf_relax_adjoint reverses the last entry: it adds dL/dF * dF/dy to lambda_y
+// (F = top-plate force at the end of that call), then, segment by segment from
+// the last, restores the checkpoint, recomputes the segment's states, and
+// walks it backwards with m = dt lambda_y + lambda_v:
+//   lambda_y <- lambda_y + dt (J_el + J_plate) m, lambda_v <- c m,
+// accumulating dt m . df/d(mu, kappa, w) per cell in double.
 #include "ctx.h"
 
 namespace {
@@ -20,10 +22,14 @@ void free_adjoint(cf_ctx *c) {
     c->ckpt.clear();
     c->ck_used = 0;
     c->tape.clear();
+    dfree(c->vel_r);
     dfree(c->lam);
+    dfree(c->lamv);
+    dfree(c->mvec);
     dfree(c->jv);
     dfree(c->vtmp);
     dfree(c->seg);
+    dfree(c->segv);
     dfree(c->grad);
     dfree(c->gtmp);
     dfree(c->pforce);
@@ -40,17 +46,23 @@ cf_status ensure_adjoint(cf_ctx *c) {
     if (c->adj_V == c->V && c->adj_C == C) return CF_OK;
     std::vector<float> zlo = c->zlo_h, zhi = c->zhi_h;
     free_adjoint(c);
+    CUDA_TRY(c, dalloc(&c->vel_r, c->V));
     CUDA_TRY(c, dalloc(&c->lam, c->V));
+    CUDA_TRY(c, dalloc(&c->lamv, c->V));
+    CUDA_TRY(c, dalloc(&c->mvec, c->V));
     CUDA_TRY(c, dalloc(&c->jv, c->V));
     CUDA_TRY(c, dalloc(&c->vtmp, c->V));
     CUDA_TRY(c, dalloc(&c->seg, (size_t)(kTapeStride + 1) * c->V));
+    CUDA_TRY(c, dalloc(&c->segv, (size_t)(kTapeStride + 1) * c->V));
     CUDA_TRY(c, dalloc(&c->grad, 3 * (size_t)C));
     CUDA_TRY(c, dalloc(&c->gtmp, 3 * (size_t)C));
     CUDA_TRY(c, dalloc(&c->pforce, C));
     CUDA_TRY(c, dalloc(&c->dF, C));
     CUDA_TRY(c, dalloc(&c->zlo, C));
     CUDA_TRY(c, dalloc(&c->zhi, C));
+    CUDA_TRY(c, cudaMemsetAsync(c->vel_r, 0, sizeof(float4) * c->V, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->lam, 0, sizeof(float4) * c->V, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->lamv, 0, sizeof(float4) * c->V, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->grad, 0, sizeof(double) * 3 * C, c->stream));
     c->adj_V = c->V;
     c->adj_C = C;
@@ -72,11 +84,19 @@ cf_status upload_plates(cf_ctx *c, const std::vector<float> &zlo, const std::vec
     return CF_OK;
 }
 
-// forces at u into c->fv, then one damped step u_in -> u_out
-cf_status relax_step(cf_ctx *c, const MeshView &m, const float4 *u_in, float4 *u_out, float dt, float kp) {
+// forces at u into c->fv, then one damped step (u_in, v_in) -> (u_out, v_out)
+cf_status relax_step(cf_ctx *c, const MeshView &m, const float4 *u_in, const float4 *v_in, float4 *u_out,
+                     float4 *v_out, float dt, float cd, float kp) {
     CUDA_TRY(c, launch_tet_force(m, u_in, c->d_err, nullptr, nullptr, nullptr, c->stream));
     CUDA_TRY(c, launch_gather_spread(m, u_in, nullptr, nullptr, c->d_err, c->stream));
-    CUDA_TRY(c, launch_plate_step(m, u_in, c->fv, u_out, dt, kp, c->zlo, c->zhi, c->d_err, c->stream));
+    CUDA_TRY(c, launch_plate_step(m, u_in, v_in, c->fv, u_out, v_out, dt, cd, kp, c->zlo, c->zhi, c->d_err,
+                                  c->stream));
+    return CF_OK;
+}
+
+cf_status save_state(cf_ctx *c, float4 *dst, const float4 *u, const float4 *v) {
+    CUDA_TRY(c, cudaMemcpyAsync(dst, u, sizeof(float4) * c->V, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(dst + c->V, v, sizeof(float4) * c->V, cudaMemcpyDeviceToDevice, c->stream));
     return CF_OK;
 }
 
@@ -110,18 +130,21 @@ cf_status cf_plates_set(cf_ctx *c, double k_plate, const double *z_lo, const dou
     return st != CF_OK ? st : wait_stream(c);
 }
 
-cf_status cf_relax(cf_ctx *c, int32_t n, double dt, int32_t record) {
+cf_status cf_relax(cf_ctx *c, int32_t n, double dt, double damping, int32_t record) {
     cf_status st = need_cells(c);
     if (st != CF_OK) return st;
     DeviceGuard dg(c->device);
     if ((int)c->zlo_h.size() != (int)c->cells.size()) return fail(c, CF_ESTATE, "call cf_plates_set first");
     if (n < 1 || !(dt > 0.0) || !std::isfinite(dt)) return fail(c, CF_EINVAL, "need n >= 1 and dt > 0");
+    if (!(damping >= 0.0 && damping < 1.0)) return fail(c, CF_EINVAL, "need 0 <= damping < 1");
     const MeshView m = view(c);
     float4 *u = c->u[c->cur];
+    const float cd = (float)damping;
     cf_ctx::TapeEntry e{};
     if (record) {
         e.n = n;
         e.dt = (float)dt;
+        e.c = cd;
         e.kp = c->k_plate;
         e.zlo = c->zlo_h;
         e.zhi = c->zhi_h;
@@ -129,20 +152,21 @@ cf_status cf_relax(cf_ctx *c, int32_t n, double dt, int32_t record) {
         e.nck = (n - 1) / kTapeStride + 2;
         while ((int)c->ckpt.size() < e.ck0 + e.nck) {
             float4 *p = nullptr;
-            CUDA_TRY(c, dalloc(&p, c->V));
+            CUDA_TRY(c, dalloc(&p, 2 * (size_t)c->V));
             c->ckpt.push_back(p);
         }
     }
     for (int k = 0; k < n; ++k) {
-        if (record && k % kTapeStride == 0)
-            CUDA_TRY(c, cudaMemcpyAsync(c->ckpt[e.ck0 + k / kTapeStride], u, sizeof(float4) * c->V,
-                                        cudaMemcpyDeviceToDevice, c->stream));
-        st = relax_step(c, m, u, u, (float)dt, c->k_plate);
+        if (record && k % kTapeStride == 0) {
+            st = save_state(c, c->ckpt[e.ck0 + k / kTapeStride], u, c->vel_r);
+            if (st != CF_OK) return st;
+        }
+        st = relax_step(c, m, u, c->vel_r, u, c->vel_r, (float)dt, cd, c->k_plate);
         if (st != CF_OK) return st;
     }
     if (record) {
-        CUDA_TRY(c, cudaMemcpyAsync(c->ckpt[e.ck0 + e.nck - 1], u, sizeof(float4) * c->V, cudaMemcpyDeviceToDevice,
-                                    c->stream));
+        st = save_state(c, c->ckpt[e.ck0 + e.nck - 1], u, c->vel_r);
+        if (st != CF_OK) return st;
         c->ck_used = e.ck0 + e.nck;
         c->tape.push_back(e);
     }
@@ -168,7 +192,9 @@ cf_status cf_tape_clear(cf_ctx *c) {
     DeviceGuard dg(c->device);
     c->tape.clear();
     c->ck_used = 0;
+    CUDA_TRY(c, cudaMemsetAsync(c->vel_r, 0, sizeof(float4) * c->V, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->lam, 0, sizeof(float4) * c->V, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->lamv, 0, sizeof(float4) * c->V, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->grad, 0, sizeof(double) * 3 * c->cells.size(), c->stream));
     return wait_stream(c);
 }
@@ -188,18 +214,22 @@ cf_status cf_relax_adjoint(cf_ctx *c, const double *dF) {
     CUDA_TRY(c, launch_adj_seed(m, c->ckpt[e.ck0 + e.nck - 1], e.kp, c->zlo, c->zhi, c->dF, c->lam, c->stream));
     for (int j = e.nck - 2; j >= 0; --j) {
         const int s0 = j * kTapeStride, len = std::min(kTapeStride, e.n - s0);
-        float4 *seg = c->seg;
-        CUDA_TRY(c, cudaMemcpyAsync(seg, c->ckpt[e.ck0 + j], sizeof(float4) * c->V, cudaMemcpyDeviceToDevice,
-                                    c->stream));
-        for (int i = 0; i + 1 < len; ++i) {  // positions of the segment's steps
-            st = relax_step(c, m, seg + (size_t)i * c->V, seg + (size_t)(i + 1) * c->V, e.dt, e.kp);
+        const size_t V = (size_t)c->V;
+        const float4 *ck = c->ckpt[e.ck0 + j];
+        CUDA_TRY(c, cudaMemcpyAsync(c->seg, ck, sizeof(float4) * V, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->segv, ck + V, sizeof(float4) * V, cudaMemcpyDeviceToDevice, c->stream));
+        for (int i = 0; i + 1 < len; ++i) {  // states of the segment's steps
+            st = relax_step(c, m, c->seg + i * V, c->segv + i * V, c->seg + (i + 1) * V, c->segv + (i + 1) * V, e.dt,
+                            e.c, e.kp);
             if (st != CF_OK) return st;
         }
         for (int i = len - 1; i >= 0; --i) {
-            const float4 *y = seg + (size_t)i * c->V;
-            CUDA_TRY(c, launch_force_jvp(m, y, c->lam, c->jv, c->d_err, c->stream));
-            CUDA_TRY(c, launch_param_vjp(m, y, c->lam, (double)e.dt, c->grad, c->stream));
-            CUDA_TRY(c, launch_adj_step(m, y, c->jv, c->lam, e.dt, e.kp, c->zlo, c->zhi, c->stream));
+            const float4 *y = c->seg + i * V;
+            CUDA_TRY(c, launch_adj_m(c->V, c->lam, c->lamv, e.dt, c->mvec, c->stream));
+            CUDA_TRY(c, launch_force_jvp(m, y, c->mvec, c->jv, c->d_err, c->stream));
+            CUDA_TRY(c, launch_param_vjp(m, y, c->mvec, (double)e.dt, c->grad, c->stream));
+            CUDA_TRY(c, launch_adj_step(m, y, c->jv, c->mvec, c->lam, c->lamv, e.dt, e.c, e.kp, c->zlo, c->zhi,
+                                        c->stream));
         }
     }
     c->tape.pop_back();

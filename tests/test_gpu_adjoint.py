@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 RNG = np.random.default_rng(33)
 STRAINS = [0.1, 0.2, 0.3]
-STEPS, DT, KP = 60, 0.004, 20.0
+STEPS, DT, KP, RAMP = 60, 0.004 ** 0.5, 20.0, 3
 
 
 @pytest.fixture(scope="module")
@@ -97,22 +97,23 @@ def test_compression_matches_oracle(P):
     m = oracle.Mesh(cells)
     z_lo, radius = protocol_geometry(cells)
     ctx, ids = setup(P, cells)
-    run = Compression(ctx, ids, m.x, z_lo, radius, STRAINS, STEPS, DT, KP)
+    run = Compression(ctx, ids, m.x, z_lo, radius, STRAINS, STEPS, DT, KP, RAMP)
     F = run.run(m.mu, m.kappa, m.w, record=False)
-    F_ref, y_ref = cp.protocol(m, m.x, z_lo, radius, STRAINS, STEPS, DT, KP)
+    F_ref, y_ref = cp.protocol(m, m.x, z_lo, radius, STRAINS, STEPS, DT, KP, RAMP)
     assert (F_ref > 0).all()
     assert rel(F, F_ref) <= 1e-5
     assert rel(P.cf_get_positions(ctx, P.CF_ALL_CELLS) - m.x, y_ref - m.x) <= 1e-5
 
 
-def oracle_loss(cells, theta, target, z_lo, radius):
+def oracle_loss(cells, theta, target, z_lo, radius, dt=DT, damping=0.0):
     m = oracle.Mesh(cells)
     m.mu[:], m.kappa[:], m.w[:] = theta[:, 0], theta[:, 1], theta[:, 2]
-    F, _ = cp.protocol(m, m.x, z_lo, radius, STRAINS, STEPS, DT, KP)
+    F, _ = cp.protocol(m, m.x, z_lo, radius, STRAINS, STEPS, dt, KP, RAMP, damping)
     return float(((F - target) ** 2).sum())
 
 
-def test_adjoint_gradient_matches_oracle_finite_differences(P):
+@pytest.mark.parametrize("damping", [0.0, 0.8])
+def test_adjoint_gradient_matches_oracle_finite_differences(P, damping):
     torch = pytest.importorskip("torch")
     from paper_2003_03130_gb300.adjoint import Compression, CompressionCurve
 
@@ -120,10 +121,11 @@ def test_adjoint_gradient_matches_oracle_finite_differences(P):
     cells = two_cells()
     m = oracle.Mesh(cells)
     z_lo, radius = protocol_geometry(cells)
-    target, _ = cp.protocol(oracle.Mesh(hidden), m.x, z_lo, radius, STRAINS, STEPS, DT, KP)
+    dt = DT if damping == 0.0 else 0.05
+    target, _ = cp.protocol(oracle.Mesh(hidden), m.x, z_lo, radius, STRAINS, STEPS, dt, KP, RAMP, damping)
 
     ctx, ids = setup(P, cells)
-    run = Compression(ctx, ids, m.x, z_lo, radius, STRAINS, STEPS, DT, KP)
+    run = Compression(ctx, ids, m.x, z_lo, radius, STRAINS, STEPS, dt, KP, RAMP, damping)
     mu = torch.tensor(m.mu, dtype=torch.float64, requires_grad=True)
     kappa = torch.tensor(m.kappa, dtype=torch.float64, requires_grad=True)
     w = torch.tensor(m.w, dtype=torch.float64, requires_grad=True)
@@ -140,8 +142,40 @@ def test_adjoint_gradient_matches_oracle_finite_differences(P):
             tp, tm = theta.copy(), theta.copy()
             tp[c, k] += h
             tm[c, k] -= h
-            fd[c, k] = (oracle_loss(cells, tp, target, z_lo, radius) -
-                        oracle_loss(cells, tm, target, z_lo, radius)) / (2 * h)
-    print("adjoint", got.tolist(), "fd", fd.tolist(), "rel", rel(got, fd))
+            fd[c, k] = (oracle_loss(cells, tp, target, z_lo, radius, dt, damping) -
+                        oracle_loss(cells, tm, target, z_lo, radius, dt, damping)) / (2 * h)
+    print("damping", damping, "adjoint", got.tolist(), "fd", fd.tolist(), "rel", rel(got, fd))
     assert rel(got, fd) <= 1e-4
-    assert abs(loss.item() - oracle_loss(cells, theta, target, z_lo, radius)) <= 1e-4 * loss.item()
+    assert abs(loss.item() - oracle_loss(cells, theta, target, z_lo, radius, dt, damping)) <= 1e-4 * loss.item()
+
+
+def test_fit_recovers_hidden_moduli(P):
+    """Adam on (log mu, log kappa, logit w) with adjoint gradients brings the
+    loss of a synthetic force-strain curve down and moves the moduli towards
+    the hidden ones."""
+    torch = pytest.importorskip("torch")
+    from paper_2003_03130_gb300.adjoint import Compression, CompressionCurve
+
+    hidden = two_cells(mu=(1.3, 0.8), kappa=(22.0, 16.0), w=(0.75, 0.3))
+    cells = two_cells(mu=(1.0, 1.0), kappa=(20.0, 20.0), w=(0.5, 0.5))
+    m = oracle.Mesh(cells)
+    z_lo, radius = protocol_geometry(cells)
+    strains, steps, dt, damping = [0.1, 0.2, 0.3, 0.4], 200, 0.05, 0.9
+    ctx, ids = setup(P, cells)
+    run = Compression(ctx, ids, m.x, z_lo, radius, strains, steps, dt, KP, RAMP, damping)
+    hm = oracle.Mesh(hidden)
+    target = torch.as_tensor(run.run(hm.mu, hm.kappa, hm.w, record=False))
+    th = torch.tensor([[0.0, np.log(20.0), 0.0]] * 2, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([th], lr=0.05)
+    losses = []
+    for _ in range(40):
+        F = CompressionCurve.apply(torch.exp(th[:, 0]), torch.exp(th[:, 1]), torch.sigmoid(th[:, 2]), run)
+        loss = (((F - target) ** 2).sum(1) / (target ** 2).sum(1)).sum()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    mu = torch.exp(th[:, 0]).detach().numpy()
+    print("losses", losses[0], losses[-1], "mu", mu, "hidden", hm.mu)
+    assert losses[-1] < 0.05 * losses[0]
+    assert np.abs(mu / hm.mu - 1).max() < np.abs(1.0 / hm.mu - 1).max()

@@ -40,7 +40,7 @@ def test_relaxation_decreases_total_energy():
     E = lambda y: m.energy(y) + cp.plate_energy(y, 10.0, zl, zh)  # noqa: E731
     e = E(y)
     for _ in range(50):
-        y = cp.relax(m, y, 1, 0.004, 10.0, [-3.0], [2.0])
+        y, _ = cp.relax(m, y, 1, 0.004 ** 0.5, 10.0, [-3.0], [2.0])
         e2 = E(y)
         assert e2 <= e + 1e-12
         e = e2
@@ -50,5 +50,5 @@ def test_compressed_cell_pushes_back():
     """A compressed cell pushes the top plate harder at larger strain."""
     x, t = sphere_tet_mesh(3.0, 1.2)
     m = oracle.Mesh([Cell(x, t, x, 1.0, 10.0, 0.5)])
-    F, _ = cp.protocol(m, x, [x[:, 2].min()], [3.0], [0.1, 0.3], 200, 0.004, 20.0)
+    F, _ = cp.protocol(m, x, [x[:, 2].min()], [3.0], [0.1, 0.3], 200, 0.004 ** 0.5, 20.0)
     assert 0 < F[0, 0] < F[0, 1]

@@ -160,6 +160,40 @@ def batched_channel(ncells: int = 400, nx: int = 512, ny: int = 256, nz: int = 2
                     cells=cells, steps=steps)
 
 
+@dataclass
+class CompressionSet:
+    """Cells to compress between plates, with their hidden moduli."""
+    cells: list
+    hidden_mu: np.ndarray
+    hidden_kappa: np.ndarray
+    hidden_w: np.ndarray
+    strains: list
+    steps: int
+    dt: float
+    damping: float
+    k_plate: float
+    ramp: int
+
+
+def compression_set(ncells: int = 64, R: float = 10.0, h: float = 1.45, steps: int = 2000, seed: int = 5):
+    """64 spheres of radius 10 (8,256 tets each) spaced apart, each with
+    hidden moduli (mu log-uniform in [0.7, 1.4], kappa = 20 mu x U(0.8, 1.25),
+    i.e. a Poisson ratio near 0.475, w uniform in [0.2, 0.9]); protocol: 8
+    strain levels to 80 %, 2,000 damped steps per level (dt 0.03, velocity
+    retention 0.95), plate stiffness 50, the plate approaching in 10 moves.
+    Every cell starts from mu = 1, kappa = 20, w = 0.5."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x, tets = sphere_tet_mesh(R, h)
+    cells = []
+    for k in range(ncells):
+        off = np.array([3.0 * R * (k % 4), 3.0 * R * ((k // 4) % 4), 3.0 * R * (k // 16)])
+        cells.append(Cell(x_ref=x + off, tets=tets, y0=x + off, mu=1.0, kappa=20.0, w=0.5))
+    mu = np.exp(rng.uniform(np.log(0.7), np.log(1.4), ncells))
+    kappa = 20.0 * mu * rng.uniform(0.8, 1.25, ncells)
+    w = rng.uniform(0.2, 0.9, ncells)
+    return CompressionSet(cells, mu, kappa, w, [0.1 * (i + 1) for i in range(8)], steps, 0.03, 0.95, 50.0, 10)
+
+
 def random_displacements(cell: Cell, amplitude: float, seed: int) -> np.ndarray:
     """Positions of ``cell`` perturbed by ``amplitude * U(-1, 1)``."""
     return perturb(cell.x_ref, amplitude, seed)
