@@ -50,6 +50,8 @@ def parse():
                          "512 x 256 x 256 channel; compression: fit the moduli of 64 cells to synthetic "
                          "force-strain curves with the adjoint")
     ap.add_argument("--fit-iters", type=int, default=10, help="Adam iterations of the compression fit")
+    ap.add_argument("--cells", type=int, default=400, help="cells of the suspension workload")
+    ap.add_argument("--box", default="512,256,256", help="lattice of the suspension workload")
     ap.add_argument("--ca", type=float, default=0.2)
     ap.add_argument("--w", type=float, default=0.5)
     ap.add_argument("--profile-steps", type=int, default=2000)
@@ -65,7 +67,8 @@ def workload(args):
     from workloads import configs
 
     if args.workload == "suspension":
-        return configs.batched_channel()
+        nx, ny, nz = (int(v) for v in args.box.split(","))
+        return configs.batched_channel(ncells=args.cells, nx=nx, ny=ny, nz=nz)
     return configs.production_shear(ca=args.ca, w=args.w, n=args.n)
 
 
@@ -133,6 +136,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The slowest rank's time: all-reduce MAX (identity on one rank)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 def support_nodes(y, dims):
@@ -272,10 +293,7 @@ def run_ours(args):
         P.cf_synchronize(ctx)
         ms = ev0.elapsed_time(ev1)
         barrier()
-        if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{dev}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, device=f"cuda:{dev}")
 
         # per-kernel durations: CUDA events around every launch, same stream
         kms, near_nodes = P.cf_step_profiled(ctx, args.profile_steps)
@@ -293,12 +311,12 @@ def run_ours(args):
             P.cf_step(ctx, 1)
             P.cf_get_positions(ctx, P.CF_ALL_CELLS, out=y_out)
             y_in[...] = y_out
-        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{dev}")
         barrier()
         y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
         P.cf_destroy(ctx)
 
-    steps_per_s = world * K / (ms / 1e3)
+    steps_per_s = job_rate(K, world, ms / 1e3)
     # dominant kernel: the far-field stream-collide (every node outside the
     # force region; populations only)
     far_nodes = wl.n_nodes - near_nodes
@@ -324,8 +342,8 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded sphere mesh, fluid at rest at t=0)",
         "config": config_of(wl),
-        "mlups": world * wl.n_nodes * K / (ms / 1e3) / 1e6,
-        "tet_forces_per_s": world * wl.n_tets * K / (ms / 1e3),
+        "mlups": job_rate(wl.n_nodes * K, world, ms / 1e3) / 1e6,
+        "tet_forces_per_s": job_rate(wl.n_tets * K, world, ms / 1e3),
         "gpu_launches": 5 * K + 1,
         "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
         "kernel_share": dict(zip(KERNELS, [float(x) / step_ms_profiled for x in kms])),
@@ -345,7 +363,7 @@ def run_ours(args):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
         },
         "e2e": {
-            "value": world * args.e2e_steps / e2e_s,
+            "value": job_rate(args.e2e_steps, world, e2e_s),
             "unit": "steps/s",
             "h2d_bytes_per_step": int(nv * 3 * 8),
             "d2h_bytes_per_step": int(nv * 3 * 8),
