@@ -128,6 +128,13 @@ cf_status cf_step(cf_ctx *ctx, int32_t n);
  * cf_get_*). */
 cf_status cf_step_async(cf_ctx *ctx, int32_t n);
 
+/* Build, without running anything, every CUDA graph that cf_step or
+ * cf_step_async of n steps from the current state would build on first use
+ * (graph capture and instantiation take milliseconds; after this call the
+ * n-step call only launches). Positions, populations and the step counter
+ * are unchanged. CF_ESTATE before cf_lbm_init, CF_EINVAL for n < 0. */
+cf_status cf_prepare_steps(cf_ctx *ctx, int32_t n);
+
 /* Wait for the context's stream (polling, with the host timeout) and return
  * the accumulated device error status. */
 cf_status cf_synchronize(cf_ctx *ctx);

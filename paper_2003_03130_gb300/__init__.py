@@ -54,6 +54,7 @@ def lib():
             "cf_set_material": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
             "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_prepare_steps": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_synchronize": ([vp], ctypes.c_int),
             "cf_compute_forces": ([vp], ctypes.c_int),
             "cf_step_profiled": ([vp, ctypes.c_int32, _d, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -219,6 +220,11 @@ def cf_step(ctx, n: int = 1):
 
 def cf_step_async(ctx, n: int = 1):
     _check(ctx, lib().cf_step_async(ctx.handle, n))
+
+
+def cf_prepare_steps(ctx, n: int):
+    """Instantiate the step graphs an n-step call would use, without running."""
+    _check(ctx, lib().cf_prepare_steps(ctx.handle, n))
 
 
 def cf_synchronize(ctx):

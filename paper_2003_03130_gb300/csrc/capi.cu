@@ -159,16 +159,57 @@ cf_status get_graph(cf_ctx *c, Kind kind, int p, int s, int nsteps, cudaGraphExe
     return CF_OK;
 }
 
-// Launch one graph of `nsteps` steps at the context's phase and advance it.
-cf_status launch_steps(cf_ctx *c, Kind kind, int nsteps) {
+// Launch one graph of `nsteps` steps at the context's phase and advance it;
+// with launch = false only make sure the graph exists.
+cf_status launch_steps(cf_ctx *c, Kind kind, int nsteps, bool launch = true) {
     cudaGraphExec_t g;
     const int s = (int)(c->tstep % 3);
     cf_status st = get_graph(c, kind, c->cur, s, nsteps, &g);
     if (st != CF_OK) return st;
-    CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
+    if (launch) CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
     c->cur ^= nsteps & 1;
     c->tstep += nsteps;
     return CF_OK;
+}
+
+// The graphs of n steps from the current state: the first step, chunks of
+// kChunk, single steps, then K5 of the last step (with cells); or chunks of
+// fluid-only steps. launch = false instantiates them without running and
+// leaves the state as it was.
+cf_status schedule_steps(cf_ctx *c, int32_t n, bool launch) {
+    const int cur0 = c->cur;
+    const long long t0 = c->tstep;
+    cf_status st = CF_OK;
+    if (c->T == 0) {
+        int left = n;
+        while (st == CF_OK && left >= kChunk) {
+            st = launch_steps(c, Kind::Fluid, kChunk, launch);
+            left -= kChunk;
+        }
+        while (st == CF_OK && left > 0) {
+            st = launch_steps(c, Kind::Fluid, 1, launch);
+            --left;
+        }
+    } else {
+        st = launch_steps(c, Kind::First, 1, launch);
+        int left = n - 1;
+        while (st == CF_OK && left >= kChunk) {
+            st = launch_steps(c, Kind::Mid, kChunk, launch);
+            left -= kChunk;
+        }
+        while (st == CF_OK && left > 0) {
+            st = launch_steps(c, Kind::Mid, 1, launch);
+            --left;
+        }
+        cudaGraphExec_t g;
+        if (st == CF_OK) st = get_graph(c, Kind::Tail, c->cur ^ 1, 0, 1, &g);  // parity of the last step
+        if (st == CF_OK && launch) CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
+    }
+    if (!launch) {
+        c->cur = cur0;
+        c->tstep = t0;
+    }
+    return st;
 }
 
 }  // namespace
@@ -504,36 +545,16 @@ cf_status cf_step_async(cf_ctx *c, int32_t n) {
     if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
     if (n == 0) return CF_OK;
-    cf_status st = CF_OK;
-    if (c->T == 0) {  // fluid only
-        int left = n;
-        while (st == CF_OK && left >= kChunk) {
-            st = launch_steps(c, Kind::Fluid, kChunk);
-            left -= kChunk;
-        }
-        while (st == CF_OK && left > 0) {
-            st = launch_steps(c, Kind::Fluid, 1);
-            --left;
-        }
-        return st;
-    }
-    st = launch_steps(c, Kind::First, 1);
-    int left = n - 1;
-    while (st == CF_OK && left >= kChunk) {
-        st = launch_steps(c, Kind::Mid, kChunk);
-        left -= kChunk;
-    }
-    while (st == CF_OK && left > 0) {
-        st = launch_steps(c, Kind::Mid, 1);
-        --left;
-    }
-    if (st != CF_OK) return st;
-    // K5 of the last step: parity of that step is cur ^ 1
-    cudaGraphExec_t g;
-    st = get_graph(c, Kind::Tail, c->cur ^ 1, 0, 1, &g);
-    if (st != CF_OK) return st;
-    CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
-    return CF_OK;
+    return schedule_steps(c, n, true);
+}
+
+cf_status cf_prepare_steps(cf_ctx *c, int32_t n) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_prepare_steps needs cf_lbm_init first");
+    if (n == 0) return CF_OK;
+    return schedule_steps(c, n, false);
 }
 
 cf_status cf_synchronize(cf_ctx *c) {
@@ -572,12 +593,13 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
             const int sph = (int)((c->tstep) % 3);
             int *use = region_slot(c, sph), *accb = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
-            cudaEventRecord(E[0], s);
-            if (cells && t > 0) e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s);
-            if (cells && t == 0 && e == cudaSuccess) {
+            if (cells && t == 0) {  // region of the first step: not timed
                 e = cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), s);
                 if (e == cudaSuccess) e = launch_support_box(m, c->u[p], c->lp, use, s);
             }
+            cudaEventRecord(E[0], s);
+            if (cells && t > 0 && e == cudaSuccess)
+                e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s);
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
                 e = cudaMemsetAsync(accb, 0x7f, 6 * sizeof(int), s);
