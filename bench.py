@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--fit-iters", type=int, default=10, help="Adam iterations of the compression fit")
     ap.add_argument("--cells", type=int, default=400, help="cells of the suspension workload")
     ap.add_argument("--box", default="512,256,256", help="lattice of the suspension workload")
+    ap.add_argument("--delta", choices=("trilinear", "peskin4"), default="trilinear",
+                    help="immersed-boundary delta kernel")
     ap.add_argument("--ca", type=float, default=0.2)
     ap.add_argument("--w", type=float, default=0.5)
     ap.add_argument("--profile-steps", type=int, default=2000)
@@ -69,8 +71,11 @@ def workload(args):
 
     if args.workload == "suspension":
         nx, ny, nz = (int(v) for v in args.box.split(","))
-        return configs.batched_channel(ncells=args.cells, nx=nx, ny=ny, nz=nz)
-    return configs.production_shear(ca=args.ca, w=args.w, n=args.n)
+        wl = configs.batched_channel(ncells=args.cells, nx=nx, ny=ny, nz=nz)
+    else:
+        wl = configs.production_shear(ca=args.ca, w=args.w, n=args.n)
+    wl.delta = {"trilinear": 2, "peskin4": 4}[args.delta]
+    return wl
 
 
 def config_of(wl):
@@ -81,6 +86,7 @@ def config_of(wl):
         "n_tets": wl.n_tets,
         "tau": wl.tau,
         "u_wall": [wl.u_wall_lo, wl.u_wall_hi],
+        "delta": {2: "trilinear", 4: "peskin4"}[wl.delta],
         "parallelism": "replicas",
         "l2": "no flush: populations 2 x %.0f MB > 129 MB L2" % (19 * 4 * wl.n_nodes / 1e6),
     }
@@ -346,7 +352,7 @@ def run_ours(args):
     tag = (f"{wl.nx}cubed" if wl.nx == wl.ny == wl.nz else f"{wl.nx}x{wl.ny}x{wl.nz}") + (
         f"_{len(wl.cells)}cells" if args.workload == "suspension" else "")
     tag = ("suspension_" if args.workload == "suspension" else "") + tag
-    traffic = traffic_record(dom, tag)
+    traffic = traffic_record(dom, tag) if wl.delta == 2 else None
     step_ms_profiled = float(sum(kms))
     out = {
         "metric": METRIC,
@@ -438,10 +444,10 @@ def run_reference(args):
         L.ora_tet_force(t0, t1, ip(mesh.tets), dp(mesh.B), dp(mesh.V0), dp(u), ip(cell), dp(mesh.mu),
                         dp(mesh.kappa), dp(mesh.w), dp(fc), None)
         L.ora_gather(v0, v1, ip(mesh.ptr), ip(mesh.idx), dp(fc), dp(fv))
-        L.ora_spread(v0, v1, dp(sim.y), dp(fv), wl.nx, wl.ny, wl.nz, dp(sim.Fn))
+        L.ora_spread(v0, v1, dp(sim.y), dp(fv), wl.nx, wl.ny, wl.nz, wl.delta, dp(sim.Fn))
         L.ora_lbm_step(wl.nx, wl.ny, wl.nz, wl.tau, wl.u_wall_lo, wl.u_wall_hi, dp(fl.g), dp(fl.f), dp(sim.Fn),
                        dp(fout), dp(fl.rho), dp(fl.u), n0, n1)
-        L.ora_interp(v0, v1, dp(sim.y), dp(fl.u), wl.nx, wl.ny, wl.nz, dp(vel))
+        L.ora_interp(v0, v1, dp(sim.y), dp(fl.u), wl.nx, wl.ny, wl.nz, wl.delta, dp(vel))
         sim.y[v0:v1] += vel[v0:v1]
 
     t = time.perf_counter()

@@ -75,6 +75,20 @@ void cf_destroy(cf_ctx *ctx);
 enum { CF_POP_F32 = 0, CF_POP_F16 = 1, CF_POP_BF16 = 2 };
 cf_status cf_set_population_format(cf_ctx *ctx, int32_t format);
 
+/* Immersed-boundary delta kernel for the spreading of vertex forces and the
+ * interpolation of the fluid velocity (the paper does not name its kernel),
+ * from the next cf_lbm_init on: delta_h(r) = phi(r_x) phi(r_y) phi(r_z) with
+ *   CF_DELTA_TRILINEAR (2): phi(r) = max(0, 1 - |r|), 2 nodes per axis;
+ *   CF_DELTA_PESKIN4   (4): Peskin's four-point kernel (Acta Numerica 2002),
+ *     phi(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4r^2))/8 for |r| <= 1,
+ *              (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2))/8 for 1 <= |r| <= 2,
+ *     4 nodes per axis.
+ * The value is the support width. Every support node must lie in
+ * 0 <= y <= ny-1 (else CF_EDOMAIN from the step). Default
+ * CF_DELTA_TRILINEAR. Errors: CF_EINVAL for any other value. */
+enum { CF_DELTA_TRILINEAR = 2, CF_DELTA_PESKIN4 = 4 };
+cf_status cf_set_delta(cf_ctx *ctx, int32_t kernel);
+
 /* Lattice-Boltzmann fluid on nx*ny*nz nodes (Sec. 6.1 box), D3Q19 BGK with
  * relaxation time tau (> 1/2), Guo forcing, halfway bounce-back walls at
  * y = -1/2 moving at (u_wall_lo_x, 0, 0) and y = ny-1/2 moving at

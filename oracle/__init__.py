@@ -53,9 +53,11 @@ def lib():
         L.ora_csr.argtypes = [ctypes.c_int32, ctypes.c_int32, _i, _i, _i]
         L.ora_tet_force.argtypes = [ctypes.c_int32, ctypes.c_int32, _i, _d, _d, _d, _i, _d, _d, _d, _d, _d]
         L.ora_gather.argtypes = [ctypes.c_int32, ctypes.c_int32, _i, _i, _d, _d]
-        L.ora_spread.argtypes = [ctypes.c_int32, ctypes.c_int32, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d]
+        L.ora_spread.argtypes = [ctypes.c_int32, ctypes.c_int32, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, _d]
         L.ora_spread.restype = ctypes.c_int
-        L.ora_interp.argtypes = [ctypes.c_int32, ctypes.c_int32, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d]
+        L.ora_interp.argtypes = [ctypes.c_int32, ctypes.c_int32, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, _d]
         L.ora_interp.restype = ctypes.c_int
         L.ora_lbm_velocities.argtypes = [_i, _d]
         L.ora_lbm_equilibrium.argtypes = [ctypes.c_int64, ctypes.c_double, _d, _d]
@@ -189,21 +191,29 @@ class DomainError(ValueError):
     pass
 
 
-def spread(y, f, nx, ny, nz, out=None):
+def _width(width):
+    if width not in (2, 4):
+        raise ValueError("delta support width must be 2 (trilinear) or 4 (Peskin four-point)")
+    return width
+
+
+def spread(y, f, nx, ny, nz, out=None, width=2):
+    """F(x) += sum_v f_v delta_h(x - y_v), delta of support width 2 or 4."""
     y, f = _f64(y), _f64(f)
     Fn = np.zeros((nz, ny, nx, 3)) if out is None else out
-    bad = lib().ora_spread(0, len(y), _p(y), _p(f), nx, ny, nz, _p(Fn))
+    bad = lib().ora_spread(0, len(y), _p(y), _p(f), nx, ny, nz, _width(width), _p(Fn))
     if bad:
         raise DomainError(f"{bad} vertices have delta support outside the walls")
     return Fn
 
 
-def interp(y, ufield):
+def interp(y, ufield, width=2):
+    """v(y_v) = sum_x u(x) delta_h(x - y_v), delta of support width 2 or 4."""
     y = _f64(y)
     ufield = _f64(ufield)
     nz, ny, nx, _ = ufield.shape
     v = np.zeros((len(y), 3))
-    bad = lib().ora_interp(0, len(y), _p(y), _p(ufield), nx, ny, nz, _p(v))
+    bad = lib().ora_interp(0, len(y), _p(y), _p(ufield), nx, ny, nz, _width(width), _p(v))
     if bad:
         raise DomainError(f"{bad} vertices have delta support outside the walls")
     return v
@@ -260,6 +270,7 @@ class Coupled:
         self.y = np.concatenate([_f64(c.y0) for c in wl.cells]) if wl.cells else np.zeros((0, 3))
         self.Fn = np.zeros((wl.nz, wl.ny, wl.nx, 3))
         self.last_forces = np.zeros_like(self.y)
+        self.width = getattr(wl, "delta", 2)
 
     def step(self, n=1):
         fl = self.fluid
@@ -268,8 +279,8 @@ class Coupled:
             if self.mesh is not None:
                 fv = self.mesh.forces(self.y)                       # 1. elastic forces at y^t
                 self.last_forces = fv
-                spread(self.y, fv, fl.nx, fl.ny, fl.nz, out=self.Fn)  # 2. F(t)
+                spread(self.y, fv, fl.nx, fl.ny, fl.nz, out=self.Fn, width=self.width)  # 2. F(t)
             fl.step(self.Fn)                                         # 3. LB step, u(t)
             if self.mesh is not None:
-                v = interp(self.y, fl.u)                            # 4. u(t) at y^t
+                v = interp(self.y, fl.u, width=self.width)          # 4. u(t) at y^t
                 self.y = self.y + v                                  # 5. y^{t+1}

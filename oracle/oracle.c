@@ -20,7 +20,8 @@
  * step order) the readings are:
  *   D3Q19, BGK with relaxation time tau, Guo forcing, halfway bounce-back with
  *   a moving-wall term (rho_0 = 1), walls half a spacing outside rows y = 0
- *   and y = ny-1, periodic x and z; trilinear two-point delta kernel.
+ *   and y = ny-1, periodic x and z; trilinear two-point delta kernel, or
+ *   Peskin's four-point kernel as the alternative.
  *
  * Parity pins for every function live in the non-GPU tests.
  */
@@ -237,15 +238,30 @@ void ora_gather(int32_t v0, int32_t v1, const int32_t *ptr, const int32_t *idx,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Immersed boundary (Sec. 6; kernel not given in the paper): trilinear       */
-/* two-point delta, delta_h(r) = phi(r_x) phi(r_y) phi(r_z),                  */
-/* phi(r) = max(0, 1 - |r|). Its support around a point y is the 8 nodes      */
-/* floor(y) + {0,1}^3; x and z wrap periodically, y must stay in [0, ny-1].   */
+/* Immersed boundary (Sec. 6; kernel not given in the paper): a separable    */
+/* delta_h(r) = phi(r_x) phi(r_y) phi(r_z) of support width 2 or 4 nodes per  */
+/* axis:                                                                      */
+/*   width 2, trilinear: phi(r) = max(0, 1 - |r|);                            */
+/*   width 4, Peskin's four-point kernel (Acta Numerica 2002, Sec. 6):        */
+/*     phi(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4 r^2)) / 8    for |r| <= 1,      */
+/*              (5 - 2|r| - sqrt(-7 + 12|r| - 4 r^2)) / 8  for 1 <= |r| <= 2, */
+/*              0 otherwise.                                                  */
+/* The support of a point p on one axis is the nodes floor(p) - (width/2 - 1) */
+/* + {0, .., width-1}; x and z wrap periodically, y must stay in [0, ny-1].   */
 /* ------------------------------------------------------------------------ */
-static double phi(double r) {
+static double phi2(double r) {
     r = fabs(r);
     return r < 1.0 ? 1.0 - r : 0.0;
 }
+
+static double phi4(double r) {
+    r = fabs(r);
+    if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r)) / 8.0;
+    if (r <= 2.0) return (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r)) / 8.0;
+    return 0.0;
+}
+
+static double phi(double r, int width) { return width == 4 ? phi4(r) : phi2(r); }
 
 static int wrap(int i, int n) {
     int m = i % n;
@@ -255,17 +271,18 @@ static int wrap(int i, int n) {
 /* F(x) += sum_v f_v delta_h(x - y_v). Returns the number of vertices whose  */
 /* support leaves 0 <= y <= ny-1 (those are skipped).                         */
 int ora_spread(int32_t v0, int32_t v1, const double *y, const double *f,
-               int nx, int ny, int nz, double *Fn) {
+               int nx, int ny, int nz, int width, double *Fn) {
     int bad = 0;
     for (int32_t v = v0; v < v1; ++v) {
         const double *p = y + 3 * v;
-        int bx = (int)floor(p[0]), by = (int)floor(p[1]), bz = (int)floor(p[2]);
-        if (by < 0 || by + 1 > ny - 1) { ++bad; continue; }
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
+        int lo = width / 2 - 1;
+        int bx = (int)floor(p[0]) - lo, by = (int)floor(p[1]) - lo, bz = (int)floor(p[2]) - lo;
+        if (by < 0 || by + width - 1 > ny - 1) { ++bad; continue; }
+        for (int dz = 0; dz < width; ++dz)
+            for (int dy = 0; dy < width; ++dy)
+                for (int dx = 0; dx < width; ++dx) {
                     int X = bx + dx, Y = by + dy, Z = bz + dz;
-                    double d = phi(X - p[0]) * phi(Y - p[1]) * phi(Z - p[2]);
+                    double d = phi(X - p[0], width) * phi(Y - p[1], width) * phi(Z - p[2], width);
                     size_t n = (size_t)wrap(X, nx) + (size_t)nx * ((size_t)Y + (size_t)ny * (size_t)wrap(Z, nz));
                     for (int i = 0; i < 3; ++i) Fn[3 * n + i] += d * f[3 * v + i];
                 }
@@ -275,20 +292,21 @@ int ora_spread(int32_t v0, int32_t v1, const double *y, const double *f,
 
 /* v(y_v) = sum_x u(x) delta_h(x - y_v). Same support rule as ora_spread.    */
 int ora_interp(int32_t v0, int32_t v1, const double *y, const double *un,
-               int nx, int ny, int nz, double *vel) {
+               int nx, int ny, int nz, int width, double *vel) {
     int bad = 0;
     for (int32_t v = v0; v < v1; ++v) {
         const double *p = y + 3 * v;
-        int bx = (int)floor(p[0]), by = (int)floor(p[1]), bz = (int)floor(p[2]);
+        int lo = width / 2 - 1;
+        int bx = (int)floor(p[0]) - lo, by = (int)floor(p[1]) - lo, bz = (int)floor(p[2]) - lo;
         double s[3] = {0.0, 0.0, 0.0};
-        if (by < 0 || by + 1 > ny - 1) {
+        if (by < 0 || by + width - 1 > ny - 1) {
             ++bad;
         } else {
-            for (int dz = 0; dz < 2; ++dz)
-                for (int dy = 0; dy < 2; ++dy)
-                    for (int dx = 0; dx < 2; ++dx) {
+            for (int dz = 0; dz < width; ++dz)
+                for (int dy = 0; dy < width; ++dy)
+                    for (int dx = 0; dx < width; ++dx) {
                         int X = bx + dx, Y = by + dy, Z = bz + dz;
-                        double d = phi(X - p[0]) * phi(Y - p[1]) * phi(Z - p[2]);
+                        double d = phi(X - p[0], width) * phi(Y - p[1], width) * phi(Z - p[2], width);
                         size_t n = (size_t)wrap(X, nx) + (size_t)nx * ((size_t)Y + (size_t)ny * (size_t)wrap(Z, nz));
                         for (int i = 0; i < 3; ++i) s[i] += d * un[3 * n + i];
                     }

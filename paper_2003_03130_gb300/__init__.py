@@ -46,6 +46,7 @@ def lib():
             "cf_create": ([ctypes.POINTER(vp), ctypes.c_int, vp], ctypes.c_int),
             "cf_destroy": ([vp], None),
             "cf_set_population_format": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_set_delta": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_lbm_init": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, _d], ctypes.c_int),
             "cf_mesh_init": ([vp, ctypes.c_int32, _d, ctypes.c_int32, _i, _d, _i], ctypes.c_int),
@@ -169,6 +170,17 @@ def cf_set_population_format(ctx, fmt):
     "bf16"; applies at the next cf_lbm_init."""
     fmt = POP_FORMATS.get(fmt, fmt)
     _check(ctx, lib().cf_set_population_format(ctx.handle, int(fmt)))
+
+
+CF_DELTA_TRILINEAR, CF_DELTA_PESKIN4 = 2, 4
+DELTAS = {"trilinear": CF_DELTA_TRILINEAR, "peskin4": CF_DELTA_PESKIN4}
+
+
+def cf_set_delta(ctx, kernel):
+    """``kernel``: CF_DELTA_TRILINEAR / CF_DELTA_PESKIN4 (the support width,
+    2 or 4) or "trilinear" / "peskin4"; applies at the next cf_lbm_init."""
+    kernel = DELTAS.get(kernel, kernel)
+    _check(ctx, lib().cf_set_delta(ctx.handle, int(kernel)))
 
 
 def cf_lbm_init(ctx, nx, ny, nz, tau, u_wall_lo_x, u_wall_hi_x, body_force=None):
@@ -383,6 +395,7 @@ def cf_force_param_vjp(ctx, lam):
 def load_workload(ctx, wl):
     """Set up a :class:`workloads.configs.Workload` on the device: fluid, then
     every cell with its material. Returns the cell ids."""
+    cf_set_delta(ctx, getattr(wl, "delta", CF_DELTA_TRILINEAR))
     cf_lbm_init(ctx, wl.nx, wl.ny, wl.nz, wl.tau, wl.u_wall_lo, wl.u_wall_hi, wl.body_force)
     if not wl.cells:
         return []

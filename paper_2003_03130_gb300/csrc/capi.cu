@@ -314,6 +314,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     p.gx = g ? (float)g[0] : 0.f;
     p.gy = g ? (float)g[1] : 0.f;
     p.gz = g ? (float)g[2] : 0.f;
+    p.dw = c->delta_w;
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
     CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
@@ -338,6 +339,14 @@ cf_status cf_set_population_format(cf_ctx *c, int32_t format) {
     if (format != CF_POP_F32 && format != CF_POP_F16 && format != CF_POP_BF16)
         return fail(c, CF_EINVAL, "unknown population format %d", format);
     c->pop_format = format;
+    return CF_OK;
+}
+
+cf_status cf_set_delta(cf_ctx *c, int32_t kernel) {
+    if (!c) return CF_EINVAL;
+    if (kernel != CF_DELTA_TRILINEAR && kernel != CF_DELTA_PESKIN4)
+        return fail(c, CF_EINVAL, "unknown delta kernel %d", kernel);
+    c->delta_w = kernel;
     return CF_OK;
 }
 

@@ -49,6 +49,7 @@ struct cf_ctx {
     bool lbm_ready = false;
     LbmParams lp{};
     int pop_format = POP_F32;  // storage of the populations (next cf_lbm_init)
+    int delta_w = 2;           // delta kernel support width (next cf_lbm_init)
     void *f[2] = {nullptr, nullptr};
     float *F = nullptr;
     float *vel = nullptr;  // u(t) on the force region, [3][N]

@@ -1,20 +1,26 @@
 // Immersed-boundary coupling (Sec. 6: the cell is coupled to the fluid by an
-// immersed-boundary method; the kernel is not given there). Trilinear
-// two-point delta: delta_h(r) = phi(r_x) phi(r_y) phi(r_z), phi(r) =
-// max(0, 1 - |r|), nonzero on the 8 nodes floor(y) + {0,1}^3. Every vertex,
-// interior ones included, is a coupling point (the fluid fills the cell).
+// immersed-boundary method; the kernel is not given there). Separable delta
+// kernel of support width W per axis (internal.cuh): the trilinear two-point
+// kernel (W = 2, 8 nodes per vertex) or Peskin's four-point kernel (W = 4,
+// 64 nodes per vertex). Every vertex, interior ones included, is a coupling
+// point (the fluid fills the cell).
 //
 // K2+K3 (k_gather_spread), four threads per vertex:
 //   f_v = sum of the corner forces in the vertex's incidence row, in a fixed
 //         order (strided partial sums combined by a fixed shuffle tree) -
 //         deterministic, no atomics (Sec. 3.1 defines forces per tet corner;
 //         the vertex force is their sum);
-//   F(x) += f_v delta_h(x - y_v) on the 8 support nodes (float atomics:
-//         the spread field is exact up to the order of those additions).
+//   F(x) += f_v delta_h(x - y_v) on the W^3 support nodes: for W = 2 lane
+//         (dz, dy) takes the two nodes of its x row, for W = 4 lane dz the
+//         16 nodes of its z plane (float atomics: the spread field is exact
+//         up to the order of those additions).
 // K5 (k_interp_advect), eight threads per vertex:
 //   y^{t+1} = y^t + sum_x u(x) delta_h(x - y^t), with u(t) as stored by the
 //   near-field stream-collide on every node of the force region (which holds
-//   the support of y^t).
+//   the support of y^t); each lane sums W^3 / 8 nodes in a fixed order (for
+//   W = 2 lane (dz, dy, dx) its node, for W = 4 lane (dz, j) the rows
+//   dy = 2j, 2j + 1 of plane dz = 0..3) and the eight partial sums meet in a
+//   fixed shuffle tree.
 #include <climits>
 
 #include "internal.cuh"
@@ -41,38 +47,45 @@ __device__ __forceinline__ void box_accumulate(int (&v)[6], int *slot) {
     }
 }
 
-// Support nodes of one vertex as a box: wrapped x/z pairs, y pair.
+// Support nodes of one vertex as a box: x and z wrapped (a support across
+// the periodic seam covers the whole axis), y as is.
+template <int W>
 __device__ __forceinline__ void support_box(const Support &s, const LbmParams &p, int (&v)[6]) {
-    const int X0 = wrapi(s.bx, p.nx), X1 = wrapi(s.bx + 1, p.nx);
-    const int Z0 = wrapi(s.bz, p.nz), Z1 = wrapi(s.bz + 1, p.nz);
-    v[0] = min(X0, X1);
+    const int X0 = wrapi(s.bx, p.nx), Z0 = wrapi(s.bz, p.nz);
+    const bool sx = X0 + W - 1 > p.nx - 1, sz = Z0 + W - 1 > p.nz - 1;
+    v[0] = sx ? 0 : X0;
     v[1] = s.by;
-    v[2] = min(Z0, Z1);
-    v[3] = -max(X0, X1);
-    v[4] = -(s.by + 1);
-    v[5] = -max(Z0, Z1);
+    v[2] = sz ? 0 : Z0;
+    v[3] = -(sx ? p.nx - 1 : X0 + W - 1);
+    v[4] = -(s.by + W - 1);
+    v[5] = -(sz ? p.nz - 1 : Z0 + W - 1);
 }
 
+template <int W>
 __global__ void __launch_bounds__(256) k_support_box(MeshView m, const float4 *__restrict__ u, LbmParams p,
                                                      int *box_out) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX};
     Support s;
-    if (v < m.V && support_of(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) support_box(s, p, b);
+    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) support_box<W>(s, p, b);
     box_accumulate(b, box_out);
 }
 
 cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmParams &p, int *box_out,
                                cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
-    k_support_box<<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, box_out);
+    if (p.dw == 4)
+        k_support_box<4><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, box_out);
+    else
+        k_support_box<2><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, box_out);
     return cudaGetLastError();
 }
 
 // Four lanes per vertex: lane k sums the entries k, k+4, k+8, ... of the
 // incidence row, the four partial sums are combined by a fixed shuffle tree
-// (the same order every call: deterministic), and lane k spreads onto the
-// support nodes 2k and 2k+1.
+// (the same order every call: deterministic), and lane k spreads onto its
+// share of the support nodes.
+template <int W>
 __global__ void __launch_bounds__(128) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
                                                        int do_spread, unsigned *err, int *box_out,
                                                        const int *__restrict__ box_in) {
@@ -104,26 +117,53 @@ __global__ void __launch_bounds__(128) k_gather_spread(MeshView m, const float4 
         }
         Support s;
         if (!do_spread) {
-        } else if (!support_of(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+        } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
             if (lane == 0) atomicOr(err, ERR_DOMAIN);
         } else {
-            support_box(s, p, b);
+            support_box<W>(s, p, b);
             if (box_in && lane == 0) {
                 const NodeBox r = region_of(box_in, p.nx, p.ny, p.nz);
                 if (!(in_region(r, -b[3], -b[4], -b[5], p.nx, p.nz) && in_region(r, b[0], b[1], b[2], p.nx, p.nz)))
                     atomicOr(err, ERR_MOVED);
             }
             const int N = (int)p.N;
-            const int dz = lane >> 1, dy = lane & 1;
-            const int Z = wrapi(s.bz + dz, p.nz);
-            const float wyz = (dy ? s.fy : 1.f - s.fy) * (dz ? s.fz : 1.f - s.fz);
+            float wx[W], wy[W], wz[W];
+            delta_weights<W>(s.fx, wx);
+            delta_weights<W>(s.fy, wy);
+            delta_weights<W>(s.fz, wz);
+            if constexpr (W == 2) {  // lane = (dz, dy), two nodes along x
+                const int dz = lane >> 1, dy = lane & 1;
+                const int Z = wrapi(s.bz + dz, p.nz);
+                const float wyz = wy[dy] * wz[dz];
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
-                const float w = (dx ? s.fx : 1.f - s.fx) * wyz;
-                atomicAdd(F + n, w * fx);
-                atomicAdd(F + N + n, w * fy);
-                atomicAdd(F + 2 * N + n, w * fz);
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
+                    const float w = wx[dx] * wyz;
+                    atomicAdd(F + n, w * fx);
+                    atomicAdd(F + N + n, w * fy);
+                    atomicAdd(F + 2 * N + n, w * fz);
+                }
+            } else {  // lane = dz, a W x W plane
+                const int Z = wrapi(s.bz + lane, p.nz);
+                float wzl = wz[0];
+#pragma unroll
+                for (int k = 1; k < W; ++k) wzl = lane == k ? wz[k] : wzl;  // no local-memory indexing
+                int X[W];
+#pragma unroll
+                for (int dx = 0; dx < W; ++dx) X[dx] = wrapi(s.bx + dx, p.nx);
+#pragma unroll
+                for (int dy = 0; dy < W; ++dy) {
+                    const int row = p.nx * (s.by + dy + p.ny * Z);
+                    const float wyz = wy[dy] * wzl;
+#pragma unroll
+                    for (int dx = 0; dx < W; ++dx) {
+                        const int n = X[dx] + row;
+                        const float w = wx[dx] * wyz;
+                        atomicAdd(F + n, w * fx);
+                        atomicAdd(F + N + n, w * fy);
+                        atomicAdd(F + 2 * N + n, w * fz);
+                    }
+                }
             }
         }
     }
@@ -136,17 +176,22 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, c
     LbmParams p{};
     if (lp) p = *lp;
     const long long threads = 4LL * m.V;
-    k_gather_spread<<<(int)((threads + 127) / 128), 128, 0, s>>>(m, u, F, p, (F && lp) ? 1 : 0, err, box_out, box_in);
+    const int blocks = (int)((threads + 127) / 128), spread = (F && lp) ? 1 : 0;
+    if (p.dw == 4)
+        k_gather_spread<4><<<blocks, 128, 0, s>>>(m, u, F, p, spread, err, box_out, box_in);
+    else
+        k_gather_spread<2><<<blocks, 128, 0, s>>>(m, u, F, p, spread, err, box_out, box_in);
     return cudaGetLastError();
 }
 
-// Eight threads per vertex, one per support node; the group of eight sums
-// its contributions with shuffles.
+// Eight threads per vertex, each summing W^3 / 8 support nodes; the group of
+// eight combines its partial sums with shuffles.
+template <int W>
 __global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
                                                        unsigned *err) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = g >> 3, corner = g & 7;
+    const int v = g >> 3, lane = g & 7;
     const bool live = v < m.V;
     float4 uc = make_float4(0.f, 0.f, 0.f, 0.f);
     float vx = 0.f, vy = 0.f, vz = 0.f;
@@ -154,15 +199,38 @@ __global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *
     if (live) {
         uc = __ldg(u_cur + v);
         Support s;
-        ok = support_of(m.origin, __ldg(m.xr + v), uc, p.ny, s);
+        ok = support_of<W>(m.origin, __ldg(m.xr + v), uc, p.ny, s);
         if (ok) {
-            const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
             const int N = (int)p.N;
-            const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * wrapi(s.bz + dz, p.nz));
-            const float w = (dx ? s.fx : 1.f - s.fx) * (dy ? s.fy : 1.f - s.fy) * (dz ? s.fz : 1.f - s.fz);
-            vx = w * __ldg(vel + n);
-            vy = w * __ldg(vel + N + n);
-            vz = w * __ldg(vel + 2 * N + n);
+            float wx[W], wy[W], wz[W];
+            delta_weights<W>(s.fx, wx);
+            delta_weights<W>(s.fy, wy);
+            delta_weights<W>(s.fz, wz);
+            if constexpr (W == 2) {  // lane = corner (dx, dy, dz)
+                const int dx = lane & 1, dy = (lane >> 1) & 1, dz = lane >> 2;
+                const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * wrapi(s.bz + dz, p.nz));
+                const float w = wx[dx] * wy[dy] * wz[dz];
+                vx = w * __ldg(vel + n);
+                vy = w * __ldg(vel + N + n);
+                vz = w * __ldg(vel + 2 * N + n);
+            } else {  // lane = (dz, row pair): plane dz = lane >> 1, rows dy = 2 (lane & 1) + {0, 1}
+                const int dz = lane >> 1, dy0 = 2 * (lane & 1);
+                const int Z = wrapi(s.bz + dz, p.nz);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int dy = dy0 + j;
+                    const int row = p.nx * (s.by + dy + p.ny * Z);
+                    const float wyz = wy[dy] * wz[dz];
+#pragma unroll
+                    for (int dx = 0; dx < W; ++dx) {
+                        const int n = wrapi(s.bx + dx, p.nx) + row;
+                        const float w = wx[dx] * wyz;
+                        vx = fmaf(w, __ldg(vel + n), vx);
+                        vy = fmaf(w, __ldg(vel + N + n), vy);
+                        vz = fmaf(w, __ldg(vel + 2 * N + n), vz);
+                    }
+                }
+            }
         }
     }
 #pragma unroll
@@ -171,7 +239,7 @@ __global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *
         vy += __shfl_xor_sync(0xffffffffu, vy, o);
         vz += __shfl_xor_sync(0xffffffffu, vz, o);
     }
-    if (!live || corner != 0) return;
+    if (!live || lane != 0) return;
     if (!ok) {
         atomicOr(err, ERR_DOMAIN);
         u_next[v] = uc;
@@ -186,7 +254,11 @@ cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmP
                                  float4 *u_next, unsigned *err, cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
     const long long threads = 8LL * m.V;
-    k_interp_advect<<<(int)((threads + 127) / 128), 128, 0, s>>>(m, vel, p, u_cur, u_next, err);
+    const int blocks = (int)((threads + 127) / 128);
+    if (p.dw == 4)
+        k_interp_advect<4><<<blocks, 128, 0, s>>>(m, vel, p, u_cur, u_next, err);
+    else
+        k_interp_advect<2><<<blocks, 128, 0, s>>>(m, vel, p, u_cur, u_next, err);
     return cudaGetLastError();
 }
 

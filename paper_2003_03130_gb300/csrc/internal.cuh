@@ -63,6 +63,7 @@ struct LbmParams {
     float guo;          // 1 - 1/(2 tau)
     float uw_lo, uw_hi; // wall x velocities at y = -1/2 and y = ny - 1/2
     float gx, gy, gz;   // uniform body-force density
+    int dw;             // delta kernel: support width 2 (trilinear) or 4 (Peskin)
 };
 
 struct MeshView {
@@ -80,18 +81,26 @@ struct MeshView {
     float4 *fv;            // [V]: vertex force
 };
 
-// Trilinear delta support of a vertex at x + u: lower corner (absolute node,
-// x and z not yet wrapped) and fractional offsets. False if the position is
-// not finite, absurdly far away, or the support leaves 0 <= y <= ny-1. Shared
-// by the spread, the interpolation and the clearing of F so that all three
-// see exactly the same node set.
+// Delta kernels delta_h(r) = phi(r_x) phi(r_y) phi(r_z) of support width W
+// (nodes per axis):
+//   W = 2, trilinear:  phi(r) = max(0, 1 - |r|);
+//   W = 4, Peskin's four-point kernel (C. S. Peskin, The immersed boundary
+//          method, Acta Numerica 11, 2002, Sec. 6):
+//          phi(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4r^2)) / 8   for |r| <= 1,
+//                   (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2)) / 8  for 1 <= |r| <= 2,
+//                   0 beyond.
+// The support of a point p on one axis is the W nodes lo + k, k = 0..W-1,
+// with lo = floor(p) - (W/2 - 1). Shared by the spread, the interpolation
+// and the clearing of F so that all three see exactly the same node set.
 struct Support {
-    int bx, by, bz;
-    float fx, fy, fz;
+    int bx, by, bz;     // lower corner lo (absolute node, x and z not yet wrapped)
+    float fx, fy, fz;   // p - floor(p) per axis, in [0, 1)
 };
 
-__device__ __forceinline__ bool support_of(const int *__restrict__ origin, float4 xr, float4 u, int ny,
-                                           Support &s) {
+// False if the position is not finite, absurdly far away, or the support
+// leaves 0 <= y <= ny-1.
+template <int W>
+__device__ __forceinline__ bool support_of(const int *__restrict__ origin, float4 xr, float4 u, int ny, Support &s) {
     const int c = __float_as_int(xr.w);
     const float px = xr.x + u.x, py = xr.y + u.y, pz = xr.z + u.z;
     if (!(fabsf(px) < 1e6f && fabsf(py) < 1e6f && fabsf(pz) < 1e6f)) return false;  // also NaN
@@ -99,10 +108,29 @@ __device__ __forceinline__ bool support_of(const int *__restrict__ origin, float
     s.fx = px - lx;
     s.fy = py - ly;
     s.fz = pz - lz;
-    s.bx = (int)lx + __ldg(origin + 3 * c + 0);
-    s.by = (int)ly + __ldg(origin + 3 * c + 1);
-    s.bz = (int)lz + __ldg(origin + 3 * c + 2);
-    return s.by >= 0 && s.by + 1 <= ny - 1;
+    s.bx = (int)lx + __ldg(origin + 3 * c + 0) - (W / 2 - 1);
+    s.by = (int)ly + __ldg(origin + 3 * c + 1) - (W / 2 - 1);
+    s.bz = (int)lz + __ldg(origin + 3 * c + 2) - (W / 2 - 1);
+    return s.by >= 0 && s.by + W - 1 <= ny - 1;
+}
+
+// One-axis weights phi(p - (lo + k)), k = 0..W-1, from f = p - floor(p).
+// For W = 4 the distances are 1 + f, f, 1 - f, 2 - f, and both branches of
+// phi reduce to the same root q = sqrt(1 + 4f - 4f^2).
+template <int W>
+__device__ __forceinline__ void delta_weights(float f, float (&w)[W]);
+template <>
+__device__ __forceinline__ void delta_weights<2>(float f, float (&w)[2]) {
+    w[0] = 1.f - f;
+    w[1] = f;
+}
+template <>
+__device__ __forceinline__ void delta_weights<4>(float f, float (&w)[4]) {
+    const float q = sqrtf(fmaf(4.f * f, 1.f - f, 1.f));
+    w[0] = 0.125f * (3.f - 2.f * f - q);
+    w[1] = 0.125f * (3.f - 2.f * f + q);
+    w[2] = 0.125f * (1.f + 2.f * f + q);
+    w[3] = 0.125f * (1.f + 2.f * f - q);
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {

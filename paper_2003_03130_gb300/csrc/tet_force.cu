@@ -6,30 +6,39 @@
 
 namespace cf {
 
+// Zero the force field on the delta support of x + u_prev: every nonzero
+// entry of F was spread there in the previous step.
+template <int W>
+__device__ __forceinline__ void clear_support(const MeshView &m, const float4 *__restrict__ u_prev, float *F,
+                                              const LbmParams &lp, int v) {
+    Support sp;
+    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u_prev + v), lp.ny, sp)) return;  // nothing was spread
+    const int N = (int)lp.N;
+#pragma unroll
+    for (int dz = 0; dz < W; ++dz) {
+        const int Z = wrapi(sp.bz + dz, lp.nz);
+#pragma unroll
+        for (int dy = 0; dy < W; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < W; ++dx) {
+                const int n = wrapi(sp.bx + dx, lp.nx) + lp.nx * (sp.by + dy + lp.ny * Z);
+                F[n] = 0.f;
+                F[N + n] = 0.f;
+                F[2 * N + n] = 0.f;
+            }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
                                                    int tet_blocks, const float4 *__restrict__ u_prev,
                                                    float *__restrict__ F, LbmParams lp) {
     if ((int)blockIdx.x >= tet_blocks) {
-        // Zero the force field on the delta support of x + u_prev: every
-        // nonzero entry of F was spread there in the previous step.
         const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
         if (v >= m.V) return;
-        Support sp;
-        if (!support_of(m.origin, __ldg(m.xr + v), __ldg(u_prev + v), lp.ny, sp)) return;  // nothing was spread
-        const int N = (int)lp.N;
-#pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-            const int Z = wrapi(sp.bz + dz, lp.nz);
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int n = wrapi(sp.bx + dx, lp.nx) + lp.nx * (sp.by + dy + lp.ny * Z);
-                    F[n] = 0.f;
-                    F[N + n] = 0.f;
-                    F[2 * N + n] = 0.f;
-                }
-        }
+        if (lp.dw == 4)
+            clear_support<4>(m, u_prev, F, lp, v);
+        else
+            clear_support<2>(m, u_prev, F, lp, v);
         return;
     }
     const int t = blockIdx.x * blockDim.x + threadIdx.x;

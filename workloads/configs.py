@@ -46,6 +46,7 @@ class Workload:
     body_force: tuple = (0.0, 0.0, 0.0)
     cells: list = field(default_factory=list)
     steps: int = 100
+    delta: int = 2  # immersed-boundary delta kernel: support width 2 (trilinear) or 4 (Peskin four-point)
 
     @property
     def n_nodes(self) -> int:
