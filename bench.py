@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--box", default="512,256,256", help="lattice of the suspension workload")
     ap.add_argument("--delta", choices=("trilinear", "peskin4"), default="trilinear",
                     help="immersed-boundary delta kernel")
+    ap.add_argument("--autotune-steps", type=int, default=20,
+                    help="steps per launch-shape candidate of the autotuner in the warm-up (0: default shape)")
     ap.add_argument("--ca", type=float, default=0.2)
     ap.add_argument("--w", type=float, default=0.5)
     ap.add_argument("--profile-steps", type=int, default=2000)
@@ -289,6 +291,7 @@ def run_ours(args):
         ctx = P.cf_create(dev, stream.cuda_stream)
         ids = P.load_workload(ctx, wl)
         P.cf_step(ctx, W)
+        shape = P.cf_autotune(ctx, args.autotune_steps) if args.autotune_steps > 0 else P.cf_get_launch_shape(ctx)
         P.cf_prepare_steps(ctx, K)  # graph instantiation stays out of the timed region
         barrier()
         torch.cuda.synchronize(dev)
@@ -371,6 +374,7 @@ def run_ours(args):
         "mlups": job_rate(wl.n_nodes * K, world, ms / 1e3) / 1e6,
         "tet_forces_per_s": job_rate(wl.n_tets * K, world, ms / 1e3),
         "gpu_launches": 5 * K + 1,
+        "launch_shape": shape,
         "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
         "kernel_share": dict(zip(KERNELS, [float(x) / step_ms_profiled for x in kms])),
         "roofline": {

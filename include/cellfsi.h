@@ -163,6 +163,35 @@ cf_status cf_synchronize(cf_ctx *ctx);
  * Synchronises; returns the first device error. */
 cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *near_nodes);
 
+/* Launch shapes of the step kernels, as CF_SHAPE_LEN int32 values:
+ *   [0..2] x, y, z extent in nodes of the force-region tiles: 16x4x4
+ *          (default), 32x4x2, 32x2x4 or 8x8x4 (the lattice is cut into tiles;
+ *          the near-field stream-collide updates the tiles that meet a
+ *          vertex's delta support, the far field the others);
+ *   [3]    threads per block of the tet-force kernel (default 64);
+ *   [4]    threads per block of the vertex-sum + spread kernel (default 128);
+ *   [5]    threads per block of the interpolation kernel (default 128);
+ *   [6]    blocks of the near-field stream-collide (default 5 per SM).
+ * Block sizes are multiples of 32 in [32, 256]; near blocks in [1, 65535].
+ * No shape changes a computed value beyond the rounding order of the spread
+ * (float atomics). cf_set_launch_shape applies from the next cf_step call;
+ * CF_EINVAL for a value outside these sets. */
+#define CF_SHAPE_LEN 7
+cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
+cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
+
+/* Autotuner: picks the launch shape by timing the step kernels on the
+ * context's own state. One knob at a time (tile shape, near-field blocks,
+ * tet-force, spread and interpolation block sizes), every candidate runs
+ * steps_per_candidate (>= 1) coupled steps with CUDA events around each
+ * kernel, and the candidate with the least summed time of the kernels the
+ * knob shapes is kept. The simulation advances by those steps exactly as
+ * under cf_step (18 candidates in all). A fluid-only context has nothing to
+ * tune and does not advance. shape_out (may be NULL) receives the chosen
+ * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
+ * of the steps as cf_step. */
+cf_status cf_autotune(cf_ctx *ctx, int32_t steps_per_candidate, int32_t *shape_out);
+
 /* Elastic vertex forces at the current positions only (Sec. 3.1 per tet,
  * summed per vertex), without touching the fluid. */
 cf_status cf_compute_forces(cf_ctx *ctx);

@@ -56,6 +56,9 @@ def lib():
             "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_prepare_steps": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_get_launch_shape": ([vp, _i], ctypes.c_int),
+            "cf_set_launch_shape": ([vp, _i], ctypes.c_int),
+            "cf_autotune": ([vp, ctypes.c_int32, _i], ctypes.c_int),
             "cf_synchronize": ([vp], ctypes.c_int),
             "cf_compute_forces": ([vp], ctypes.c_int),
             "cf_step_profiled": ([vp, ctypes.c_int32, _d, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -237,6 +240,39 @@ def cf_step_async(ctx, n: int = 1):
 def cf_prepare_steps(ctx, n: int):
     """Instantiate the step graphs an n-step call would use, without running."""
     _check(ctx, lib().cf_prepare_steps(ctx.handle, n))
+
+
+CF_SHAPE_LEN = 7
+SHAPE_KEYS = ("tile_x", "tile_y", "tile_z", "tet_block", "gather_block", "interp_block", "near_blocks")
+
+
+def cf_get_launch_shape(ctx):
+    """The launch shape as a dict over SHAPE_KEYS."""
+    out = np.zeros(CF_SHAPE_LEN, np.int32)
+    _check(ctx, lib().cf_get_launch_shape(ctx.handle, _p(out, _i)))
+    return dict(zip(SHAPE_KEYS, (int(v) for v in out)))
+
+
+def cf_set_launch_shape(ctx, shape):
+    """``shape``: a dict over SHAPE_KEYS (missing keys keep their value) or
+    CF_SHAPE_LEN ints; applies from the next step call."""
+    if isinstance(shape, dict):
+        cur = cf_get_launch_shape(ctx)
+        cur.update(shape)
+        shape = [cur[k] for k in SHAPE_KEYS]
+    arr = np.ascontiguousarray(shape, np.int32)
+    if arr.shape != (CF_SHAPE_LEN,):
+        raise ValueError(f"need {CF_SHAPE_LEN} values")
+    _check(ctx, lib().cf_set_launch_shape(ctx.handle, _p(arr, _i)))
+
+
+def cf_autotune(ctx, steps_per_candidate=20):
+    """Time the launch-shape candidates on the context's own state (the
+    simulation advances 18 x steps_per_candidate steps) and keep the
+    fastest; returns the chosen shape."""
+    out = np.zeros(CF_SHAPE_LEN, np.int32)
+    _check(ctx, lib().cf_autotune(ctx.handle, steps_per_candidate, _p(out, _i)))
+    return dict(zip(SHAPE_KEYS, (int(v) for v in out)))
 
 
 def cf_synchronize(ctx):

@@ -7,12 +7,13 @@
 //   K4  stream + collide with F, populations f[p] -> f[1-p]
 //   K5  interpolate u(t) at y^t, y^{t+1} = y^t + u  (u[p] -> u[1-p])
 // With cells present, K4 is split by a force region around the cells: the
-// far part (every node outside the region, ~all of the lattice, no force
-// read) runs on a second stream concurrently with the cell chain
+// far part (the tiles of 256 nodes outside the region, no force read) runs
+// on a second stream concurrently with the cell chain
 // K5(t-1) -> K1(t) -> K23(t); after the join the near part updates the
-// region with the force field. The region of step t is the support box of
-// y^{t-1} grown by one node (a vertex moves less than one spacing per step;
-// K23 checks this and raises CF_EUNSTABLE otherwise). A cf_step call is a
+// region's tiles with the force field. The region of step t is the set of
+// tiles that meet the delta support of y^{t-1} grown by one node (a vertex
+// moves less than one spacing per step; K23 checks that the support of y^t
+// lies in it and raises CF_EUNSTABLE otherwise). A cf_step call is a
 // "first" step graph (region from the current positions, no K5 before it),
 // n - 1 pipelined step graphs and a final K5. Populations and displacements
 // are double-buffered with one shared parity; each graph is captured once per
@@ -45,13 +46,26 @@ constexpr int kChunk = 12;
 
 enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3 };
 
-// Region slots of step t (phase s = t % 3): the step's force region is slot
-// (s + 2) % 3 (written by step t - 1, or by the support box of the current
-// positions in the first step of a call); the step accumulates the support
-// box of y^t into slot s for step t + 1. Three slots keep a slot from being
-// reset while a far-field kernel two steps back may still read it.
-int *region_slot(cf_ctx *c, int s) { return c->box + 8 * ((s + 2) % 3); }
-int *accum_slot(cf_ctx *c, int s) { return c->box + 8 * s; }
+// Region slots of step t (phase s = t % 3): the step's force region is mask
+// slot (s + 2) % 3 (marked by step t - 1, or from the current positions in
+// the first step of a call); the step marks the region of step t + 1 into
+// slot s. Three slots keep a slot from being cleared while a far-field kernel
+// two steps back may still read it.
+unsigned char *region_slot(cf_ctx *c, int s) { return c->mask + c->mask_stride * ((s + 2) % 3); }
+unsigned char *accum_slot(cf_ctx *c, int s) { return c->mask + c->mask_stride * s; }
+size_t mask_bytes(const LbmParams &p) { return (size_t)p.ntx * p.nty * p.ntz; }
+
+// Tile fields of the lattice parameters for tile shape k.
+void set_tiles(LbmParams &p, int k) {
+    p.tlx = kTileShapes[k][0];
+    p.tly = kTileShapes[k][1];
+    p.tlz = kTileShapes[k][2];
+    p.ntx = (p.nx + (1 << p.tlx) - 1) >> p.tlx;
+    p.nty = (p.ny + (1 << p.tly) - 1) >> p.tly;
+    p.ntz = (p.nz + (1 << p.tlz) - 1) >> p.tlz;
+}
+
+int near_blocks(const cf_ctx *c) { return c->shape.near_blocks > 0 ? c->shape.near_blocks : 5 * c->sms; }
 
 // Enqueue `nsteps` steps starting at parity p0 and phase s0 on two streams:
 // sf carries the far-field stream-collide, sc the cell chain and the near
@@ -63,8 +77,10 @@ int *accum_slot(cf_ctx *c, int s) { return c->box + 8 * s; }
 cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaStream_t sf, cudaStream_t sc,
                         cudaEvent_t *ev) {
     const MeshView m = view(c);
+    const Shape &sh = c->shape;
+    const size_t mb = mask_bytes(c->lp);
     if (kind == Kind::Tail) {  // K5 of the last step (parity p0)
-        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sf));
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sf, sh.interp_block));
         return CF_OK;
     }
     if (kind == Kind::Fluid) {
@@ -76,25 +92,25 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     }
     cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
     if (kind == Kind::First) {
-        int *use = region_slot(c, s0);
-        CUDA_TRY(c, cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), sf));
-        CUDA_TRY(c, launch_support_box(m, c->u[p0], c->lp, use, sf));
+        unsigned char *use = region_slot(c, s0);
+        CUDA_TRY(c, cudaMemsetAsync(use, 0, mb, sf));
+        CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, sf));
     }
     CUDA_TRY(c, cudaEventRecord(fork, sf));
     CUDA_TRY(c, cudaStreamWaitEvent(sc, fork, 0));
     for (int i = 0; i < nsteps; ++i) {
         const int p = p0 ^ (i & 1), s = (s0 + i) % 3;
-        int *use = region_slot(c, s), *acc = accum_slot(c, s);
+        unsigned char *use = region_slot(c, s), *acc = accum_slot(c, s);
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
         CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
         if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
-            CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc));
-        CUDA_TRY(c, cudaMemsetAsync(acc, 0x7f, 6 * sizeof(int), sc));
-        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc));
-        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, acc, use));
+            CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
+        CUDA_TRY(c, cudaMemsetAsync(acc, 0, mb, sc));
+        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc, sh.tet_block));
+        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, acc, use, sh.gather_block));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, sc));
+        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, sc, near_blocks(c)));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
@@ -224,6 +240,8 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
     cf_ctx *c = new cf_ctx();
     c->device = device;
     DeviceGuard g(device);
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->sms < 1)
+        c->sms = 152;
     if (const char *t = getenv("CELLFSI_TIMEOUT_S")) c->timeout_s = atof(t);
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
@@ -235,7 +253,7 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         c->own_stream = true;
     }
     if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
-        dalloc(&c->box, 24) != cudaSuccess || dalloc(&c->taylor_out, 10) != cudaSuccess ||
+        dalloc(&c->taylor_out, 10) != cudaSuccess ||
         dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
@@ -251,7 +269,7 @@ void cf_destroy(cf_ctx *c) {
     drop_graphs(c);
     dfree(c->d_err);
     dfree(c->d_status);
-    dfree(c->box);
+    dfree(c->mask);
     dfree(c->f[0]);
     dfree(c->f[1]);
     dfree(c->F);
@@ -300,6 +318,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     dfree(c->f[1]);
     dfree(c->F);
     dfree(c->vel);
+    dfree(c->mask);
     c->lbm_ready = false;
     LbmParams p{};
     p.fmt = c->pop_format;
@@ -315,11 +334,21 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     p.gy = g ? (float)g[1] : 0.f;
     p.gz = g ? (float)g[2] : 0.f;
     p.dw = c->delta_w;
+    // masks sized for the largest tile count of any tile shape
+    size_t mstride = 0;
+    for (int k = 0; k < kNumTileShapes; ++k) {
+        set_tiles(p, k);
+        mstride = std::max(mstride, mask_bytes(p));
+    }
+    set_tiles(p, c->shape.tile);
+    c->mask_stride = (mstride + 255) / 256 * 256;
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
     CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
     CUDA_TRY(c, dalloc(&c->F, 3 * (size_t)N));
     CUDA_TRY(c, dalloc(&c->vel, 3 * (size_t)N));
+    CUDA_TRY(c, dalloc(&c->mask, 3 * c->mask_stride));
+    CUDA_TRY(c, cudaMemsetAsync(c->mask, 0, 3 * c->mask_stride, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float) * 3 * (size_t)N, c->stream));
@@ -578,51 +607,57 @@ cf_status cf_step(cf_ctx *c, int32_t n) {
     return cf_synchronize(c);
 }
 
-cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *near_nodes) {
-    if (!c || !kernel_ms) return CF_EINVAL;
-    DeviceGuard dg(c->device);
-    if (n < 1) return fail(c, CF_EINVAL, "n must be >= 1");
-    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
-    // per step: [K5 of the previous step], K1, K23, far, near (or the whole
-    // lattice without cells); the final K5 is timed with the interpolations
+}  // extern "C"
+
+namespace {
+
+// n steps with the same kernels as cf_step, launched one after another on the
+// context's stream with a CUDA event pair around every kernel, in launch
+// shape sh. acc[] receives the summed milliseconds of [tet force, gather +
+// spread, far LBM, near LBM (or whole-lattice LBM without cells),
+// interpolation]; the state advances exactly as under cf_step(n).
+cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
     const int BATCH = 32, NE = 6;
     std::vector<cudaEvent_t> ev(NE * BATCH + 2);
     for (auto &e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(c, CF_ECUDA, "event create failed");
-    double acc[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < 5; ++k) acc[k] = 0.0;
     cf_status st = CF_OK;
     const MeshView m = view(c);
     const bool cells = c->T > 0;
     cudaStream_t s = c->stream;
+    const size_t mb = mask_bytes(c->lp);
+    const int nb = sh.near_blocks > 0 ? sh.near_blocks : 5 * c->sms;
     for (int done = 0; done < n && st == CF_OK;) {
         const int b = std::min(BATCH, n - done);
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < b && e == cudaSuccess; ++i) {
             const int p = c->cur, t = done + i;
             const int sph = (int)((c->tstep) % 3);
-            int *use = region_slot(c, sph), *accb = accum_slot(c, sph);
+            unsigned char *use = region_slot(c, sph), *accm = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
             if (cells && t == 0) {  // region of the first step: not timed
-                e = cudaMemsetAsync(use, 0x7f, 6 * sizeof(int), s);
-                if (e == cudaSuccess) e = launch_support_box(m, c->u[p], c->lp, use, s);
+                e = cudaMemsetAsync(use, 0, mb, s);
+                if (e == cudaSuccess) e = launch_mark_region(m, c->u[p], c->lp, use, s);
             }
             cudaEventRecord(E[0], s);
             if (cells && t > 0 && e == cudaSuccess)
-                e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s);
+                e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s, sh.interp_block);
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
-                e = cudaMemsetAsync(accb, 0x7f, 6 * sizeof(int), s);
-                if (e == cudaSuccess) e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s);
+                e = cudaMemsetAsync(accm, 0, mb, s);
+                if (e == cudaSuccess)
+                    e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block);
             }
             cudaEventRecord(E[2], s);
             if (cells && e == cudaSuccess)
-                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, accb, use);
+                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, accm, use, sh.gather_block);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
                 e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, s)
                           : launch_lbm(c->f[p], c->f[1 - p], c->lp, s);
             cudaEventRecord(E[4], s);
-            if (cells && e == cudaSuccess) e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s);
+            if (cells && e == cudaSuccess) e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s, nb);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
             c->tstep += 1;
@@ -633,7 +668,7 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
         }
         st = wait_stream(c);
         // event pairs -> [interp, tet, gather+spread, far, near]
-        const int slot[5] = {0, 1, 2, 3, 4};
+        const int slot[5] = {4, 0, 1, 2, 3};
         for (int i = 0; i < b && st == CF_OK; ++i)
             for (int k = 0; k < 5; ++k) {
                 float ms = 0.f;
@@ -645,38 +680,150 @@ cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *nea
     if (st == CF_OK && cells) {  // final K5
         const int p = c->cur ^ 1;
         cudaEventRecord(ev[NE * BATCH], s);
-        cudaError_t e = launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s);
+        cudaError_t e = launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s, sh.interp_block);
         cudaEventRecord(ev[NE * BATCH + 1], s);
         st = e == cudaSuccess ? wait_stream(c) : fail(c, CF_ECUDA, "launch failed: %s", cudaGetErrorString(e));
         float ms = 0.f;
         if (st == CF_OK) cudaEventElapsedTime(&ms, ev[NE * BATCH], ev[NE * BATCH + 1]);
-        acc[0] += ms;
-    }
-    if (st == CF_OK && near_nodes) {
-        *near_nodes = 0;
-        if (cells) {  // size of the region the last step used
-            int h[6];
-            const int *last = region_slot(c, (int)((c->tstep - 1) % 3));
-            CUDA_TRY(c, cudaMemcpyAsync(h, last, sizeof h, cudaMemcpyDeviceToHost, s));
-            st = wait_stream(c);
-            const LbmParams &p = c->lp;
-            if (st == CF_OK && h[0] <= -h[3]) {
-                const long long lx = std::min<long long>(p.nx, -h[3] - h[0] + 3);
-                const long long lz = std::min<long long>(p.nz, -h[5] - h[2] + 3);
-                const long long ly = std::min(p.ny - 1, -h[4] + 1) - std::max(0, h[1] - 1) + 1;
-                *near_nodes = lx * ly * lz;
-            }
-        }
+        acc[4] += ms;
     }
     for (auto &e : ev) cudaEventDestroy(e);
+    return st;
+}
+
+// Lattice nodes in the marked tiles of the region the last step used.
+cf_status region_nodes(cf_ctx *c, long long *out) {
+    *out = 0;
+    if (c->T == 0 || c->tstep == 0) return CF_OK;
+    const LbmParams &p = c->lp;
+    std::vector<unsigned char> h(mask_bytes(p));
+    const unsigned char *last = region_slot(c, (int)((c->tstep - 1) % 3));
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), last, h.size(), cudaMemcpyDeviceToHost, c->stream));
+    cf_status st = wait_stream(c);
     if (st != CF_OK) return st;
-    // report order: tet force, gather + spread, far LBM, near LBM, interpolation
-    kernel_ms[0] = acc[1] / n;
-    kernel_ms[1] = acc[2] / n;
-    kernel_ms[2] = acc[3] / n;
-    kernel_ms[3] = acc[4] / n;
-    kernel_ms[4] = acc[0] / n;
+    const int tx = 1 << p.tlx, ty = 1 << p.tly, tz = 1 << p.tlz;
+    for (size_t t = 0; t < h.size(); ++t) {
+        if (!h[t]) continue;
+        const int ix = (int)(t % p.ntx), iy = (int)((t / p.ntx) % p.nty), iz = (int)(t / ((size_t)p.ntx * p.nty));
+        const long long ex = std::min(tx, p.nx - ix * tx), ey = std::min(ty, p.ny - iy * ty),
+                        ez = std::min(tz, p.nz - iz * tz);
+        *out += ex * ey * ez;
+    }
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cf_status cf_step_profiled(cf_ctx *c, int32_t n, double *kernel_ms, int64_t *near_nodes) {
+    if (!c || !kernel_ms) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (n < 1) return fail(c, CF_EINVAL, "n must be >= 1");
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step needs cf_lbm_init first");
+    double acc[5];
+    cf_status st = timed_steps(c, n, c->shape, acc);
+    if (st == CF_OK && near_nodes) {
+        long long nn = 0;
+        st = region_nodes(c, &nn);
+        *near_nodes = nn;
+    }
+    if (st != CF_OK) return st;
+    for (int k = 0; k < 5; ++k) kernel_ms[k] = acc[k] / n;
     return consume_errors(c);
+}
+
+cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
+    if (!c || !shape) return CF_EINVAL;
+    const Shape &sh = c->shape;
+    shape[0] = 1 << kTileShapes[sh.tile][0];
+    shape[1] = 1 << kTileShapes[sh.tile][1];
+    shape[2] = 1 << kTileShapes[sh.tile][2];
+    shape[3] = sh.tet_block;
+    shape[4] = sh.gather_block;
+    shape[5] = sh.interp_block;
+    shape[6] = near_blocks(c);
+    return CF_OK;
+}
+
+cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
+    if (!c || !shape) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    Shape sh;
+    sh.tile = -1;
+    for (int k = 0; k < kNumTileShapes; ++k)
+        if (shape[0] == 1 << kTileShapes[k][0] && shape[1] == 1 << kTileShapes[k][1] &&
+            shape[2] == 1 << kTileShapes[k][2])
+            sh.tile = k;
+    if (sh.tile < 0)
+        return fail(c, CF_EINVAL, "tile %dx%dx%d is not one of 16x4x4, 32x4x2, 32x2x4, 8x8x4", shape[0], shape[1],
+                    shape[2]);
+    for (int k = 3; k < 6; ++k)
+        if (shape[k] < 32 || shape[k] > 256 || shape[k] % 32)
+            return fail(c, CF_EINVAL, "block size %d: need a multiple of 32 in [32, 256]", shape[k]);
+    if (shape[6] < 1 || shape[6] > 65535) return fail(c, CF_EINVAL, "near-field blocks must be in [1, 65535]");
+    sh.tet_block = shape[3];
+    sh.gather_block = shape[4];
+    sh.interp_block = shape[5];
+    sh.near_blocks = shape[6];
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
+    drop_graphs(c);
+    c->shape = sh;
+    if (c->lbm_ready) set_tiles(c->lp, sh.tile);
+    return CF_OK;
+}
+
+cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (steps_per_candidate < 1) return fail(c, CF_EINVAL, "steps_per_candidate must be >= 1");
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_autotune needs cf_lbm_init first");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    if (c->T > 0) {
+        // one knob at a time, the others at their best so far; a knob is
+        // judged by the kernels it shapes (slots of timed_steps' sums)
+        struct Knob {
+            int Shape::*field;
+            std::vector<int> cands;
+            std::vector<int> slots;
+        };
+        const Knob knobs[] = {
+            {&Shape::tile, {0, 1, 2, 3}, {1, 2, 3}},
+            {&Shape::near_blocks, {2 * c->sms, 5 * c->sms, 8 * c->sms}, {3}},
+            {&Shape::tet_block, {64, 128, 256}, {0}},
+            {&Shape::gather_block, {64, 128, 256}, {1}},
+            {&Shape::interp_block, {64, 128, 256}, {4}},
+        };
+        Shape best = c->shape;
+        if (best.near_blocks <= 0) best.near_blocks = 5 * c->sms;
+        for (const Knob &k : knobs) {
+            double tbest = 1e300;
+            int vbest = best.*k.field;
+            for (int v : k.cands) {
+                Shape sh = best;
+                sh.*k.field = v;
+                set_tiles(c->lp, sh.tile);
+                double acc[5];
+                cf_status st = timed_steps(c, steps_per_candidate, sh, acc);
+                if (st == CF_OK) st = consume_errors(c);
+                if (st != CF_OK) {
+                    set_tiles(c->lp, c->shape.tile);
+                    return st;
+                }
+                double t = 0.0;
+                for (int slot : k.slots) t += acc[slot];
+                if (t < tbest) {
+                    tbest = t;
+                    vbest = v;
+                }
+            }
+            best.*k.field = vbest;
+        }
+        c->shape = best;
+        set_tiles(c->lp, best.tile);
+    }
+    return shape_out ? cf_get_launch_shape(c, shape_out) : CF_OK;
 }
 
 cf_status cf_compute_forces(cf_ctx *c) {

@@ -26,6 +26,18 @@ struct CellInfo {
     float4 mat;
 };
 
+// Force-region tile shapes (log2 of the x, y, z extents; 256 nodes each).
+constexpr int kTileShapes[4][3] = {{4, 2, 2}, {5, 2, 1}, {5, 1, 2}, {3, 3, 2}};
+constexpr int kNumTileShapes = 4;
+
+// Launch shapes of the step kernels. None changes a computed value: every
+// kernel computes each tet, vertex or node the same way whatever its block.
+struct Shape {
+    int tile = 0;  // index into kTileShapes
+    int tet_block = 64, gather_block = 128, interp_block = 128;
+    int near_blocks = 0;  // 0: 5 blocks per SM
+};
+
 }  // namespace cf
 
 using namespace cf;
@@ -68,7 +80,11 @@ struct cf_ctx {
     double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
     double *taylor_partial = nullptr, *taylor_out = nullptr;
 
-    int *box = nullptr;  // three force-region slots of 8 ints (see NodeBox)
+    // force-region tile masks: three slots of mask_stride bytes
+    unsigned char *mask = nullptr;
+    size_t mask_stride = 0;
+    Shape shape;
+    int sms = 152;  // multiprocessors of the device
 
     // compression between plates and its adjoint (csrc/plates.cu)
     struct TapeEntry {

@@ -21,78 +21,58 @@
 //   W = 2 lane (dz, dy, dx) its node, for W = 4 lane (dz, j) the rows
 //   dy = 2j, 2j + 1 of plane dz = 0..3) and the eight partial sums meet in a
 //   fixed shuffle tree.
-#include <climits>
-
 #include "internal.cuh"
 
 namespace cf {
 
-// Block-wide minimum of 6 ints folded into a box slot with one atomicMin
-// per value per block. Every thread of the block must call it.
-__device__ __forceinline__ void box_accumulate(int (&v)[6], int *slot) {
-    __shared__ int red[32][6];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        int m = INT_MAX;
-        for (int w = 0; w < nwarps; ++w) m = min(m, red[w][threadIdx.x]);
-        if (m != INT_MAX) atomicMin(slot + threadIdx.x, m);
-    }
+// Mark the tiles of the force region around one vertex: its support grown by
+// one node per side (y clamped to the lattice).
+template <int W>
+__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, unsigned char *mask) {
+    for_each_tile(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W,
+                  [&](int t) { mask[t] = 1; });
 }
 
-// Support nodes of one vertex as a box: x and z wrapped (a support across
-// the periodic seam covers the whole axis), y as is.
+// True if every support node of the vertex lies in a marked tile.
 template <int W>
-__device__ __forceinline__ void support_box(const Support &s, const LbmParams &p, int (&v)[6]) {
-    const int X0 = wrapi(s.bx, p.nx), Z0 = wrapi(s.bz, p.nz);
-    const bool sx = X0 + W - 1 > p.nx - 1, sz = Z0 + W - 1 > p.nz - 1;
-    v[0] = sx ? 0 : X0;
-    v[1] = s.by;
-    v[2] = sz ? 0 : Z0;
-    v[3] = -(sx ? p.nx - 1 : X0 + W - 1);
-    v[4] = -(s.by + W - 1);
-    v[5] = -(sz ? p.nz - 1 : Z0 + W - 1);
+__device__ __forceinline__ bool region_covers(const Support &s, const LbmParams &p,
+                                              const unsigned char *__restrict__ mask) {
+    bool ok = true;
+    for_each_tile(p, s.bx, s.bx + W - 1, s.by, s.by + W - 1, s.bz, s.bz + W - 1,
+                  [&](int t) { ok = ok && mask[t]; });
+    return ok;
 }
 
 template <int W>
-__global__ void __launch_bounds__(256) k_support_box(MeshView m, const float4 *__restrict__ u, LbmParams p,
-                                                     int *box_out) {
+__global__ void __launch_bounds__(256) k_mark_region(MeshView m, const float4 *__restrict__ u, LbmParams p,
+                                                     unsigned char *mask) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX};
     Support s;
-    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) support_box<W>(s, p, b);
-    box_accumulate(b, box_out);
+    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) mark_region<W>(s, p, mask);
 }
 
-cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmParams &p, int *box_out,
+cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, unsigned char *mask,
                                cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
     if (p.dw == 4)
-        k_support_box<4><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, box_out);
+        k_mark_region<4><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, mask);
     else
-        k_support_box<2><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, box_out);
+        k_mark_region<2><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, mask);
     return cudaGetLastError();
 }
 
 // Four lanes per vertex: lane k sums the entries k, k+4, k+8, ... of the
 // incidence row, the four partial sums are combined by a fixed shuffle tree
 // (the same order every call: deterministic), and lane k spreads onto its
-// share of the support nodes.
+// share of the support nodes; lane 0 checks that the support lies in the
+// step's force region and lane 1 marks the next step's region.
 template <int W>
-__global__ void __launch_bounds__(128) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
-                                                       int do_spread, unsigned *err, int *box_out,
-                                                       const int *__restrict__ box_in) {
+__global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
+                                                       int do_spread, unsigned *err, unsigned char *mark_out,
+                                                       const unsigned char *__restrict__ mask_in) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = g >> 2, lane = g & 3;
     const bool live = v < m.V;
-    int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX, INT_MAX};
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (live) {
         const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
@@ -120,12 +100,8 @@ __global__ void __launch_bounds__(128) k_gather_spread(MeshView m, const float4 
         } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
             if (lane == 0) atomicOr(err, ERR_DOMAIN);
         } else {
-            support_box<W>(s, p, b);
-            if (box_in && lane == 0) {
-                const NodeBox r = region_of(box_in, p.nx, p.ny, p.nz);
-                if (!(in_region(r, -b[3], -b[4], -b[5], p.nx, p.nz) && in_region(r, b[0], b[1], b[2], p.nx, p.nz)))
-                    atomicOr(err, ERR_MOVED);
-            }
+            if (mask_in && lane == 0 && !region_covers<W>(s, p, mask_in)) atomicOr(err, ERR_MOVED);
+            if (mark_out && lane == 1) mark_region<W>(s, p, mark_out);
             const int N = (int)p.N;
             float wx[W], wy[W], wz[W];
             delta_weights<W>(s.fx, wx);
@@ -167,27 +143,31 @@ __global__ void __launch_bounds__(128) k_gather_spread(MeshView m, const float4 
             }
         }
     }
-    if (box_out) box_accumulate(b, box_out);
 }
 
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, int *box_out, const int *box_in) {
+                                 cudaStream_t s, unsigned char *mark_out, const unsigned char *mask_in, int block) {
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
+    const int bs = block > 0 ? block : 128;
     const long long threads = 4LL * m.V;
-    const int blocks = (int)((threads + 127) / 128), spread = (F && lp) ? 1 : 0;
+    const int blocks = (int)((threads + bs - 1) / bs), spread = (F && lp) ? 1 : 0;
+    if (!spread) {
+        mark_out = nullptr;
+        mask_in = nullptr;
+    }
     if (p.dw == 4)
-        k_gather_spread<4><<<blocks, 128, 0, s>>>(m, u, F, p, spread, err, box_out, box_in);
+        k_gather_spread<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark_out, mask_in);
     else
-        k_gather_spread<2><<<blocks, 128, 0, s>>>(m, u, F, p, spread, err, box_out, box_in);
+        k_gather_spread<2><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark_out, mask_in);
     return cudaGetLastError();
 }
 
 // Eight threads per vertex, each summing W^3 / 8 support nodes; the group of
 // eight combines its partial sums with shuffles.
 template <int W>
-__global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *__restrict__ vel, LbmParams p,
+__global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const float *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
                                                        unsigned *err) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,14 +231,15 @@ __global__ void __launch_bounds__(128) k_interp_advect(MeshView m, const float *
 }
 
 cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
-                                 float4 *u_next, unsigned *err, cudaStream_t s) {
+                                 float4 *u_next, unsigned *err, cudaStream_t s, int block) {
     if (m.V == 0) return cudaSuccess;
+    const int bs = block > 0 ? block : 128;
     const long long threads = 8LL * m.V;
-    const int blocks = (int)((threads + 127) / 128);
+    const int blocks = (int)((threads + bs - 1) / bs);
     if (p.dw == 4)
-        k_interp_advect<4><<<blocks, 128, 0, s>>>(m, vel, p, u_cur, u_next, err);
+        k_interp_advect<4><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err);
     else
-        k_interp_advect<2><<<blocks, 128, 0, s>>>(m, vel, p, u_cur, u_next, err);
+        k_interp_advect<2><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err);
     return cudaGetLastError();
 }
 

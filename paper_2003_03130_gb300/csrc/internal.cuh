@@ -64,6 +64,11 @@ struct LbmParams {
     float uw_lo, uw_hi; // wall x velocities at y = -1/2 and y = ny - 1/2
     float gx, gy, gz;   // uniform body-force density
     int dw;             // delta kernel: support width 2 (trilinear) or 4 (Peskin)
+    // force-region tiles of 2^tlx x 2^tly x 2^tlz = 256 nodes (x fastest;
+    // the last tile of an axis may stick out of the lattice), ntx * nty * ntz
+    // of them
+    int tlx, tly, tlz;
+    int ntx, nty, ntz;
 };
 
 struct MeshView {
@@ -133,48 +138,72 @@ __device__ __forceinline__ void delta_weights<4>(float f, float (&w)[4]) {
     w[3] = 0.125f * (1.f + 2.f * f - q);
 }
 
-__device__ __forceinline__ int wrapi(int i, int n) {
+__host__ __device__ __forceinline__ int wrapi(int i, int n) {
     const int r = i % n;
     return r < 0 ? r + n : r;
 }
 
-// Force region of a step. A box slot holds the bounding box of the delta
-// support nodes of all vertices as 6 ints {min x, min y, min z, -max x,
-// -max y, -max z} (x and z wrapped into the lattice), all accumulated with
-// atomicMin from INT_MAX. The region a step uses is that box grown by one
-// node in every direction (x, z periodic as start + length; y clamped).
-struct NodeBox {
-    int x0, lx, y0, y1, z0, lz;
+// Force region of a step: a byte per tile, 1 where the tile holds a node
+// that may carry force in that step. A step's region marks every tile that
+// meets the delta support of a vertex grown by one node per side (a vertex
+// moves less than one spacing per step, so the support at the next step
+// stays inside). Nodes of unmarked tiles see no force.
+constexpr int kTileNodes = 256;
+
+__host__ __device__ __forceinline__ int tile_index(const LbmParams &p, int tx, int ty, int tz) {
+    return (tz * p.nty + ty) * p.ntx + tx;
+}
+
+// Tiles met by the node range [lo, hi] on one axis: the first tile t0 and
+// the count; tiles are t0, t0 + 1, ... modulo nt (a periodic range wraps
+// from the last tile to tile 0). `periodic` false: lo and hi already lie in
+// [0, n).
+struct TileRange {
+    int t0, cnt;
 };
 
-__device__ __forceinline__ NodeBox region_of(const int *__restrict__ slot, int nx, int ny, int nz) {
-    NodeBox b;
-    const int xmin = slot[0], ymin = slot[1], zmin = slot[2];
-    const int xmax = -slot[3], ymax = -slot[4], zmax = -slot[5];
-    if (xmin > xmax) {  // empty: no vertex spread anything
-        b.x0 = 0; b.lx = 0; b.y0 = 1; b.y1 = 0; b.z0 = 0; b.lz = 0;
-        return b;
+__host__ __device__ __forceinline__ TileRange tile_range(int lo, int hi, int n, int lg, int nt, bool periodic) {
+    TileRange r;
+    if (!periodic) {
+        r.t0 = lo >> lg;
+        r.cnt = (hi >> lg) - r.t0 + 1;
+        return r;
     }
-    b.lx = xmax - xmin + 3;
-    b.x0 = xmin - 1;
-    if (b.lx >= nx) { b.x0 = 0; b.lx = nx; }
-    b.lz = zmax - zmin + 3;
-    b.z0 = zmin - 1;
-    if (b.lz >= nz) { b.z0 = 0; b.lz = nz; }
-    b.y0 = ymin - 1 < 0 ? 0 : ymin - 1;
-    b.y1 = ymax + 1 > ny - 1 ? ny - 1 : ymax + 1;
-    return b;
+    if (hi - lo + 1 >= n) {
+        r.t0 = 0;
+        r.cnt = nt;
+        return r;
+    }
+    const int lw = wrapi(lo, n), hw = wrapi(hi, n);
+    r.t0 = lw >> lg;
+    const int t1 = hw >> lg;
+    if (hw >= lw) {
+        r.cnt = t1 - r.t0 + 1;
+    } else {  // crosses the seam: t0 .. nt-1, then 0 .. t1
+        r.cnt = t1 - r.t0 + nt + 1;
+        if (r.cnt > nt) r.cnt = nt;
+    }
+    return r;
 }
 
-// offset of a periodic coordinate from the region start, in [0, n)
-__device__ __forceinline__ int region_off(int c, int c0, int n) {
-    int d = c - c0;
-    d %= n;
-    return d < 0 ? d + n : d;
-}
-
-__device__ __forceinline__ bool in_region(const NodeBox &b, int x, int y, int z, int nx, int nz) {
-    return y >= b.y0 && y <= b.y1 && region_off(x, b.x0, nx) < b.lx && region_off(z, b.z0, nz) < b.lz;
+// Visit the tiles met by the node box [x0,x1] x [y0,y1] x [z0,z1] (x and z
+// unwrapped, y clamped to the lattice by the caller).
+template <class Fn>
+__host__ __device__ __forceinline__ void for_each_tile(const LbmParams &p, int x0, int x1, int y0, int y1, int z0, int z1,
+                                              Fn &&fn) {
+    const TileRange rx = tile_range(x0, x1, p.nx, p.tlx, p.ntx, true);
+    const TileRange ry = tile_range(y0, y1, p.ny, p.tly, p.nty, false);
+    const TileRange rz = tile_range(z0, z1, p.nz, p.tlz, p.ntz, true);
+    for (int k = 0; k < rz.cnt; ++k) {
+        int tz = rz.t0 + k;
+        tz -= tz >= p.ntz ? p.ntz : 0;
+        for (int j = 0; j < ry.cnt; ++j)
+            for (int i = 0; i < rx.cnt; ++i) {
+                int tx = rx.t0 + i;
+                tx -= tx >= p.ntx ? p.ntx : 0;
+                fn(tile_index(p, tx, ry.t0 + j, tz));
+            }
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -199,7 +228,7 @@ cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cud
 // non-null the same launch also zeroes the force field on the delta support
 // of the positions x + u_prev (where the previous step spread its forces).
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
-                             const LbmParams *lp, cudaStream_t s);
+                             const LbmParams *lp, cudaStream_t s, int block = 0);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
@@ -209,24 +238,28 @@ cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, do
 cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
-// same threads spread their vertex force onto the lattice. With box_out the
-// bounding box of the support nodes is accumulated into that slot; with
-// box_in every support node must lie in the region of that slot (else
-// ERR_MOVED).
+// same threads spread their vertex force onto the lattice. With mark_out the
+// tiles of the next step's force region (support grown by one node) are
+// marked in that mask; with mask_in every support node must lie in a marked
+// tile of that mask (else ERR_MOVED).
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, int *box_out = nullptr, const int *box_in = nullptr);
-// Bounding box of the support nodes of x + u into a slot (reset by the caller).
-cudaError_t launch_support_box(const MeshView &m, const float4 *u, const LbmParams &p, int *box_out,
+                                 cudaStream_t s, unsigned char *mark_out = nullptr,
+                                 const unsigned char *mask_in = nullptr, int block = 0);
+// Mark the force region of the positions x + u (support grown by one node)
+// in a tile mask (cleared by the caller).
+cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, unsigned char *mask,
                                cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStream_t s);
-// K4 split by the force region of a slot: far = every node outside it, with
-// no force-field read; near = the nodes inside it, with the force field, also
-// storing u(t) there.
-cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const int *box, cudaStream_t s);
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *box,
-                            float *vel, cudaStream_t s);
+// K4 split by the force region of a tile mask: far = the unmarked tiles, one
+// block per tile, with no force-field read; near = the marked tiles, blocks
+// striding over the tiles, with the force field, also storing u(t) there
+// (near_blocks: grid size, 0 = default).
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned char *mask,
+                           cudaStream_t s);
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p,
+                            const unsigned char *mask, float *vel, cudaStream_t s, int near_blocks = 0);
 // True for the device functions of the far-field kernels (to tell their graph
 // nodes apart).
 bool is_lbm_far_kernel(const void *fn);
@@ -234,7 +267,7 @@ size_t pop_bytes(int fmt);
 // K5: velocity u(t) (stored by the near-field stream-collide) interpolated at
 // x + u_cur; u_next = u_cur + velocity.
 cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
-                                 float4 *u_next, unsigned *err, cudaStream_t s);
+                                 float4 *u_next, unsigned *err, cudaStream_t s, int block = 0);
 // Compression between plates and the adjoint (csrc/adjoint.cu).
 // out = J_el v at displacements u (vertex sums of the corner tangents; uses m.fc).
 cudaError_t launch_force_jvp(const MeshView &m, const float4 *u, const float4 *v, float4 *out, unsigned *err,

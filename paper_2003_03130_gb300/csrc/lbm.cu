@@ -21,9 +21,11 @@
 // touched once per step, and the hint keeps the cells' few MB of mesh data
 // resident in L2 while the lattice streams through it.
 //
-// One node per thread, 128 threads along x: 19 independent coalesced loads
-// per node (x-shifted rows are off by one word; neighbouring warps share the
-// lines in L2), the collide, 19 coalesced stores.
+// One node per thread: 19 independent coalesced loads per node (x-shifted
+// rows are off by one word; neighbouring warps share the lines in L2), the
+// collide, 19 coalesced stores. Fluid-only runs take rows of 128 nodes along
+// x; with cells the lattice is cut into tiles of 256 nodes (x fastest), the
+// unit of the force region.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -236,41 +238,44 @@ __global__ void __launch_bounds__(128) k_lbm(const T *__restrict__ fin, T *__res
         lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
 }
 
-// Every node outside the force region (F is zero there: no force-field read).
+// Node of thread i in tile (tx, ty, tz): x fastest within the tile. False if
+// the node lies outside the lattice (partial tiles at the upper ends).
+__device__ __forceinline__ bool tile_node(const LbmParams &p, int tx, int ty, int tz, int i, int &x, int &y, int &z) {
+    x = (tx << p.tlx) + (i & ((1 << p.tlx) - 1));
+    y = (ty << p.tly) + ((i >> p.tlx) & ((1 << p.tly) - 1));
+    z = (tz << p.tlz) + (i >> (p.tlx + p.tly));
+    return x < p.nx && y < p.ny && z < p.nz;
+}
+
+// The unmarked tiles, one block of 256 threads per tile (grid = tiles per
+// axis), one node per thread (F is zero there: no force-field read). Marked
+// tiles' blocks return at once.
 template <class T>
-__global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
-                                                 const int *__restrict__ box) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
-    if (y >= b.y0 && y <= b.y1 && region_off(z, b.z0, p.nz) < b.lz && region_off(x, b.x0, p.nx) < b.lx) return;
+__global__ void __launch_bounds__(kTileNodes, 5) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout,
+                                                           LbmParams p, const unsigned char *__restrict__ mask) {
+    if (mask[tile_index(p, blockIdx.x, blockIdx.y, blockIdx.z)]) return;
+    int x, y, z;
+    if (!tile_node(p, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, x, y, z)) return;
     if (y > 0 && y < p.ny - 1)
         lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr);
     else
         lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
 }
 
-// The nodes inside the force region, with the force field; also stores u(t)
-// there. The grid is fixed when a step is captured while the region moves
-// with the cells, so threads stride over the region's nodes.
+// The marked tiles, with the force field; also stores u(t) there. The grid
+// is fixed when a step is captured while the region moves with the cells,
+// so blocks stride over the tiles and skip the unmarked ones.
 template <class T>
-__global__ void __launch_bounds__(128) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
-                                                  const float *__restrict__ F, LbmParams p,
-                                                  const int *__restrict__ box, float *__restrict__ vel) {
-    const NodeBox b = region_of(box, p.nx, p.ny, p.nz);
-    const int ly = b.y1 - b.y0 + 1;
-    if (ly <= 0 || b.lx <= 0 || b.lz <= 0) return;
-    const int plane = b.lx * ly, total = plane * b.lz;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int k = i / plane, r = i - k * plane;
-        const int j = r / b.lx, xi = r - j * b.lx;
-        int x = b.x0 + xi, z = b.z0 + k;
-        x -= x >= p.nx ? p.nx : 0;
-        x += x < 0 ? p.nx : 0;
-        z -= z >= p.nz ? p.nz : 0;
-        z += z < 0 ? p.nz : 0;
-        const int y = b.y0 + j;
+__global__ void __launch_bounds__(kTileNodes, 4) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
+                                                         const float *__restrict__ F, LbmParams p,
+                                                         const unsigned char *__restrict__ mask,
+                                                         float *__restrict__ vel) {
+    const int ntiles = p.ntx * p.nty * p.ntz;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (!mask[tile]) continue;
+        const int tx = tile % p.ntx, r = tile / p.ntx;
+        int x, y, z;
+        if (!tile_node(p, tx, r % p.nty, r / p.nty, threadIdx.x, x, y, z)) continue;
         if (y > 0 && y < p.ny - 1)
             lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel);
         else
@@ -317,20 +322,21 @@ static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, cudaSt
 }
 
 template <class T>
-static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const int *box, cudaStream_t s) {
-    const int bx = p.nx < 128 ? p.nx : 128;
-    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-    k_lbm_far<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, box);
+static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned char *mask, cudaStream_t s) {
+    k_lbm_far<T><<<dim3(p.ntx, p.nty, p.ntz), kTileNodes, 0, s>>>(static_cast<const T *>(fin),
+                                                                  static_cast<T *>(fout), p, mask);
     return cudaGetLastError();
 }
 
 template <class T>
-static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const int *box, float *vel,
-                          cudaStream_t s) {
-    // one pass over regions up to ~155k nodes (8 blocks of 128 per SM)
-    const long long cap = (p.N + 127) / 128;
-    const int blocks = (int)(cap < 1216 ? cap : 1216);
-    k_lbm_near<T><<<blocks, 128, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, box, vel);
+static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned char *mask,
+                          float *vel, cudaStream_t s, int near_blocks) {
+    // default: 5 blocks of 256 per SM on 152 SMs (the occupancy of the
+    // kernel at its register count)
+    const int ntiles = p.ntx * p.nty * p.ntz;
+    const int want = near_blocks > 0 ? near_blocks : 760;
+    const int blocks = ntiles < want ? ntiles : want;
+    k_lbm_near<T><<<blocks, kTileNodes, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, mask, vel);
     return cudaGetLastError();
 }
 
@@ -347,20 +353,21 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStre
     }
 }
 
-cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const int *box, cudaStream_t s) {
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned char *mask,
+                           cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return far_t<__half>(fin, fout, p, box, s);
-        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, box, s);
-        default: return far_t<float>(fin, fout, p, box, s);
+        case POP_F16: return far_t<__half>(fin, fout, p, mask, s);
+        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, mask, s);
+        default: return far_t<float>(fin, fout, p, mask, s);
     }
 }
 
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *box,
-                            float *vel, cudaStream_t s) {
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p,
+                            const unsigned char *mask, float *vel, cudaStream_t s, int near_blocks) {
     switch (p.fmt) {
-        case POP_F16: return near_t<__half>(fin, fout, F, p, box, vel, s);
-        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, box, vel, s);
-        default: return near_t<float>(fin, fout, F, p, box, vel, s);
+        case POP_F16: return near_t<__half>(fin, fout, F, p, mask, vel, s, near_blocks);
+        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, mask, vel, s, near_blocks);
+        default: return near_t<float>(fin, fout, F, p, mask, vel, s, near_blocks);
     }
 }
 

@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(256) k_tet_force(MeshView m, const float4 *__r
 }
 
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
-                             const LbmParams *lp, cudaStream_t s) {
+                             const LbmParams *lp, cudaStream_t s, int block) {
     if (m.T == 0) return cudaSuccess;
-    const int bs = 64;  // ~20k tets: enough blocks for every SM
+    const int bs = block > 0 ? block : 64;  // default: ~20k tets still give every SM blocks
     const int tb = (m.T + bs - 1) / bs;
     const int cb = (u_prev && F && lp) ? (m.V + bs - 1) / bs : 0;
     LbmParams p{};

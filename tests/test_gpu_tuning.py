@@ -1,0 +1,143 @@
+"""GPU: launch shapes and the autotuner. Every tile shape and block size
+must give the oracle's result (the same tolerance as the default shape),
+the autotuner must advance the state exactly like cf_step, and invalid
+shapes are status codes."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import configs
+from workloads.configs import Cell, Workload
+from workloads.mesh import perturb, sphere_tet_mesh
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TILES = [(16, 4, 4), (32, 4, 2), (32, 2, 4), (8, 8, 4)]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2003_03130_gb300 import build
+
+    build.build()
+    import paper_2003_03130_gb300 as P
+
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def reference_20():
+    wl = configs.small_shear()
+    sim = oracle.Coupled(wl)
+    sim.step(20)
+    return wl, sim
+
+
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("blocks", [(64, 128, 128, 152), (256, 64, 256, 1216), (128, 256, 64, 7)])
+def test_every_shape_matches_the_oracle(P, reference_20, tile, blocks):
+    wl, sim = reference_20
+    ctx = P.cf_create(0)
+    P.cf_set_launch_shape(ctx, list(tile) + list(blocks))
+    (cid,) = P.load_workload(ctx, wl)
+    got = P.cf_get_launch_shape(ctx)
+    assert [got[k] for k in P.SHAPE_KEYS] == list(tile) + list(blocks)
+    P.cf_step(ctx, 12)
+    P.cf_step_profiled(ctx, 3)
+    P.cf_step(ctx, 5)
+    y0 = wl.cells[0].y0
+    assert rel(P.cf_get_positions(ctx, cid) - y0, sim.y - y0) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+    P.cf_destroy(ctx)
+
+
+def test_shape_change_between_calls(P, reference_20):
+    wl, sim = reference_20
+    ctx = P.cf_create(0)
+    (cid,) = P.load_workload(ctx, wl)
+    for k, tile in enumerate(TILES):
+        P.cf_set_launch_shape(ctx, {"tile_x": tile[0], "tile_y": tile[1], "tile_z": tile[2]})
+        P.cf_step(ctx, 5)
+    y0 = wl.cells[0].y0
+    assert rel(P.cf_get_positions(ctx, cid) - y0, sim.y - y0) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_autotune_advances_like_cf_step(P):
+    """18 candidates x 2 steps = 36 steps, then 10 more with the chosen
+    shape: positions and fluid as the oracle's after 46 steps."""
+    cells = [Cell(*_cell((9.3, 8.7, 10.1), 5)), Cell(*_cell((28.2, 17.4, 7.9), 6, R=3.5, h=1.2))]
+    wl = Workload("ragged", 41, 27, 19, 0.9, -0.015, 0.02, body_force=(2e-6, 0.0, -1e-6), cells=cells)
+    ctx = P.cf_create(0)
+    ids = P.load_workload(ctx, wl)
+    shape = P.cf_autotune(ctx, 2)
+    assert (shape["tile_x"], shape["tile_y"], shape["tile_z"]) in TILES
+    assert shape["tet_block"] in (64, 128, 256) and shape["gather_block"] in (64, 128, 256)
+    assert shape["interp_block"] in (64, 128, 256)
+    assert P.cf_get_launch_shape(ctx) == shape
+    P.cf_step(ctx, 10)
+    sim = oracle.Coupled(wl)
+    sim.step(46)
+    y0 = np.concatenate([c.y0 for c in cells])
+    y = np.concatenate([P.cf_get_positions(ctx, i) for i in ids])
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def _cell(centre, seed, R=4.0, h=1.3):
+    x, t = sphere_tet_mesh(R, h)
+    x = x + np.asarray(centre)
+    return x, t, perturb(x, 0.1, seed), 2e-3, 0.1, 0.7
+
+
+def test_autotune_without_cells_keeps_the_state(P):
+    ctx = P.cf_create(0)
+    P.cf_lbm_init(ctx, 16, 16, 8, 0.8, -0.02, 0.02)
+    P.cf_step(ctx, 10)
+    u = P.cf_get_velocity(ctx)
+    P.cf_autotune(ctx, 3)
+    assert np.array_equal(P.cf_get_velocity(ctx), u)
+
+
+def test_seam_on_a_lattice_smaller_than_two_tiles(P):
+    """nx = 20 with 16-node tiles: the last tile is partial and a support
+    that crosses the x seam meets both tiles."""
+    x, t = sphere_tet_mesh(4.0, 1.3)
+    x = x + np.array([0.3, 12.0, 17.6])
+    cell = Cell(x, t, perturb(x, 0.1, 8), 2e-3, 0.2, 0.6)
+    wl = Workload("seam20", 20, 24, 18, 1.0, -0.02, 0.02, cells=[cell])
+    ctx = P.cf_create(0)
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 25)
+    sim = oracle.Coupled(wl)
+    sim.step(25)
+    assert rel(P.cf_get_positions(ctx, cid) - cell.y0, sim.y - cell.y0) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+    _, near = P.cf_step_profiled(ctx, 1)
+    assert 0 < near <= 20 * 24 * 18
+
+
+def test_invalid_shapes_are_status_codes(P):
+    from paper_2003_03130_gb300 import CellFSIError
+
+    ctx = P.cf_create(0)
+    good = [16, 4, 4, 64, 128, 128, 760]
+    for k, bad in ((0, 64), (1, 8), (3, 48), (4, 512), (5, 0), (6, 0), (6, 70000)):
+        shape = list(good)
+        shape[k] = bad
+        with pytest.raises(CellFSIError) as e:
+            P.cf_set_launch_shape(ctx, shape)
+        assert e.value.name == "CF_EINVAL"
+    with pytest.raises(CellFSIError) as e:
+        P.cf_autotune(ctx, 2)
+    assert e.value.name == "CF_ESTATE"
+    P.cf_lbm_init(ctx, 8, 8, 8, 1.0, 0.0, 0.0)
+    with pytest.raises(CellFSIError) as e:
+        P.cf_autotune(ctx, 0)
+    assert e.value.name == "CF_EINVAL"
+    P.cf_destroy(ctx)
