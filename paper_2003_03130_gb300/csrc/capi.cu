@@ -46,14 +46,26 @@ constexpr int kChunk = 12;
 
 enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3 };
 
-// Region slots of step t (phase s = t % 3): the step's force region is mask
-// slot (s + 2) % 3 (marked by step t - 1, or from the current positions in
-// the first step of a call); the step marks the region of step t + 1 into
-// slot s. Three slots keep a slot from being cleared while a far-field kernel
-// two steps back may still read it.
-unsigned char *region_slot(cf_ctx *c, int s) { return c->mask + c->mask_stride * ((s + 2) % 3); }
-unsigned char *accum_slot(cf_ctx *c, int s) { return c->mask + c->mask_stride * s; }
-size_t mask_bytes(const LbmParams &p) { return (size_t)p.ntx * p.nty * p.ntz; }
+// Region slots of step t (phase s = t % 3): the step's force region is slot
+// (s + 2) % 3 (filled by step t - 1, or from the current positions in the
+// first step of a call); the step fills the region of step t + 1 into slot
+// s. Three slots keep a slot from being cleared while a far-field kernel two
+// steps back may still read it.
+size_t tiles_of(const LbmParams &p) { return (size_t)p.ntx * p.nty * p.ntz; }
+
+RegionSlot slot_at(cf_ctx *c, int k) {
+    unsigned *base = c->region + c->region_stride * k;
+    return RegionSlot{base + 32, (int *)base, (int *)(base + 32 + c->region_bits_max)};
+}
+RegionSlot region_slot(cf_ctx *c, int s) { return slot_at(c, (s + 2) % 3); }
+RegionSlot accum_slot(cf_ctx *c, int s) { return slot_at(c, s); }
+
+// Empty a slot: its count and the bitset of the current tiling.
+cudaError_t clear_slot(const cf_ctx *c, const RegionSlot &r, cudaStream_t s) {
+    return cudaMemsetAsync(r.count, 0, sizeof(unsigned) * (32 + (tiles_of(c->lp) + 31) / 32), s);
+}
+
+int near_grid(const cf_ctx *c) { return 8 * c->sms; }
 
 // Tile fields of the lattice parameters for tile shape k.
 void set_tiles(LbmParams &p, int k) {
@@ -64,8 +76,6 @@ void set_tiles(LbmParams &p, int k) {
     p.nty = (p.ny + (1 << p.tly) - 1) >> p.tly;
     p.ntz = (p.nz + (1 << p.tlz) - 1) >> p.tlz;
 }
-
-int near_blocks(const cf_ctx *c) { return c->shape.near_blocks > 0 ? c->shape.near_blocks : 5 * c->sms; }
 
 // Enqueue `nsteps` steps starting at parity p0 and phase s0 on two streams:
 // sf carries the far-field stream-collide, sc the cell chain and the near
@@ -78,7 +88,6 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
                         cudaEvent_t *ev) {
     const MeshView m = view(c);
     const Shape &sh = c->shape;
-    const size_t mb = mask_bytes(c->lp);
     if (kind == Kind::Tail) {  // K5 of the last step (parity p0)
         CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sf, sh.interp_block));
         return CF_OK;
@@ -92,25 +101,25 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     }
     cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
     if (kind == Kind::First) {
-        unsigned char *use = region_slot(c, s0);
-        CUDA_TRY(c, cudaMemsetAsync(use, 0, mb, sf));
+        const RegionSlot use = region_slot(c, s0);
+        CUDA_TRY(c, clear_slot(c, use, sf));
         CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, sf));
     }
     CUDA_TRY(c, cudaEventRecord(fork, sf));
     CUDA_TRY(c, cudaStreamWaitEvent(sc, fork, 0));
     for (int i = 0; i < nsteps; ++i) {
         const int p = p0 ^ (i & 1), s = (s0 + i) % 3;
-        unsigned char *use = region_slot(c, s), *acc = accum_slot(c, s);
+        const RegionSlot use = region_slot(c, s), acc = accum_slot(c, s);
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, sf));
+        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
         if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
-        CUDA_TRY(c, cudaMemsetAsync(acc, 0, mb, sc));
+        CUDA_TRY(c, clear_slot(c, acc, sc));
         CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc, sh.tet_block));
-        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, acc, use, sh.gather_block));
+        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, &acc, use.bits, sh.gather_block));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, sc, near_blocks(c)));
+        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c), sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
@@ -269,7 +278,7 @@ void cf_destroy(cf_ctx *c) {
     drop_graphs(c);
     dfree(c->d_err);
     dfree(c->d_status);
-    dfree(c->mask);
+    dfree(c->region);
     dfree(c->f[0]);
     dfree(c->f[1]);
     dfree(c->F);
@@ -318,7 +327,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     dfree(c->f[1]);
     dfree(c->F);
     dfree(c->vel);
-    dfree(c->mask);
+    dfree(c->region);
     c->lbm_ready = false;
     LbmParams p{};
     p.fmt = c->pop_format;
@@ -334,21 +343,22 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     p.gy = g ? (float)g[1] : 0.f;
     p.gz = g ? (float)g[2] : 0.f;
     p.dw = c->delta_w;
-    // masks sized for the largest tile count of any tile shape
-    size_t mstride = 0;
+    // region slots sized for the largest tile count of any tile shape
+    size_t tmax = 0;
     for (int k = 0; k < kNumTileShapes; ++k) {
         set_tiles(p, k);
-        mstride = std::max(mstride, mask_bytes(p));
+        tmax = std::max(tmax, tiles_of(p));
     }
     set_tiles(p, c->shape.tile);
-    c->mask_stride = (mstride + 255) / 256 * 256;
+    c->region_bits_max = (tmax + 31) / 32;
+    c->region_stride = (32 + c->region_bits_max + tmax + 31) / 32 * 32;
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
     CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
     CUDA_TRY(c, dalloc(&c->F, 3 * (size_t)N));
     CUDA_TRY(c, dalloc(&c->vel, 3 * (size_t)N));
-    CUDA_TRY(c, dalloc(&c->mask, 3 * c->mask_stride));
-    CUDA_TRY(c, cudaMemsetAsync(c->mask, 0, 3 * c->mask_stride, c->stream));
+    CUDA_TRY(c, dalloc(&c->region, 3 * c->region_stride));
+    CUDA_TRY(c, cudaMemsetAsync(c->region, 0, sizeof(unsigned) * 3 * c->region_stride, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float) * 3 * (size_t)N, c->stream));
@@ -626,18 +636,16 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
     const MeshView m = view(c);
     const bool cells = c->T > 0;
     cudaStream_t s = c->stream;
-    const size_t mb = mask_bytes(c->lp);
-    const int nb = sh.near_blocks > 0 ? sh.near_blocks : 5 * c->sms;
     for (int done = 0; done < n && st == CF_OK;) {
         const int b = std::min(BATCH, n - done);
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < b && e == cudaSuccess; ++i) {
             const int p = c->cur, t = done + i;
             const int sph = (int)((c->tstep) % 3);
-            unsigned char *use = region_slot(c, sph), *accm = accum_slot(c, sph);
+            const RegionSlot use = region_slot(c, sph), accm = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
             if (cells && t == 0) {  // region of the first step: not timed
-                e = cudaMemsetAsync(use, 0, mb, s);
+                e = clear_slot(c, use, s);
                 if (e == cudaSuccess) e = launch_mark_region(m, c->u[p], c->lp, use, s);
             }
             cudaEventRecord(E[0], s);
@@ -645,19 +653,20 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                 e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s, sh.interp_block);
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
-                e = cudaMemsetAsync(accm, 0, mb, s);
+                e = clear_slot(c, accm, s);
                 if (e == cudaSuccess)
                     e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block);
             }
             cudaEventRecord(E[2], s);
             if (cells && e == cudaSuccess)
-                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, accm, use, sh.gather_block);
+                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, &accm, use.bits, sh.gather_block);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
-                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use, s)
+                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, s)
                           : launch_lbm(c->f[p], c->f[1 - p], c->lp, s);
             cudaEventRecord(E[4], s);
-            if (cells && e == cudaSuccess) e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use, c->vel, s, nb);
+            if (cells && e == cudaSuccess)
+                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c), s);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
             c->tstep += 1;
@@ -691,20 +700,23 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
     return st;
 }
 
-// Lattice nodes in the marked tiles of the region the last step used.
+// Lattice nodes in the tiles of the region the last step used.
 cf_status region_nodes(cf_ctx *c, long long *out) {
     *out = 0;
     if (c->T == 0 || c->tstep == 0) return CF_OK;
     const LbmParams &p = c->lp;
-    std::vector<unsigned char> h(mask_bytes(p));
-    const unsigned char *last = region_slot(c, (int)((c->tstep - 1) % 3));
-    CUDA_TRY(c, cudaMemcpyAsync(h.data(), last, h.size(), cudaMemcpyDeviceToHost, c->stream));
+    const RegionSlot last = region_slot(c, (int)((c->tstep - 1) % 3));
+    int cnt = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&cnt, last.count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     cf_status st = wait_stream(c);
+    if (st != CF_OK || cnt <= 0) return st;
+    std::vector<int> h(cnt);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), last.tiles, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    st = wait_stream(c);
     if (st != CF_OK) return st;
     const int tx = 1 << p.tlx, ty = 1 << p.tly, tz = 1 << p.tlz;
-    for (size_t t = 0; t < h.size(); ++t) {
-        if (!h[t]) continue;
-        const int ix = (int)(t % p.ntx), iy = (int)((t / p.ntx) % p.nty), iz = (int)(t / ((size_t)p.ntx * p.nty));
+    for (int t : h) {
+        const int ix = t % p.ntx, iy = (t / p.ntx) % p.nty, iz = t / (p.ntx * p.nty);
         const long long ex = std::min(tx, p.nx - ix * tx), ey = std::min(ty, p.ny - iy * ty),
                         ez = std::min(tz, p.nz - iz * tz);
         *out += ex * ey * ez;
@@ -742,7 +754,6 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[3] = sh.tet_block;
     shape[4] = sh.gather_block;
     shape[5] = sh.interp_block;
-    shape[6] = near_blocks(c);
     return CF_OK;
 }
 
@@ -761,11 +772,9 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     for (int k = 3; k < 6; ++k)
         if (shape[k] < 32 || shape[k] > 256 || shape[k] % 32)
             return fail(c, CF_EINVAL, "block size %d: need a multiple of 32 in [32, 256]", shape[k]);
-    if (shape[6] < 1 || shape[6] > 65535) return fail(c, CF_EINVAL, "near-field blocks must be in [1, 65535]");
     sh.tet_block = shape[3];
     sh.gather_block = shape[4];
     sh.interp_block = shape[5];
-    sh.near_blocks = shape[6];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -790,13 +799,11 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
         };
         const Knob knobs[] = {
             {&Shape::tile, {0, 1, 2, 3}, {1, 2, 3}},
-            {&Shape::near_blocks, {2 * c->sms, 5 * c->sms, 8 * c->sms}, {3}},
             {&Shape::tet_block, {64, 128, 256}, {0}},
             {&Shape::gather_block, {64, 128, 256}, {1}},
             {&Shape::interp_block, {64, 128, 256}, {4}},
         };
         Shape best = c->shape;
-        if (best.near_blocks <= 0) best.near_blocks = 5 * c->sms;
         for (const Knob &k : knobs) {
             double tbest = 1e300;
             int vbest = best.*k.field;

@@ -35,7 +35,6 @@ constexpr int kNumTileShapes = 4;
 struct Shape {
     int tile = 0;  // index into kTileShapes
     int tet_block = 64, gather_block = 128, interp_block = 128;
-    int near_blocks = 0;  // 0: 5 blocks per SM
 };
 
 }  // namespace cf
@@ -80,9 +79,10 @@ struct cf_ctx {
     double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
     double *taylor_partial = nullptr, *taylor_out = nullptr;
 
-    // force-region tile masks: three slots of mask_stride bytes
-    unsigned char *mask = nullptr;
-    size_t mask_stride = 0;
+    // force regions: three slots of region_stride words, each [count, 31
+    // words of padding, bitset over the tiles, tile list]
+    unsigned *region = nullptr;
+    size_t region_stride = 0, region_bits_max = 0;
     Shape shape;
     int sms = 152;  // multiprocessors of the device
 

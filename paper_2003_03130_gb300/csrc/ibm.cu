@@ -25,39 +25,39 @@
 
 namespace cf {
 
-// Mark the tiles of the force region around one vertex: its support grown by
+// Add the tiles of the force region around one vertex: its support grown by
 // one node per side (y clamped to the lattice).
 template <int W>
-__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, unsigned char *mask) {
+__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, const RegionSlot &r) {
     for_each_tile(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W,
-                  [&](int t) { mask[t] = 1; });
+                  [&](int t) { region_add(r, t); });
 }
 
-// True if every support node of the vertex lies in a marked tile.
+// True if every support node of the vertex lies in a tile of the region.
 template <int W>
 __device__ __forceinline__ bool region_covers(const Support &s, const LbmParams &p,
-                                              const unsigned char *__restrict__ mask) {
+                                              const unsigned *__restrict__ bits) {
     bool ok = true;
     for_each_tile(p, s.bx, s.bx + W - 1, s.by, s.by + W - 1, s.bz, s.bz + W - 1,
-                  [&](int t) { ok = ok && mask[t]; });
+                  [&](int t) { ok = ok && region_has(bits, t); });
     return ok;
 }
 
 template <int W>
 __global__ void __launch_bounds__(256) k_mark_region(MeshView m, const float4 *__restrict__ u, LbmParams p,
-                                                     unsigned char *mask) {
+                                                     RegionSlot r) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     Support s;
-    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) mark_region<W>(s, p, mask);
+    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) mark_region<W>(s, p, r);
 }
 
-cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, unsigned char *mask,
+cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, const RegionSlot &r,
                                cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
     if (p.dw == 4)
-        k_mark_region<4><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, mask);
+        k_mark_region<4><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, r);
     else
-        k_mark_region<2><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, mask);
+        k_mark_region<2><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, r);
     return cudaGetLastError();
 }
 
@@ -68,8 +68,8 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
 // step's force region and lane 1 marks the next step's region.
 template <int W>
 __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
-                                                       int do_spread, unsigned *err, unsigned char *mark_out,
-                                                       const unsigned char *__restrict__ mask_in) {
+                                                       int do_spread, unsigned *err, RegionSlot mark_out,
+                                                       const unsigned *__restrict__ bits_in) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = g >> 2, lane = g & 3;
     const bool live = v < m.V;
@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const floa
         } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
             if (lane == 0) atomicOr(err, ERR_DOMAIN);
         } else {
-            if (mask_in && lane == 0 && !region_covers<W>(s, p, mask_in)) atomicOr(err, ERR_MOVED);
-            if (mark_out && lane == 1) mark_region<W>(s, p, mark_out);
+            if (bits_in && lane == 0 && !region_covers<W>(s, p, bits_in)) atomicOr(err, ERR_MOVED);
+            if (mark_out.bits && lane == 1) mark_region<W>(s, p, mark_out);
             const int N = (int)p.N;
             float wx[W], wy[W], wz[W];
             delta_weights<W>(s.fx, wx);
@@ -146,21 +146,20 @@ __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const floa
 }
 
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, unsigned char *mark_out, const unsigned char *mask_in, int block) {
+                                 cudaStream_t s, const RegionSlot *mark_out, const unsigned *bits_in, int block) {
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
     const int bs = block > 0 ? block : 128;
     const long long threads = 4LL * m.V;
     const int blocks = (int)((threads + bs - 1) / bs), spread = (F && lp) ? 1 : 0;
-    if (!spread) {
-        mark_out = nullptr;
-        mask_in = nullptr;
-    }
+    RegionSlot mark{nullptr, nullptr, nullptr};
+    if (spread && mark_out) mark = *mark_out;
+    if (!spread) bits_in = nullptr;
     if (p.dw == 4)
-        k_gather_spread<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark_out, mask_in);
+        k_gather_spread<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark, bits_in);
     else
-        k_gather_spread<2><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark_out, mask_in);
+        k_gather_spread<2><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark, bits_in);
     return cudaGetLastError();
 }
 

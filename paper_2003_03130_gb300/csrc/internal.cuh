@@ -143,12 +143,31 @@ __host__ __device__ __forceinline__ int wrapi(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Force region of a step: a byte per tile, 1 where the tile holds a node
-// that may carry force in that step. A step's region marks every tile that
-// meets the delta support of a vertex grown by one node per side (a vertex
-// moves less than one spacing per step, so the support at the next step
-// stays inside). Nodes of unmarked tiles see no force.
+// Force region of a step: the set of tiles that hold a node that may carry
+// force in that step, as a bitset over the tiles plus the list of the set's
+// tiles (in no particular order) and its length. A step's region holds every
+// tile that meets the delta support of a vertex grown by one node per side
+// (a vertex moves less than one spacing per step, so the support at the next
+// step stays inside). Nodes outside the region see no force.
 constexpr int kTileNodes = 256;
+
+struct RegionSlot {
+    unsigned *bits;  // [ceil(tiles / 32)], followed by the count
+    int *count;
+    int *tiles;      // [tiles]
+};
+
+__device__ __forceinline__ bool region_has(const unsigned *__restrict__ bits, int t) {
+    return (bits[t >> 5] >> (t & 31)) & 1u;
+}
+
+// Add tile t: the first thread to set its bit appends it to the list. The
+// plain read skips the atomic for the (many) tiles already in.
+__device__ __forceinline__ void region_add(const RegionSlot &r, int t) {
+    const unsigned bit = 1u << (t & 31);
+    if (r.bits[t >> 5] & bit) return;
+    if (!(atomicOr(r.bits + (t >> 5), bit) & bit)) r.tiles[atomicAdd(r.count, 1)] = t;
+}
 
 __host__ __device__ __forceinline__ int tile_index(const LbmParams &p, int tx, int ty, int tz) {
     return (tz * p.nty + ty) * p.ntx + tx;
@@ -164,7 +183,7 @@ struct TileRange {
 
 __host__ __device__ __forceinline__ TileRange tile_range(int lo, int hi, int n, int lg, int nt, bool periodic) {
     TileRange r;
-    if (!periodic) {
+    if (!periodic || (lo >= 0 && hi < n)) {  // no wrap
         r.t0 = lo >> lg;
         r.cnt = (hi >> lg) - r.t0 + 1;
         return r;
@@ -240,26 +259,25 @@ cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, do
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
 // same threads spread their vertex force onto the lattice. With mark_out the
 // tiles of the next step's force region (support grown by one node) are
-// marked in that mask; with mask_in every support node must lie in a marked
-// tile of that mask (else ERR_MOVED).
+// added to that region; with bits_in every support node must lie in a tile
+// of that region (else ERR_MOVED).
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, unsigned char *mark_out = nullptr,
-                                 const unsigned char *mask_in = nullptr, int block = 0);
-// Mark the force region of the positions x + u (support grown by one node)
-// in a tile mask (cleared by the caller).
-cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, unsigned char *mask,
+                                 cudaStream_t s, const RegionSlot *mark_out = nullptr,
+                                 const unsigned *bits_in = nullptr, int block = 0);
+// Add the force region of the positions x + u (support grown by one node) to
+// a region slot (cleared by the caller).
+cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, const RegionSlot &r,
                                cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStream_t s);
-// K4 split by the force region of a tile mask: far = the unmarked tiles, one
-// block per tile, with no force-field read; near = the marked tiles, blocks
-// striding over the tiles, with the force field, also storing u(t) there
-// (near_blocks: grid size, 0 = default).
-cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned char *mask,
-                           cudaStream_t s);
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p,
-                            const unsigned char *mask, float *vel, cudaStream_t s, int near_blocks = 0);
+// K4 split by the force region: far = the tiles outside it (two blocks per
+// tile of the lattice; those of region tiles return at once), with no
+// force-field read; near = the region's tiles from its list (blocks stride
+// over the list), with the force field, also storing u(t) there.
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, cudaStream_t s);
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
+                            const int *tiles, float *vel, int blocks, cudaStream_t s);
 // True for the device functions of the far-field kernels (to tell their graph
 // nodes apart).
 bool is_lbm_far_kernel(const void *fn);

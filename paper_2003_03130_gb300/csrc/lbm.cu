@@ -25,7 +25,7 @@
 // rows are off by one word; neighbouring warps share the lines in L2), the
 // collide, 19 coalesced stores. Fluid-only runs take rows of 128 nodes along
 // x; with cells the lattice is cut into tiles of 256 nodes (x fastest), the
-// unit of the force region.
+// unit of the force region, two blocks of 128 threads per tile.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -247,35 +247,39 @@ __device__ __forceinline__ bool tile_node(const LbmParams &p, int tx, int ty, in
     return x < p.nx && y < p.ny && z < p.nz;
 }
 
-// The unmarked tiles, one block of 256 threads per tile (grid = tiles per
-// axis), one node per thread (F is zero there: no force-field read). Marked
-// tiles' blocks return at once.
+// Half a tile per block: 128 threads, one node each; the far-field grid is
+// (2 ntx, nty, ntz), block x = 2 * tile x + half.
+constexpr int kTileBlock = kTileNodes / 2;
+
+// The tiles outside the force region (F is zero there: no force-field
+// read). Blocks of region tiles return at once.
 template <class T>
-__global__ void __launch_bounds__(kTileNodes, 5) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout,
-                                                           LbmParams p, const unsigned char *__restrict__ mask) {
-    if (mask[tile_index(p, blockIdx.x, blockIdx.y, blockIdx.z)]) return;
+__global__ void __launch_bounds__(kTileBlock, 8) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout,
+                                                           LbmParams p, const unsigned *__restrict__ bits) {
+    const int tx = blockIdx.x >> 1;
+    if (region_has(bits, tile_index(p, tx, blockIdx.y, blockIdx.z))) return;
     int x, y, z;
-    if (!tile_node(p, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, x, y, z)) return;
+    if (!tile_node(p, tx, blockIdx.y, blockIdx.z, (blockIdx.x & 1) * kTileBlock + threadIdx.x, x, y, z)) return;
     if (y > 0 && y < p.ny - 1)
         lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr);
     else
         lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
 }
 
-// The marked tiles, with the force field; also stores u(t) there. The grid
-// is fixed when a step is captured while the region moves with the cells,
-// so blocks stride over the tiles and skip the unmarked ones.
+// The force region's tiles from its list, with the force field; also stores
+// u(t) there. The grid is fixed when a step is captured while the region
+// moves with the cells, so blocks stride over the list's half tiles.
 template <class T>
-__global__ void __launch_bounds__(kTileNodes, 4) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
-                                                         const float *__restrict__ F, LbmParams p,
-                                                         const unsigned char *__restrict__ mask,
-                                                         float *__restrict__ vel) {
-    const int ntiles = p.ntx * p.nty * p.ntz;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (!mask[tile]) continue;
+__global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
+                                                            const float *__restrict__ F, LbmParams p,
+                                                            const int *__restrict__ count,
+                                                            const int *__restrict__ tiles, float *__restrict__ vel) {
+    const int halves = 2 * *count;
+    for (int w = blockIdx.x; w < halves; w += gridDim.x) {
+        const int tile = tiles[w >> 1];
         const int tx = tile % p.ntx, r = tile / p.ntx;
         int x, y, z;
-        if (!tile_node(p, tx, r % p.nty, r / p.nty, threadIdx.x, x, y, z)) continue;
+        if (!tile_node(p, tx, r % p.nty, r / p.nty, (w & 1) * kTileBlock + threadIdx.x, x, y, z)) continue;
         if (y > 0 && y < p.ny - 1)
             lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel);
         else
@@ -322,21 +326,17 @@ static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, cudaSt
 }
 
 template <class T>
-static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned char *mask, cudaStream_t s) {
-    k_lbm_far<T><<<dim3(p.ntx, p.nty, p.ntz), kTileNodes, 0, s>>>(static_cast<const T *>(fin),
-                                                                  static_cast<T *>(fout), p, mask);
+static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, cudaStream_t s) {
+    k_lbm_far<T><<<dim3(2 * p.ntx, p.nty, p.ntz), kTileBlock, 0, s>>>(static_cast<const T *>(fin),
+                                                                      static_cast<T *>(fout), p, bits);
     return cudaGetLastError();
 }
 
 template <class T>
-static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned char *mask,
-                          float *vel, cudaStream_t s, int near_blocks) {
-    // default: 5 blocks of 256 per SM on 152 SMs (the occupancy of the
-    // kernel at its register count)
-    const int ntiles = p.ntx * p.nty * p.ntz;
-    const int want = near_blocks > 0 ? near_blocks : 760;
-    const int blocks = ntiles < want ? ntiles : want;
-    k_lbm_near<T><<<blocks, kTileNodes, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, mask, vel);
+static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
+                          const int *tiles, float *vel, int blocks, cudaStream_t s) {
+    k_lbm_near<T><<<blocks, kTileBlock, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, count,
+                                                tiles, vel);
     return cudaGetLastError();
 }
 
@@ -353,21 +353,20 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStre
     }
 }
 
-cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned char *mask,
-                           cudaStream_t s) {
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return far_t<__half>(fin, fout, p, mask, s);
-        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, mask, s);
-        default: return far_t<float>(fin, fout, p, mask, s);
+        case POP_F16: return far_t<__half>(fin, fout, p, bits, s);
+        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, bits, s);
+        default: return far_t<float>(fin, fout, p, bits, s);
     }
 }
 
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p,
-                            const unsigned char *mask, float *vel, cudaStream_t s, int near_blocks) {
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
+                            const int *tiles, float *vel, int blocks, cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return near_t<__half>(fin, fout, F, p, mask, vel, s, near_blocks);
-        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, mask, vel, s, near_blocks);
-        default: return near_t<float>(fin, fout, F, p, mask, vel, s, near_blocks);
+        case POP_F16: return near_t<__half>(fin, fout, F, p, count, tiles, vel, blocks, s);
+        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, count, tiles, vel, blocks, s);
+        default: return near_t<float>(fin, fout, F, p, count, tiles, vel, blocks, s);
     }
 }
 

@@ -39,7 +39,7 @@ def reference_20():
 
 
 @pytest.mark.parametrize("tile", TILES)
-@pytest.mark.parametrize("blocks", [(64, 128, 128, 152), (256, 64, 256, 1216), (128, 256, 64, 7)])
+@pytest.mark.parametrize("blocks", [(64, 128, 128), (256, 64, 256), (128, 256, 64)])
 def test_every_shape_matches_the_oracle(P, reference_20, tile, blocks):
     wl, sim = reference_20
     ctx = P.cf_create(0)
@@ -69,8 +69,8 @@ def test_shape_change_between_calls(P, reference_20):
 
 
 def test_autotune_advances_like_cf_step(P):
-    """18 candidates x 2 steps = 36 steps, then 10 more with the chosen
-    shape: positions and fluid as the oracle's after 46 steps."""
+    """13 candidates x 2 steps = 26 steps, then 10 more with the chosen
+    shape: positions and fluid as the oracle's after 36 steps."""
     cells = [Cell(*_cell((9.3, 8.7, 10.1), 5)), Cell(*_cell((28.2, 17.4, 7.9), 6, R=3.5, h=1.2))]
     wl = Workload("ragged", 41, 27, 19, 0.9, -0.015, 0.02, body_force=(2e-6, 0.0, -1e-6), cells=cells)
     ctx = P.cf_create(0)
@@ -82,7 +82,7 @@ def test_autotune_advances_like_cf_step(P):
     assert P.cf_get_launch_shape(ctx) == shape
     P.cf_step(ctx, 10)
     sim = oracle.Coupled(wl)
-    sim.step(46)
+    sim.step(36)
     y0 = np.concatenate([c.y0 for c in cells])
     y = np.concatenate([P.cf_get_positions(ctx, i) for i in ids])
     assert rel(y - y0, sim.y - y0) <= TOL
@@ -126,8 +126,8 @@ def test_invalid_shapes_are_status_codes(P):
     from paper_2003_03130_gb300 import CellFSIError
 
     ctx = P.cf_create(0)
-    good = [16, 4, 4, 64, 128, 128, 760]
-    for k, bad in ((0, 64), (1, 8), (3, 48), (4, 512), (5, 0), (6, 0), (6, 70000)):
+    good = [16, 4, 4, 64, 128, 128]
+    for k, bad in ((0, 64), (1, 8), (2, 2), (3, 48), (4, 512), (5, 0), (5, 288)):
         shape = list(good)
         shape[k] = bad
         with pytest.raises(CellFSIError) as e:
