@@ -116,8 +116,9 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
         CUDA_TRY(c, clear_slot(c, acc, sc));
-        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc, sh.tet_block));
-        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, &acc, use.bits, sh.gather_block));
+        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc, sh.tet_block, &acc,
+                                     use.bits));
+        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, sh.gather_block));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c), sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
@@ -291,6 +292,7 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->xref64);
     dfree(c->tet);
     dfree(c->B);
+    dfree(c->Bp);
     dfree(c->V0);
     dfree(c->tcell);
     dfree(c->origin);
@@ -430,7 +432,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     int *tin = nullptr;
     auto cleanup = [&]() {
         dfree(n.xr); dfree(n.u[0]); dfree(n.u[1]); dfree(n.fv); dfree(n.fc); dfree(n.xref64); dfree(n.tet);
-        dfree(n.B); dfree(n.V0); dfree(n.tcell); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
+        dfree(n.B); dfree(n.Bp); dfree(n.V0); dfree(n.tcell); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
         dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(n.taylor_partial);
         dfree(x64); dfree(y64); dfree(tin);
     };
@@ -451,6 +453,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     TRY_N(dalloc(&n.xref64, 3 * (size_t)V1));
     TRY_N(dalloc(&n.tet, T1));
     TRY_N(dalloc(&n.B, 9 * (size_t)T1));
+    TRY_N(dalloc(&n.Bp, 3 * (size_t)T1));
     TRY_N(dalloc(&n.V0, T1));
     TRY_N(dalloc(&n.tcell, T1));
     TRY_N(dalloc(&n.origin, 3 * (size_t)C1));
@@ -513,6 +516,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
         TRY_N(launch_vertex_prepare(x64 + 3 * voff[k], y64 ? y64 + 3 * voff[k] : nullptr, nv[k], add[k].v_off,
                                     cell0 + k, add[k].origin, n.xr, n.u[0], n.u[1], n.xref64, s));
     TRY_N(launch_csr_build(n.tet, T1, V1, n.csr_ptr, n.csr_idx, n.csr_cursor, s));
+    TRY_N(launch_pack_tets(T1, n.B, n.V0, n.tcell, n.Bp, s));
     TRY_N(cudaStreamSynchronize(s));
 #undef TRY_N
     dfree(x64);
@@ -527,6 +531,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     std::swap(c->xref64, n.xref64);
     std::swap(c->tet, n.tet);
     std::swap(c->B, n.B);
+    std::swap(c->Bp, n.Bp);
     std::swap(c->V0, n.V0);
     std::swap(c->tcell, n.tcell);
     std::swap(c->origin, n.origin);
@@ -655,11 +660,12 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             if (cells && e == cudaSuccess) {
                 e = clear_slot(c, accm, s);
                 if (e == cudaSuccess)
-                    e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block);
+                    e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &accm,
+                                         use.bits);
             }
             cudaEventRecord(E[2], s);
             if (cells && e == cudaSuccess)
-                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, &accm, use.bits, sh.gather_block);
+                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
                 e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, s)

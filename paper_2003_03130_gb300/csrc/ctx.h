@@ -72,6 +72,7 @@ struct cf_ctx {
     double *xref64 = nullptr;
     int4 *tet = nullptr;
     float *B = nullptr, *V0 = nullptr;
+    float4 *Bp = nullptr;  // packed B / V0 / cell rows for the force kernel, [3][T]
     int *tcell = nullptr, *origin = nullptr;
     float4 *mat = nullptr;
     int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
@@ -156,6 +157,7 @@ MeshView view(const cf_ctx *c) {
     m.origin = c->origin;
     m.tet = c->tet;
     m.B = c->B;
+    m.Bp = c->Bp;
     m.V0 = c->V0;
     m.tcell = c->tcell;
     m.mat = c->mat;

@@ -25,24 +25,6 @@
 
 namespace cf {
 
-// Add the tiles of the force region around one vertex: its support grown by
-// one node per side (y clamped to the lattice).
-template <int W>
-__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, const RegionSlot &r) {
-    for_each_tile(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W,
-                  [&](int t) { region_add(r, t); });
-}
-
-// True if every support node of the vertex lies in a tile of the region.
-template <int W>
-__device__ __forceinline__ bool region_covers(const Support &s, const LbmParams &p,
-                                              const unsigned *__restrict__ bits) {
-    bool ok = true;
-    for_each_tile(p, s.bx, s.bx + W - 1, s.by, s.by + W - 1, s.bz, s.bz + W - 1,
-                  [&](int t) { ok = ok && region_has(bits, t); });
-    return ok;
-}
-
 template <int W>
 __global__ void __launch_bounds__(256) k_mark_region(MeshView m, const float4 *__restrict__ u, LbmParams p,
                                                      RegionSlot r) {
@@ -64,24 +46,34 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
 // Four lanes per vertex: lane k sums the entries k, k+4, k+8, ... of the
 // incidence row, the four partial sums are combined by a fixed shuffle tree
 // (the same order every call: deterministic), and lane k spreads onto its
-// share of the support nodes; lane 0 checks that the support lies in the
-// step's force region and lane 1 marks the next step's region.
+// share of the support nodes.
 template <int W>
-__global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F, LbmParams p,
-                                                       int do_spread, unsigned *err, RegionSlot mark_out,
-                                                       const unsigned *__restrict__ bits_in) {
+__global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F,
+                                                          LbmParams p, int do_spread, unsigned *err) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = g >> 2, lane = g & 3;
     const bool live = v < m.V;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (live) {
+        // the lane's entries e0 + lane, + 4, + 8, ... in groups of four: the
+        // index loads of a group, then its corner-force loads, are issued
+        // together; the sum still runs over the entries in ascending order
         const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
-        for (int e = e0 + lane; e < e1; e += 4) {
-            const int id = __ldg(m.csr_idx + e);
-            const float4 c = m.fc[(id & 3) * m.T + (id >> 2)];
-            fx += c.x;
-            fy += c.y;
-            fz += c.z;
+        for (int e = e0 + lane; e < e1; e += 16) {
+            int id[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) id[k] = e + 4 * k < e1 ? __ldg(m.csr_idx + e + 4 * k) : -1;
+            float4 c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                c[k] = id[k] >= 0 ? m.fc[(id[k] & 3) * m.T + (id[k] >> 2)] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (id[k] >= 0) {
+                    fx += c[k].x;
+                    fy += c[k].y;
+                    fz += c[k].z;
+                }
         }
     }
 #pragma unroll
@@ -100,8 +92,6 @@ __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const floa
         } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
             if (lane == 0) atomicOr(err, ERR_DOMAIN);
         } else {
-            if (bits_in && lane == 0 && !region_covers<W>(s, p, bits_in)) atomicOr(err, ERR_MOVED);
-            if (mark_out.bits && lane == 1) mark_region<W>(s, p, mark_out);
             const int N = (int)p.N;
             float wx[W], wy[W], wz[W];
             delta_weights<W>(s.fx, wx);
@@ -146,20 +136,17 @@ __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const floa
 }
 
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, const RegionSlot *mark_out, const unsigned *bits_in, int block) {
+                                 cudaStream_t s, int block) {
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
     const int bs = block > 0 ? block : 128;
     const long long threads = 4LL * m.V;
     const int blocks = (int)((threads + bs - 1) / bs), spread = (F && lp) ? 1 : 0;
-    RegionSlot mark{nullptr, nullptr, nullptr};
-    if (spread && mark_out) mark = *mark_out;
-    if (!spread) bits_in = nullptr;
     if (p.dw == 4)
-        k_gather_spread<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark, bits_in);
+        k_gather_spread<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err);
     else
-        k_gather_spread<2><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err, mark, bits_in);
+        k_gather_spread<2><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,7 @@ struct MeshView {
     const int *origin;     // [3 * ncells], integer origin of each cell
     const int4 *tet;       // [T]: global vertex indices, corner 3 = vertex 4
     const float *B;        // [9][T]: B[(3k + j) * T + t] = (J^-1)_kj
+    const float4 *Bp;      // [3][T] or null: row k of B with .w = V0, cell id (int bits), 0 for k = 0, 1, 2
     const float *V0;       // [T]
     const int *tcell;      // [T]
     const float4 *mat;     // [ncells]: mu1, mu2, kappa, w
@@ -225,6 +226,24 @@ __host__ __device__ __forceinline__ void for_each_tile(const LbmParams &p, int x
     }
 }
 
+// Add the tiles of the force region around one vertex: its support grown by
+// one node per side (y clamped to the lattice).
+template <int W>
+__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, const RegionSlot &r) {
+    for_each_tile(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W,
+                  [&](int t) { region_add(r, t); });
+}
+
+// True if every support node of the vertex lies in a tile of the region.
+template <int W>
+__device__ __forceinline__ bool region_covers(const Support &s, const LbmParams &p,
+                                              const unsigned *__restrict__ bits) {
+    bool ok = true;
+    for_each_tile(p, s.bx, s.bx + W - 1, s.by, s.by + W - 1, s.bz, s.bz + W - 1,
+                  [&](int t) { ok = ok && region_has(bits, t); });
+    return ok;
+}
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch status.
 // Once per cell (Sec. 3.2): validate, orient, B = J^-1 and V_0 in FP64;
@@ -237,17 +256,23 @@ cudaError_t launch_vertex_prepare(const double *x64, const double *y64, int nv, 
                                   const int *origin_host3, float4 *xr, float4 *u0, float4 *u1, double *xref64,
                                   cudaStream_t s);
 cudaError_t launch_csr_build(const int4 *tet, int T, int V, int *ptr, int *idx, int *cursor, cudaStream_t s);
+// Packed per-tet rows for the force kernel: Bp[k * T + t] = (B_k0, B_k1, B_k2, w_k), w = (V0, cell, 0).
+cudaError_t launch_pack_tets(int T, const float *B, const float *V0, const int *tcell, float4 *Bp, cudaStream_t s);
 cudaError_t launch_set_positions(const double *y64, int v0, int nv, const double *xref64, float4 *u,
                                  cudaStream_t s);
 cudaError_t launch_get_positions(const float4 *u, const double *xref64, int v0, int nv, double *y64,
                                  cudaStream_t s);
 cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cudaStream_t s);
 
-// K1: elastic corner forces of all tets at displacements u; when `u_prev` is
-// non-null the same launch also zeroes the force field on the delta support
-// of the positions x + u_prev (where the previous step spread its forces).
+// K1: elastic corner forces of all tets at displacements u. When `u_prev` is
+// non-null the same launch also runs one thread per vertex that zeroes the
+// force field on the delta support of x + u_prev (where the previous step
+// spread its forces), adds the tiles of the next step's force region (the
+// support of x + u grown by one node) to mark_out, and checks that the
+// support of x + u lies in the region bits_in (else ERR_MOVED).
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
-                             const LbmParams *lp, cudaStream_t s, int block = 0);
+                             const LbmParams *lp, cudaStream_t s, int block = 0, const RegionSlot *mark_out = nullptr,
+                             const unsigned *bits_in = nullptr);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
@@ -257,13 +282,9 @@ cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, do
 cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
-// same threads spread their vertex force onto the lattice. With mark_out the
-// tiles of the next step's force region (support grown by one node) are
-// added to that region; with bits_in every support node must lie in a tile
-// of that region (else ERR_MOVED).
+// same threads spread their vertex force onto the lattice.
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, const RegionSlot *mark_out = nullptr,
-                                 const unsigned *bits_in = nullptr, int block = 0);
+                                 cudaStream_t s, int block = 0);
 // Add the force region of the positions x + u (support grown by one node) to
 // a region slot (cleared by the caller).
 cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, const RegionSlot &r,

@@ -235,4 +235,20 @@ cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cud
     return cudaGetLastError();
 }
 
+__global__ void k_pack_tets(int T, const float *__restrict__ B, const float *__restrict__ V0,
+                            const int *__restrict__ tcell, float4 *__restrict__ Bp) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const float w[3] = {V0[t], __int_as_float(tcell[t]), 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        Bp[k * T + t] = make_float4(B[(3 * k + 0) * T + t], B[(3 * k + 1) * T + t], B[(3 * k + 2) * T + t], w[k]);
+}
+
+cudaError_t launch_pack_tets(int T, const float *B, const float *V0, const int *tcell, float4 *Bp, cudaStream_t s) {
+    if (T <= 0) return cudaSuccess;
+    k_pack_tets<<<(T + 255) / 256, 256, 0, s>>>(T, B, V0, tcell, Bp);
+    return cudaGetLastError();
+}
+
 }  // namespace cf

@@ -29,46 +29,64 @@ __device__ __forceinline__ void clear_support(const MeshView &m, const float4 *_
     }
 }
 
-__global__ void __launch_bounds__(256) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
+// The per-vertex part of K1: clear last step's spread, add the next step's
+// region, check this step's region.
+template <int W>
+__device__ __forceinline__ void vertex_region(const MeshView &m, const float4 *__restrict__ u,
+                                              const float4 *__restrict__ u_prev, float *F, const LbmParams &lp,
+                                              int v, const RegionSlot &mark, const unsigned *__restrict__ bits_in,
+                                              unsigned *err) {
+    clear_support<W>(m, u_prev, F, lp, v);
+    Support s;
+    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s)) return;  // K23 reports it
+    if (mark.bits) mark_region<W>(s, lp, mark);
+    if (bits_in && !region_covers<W>(s, lp, bits_in)) atomicOr(err, ERR_MOVED);
+}
+
+__global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
                                                    int tet_blocks, const float4 *__restrict__ u_prev,
-                                                   float *__restrict__ F, LbmParams lp) {
+                                                   float *__restrict__ F, LbmParams lp, RegionSlot mark,
+                                                   const unsigned *__restrict__ bits_in) {
     if ((int)blockIdx.x >= tet_blocks) {
         const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
         if (v >= m.V) return;
         if (lp.dw == 4)
-            clear_support<4>(m, u_prev, F, lp, v);
+            vertex_region<4>(m, u, u_prev, F, lp, v, mark, bits_in, err);
         else
-            clear_support<2>(m, u_prev, F, lp, v);
+            vertex_region<2>(m, u, u_prev, F, lp, v, mark, bits_in, err);
         return;
     }
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
 
     const int4 a4 = __ldg(m.tet + t);
-    float Bm[3][3];
-    load_B(m, t, Bm);
+    float Bm[3][3], V0;
+    int cell;
+    load_tet_params(m, t, Bm, V0, cell);
     float H[3][3];
     tet_grad(__ldg(u + a4.x), __ldg(u + a4.y), __ldg(u + a4.z), __ldg(u + a4.w), Bm, H);
-    const float4 mat = __ldg(m.mat + __ldg(m.tcell + t));
+    const float4 mat = __ldg(m.mat + cell);
     InvT<float> v;
     float P[3][3];
     mr_stress(H, mat.x, mat.y, mat.z, v, P);
     if (!(v.J > 0.f)) atomicOr(err, ERR_INVERTED);
     float f[4][3];
-    corner_forces(P, Bm, __ldg(m.V0 + t), f);
+    corner_forces(P, Bm, V0, f);
 #pragma unroll
     for (int a = 0; a < 4; ++a) m.fc[a * m.T + t] = make_float4(f[a][0], f[a][1], f[a][2], 0.f);
 }
 
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
-                             const LbmParams *lp, cudaStream_t s, int block) {
+                             const LbmParams *lp, cudaStream_t s, int block, const RegionSlot *mark_out,
+                             const unsigned *bits_in) {
     if (m.T == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 64;  // default: ~20k tets still give every SM blocks
     const int tb = (m.T + bs - 1) / bs;
     const int cb = (u_prev && F && lp) ? (m.V + bs - 1) / bs : 0;
     LbmParams p{};
     if (lp) p = *lp;
-    k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p);
+    const RegionSlot mark = (cb && mark_out) ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
+    k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark, cb ? bits_in : nullptr);
     return cudaGetLastError();
 }
 
