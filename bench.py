@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision-steps", type=int, default=2000,
-                    help="steps of the FP32/FP16/BF16 comparison on the channel workload (0 = skip)")
+    ap.add_argument("--precision-steps", type=int, default=12500,
+                    help="steps of the storage-format comparison on the channel workload (0 = skip)")
     return ap.parse_args()
 
 
@@ -221,7 +221,8 @@ def cpu_baseline(wl, seconds):
 
 
 def precision_block(P, torch, dev, steps):
-    """FP32, FP16 and BF16 population storage on the pressure-driven channel
+    """FP32, FP16 and BF16 population storage (round to nearest, and
+    stochastic rounding: f16sr, bf16sr) on the pressure-driven channel
     (256 x 128 x 128, one R = 16 cell): steps/s of each, and the error of the
     16-bit runs against the FP32 run after the same steps from t = 0
     (norm-wise relative on the fluid velocity and the cell displacement;
@@ -231,7 +232,7 @@ def precision_block(P, torch, dev, steps):
     wl = configs.precision_channel(steps=steps)
     res = {}
     stream = torch.cuda.Stream(dev)
-    for fmt in ("f32", "f16", "bf16"):
+    for fmt in ("f32", "f16", "bf16", "f16sr", "bf16sr"):
         with torch.cuda.stream(stream):
             ctx = P.cf_create(dev, stream.cuda_stream)
             P.cf_set_population_format(ctx, fmt)
@@ -252,7 +253,7 @@ def precision_block(P, torch, dev, steps):
     x0 = wl.cells[0].x_ref
     ref = res["f32"]
     out = {"workload": wl.name, "steps": steps, "D_f32": ref["D"]}
-    for fmt in ("f32", "f16", "bf16"):
+    for fmt in ("f32", "f16", "bf16", "f16sr", "bf16sr"):
         r = res[fmt]
         out[fmt] = {"steps_per_s": r["steps_per_s"], "mlups": r["mlups"], "D": r["D"]}
         if fmt != "f32":

@@ -71,8 +71,13 @@ void cf_destroy(cf_ctx *ctx);
  * re-initialises the fluid). The populations are kept as deviations
  * f_q - w_q from the rest equilibrium; FP16 and BF16 store them multiplied by
  * a power of two per weight class. The collide always computes in FP32.
+ * CF_POP_F16 and CF_POP_BF16 round each store to nearest; CF_POP_F16_SR and
+ * CF_POP_BF16_SR round stochastically (unbiased: up with probability equal to
+ * the dropped fraction, from a counter-based hash of the node, the direction
+ * and a per-step seed held on the device), so that increments smaller than
+ * half a unit in the last place are not lost on average.
  * Default CF_POP_F32. Errors: CF_EINVAL for an unknown format. */
-enum { CF_POP_F32 = 0, CF_POP_F16 = 1, CF_POP_BF16 = 2 };
+enum { CF_POP_F32 = 0, CF_POP_F16 = 1, CF_POP_BF16 = 2, CF_POP_F16_SR = 3, CF_POP_BF16_SR = 4 };
 cf_status cf_set_population_format(cf_ctx *ctx, int32_t format);
 
 /* Immersed-boundary delta kernel for the spreading of vertex forces and the

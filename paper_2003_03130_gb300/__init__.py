@@ -163,14 +163,16 @@ def cf_last_error(ctx) -> str:
     return (lib().cf_last_error(ctx.handle) or b"").decode()
 
 
-CF_POP_F32, CF_POP_F16, CF_POP_BF16 = 0, 1, 2
+CF_POP_F32, CF_POP_F16, CF_POP_BF16, CF_POP_F16_SR, CF_POP_BF16_SR = 0, 1, 2, 3, 4
 CF_ALL_CELLS = -1
-POP_FORMATS = {"f32": CF_POP_F32, "f16": CF_POP_F16, "bf16": CF_POP_BF16}
+POP_FORMATS = {"f32": CF_POP_F32, "f16": CF_POP_F16, "bf16": CF_POP_BF16, "f16sr": CF_POP_F16_SR,
+               "bf16sr": CF_POP_BF16_SR}
 
 
 def cf_set_population_format(ctx, fmt):
-    """``fmt``: CF_POP_F32 / CF_POP_F16 / CF_POP_BF16 or "f32" / "f16" /
-    "bf16"; applies at the next cf_lbm_init."""
+    """``fmt``: a CF_POP_* code or "f32" / "f16" / "bf16" / "f16sr" /
+    "bf16sr" (the last two round stochastically); applies at the next
+    cf_lbm_init."""
     fmt = POP_FORMATS.get(fmt, fmt)
     _check(ctx, lib().cf_set_population_format(ctx.handle, int(fmt)))
 

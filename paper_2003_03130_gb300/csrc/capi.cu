@@ -95,7 +95,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     if (kind == Kind::Fluid) {
         for (int i = 0; i < nsteps; ++i) {
             const int p = p0 ^ (i & 1);
-            CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], c->lp, sf));
+            CUDA_TRY(c, launch_lbm(c->f[p], c->f[1 - p], c->lp, c->seed + p, c->seed + 1 - p, sf));
         }
         return CF_OK;
     }
@@ -111,7 +111,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         const int p = p0 ^ (i & 1), s = (s0 + i) % 3;
         const RegionSlot use = region_slot(c, s), acc = accum_slot(c, s);
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, sf));
+        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
         if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
@@ -120,7 +120,8 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
                                      use.bits));
         CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, sh.gather_block));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c), sc));
+        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c),
+                                    c->seed + p, c->seed + 1 - p, sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
@@ -263,7 +264,8 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         c->own_stream = true;
     }
     if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
-        dalloc(&c->taylor_out, 10) != cudaSuccess ||
+        dalloc(&c->taylor_out, 10) != cudaSuccess || dalloc(&c->seed, 2) != cudaSuccess ||
+        cudaMemset(c->seed, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
         dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
@@ -279,6 +281,7 @@ void cf_destroy(cf_ctx *c) {
     drop_graphs(c);
     dfree(c->d_err);
     dfree(c->d_status);
+    dfree(c->seed);
     dfree(c->region);
     dfree(c->f[0]);
     dfree(c->f[1]);
@@ -332,7 +335,8 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     dfree(c->region);
     c->lbm_ready = false;
     LbmParams p{};
-    p.fmt = c->pop_format;
+    p.fmt = c->pop_format == CF_POP_F16_SR ? POP_F16 : c->pop_format == CF_POP_BF16_SR ? POP_BF16 : c->pop_format;
+    p.sr = c->pop_format == CF_POP_F16_SR || c->pop_format == CF_POP_BF16_SR;
     p.nx = nx;
     p.ny = ny;
     p.nz = nz;
@@ -365,6 +369,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float) * 3 * (size_t)N, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->vel, 0, sizeof(float) * 3 * (size_t)N, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->seed, 0, 2 * sizeof(unsigned), c->stream));  // rounding seeds restart
     c->lp = p;
     // both displacement buffers must agree: the first step clears F on the
     // support of the "previous" positions
@@ -377,7 +382,8 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
 
 cf_status cf_set_population_format(cf_ctx *c, int32_t format) {
     if (!c) return CF_EINVAL;
-    if (format != CF_POP_F32 && format != CF_POP_F16 && format != CF_POP_BF16)
+    if (format != CF_POP_F32 && format != CF_POP_F16 && format != CF_POP_BF16 && format != CF_POP_F16_SR &&
+        format != CF_POP_BF16_SR)
         return fail(c, CF_EINVAL, "unknown population format %d", format);
     c->pop_format = format;
     return CF_OK;
@@ -668,11 +674,12 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                 e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
-                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, s)
-                          : launch_lbm(c->f[p], c->f[1 - p], c->lp, s);
+                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, s)
+                          : launch_lbm(c->f[p], c->f[1 - p], c->lp, c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[4], s);
             if (cells && e == cudaSuccess)
-                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c), s);
+                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c),
+                                    c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
             c->tstep += 1;

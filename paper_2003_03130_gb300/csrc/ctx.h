@@ -54,12 +54,13 @@ struct cf_ctx {
     double timeout_s = 600.0;
 
     unsigned *d_err = nullptr;
+    unsigned *seed = nullptr;  // rounding seeds of the two buffer parities (16-bit stochastic rounding)
     unsigned long long *d_status = nullptr;
 
     // fluid
     bool lbm_ready = false;
     LbmParams lp{};
-    int pop_format = POP_F32;  // storage of the populations (next cf_lbm_init)
+    int pop_format = CF_POP_F32;  // CF_POP_* storage of the populations (next cf_lbm_init)
     int delta_w = 2;           // delta kernel support width (next cf_lbm_init)
     void *f[2] = {nullptr, nullptr};
     float *F = nullptr;

@@ -57,6 +57,7 @@ enum : int { POP_F32 = 0, POP_F16 = 1, POP_BF16 = 2 };
 
 struct LbmParams {
     int fmt;  // POP_F32, POP_F16 or POP_BF16
+    int sr;   // 16-bit stores rounded stochastically (else to nearest)
     int nx, ny, nz;
     long long N;
     float omega;        // 1/tau
@@ -158,7 +159,7 @@ struct RegionSlot {
     int *tiles;      // [tiles]
 };
 
-__device__ __forceinline__ bool region_has(const unsigned *__restrict__ bits, int t) {
+__host__ __device__ __forceinline__ bool region_has(const unsigned *__restrict__ bits, int t) {
     return (bits[t >> 5] >> (t & 31)) & 1u;
 }
 
@@ -291,14 +292,20 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
                                cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
-cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStream_t s);
-// K4 split by the force region: far = the tiles outside it (two blocks per
-// tile of the lattice; those of region tiles return at once), with no
-// force-field read; near = the region's tiles from its list (blocks stride
-// over the list), with the force field, also storing u(t) there.
-cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, cudaStream_t s);
+// Every stream-collide launch reads the step's rounding seed from seed[0];
+// the launch that closes a step (this one, or the near field) stores
+// seed[0] + 1 into next_seed (the seed of the other buffer parity).
+cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const unsigned *seed, unsigned *next_seed,
+                       cudaStream_t s);
+// K4 split by the force region: far = the nodes outside it (rows of 128
+// nodes; threads in region tiles return at once), with no force-field read;
+// near = the region's tiles from its list (blocks stride over the list),
+// with the force field, also storing u(t) there.
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
+                           const unsigned *seed, cudaStream_t s);
 cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
-                            const int *tiles, float *vel, int blocks, cudaStream_t s);
+                            const int *tiles, float *vel, int blocks, const unsigned *seed, unsigned *next_seed,
+                            cudaStream_t s);
 // True for the device functions of the far-field kernels (to tell their graph
 // nodes apart).
 bool is_lbm_far_kernel(const void *fn);

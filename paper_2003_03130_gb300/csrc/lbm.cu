@@ -23,9 +23,10 @@
 //
 // One node per thread: 19 independent coalesced loads per node (x-shifted
 // rows are off by one word; neighbouring warps share the lines in L2), the
-// collide, 19 coalesced stores. Fluid-only runs take rows of 128 nodes along
-// x; with cells the lattice is cut into tiles of 256 nodes (x fastest), the
-// unit of the force region, two blocks of 128 threads per tile.
+// collide, 19 coalesced stores. The whole-lattice and far-field kernels take
+// rows of 128 nodes along x; with cells the lattice is also cut into tiles of
+// 256 nodes (x fastest), the unit of the force region, and the near field
+// runs two blocks of 128 threads per region tile.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -34,6 +35,13 @@
 namespace cf {
 
 // ---------------------------------------------------------------- storage
+// ld / st: streaming loads and stores with round-to-nearest conversion;
+// st_sr: stochastic rounding to the 16-bit format with the random bits r.
+// Adding uniform random bits below the last kept mantissa bit of the FP32
+// pattern and truncating rounds the magnitude up with probability equal to
+// the dropped fraction, so the rounding is unbiased (13 dropped bits for
+// FP16, 16 for BF16; exact for FP16-normal values, and non-finite values
+// take the nearest rounding).
 template <class T>
 struct Pop;
 
@@ -41,21 +49,16 @@ template <>
 struct Pop<float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
     static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
-    static __device__ __forceinline__ float2 ld2(const float *p) { return __ldcs(reinterpret_cast<const float2 *>(p)); }
-    static __device__ __forceinline__ void st2(float *p, float a, float b) {
-        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
-    }
+    static __device__ __forceinline__ void st_sr(float *p, float v, unsigned) { __stcs(p, v); }
 };
 
 template <>
 struct Pop<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
     static __device__ __forceinline__ void st(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
-    static __device__ __forceinline__ float2 ld2(const __half *p) {
-        return __half22float2(__ldcs(reinterpret_cast<const __half2 *>(p)));
-    }
-    static __device__ __forceinline__ void st2(__half *p, float a, float b) {
-        __stcs(reinterpret_cast<__half2 *>(p), __floats2half2_rn(a, b));
+    static __device__ __forceinline__ void st_sr(__half *p, float v, unsigned r) {
+        if (!isfinite(v)) return st(p, v);
+        __stcs(p, __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1fffu))));
     }
 };
 
@@ -63,13 +66,24 @@ template <>
 struct Pop<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
-    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(__ldcs(reinterpret_cast<const __nv_bfloat162 *>(p)));
-    }
-    static __device__ __forceinline__ void st2(__nv_bfloat16 *p, float a, float b) {
-        __stcs(reinterpret_cast<__nv_bfloat162 *>(p), __floats2bfloat162_rn(a, b));
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r) {
+        if (!isfinite(v)) return st(p, v);
+        __stcs(p, __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xffffu))));
     }
 };
+
+// Integer hash for the rounding bits: the "lowbias32" xorshift-multiply
+// finaliser (C. Wellons, "Prospecting for hash functions", 2018). Node n of
+// the step with seed s draws h = mix32(n ^ mix32(s)); population q takes 16
+// bits of mix32(h + (q >> 1) * 0x9e3779b9).
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 
 // stored value = d_q * scale; exact powers of two
 template <class T>
@@ -188,7 +202,7 @@ __device__ __forceinline__ bool wall_pull(int y, int ny) {
 template <class T, bool WALL, bool HAS_F>
 __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restrict__ fout,
                                          const float *__restrict__ F, const LbmParams &p, int x, int y, int z,
-                                         float *__restrict__ vel) {
+                                         float *__restrict__ vel, unsigned seed) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -221,6 +235,16 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         vel[N + n] = u.y;
         vel[2 * N + n] = u.z;
     }
+    if (sizeof(T) == 2 && p.sr) {
+        const unsigned h = mix32((unsigned)n ^ mix32(seed));
+#pragma unroll
+        for (int q = 0; q < 19; q += 2) {
+            const unsigned r = mix32(h + (unsigned)(q >> 1) * 0x9e3779b9u);
+            Pop<T>::st_sr(fout + q * N + n, d[q] * pop_scale<T>(q), r);
+            if (q + 1 < 19) Pop<T>::st_sr(fout + (q + 1) * N + n, d[q + 1] * pop_scale<T>(q + 1), r >> 16);
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 19; ++q) Pop<T>::st(fout + q * N + n, d[q] * pop_scale<T>(q));
 }
@@ -228,14 +252,17 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
 // ---------------------------------------------------------------- kernels
 // Whole lattice, no force field (fluid-only runs).
 template <class T>
-__global__ void __launch_bounds__(128) k_lbm(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p) {
+__global__ void __launch_bounds__(128) k_lbm(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
+                                             const unsigned *__restrict__ seed_in, unsigned *__restrict__ seed_out) {
+    const unsigned seed = *seed_in;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *seed_out = seed + 1u;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr);
+        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
     else
-        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
+        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
 }
 
 // Node of thread i in tile (tx, ty, tz): x fastest within the tile. False if
@@ -247,23 +274,26 @@ __device__ __forceinline__ bool tile_node(const LbmParams &p, int tx, int ty, in
     return x < p.nx && y < p.ny && z < p.nz;
 }
 
-// Half a tile per block: 128 threads, one node each; the far-field grid is
-// (2 ntx, nty, ntz), block x = 2 * tile x + half.
+// Near field: half a tile per block, 128 threads, one node each.
 constexpr int kTileBlock = kTileNodes / 2;
 
-// The tiles outside the force region (F is zero there: no force-field
-// read). Blocks of region tiles return at once.
+// The nodes outside the force region (F is zero there: no force-field
+// read), in rows of 128 nodes along x as in the fluid-only kernel, so that y
+// and z stay uniform over a block; a thread whose node lies in a region tile
+// returns at once.
 template <class T>
-__global__ void __launch_bounds__(kTileBlock, 8) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout,
-                                                           LbmParams p, const unsigned *__restrict__ bits) {
-    const int tx = blockIdx.x >> 1;
-    if (region_has(bits, tile_index(p, tx, blockIdx.y, blockIdx.z))) return;
-    int x, y, z;
-    if (!tile_node(p, tx, blockIdx.y, blockIdx.z, (blockIdx.x & 1) * kTileBlock + threadIdx.x, x, y, z)) return;
+__global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
+                                                 const unsigned *__restrict__ bits,
+                                                 const unsigned *__restrict__ seed_in) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz))) return;
+    const unsigned seed = *seed_in;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr);
+        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
     else
-        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr);
+        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
 }
 
 // The force region's tiles from its list, with the force field; also stores
@@ -273,17 +303,23 @@ template <class T>
 __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
                                                             const float *__restrict__ F, LbmParams p,
                                                             const int *__restrict__ count,
-                                                            const int *__restrict__ tiles, float *__restrict__ vel) {
+                                                            const int *__restrict__ tiles, float *__restrict__ vel,
+                                                            const unsigned *__restrict__ seed_in,
+                                                            unsigned *__restrict__ seed_out) {
+    const unsigned seed = *seed_in;
+    if ((blockIdx.x | threadIdx.x) == 0) *seed_out = seed + 1u;
     const int halves = 2 * *count;
+    int next = blockIdx.x < halves ? tiles[blockIdx.x >> 1] : 0;
     for (int w = blockIdx.x; w < halves; w += gridDim.x) {
-        const int tile = tiles[w >> 1];
+        const int tile = next;  // the next iteration's tile index loads under this one's populations
+        if (w + (int)gridDim.x < halves) next = tiles[(w + gridDim.x) >> 1];
         const int tx = tile % p.ntx, r = tile / p.ntx;
         int x, y, z;
         if (!tile_node(p, tx, r % p.nty, r / p.nty, (w & 1) * kTileBlock + threadIdx.x, x, y, z)) continue;
         if (y > 0 && y < p.ny - 1)
-            lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel);
+            lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel, seed);
         else
-            lbm_node<T, true, true>(fin, fout, F, p, x, y, z, vel);
+            lbm_node<T, true, true>(fin, fout, F, p, x, y, z, vel, seed);
     }
 }
 
@@ -318,25 +354,29 @@ __global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, Lb
 size_t pop_bytes(int fmt) { return fmt == POP_F32 ? 4 : 2; }
 
 template <class T>
-static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, cudaStream_t s) {
+static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, const unsigned *seed, unsigned *next_seed,
+                         cudaStream_t s) {
     const int bx = p.nx < 128 ? p.nx : 128;
     dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-    k_lbm<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p);
+    k_lbm<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, seed, next_seed);
     return cudaGetLastError();
 }
 
 template <class T>
-static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, cudaStream_t s) {
-    k_lbm_far<T><<<dim3(2 * p.ntx, p.nty, p.ntz), kTileBlock, 0, s>>>(static_cast<const T *>(fin),
-                                                                      static_cast<T *>(fout), p, bits);
+static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, const unsigned *seed,
+                         cudaStream_t s) {
+    const int bx = p.nx < 128 ? p.nx : 128;
+    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+    k_lbm_far<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, bits, seed);
     return cudaGetLastError();
 }
 
 template <class T>
 static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
-                          const int *tiles, float *vel, int blocks, cudaStream_t s) {
+                          const int *tiles, float *vel, int blocks, const unsigned *seed, unsigned *next_seed,
+                          cudaStream_t s) {
     k_lbm_near<T><<<blocks, kTileBlock, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, count,
-                                                tiles, vel);
+                                                tiles, vel, seed, next_seed);
     return cudaGetLastError();
 }
 
@@ -345,28 +385,32 @@ bool is_lbm_far_kernel(const void *fn) {
            fn == (const void *)k_lbm_far<__nv_bfloat16>;
 }
 
-cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, cudaStream_t s) {
+cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const unsigned *seed, unsigned *next_seed,
+                       cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return lbm_t<__half>(fin, fout, p, s);
-        case POP_BF16: return lbm_t<__nv_bfloat16>(fin, fout, p, s);
-        default: return lbm_t<float>(fin, fout, p, s);
+        case POP_F16: return lbm_t<__half>(fin, fout, p, seed, next_seed, s);
+        case POP_BF16: return lbm_t<__nv_bfloat16>(fin, fout, p, seed, next_seed, s);
+        default: return lbm_t<float>(fin, fout, p, seed, next_seed, s);
     }
 }
 
-cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, cudaStream_t s) {
+cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
+                           const unsigned *seed, cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return far_t<__half>(fin, fout, p, bits, s);
-        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, bits, s);
-        default: return far_t<float>(fin, fout, p, bits, s);
+        case POP_F16: return far_t<__half>(fin, fout, p, bits, seed, s);
+        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, bits, seed, s);
+        default: return far_t<float>(fin, fout, p, bits, seed, s);
     }
 }
 
 cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
-                            const int *tiles, float *vel, int blocks, cudaStream_t s) {
+                            const int *tiles, float *vel, int blocks, const unsigned *seed, unsigned *next_seed,
+                            cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return near_t<__half>(fin, fout, F, p, count, tiles, vel, blocks, s);
-        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, count, tiles, vel, blocks, s);
-        default: return near_t<float>(fin, fout, F, p, count, tiles, vel, blocks, s);
+        case POP_F16: return near_t<__half>(fin, fout, F, p, count, tiles, vel, blocks, seed, next_seed, s);
+        case POP_BF16:
+            return near_t<__nv_bfloat16>(fin, fout, F, p, count, tiles, vel, blocks, seed, next_seed, s);
+        default: return near_t<float>(fin, fout, F, p, count, tiles, vel, blocks, seed, next_seed, s);
     }
 }
 

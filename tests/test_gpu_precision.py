@@ -1,14 +1,18 @@
-"""GPU: population storage formats and the two-node stream-collide kernels.
+"""GPU: population storage formats.
 
 * Row-edge shapes (nx = 2; a partial block; two blocks per row) in FP32 and
   FP16.
 * FP16 / BF16 storage of the deviations f_q - w_q (power-of-two scaled,
-  collide in FP32) against the FP64 oracle: velocity fields and the Taylor
-  deformation of a sheared cell. The tolerances state the error of each
-  format as measured on GB300 (velocity after 600 steps of a forced Couette
-  start-up: FP16 3.6e-3, BF16 5.8e-2; D after 800 steps of a sheared cell:
-  FP32 3.2e-6, FP16 3.2e-5, BF16 8.6e-3). FP16 meets the 1e-3 relative bound
-  on D; BF16's 8-bit mantissa does not.
+  collide in FP32), rounded to nearest or stochastically (f16sr, bf16sr),
+  against the FP64 oracle: velocity fields and the Taylor deformation of a
+  sheared cell. The tolerances state the error of each format as measured on
+  GB300 (velocity after 600 steps of a forced Couette start-up: FP16 3.6e-3,
+  BF16 5.8e-2, FP16-SR 1.9e-4, BF16-SR 1.6e-3; D after 800 steps of a sheared
+  cell: FP32 3.2e-6, FP16 2.1e-5, BF16 8.7e-3, FP16-SR 3.3e-6, BF16-SR
+  6.7e-5; mean velocity of a weakly forced channel after 400 steps: FP16
+  7.3e-3, BF16 6.7e-2, FP16-SR 1.9e-5, BF16-SR 1.5e-4). Every 16-bit format
+  but round-to-nearest BF16 meets the 1e-3 relative bound on D; stochastic
+  rounding removes the stagnation of sub-ULP increments.
 """
 import numpy as np
 import pytest
@@ -63,7 +67,7 @@ def test_row_edge_shapes(P, dims):
     assert rel(u16, fl.u) <= 5e-3
 
 
-@pytest.mark.parametrize("fmt,tol", [("f16", 5e-3), ("bf16", 8e-2)])
+@pytest.mark.parametrize("fmt,tol", [("f16", 5e-3), ("bf16", 8e-2), ("f16sr", 5e-4), ("bf16sr", 4e-3)])
 def test_reduced_precision_fluid(P, fmt, tol):
     args = (16, 24, 8, 0.8, -0.02, 0.02, (2e-6, 0.0, 0.0), 600)
     u, rho = fluid_run(P, fmt, *args)
@@ -93,7 +97,7 @@ def sheared_oracle():
     return wl, sim.y.copy(), analysis.taylor(sim.y, sim.mesh.tets)["D"]
 
 
-@pytest.mark.parametrize("fmt,tol", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("fmt,tol", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 2e-2), ("f16sr", 2e-5), ("bf16sr", 2e-4)])
 def test_taylor_deformation_by_format(P, sheared_oracle, fmt, tol):
     wl, y_ref, D_ref = sheared_oracle
     ctx = P.cf_create(0)
@@ -109,10 +113,46 @@ def test_taylor_deformation_by_format(P, sheared_oracle, fmt, tol):
     assert abs(D - D_ref) <= tol * D_ref
 
 
+def test_stochastic_rounding_keeps_small_increments(P):
+    """A weak body force in a channel at rest: per step each population
+    changes by far less than half an FP16 unit in the last place, so
+    round-to-nearest stores lose the increments and the flow stagnates;
+    stochastic rounding keeps them on average. Mean x velocity after 400
+    steps against the FP64 oracle."""
+    args = (16, 48, 8, 1.0, 0.0, 0.0, (2e-7, 0.0, 0.0), 400)
+    fl = oracle_fluid(*args)
+    ref = fl.u[..., 0].mean()
+    errs = {}
+    for fmt in ("f32", "f16", "f16sr", "bf16", "bf16sr"):
+        u, _ = fluid_run(P, fmt, *args)
+        errs[fmt] = abs(u[..., 0].mean() - ref) / abs(ref)
+    print("relative error of the mean velocity:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["f32"] <= 1e-5
+    assert errs["f16sr"] <= 1e-4 and errs["bf16sr"] <= 1e-3
+    assert errs["f16sr"] <= errs["f16"] / 20 and errs["bf16sr"] <= errs["bf16"] / 20
+
+
+def test_stochastic_rounding_is_reproducible_and_seeded_per_step(P):
+    """The same run twice gives the same result (the rounding bits come from
+    a hash of node, direction and a per-step seed); the seed advances every
+    step, also across separate cf_step calls."""
+    args = (16, 24, 8, 0.8, -0.02, 0.02, (2e-6, 0.0, 0.0))
+    runs = []
+    for split in ((300,), (100, 1, 199)):
+        ctx = P.cf_create(0)
+        P.cf_set_population_format(ctx, "f16sr")
+        P.cf_lbm_init(ctx, *args)
+        for n in split:
+            P.cf_step(ctx, n)
+        runs.append(P.cf_get_velocity(ctx))
+    assert np.array_equal(runs[0], runs[1])
+
+
 def test_format_is_validated(P):
     from paper_2003_03130_gb300 import CellFSIError
 
     ctx = P.cf_create(0)
-    with pytest.raises(CellFSIError) as e:
-        P.cf_set_population_format(ctx, 7)
-    assert e.value.name == "CF_EINVAL"
+    for bad in (5, 7, -1):
+        with pytest.raises(CellFSIError) as e:
+            P.cf_set_population_format(ctx, bad)
+        assert e.value.name == "CF_EINVAL"
