@@ -36,17 +36,18 @@ namespace cf {
 
 // ---------------------------------------------------------------- storage
 // ld / st: streaming loads and stores with round-to-nearest conversion;
-// st_sr: stochastic rounding to the 16-bit format with the random bits r.
-// Adding uniform random bits below the last kept mantissa bit of the FP32
-// pattern and truncating rounds the magnitude up with probability equal to
-// the dropped fraction, so the rounding is unbiased (13 dropped bits for
-// FP16, 16 for BF16; exact for FP16-normal values, and non-finite values
-// take the nearest rounding).
+// st_sr: stochastic rounding to the 16-bit format, the dither being random
+// bits below the last kept mantissa bit (13 bits for FP16, 16 for BF16).
+// Adding them to the FP32 pattern and truncating rounds the magnitude up
+// with probability equal to the dropped fraction, so the rounding is
+// unbiased (exact for FP16-normal values). The caller passes a zero dither
+// for non-finite values, which then convert as they are.
 template <class T>
 struct Pop;
 
 template <>
 struct Pop<float> {
+    static constexpr int kDropped = 0;
     static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
     static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
     static __device__ __forceinline__ void st_sr(float *p, float v, unsigned) { __stcs(p, v); }
@@ -54,28 +55,29 @@ struct Pop<float> {
 
 template <>
 struct Pop<__half> {
+    static constexpr int kDropped = 13;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
     static __device__ __forceinline__ void st(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
-    static __device__ __forceinline__ void st_sr(__half *p, float v, unsigned r) {
-        if (!isfinite(v)) return st(p, v);
-        __stcs(p, __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1fffu))));
+    static __device__ __forceinline__ void st_sr(__half *p, float v, unsigned dither) {
+        __stcs(p, __float2half_rz(__uint_as_float(__float_as_uint(v) + dither)));
     }
 };
 
 template <>
 struct Pop<__nv_bfloat16> {
+    static constexpr int kDropped = 16;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
-    static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r) {
-        if (!isfinite(v)) return st(p, v);
-        __stcs(p, __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xffffu))));
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned dither) {
+        __stcs(p, __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + dither)));
     }
 };
 
-// Integer hash for the rounding bits: the "lowbias32" xorshift-multiply
-// finaliser (C. Wellons, "Prospecting for hash functions", 2018). Node n of
-// the step with seed s draws h = mix32(n ^ mix32(s)); population q takes 16
-// bits of mix32(h + (q >> 1) * 0x9e3779b9).
+// Random bits for the dither: h = mix32(n ^ mix32(seed)) per node with the
+// "lowbias32" xorshift-multiply finaliser (C. Wellons, "Prospecting for hash
+// functions", 2018); population q takes the top bits of the Weyl step
+// h + q * 0x9e3779b9 (uniform for every q, independent across steps through
+// the seed).
 __device__ __forceinline__ unsigned mix32(unsigned x) {
     x ^= x >> 16;
     x *= 0x7feb352du;
@@ -235,15 +237,18 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         vel[N + n] = u.y;
         vel[2 * N + n] = u.z;
     }
-    if (sizeof(T) == 2 && p.sr) {
-        const unsigned h = mix32((unsigned)n ^ mix32(seed));
+    if constexpr (sizeof(T) == 2) {
+        if (p.sr) {
+            const unsigned h = mix32((unsigned)n ^ mix32(seed));
+            // a non-finite node (any NaN input makes u NaN) converts without dither
+            const unsigned mask = isfinite(u.x + u.y + u.z) ? (1u << Pop<T>::kDropped) - 1u : 0u;
 #pragma unroll
-        for (int q = 0; q < 19; q += 2) {
-            const unsigned r = mix32(h + (unsigned)(q >> 1) * 0x9e3779b9u);
-            Pop<T>::st_sr(fout + q * N + n, d[q] * pop_scale<T>(q), r);
-            if (q + 1 < 19) Pop<T>::st_sr(fout + (q + 1) * N + n, d[q + 1] * pop_scale<T>(q + 1), r >> 16);
+            for (int q = 0; q < 19; ++q) {
+                const unsigned r = (h + (unsigned)q * 0x9e3779b9u) >> (32 - Pop<T>::kDropped);
+                Pop<T>::st_sr(fout + q * N + n, d[q] * pop_scale<T>(q), r & mask);
+            }
+            return;
         }
-        return;
     }
 #pragma unroll
     for (int q = 0; q < 19; ++q) Pop<T>::st(fout + q * N + n, d[q] * pop_scale<T>(q));
