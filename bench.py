@@ -439,7 +439,7 @@ def run_reference(args):
     fv = np.zeros((V, 3))
     vel = np.zeros((V, 3))
     fout = np.empty_like(fl.f)
-    cell = mesh.cell
+    cell = mesh.tmat  # material slot of each tet
 
     def sample(k, m):
         t0, t1 = k * T // m, (k + 1) * T // m

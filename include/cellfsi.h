@@ -132,9 +132,23 @@ cf_status cf_mesh_init_batch(cf_ctx *ctx, int32_t ncells, const int32_t *nv, con
 cf_status cf_set_material(cf_ctx *ctx, int32_t cell_id, double mu, double kappa, double w);
 
 /* Materials of several cells at once: ids[ncells], mu, kappa, w as in
- * cf_set_material (all validated before any is applied). */
+ * cf_set_material (all validated before any is applied). Setting a cell's
+ * material makes it uniform again after cf_set_tet_materials. */
 cf_status cf_set_materials(cf_ctx *ctx, int32_t ncells, const int32_t *ids, const double *mu, const double *kappa,
                            const double *w);
+
+/* Materials per tet within one cell (Sec. 3.1: the force is local to each
+ * tet, so regions of a cell such as a nucleus or a cortex may carry their
+ * own elastic parameters). region[nt] assigns each of the cell's tets
+ * (in its cf_mesh_init order, after the orientation fix, which keeps tet
+ * order) to one of nreg >= 1 regions; mu[nreg], kappa[nreg], w[nreg] as in
+ * cf_set_material. Forces, energies, steps and the force JVP use the per-tet
+ * materials; the parameter gradients (cf_force_param_vjp,
+ * cf_relax_adjoint, cf_adjoint_gradients) are per cell and return
+ * CF_ESTATE while any cell has per-tet materials. Errors: CF_EINVAL (unknown
+ * cell, region index out of range, parameter range). */
+cf_status cf_set_tet_materials(cf_ctx *ctx, int32_t cell_id, const int32_t *region, int32_t nreg, const double *mu,
+                               const double *kappa, const double *w);
 
 /* Advance n >= 0 coupled time steps t -> t+1, each: elastic forces at y^t,
  * vertex sums, spread onto the lattice, one stream-collide with that force,

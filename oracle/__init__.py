@@ -147,7 +147,10 @@ def gather(ptr, idx, fc):
 
 class Mesh:
     """All cells of a run as one mesh: concatenated vertices and tets,
-    per-tet cell index, per-cell material (mu, kappa, w)."""
+    per-tet cell index, and a material table (mu, kappa, w): slot c is cell
+    c's material; a cell with per-tet regions (Sec. 3.1: the force is local,
+    so regions may differ) gets further slots, one per region, and its tets
+    point at them through ``tmat``."""
 
     def __init__(self, cells):
         xs, ts, cid, off = [], [], [], 0
@@ -161,9 +164,17 @@ class Mesh:
         self.cell = np.concatenate(cid) if cid else np.zeros(0, np.int32)
         self.tets, self.B, self.V0 = mesh_prepare(self.x, tets)
         self.ptr, self.idx = csr(len(self.x), self.tets)
-        self.mu = np.array([c.mu for c in cells], np.float64)
-        self.kappa = np.array([c.kappa for c in cells], np.float64)
-        self.w = np.array([c.w for c in cells], np.float64)
+        mats = [(c.mu, c.kappa, c.w) for c in cells]
+        self.tmat = self.cell.copy()
+        t0 = 0
+        for c in cells:
+            if getattr(c, "regions", None) is not None:
+                self.tmat[t0:t0 + len(c.tets)] = len(mats) + _i32(c.regions)
+                mats += [tuple(m) for m in c.region_materials]
+            t0 += len(c.tets)
+        self.mu = np.array([m[0] for m in mats], np.float64)
+        self.kappa = np.array([m[1] for m in mats], np.float64)
+        self.w = np.array([m[2] for m in mats], np.float64)
         self.vert_ranges = []
         o = 0
         for c in cells:
@@ -172,7 +183,7 @@ class Mesh:
 
     def forces(self, y, energy=False):
         """Vertex forces [V,3] at positions y (u = y - x)."""
-        r = tet_forces(self.tets, self.B, self.V0, _f64(y) - self.x, self.cell, self.mu, self.kappa, self.w,
+        r = tet_forces(self.tets, self.B, self.V0, _f64(y) - self.x, self.tmat, self.mu, self.kappa, self.w,
                        energy=energy)
         if energy:
             fc, en = r
@@ -180,7 +191,7 @@ class Mesh:
         return gather(self.ptr, self.idx, r)
 
     def energy(self, y):
-        _, en = tet_forces(self.tets, self.B, self.V0, _f64(y) - self.x, self.cell, self.mu, self.kappa,
+        _, en = tet_forces(self.tets, self.B, self.V0, _f64(y) - self.x, self.tmat, self.mu, self.kappa,
                            self.w, energy=True)
         return float(en.sum())
 

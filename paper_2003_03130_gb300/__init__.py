@@ -52,6 +52,7 @@ def lib():
             "cf_mesh_init": ([vp, ctypes.c_int32, _d, ctypes.c_int32, _i, _d, _i], ctypes.c_int),
             "cf_mesh_init_batch": ([vp, ctypes.c_int32, _i, _d, _i, _i, _d, _i], ctypes.c_int),
             "cf_set_materials": ([vp, ctypes.c_int32, _i, _d, _d, _d], ctypes.c_int),
+            "cf_set_tet_materials": ([vp, ctypes.c_int32, _i, ctypes.c_int32, _d, _d, _d], ctypes.c_int),
             "cf_set_material": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
             "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
@@ -229,6 +230,19 @@ def cf_set_materials(ctx, ids, mu, kappa, w):
 
 def cf_set_material(ctx, cell_id, mu, kappa, w):
     _check(ctx, lib().cf_set_material(ctx.handle, cell_id, mu, kappa, w))
+
+
+def cf_set_tet_materials(ctx, cell_id, region, mu, kappa, w):
+    """Per-tet materials of one cell: ``region`` [nt] in [0, nreg), and
+    ``mu``, ``kappa``, ``w`` [nreg]."""
+    region = np.ascontiguousarray(region, dtype=np.int32).reshape(-1)
+    mu, kappa, w = _f64(np.atleast_1d(mu)), _f64(np.atleast_1d(kappa)), _f64(np.atleast_1d(w))
+    if not (len(mu) == len(kappa) == len(w)):
+        raise ValueError("mu, kappa, w need one value per region")
+    nt = lib().cf_cell_tets(ctx.handle, cell_id)
+    if nt > 0 and len(region) != nt:
+        raise ValueError(f"region needs one entry per tet of the cell ({nt})")
+    _check(ctx, lib().cf_set_tet_materials(ctx.handle, cell_id, _p(region, _i), len(mu), _p(mu), _p(kappa), _p(w)))
 
 
 def cf_step(ctx, n: int = 1):
@@ -439,4 +453,8 @@ def load_workload(ctx, wl):
         return []
     ids = cf_mesh_init_batch(ctx, [c.x_ref for c in wl.cells], [c.tets for c in wl.cells], [c.y0 for c in wl.cells])
     cf_set_materials(ctx, ids, [c.mu for c in wl.cells], [c.kappa for c in wl.cells], [c.w for c in wl.cells])
+    for i, c in zip(ids, wl.cells):
+        if getattr(c, "regions", None) is not None:
+            m = np.asarray(c.region_materials, np.float64).reshape(-1, 3)
+            cf_set_tet_materials(ctx, i, c.regions, m[:, 0], m[:, 1], m[:, 2])
     return ids

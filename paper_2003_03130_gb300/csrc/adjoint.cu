@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) k_tet_jvp(MeshView m, const float4 *__res
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) Hd[i][j] = Dual(H[i][j], dH[i][j]);
-    const float4 mat = __ldg(m.mat + __ldg(m.tcell + t));
+    const float4 mat = __ldg(m.mat + mat_slot(m, t));
     InvT<Dual> inv;
     Dual P[3][3];
     mr_stress(Hd, mat.x, mat.y, mat.z, inv, P);

@@ -298,6 +298,7 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->Bp);
     dfree(c->V0);
     dfree(c->tcell);
+    dfree(c->tmat);
     dfree(c->origin);
     dfree(c->mat);
     dfree(c->csr_ptr);
@@ -438,7 +439,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     int *tin = nullptr;
     auto cleanup = [&]() {
         dfree(n.xr); dfree(n.u[0]); dfree(n.u[1]); dfree(n.fv); dfree(n.fc); dfree(n.xref64); dfree(n.tet);
-        dfree(n.B); dfree(n.Bp); dfree(n.V0); dfree(n.tcell); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
+        dfree(n.B); dfree(n.Bp); dfree(n.V0); dfree(n.tcell); dfree(n.tmat); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
         dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(n.taylor_partial);
         dfree(x64); dfree(y64); dfree(tin);
     };
@@ -462,8 +463,9 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     TRY_N(dalloc(&n.Bp, 3 * (size_t)T1));
     TRY_N(dalloc(&n.V0, T1));
     TRY_N(dalloc(&n.tcell, T1));
+    TRY_N(dalloc(&n.tmat, T1));
     TRY_N(dalloc(&n.origin, 3 * (size_t)C1));
-    TRY_N(dalloc(&n.mat, C1));
+    TRY_N(dalloc(&n.mat, C1 + c->rmats.size()));
     TRY_N(dalloc(&n.csr_ptr, V1 + 1));
     TRY_N(dalloc(&n.csr_idx, 4 * (size_t)T1));
     TRY_N(dalloc(&n.csr_cursor, V1));
@@ -484,9 +486,11 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
                                 cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpyAsync(n.V0, c->V0, sizeof(float) * c->T, cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpyAsync(n.tcell, c->tcell, sizeof(int) * c->T, cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpyAsync(n.tmat, c->tmat, sizeof(int) * c->T, cudaMemcpyDeviceToDevice, s));
+        TRY_N(launch_shift_slots(c->T, cell0, ncells, n.tmat, s));  // region slots follow the cells
     }
     std::vector<int> orig(3 * (size_t)C1);
-    std::vector<float4> mats(C1);
+    std::vector<float4> mats(C1 + c->rmats.size());
     for (int i = 0; i < cell0; ++i) {
         for (int a = 0; a < 3; ++a) orig[3 * i + a] = c->cells[i].origin[a];
         mats[i] = c->cells[i].mat;
@@ -495,6 +499,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
         for (int a = 0; a < 3; ++a) orig[3 * (cell0 + k) + a] = add[k].origin[a];
         mats[cell0 + k] = add[k].mat;
     }
+    for (size_t i = 0; i < c->rmats.size(); ++i) mats[C1 + i] = c->rmats[i];
     TRY_N(cudaMemcpyAsync(n.origin, orig.data(), sizeof(int) * orig.size(), cudaMemcpyHostToDevice, s));
     TRY_N(cudaMemcpyAsync(n.mat, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice, s));
     TRY_N(cudaMemcpyAsync(x64, x_ref, sizeof(double) * 3 * Vadd, cudaMemcpyHostToDevice, s));
@@ -522,7 +527,8 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
         TRY_N(launch_vertex_prepare(x64 + 3 * voff[k], y64 ? y64 + 3 * voff[k] : nullptr, nv[k], add[k].v_off,
                                     cell0 + k, add[k].origin, n.xr, n.u[0], n.u[1], n.xref64, s));
     TRY_N(launch_csr_build(n.tet, T1, V1, n.csr_ptr, n.csr_idx, n.csr_cursor, s));
-    TRY_N(launch_pack_tets(T1, n.B, n.V0, n.tcell, n.Bp, s));
+    TRY_N(cudaMemcpyAsync(n.tmat + c->T, n.tcell + c->T, sizeof(int) * (T1 - c->T), cudaMemcpyDeviceToDevice, s));
+    TRY_N(launch_pack_tets(T1, n.B, n.V0, n.tmat, n.Bp, s));
     TRY_N(cudaStreamSynchronize(s));
 #undef TRY_N
     dfree(x64);
@@ -540,8 +546,10 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     std::swap(c->Bp, n.Bp);
     std::swap(c->V0, n.V0);
     std::swap(c->tcell, n.tcell);
+    std::swap(c->tmat, n.tmat);
     std::swap(c->origin, n.origin);
     std::swap(c->mat, n.mat);
+    c->mat_cap = C1 + c->rmats.size();
     std::swap(c->csr_ptr, n.csr_ptr);
     std::swap(c->csr_idx, n.csr_idx);
     std::swap(c->csr_cursor, n.csr_cursor);
@@ -563,6 +571,57 @@ cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, c
     return cf_mesh_init_batch(c, 1, &nv, x_ref, &nt, tets, y0, cell_id_out);
 }
 
+}  // extern "C"
+
+namespace {
+
+bool material_ok(double mu, double kappa, double w) {
+    return mu >= 0.0 && kappa >= 0.0 && w >= 0.0 && w <= 1.0 && std::isfinite(mu) && std::isfinite(kappa);
+}
+
+float4 material_of(double mu, double kappa, double w) {
+    return make_float4((float)(w * mu), (float)((1.0 - w) * mu), (float)kappa, (float)w);
+}
+
+// Upload the material table [cells..., region slots...] (grown when needed).
+cf_status upload_materials(cf_ctx *c) {
+    std::vector<float4> mats(c->cells.size() + c->rmats.size());
+    for (size_t i = 0; i < c->cells.size(); ++i) mats[i] = c->cells[i].mat;
+    for (size_t i = 0; i < c->rmats.size(); ++i) mats[c->cells.size() + i] = c->rmats[i];
+    if (mats.empty()) return CF_OK;
+    if (mats.size() > c->mat_cap) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no kernel still reads the old table
+        float4 *grown = nullptr;
+        CUDA_TRY(c, dalloc(&grown, mats.size()));
+        dfree(c->mat);
+        c->mat = grown;
+        c->mat_cap = mats.size();
+        drop_graphs(c);  // captured launches hold the old table's address
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->mat, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    return CF_OK;
+}
+
+// Point the tets of a cell at material slots (slot ids on the host, or the
+// cell's own slot when null) and refresh the packed rows.
+cf_status set_tet_slots(cf_ctx *c, int id, const int *slots) {
+    const CellInfo &ci = c->cells[id];
+    if (slots) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->tmat + ci.t_off, slots, sizeof(int) * ci.nt, cudaMemcpyHostToDevice,
+                                    c->stream));
+    } else {
+        CUDA_TRY(c, cudaMemcpyAsync(c->tmat + ci.t_off, c->tcell + ci.t_off, sizeof(int) * ci.nt,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CUDA_TRY(c, launch_pack_tets(c->T, c->B, c->V0, c->tmat, c->Bp, c->stream));
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 cf_status cf_set_materials(cf_ctx *c, int32_t ncells, const int32_t *ids, const double *mu, const double *kappa,
                            const double *w) {
     if (!c) return CF_EINVAL;
@@ -570,32 +629,48 @@ cf_status cf_set_materials(cf_ctx *c, int32_t ncells, const int32_t *ids, const 
     if (ncells < 0 || (ncells > 0 && (!ids || !mu || !kappa || !w))) return fail(c, CF_EINVAL, "null arrays");
     for (int k = 0; k < ncells; ++k) {
         if (ids[k] < 0 || ids[k] >= (int)c->cells.size()) return fail(c, CF_EINVAL, "unknown cell %d", ids[k]);
-        if (!(mu[k] >= 0.0 && kappa[k] >= 0.0 && w[k] >= 0.0 && w[k] <= 1.0 && std::isfinite(mu[k]) &&
-              std::isfinite(kappa[k])))
+        if (!material_ok(mu[k], kappa[k], w[k]))
             return fail(c, CF_EINVAL, "cell %d: need mu >= 0, kappa >= 0, 0 <= w <= 1", ids[k]);
     }
-    std::vector<float4> mats(c->cells.size());
     for (int k = 0; k < ncells; ++k) {
         CellInfo &ci = c->cells[ids[k]];
-        ci.mat = make_float4((float)(w[k] * mu[k]), (float)((1.0 - w[k]) * mu[k]), (float)kappa[k], (float)w[k]);
+        ci.mat = material_of(mu[k], kappa[k], w[k]);
+        if (ci.per_tet) {  // uniform again
+            cf_status st = set_tet_slots(c, ids[k], nullptr);
+            if (st != CF_OK) return st;
+            ci.per_tet = false;
+        }
     }
-    for (size_t i = 0; i < c->cells.size(); ++i) mats[i] = c->cells[i].mat;
-    if (!mats.empty())
-        CUDA_TRY(c, cudaMemcpyAsync(c->mat, mats.data(), sizeof(float4) * mats.size(), cudaMemcpyHostToDevice,
-                                    c->stream));
-    return wait_stream(c);
+    cf_status st = upload_materials(c);
+    return st != CF_OK ? st : wait_stream(c);
 }
 
 cf_status cf_set_material(cf_ctx *c, int32_t id, double mu, double kappa, double w) {
+    return cf_set_materials(c, 1, &id, &mu, &kappa, &w);
+}
+
+cf_status cf_set_tet_materials(cf_ctx *c, int32_t id, const int32_t *region, int32_t nreg, const double *mu,
+                               const double *kappa, const double *w) {
     if (!c) return CF_EINVAL;
     DeviceGuard dg(c->device);
     if (id < 0 || id >= (int)c->cells.size()) return fail(c, CF_EINVAL, "unknown cell %d", id);
-    if (!(mu >= 0.0 && kappa >= 0.0 && w >= 0.0 && w <= 1.0 && std::isfinite(mu) && std::isfinite(kappa)))
-        return fail(c, CF_EINVAL, "need mu >= 0, kappa >= 0, 0 <= w <= 1");
+    if (nreg < 1 || !region || !mu || !kappa || !w) return fail(c, CF_EINVAL, "need nreg >= 1 and non-null arrays");
+    for (int r = 0; r < nreg; ++r)
+        if (!material_ok(mu[r], kappa[r], w[r]))
+            return fail(c, CF_EINVAL, "region %d: need mu >= 0, kappa >= 0, 0 <= w <= 1", r);
     CellInfo &ci = c->cells[id];
-    ci.mat = make_float4((float)(w * mu), (float)((1.0 - w) * mu), (float)kappa, (float)w);
-    CUDA_TRY(c, cudaMemcpyAsync(c->mat + id, &ci.mat, sizeof(float4), cudaMemcpyHostToDevice, c->stream));
-    return wait_stream(c);
+    const int base = (int)(c->cells.size() + c->rmats.size());
+    std::vector<int> slots(ci.nt);
+    for (int t = 0; t < ci.nt; ++t) {
+        if (region[t] < 0 || region[t] >= nreg)
+            return fail(c, CF_EINVAL, "tet %d: region %d out of [0, %d)", t, region[t], nreg);
+        slots[t] = base + region[t];
+    }
+    for (int r = 0; r < nreg; ++r) c->rmats.push_back(material_of(mu[r], kappa[r], w[r]));
+    cf_status st = upload_materials(c);
+    if (st == CF_OK) st = set_tet_slots(c, id, slots.data());
+    if (st == CF_OK) ci.per_tet = true;
+    return st != CF_OK ? st : wait_stream(c);
 }
 
 cf_status cf_step_async(cf_ctx *c, int32_t n) {

@@ -24,6 +24,7 @@ struct CellInfo {
     int v_off, nv, t_off, nt;
     int origin[3];
     float4 mat;
+    bool per_tet = false;  // tets carry their own material slots (cf_set_tet_materials)
 };
 
 // Force-region tile shapes (log2 of the x, y, z extents; 256 nodes each).
@@ -75,6 +76,9 @@ struct cf_ctx {
     float *B = nullptr, *V0 = nullptr;
     float4 *Bp = nullptr;  // packed B / V0 / cell rows for the force kernel, [3][T]
     int *tcell = nullptr, *origin = nullptr;
+    int *tmat = nullptr;             // [T] material slot of each tet: its cell id, or a region slot
+    std::vector<float4> rmats;       // region materials: slots ncells + i
+    size_t mat_cap = 0;              // entries allocated in mat
     float4 *mat = nullptr;
     int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
     double *energy_partial = nullptr, *energy_out = nullptr;
@@ -161,6 +165,7 @@ MeshView view(const cf_ctx *c) {
     m.Bp = c->Bp;
     m.V0 = c->V0;
     m.tcell = c->tcell;
+    m.tmat = c->tmat;
     m.mat = c->mat;
     m.csr_ptr = c->csr_ptr;
     m.csr_idx = c->csr_idx;

@@ -80,7 +80,8 @@ struct MeshView {
     const float *B;        // [9][T]: B[(3k + j) * T + t] = (J^-1)_kj
     const float4 *Bp;      // [3][T] or null: row k of B with .w = V0, cell id (int bits), 0 for k = 0, 1, 2
     const float *V0;       // [T]
-    const int *tcell;      // [T]
+    const int *tcell;      // [T]: cell of each tet
+    const int *tmat;       // [T] or null: material slot of each tet (null: the cell's slot, = cell id)
     const float4 *mat;     // [ncells]: mu1, mu2, kappa, w
     const int *csr_ptr;    // [V+1]
     const int *csr_idx;    // [4T]: entries 4 t + c, ascending per row
@@ -257,8 +258,10 @@ cudaError_t launch_vertex_prepare(const double *x64, const double *y64, int nv, 
                                   const int *origin_host3, float4 *xr, float4 *u0, float4 *u1, double *xref64,
                                   cudaStream_t s);
 cudaError_t launch_csr_build(const int4 *tet, int T, int V, int *ptr, int *idx, int *cursor, cudaStream_t s);
-// Packed per-tet rows for the force kernel: Bp[k * T + t] = (B_k0, B_k1, B_k2, w_k), w = (V0, cell, 0).
-cudaError_t launch_pack_tets(int T, const float *B, const float *V0, const int *tcell, float4 *Bp, cudaStream_t s);
+// Packed per-tet rows for the force kernel: Bp[k * T + t] = (B_k0, B_k1, B_k2, w_k), w = (V0, material slot, 0).
+cudaError_t launch_pack_tets(int T, const float *B, const float *V0, const int *tmat, float4 *Bp, cudaStream_t s);
+// tmat[t] += delta where tmat[t] >= from, t < T (material slots move up when cells are added).
+cudaError_t launch_shift_slots(int T, int from, int delta, int *tmat, cudaStream_t s);
 cudaError_t launch_set_positions(const double *y64, int v0, int nv, const double *xref64, float4 *u,
                                  cudaStream_t s);
 cudaError_t launch_get_positions(const float4 *u, const double *xref64, int v0, int nv, double *y64,

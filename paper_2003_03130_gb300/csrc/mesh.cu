@@ -236,18 +236,29 @@ cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cud
 }
 
 __global__ void k_pack_tets(int T, const float *__restrict__ B, const float *__restrict__ V0,
-                            const int *__restrict__ tcell, float4 *__restrict__ Bp) {
+                            const int *__restrict__ tmat, float4 *__restrict__ Bp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
-    const float w[3] = {V0[t], __int_as_float(tcell[t]), 0.f};
+    const float w[3] = {V0[t], __int_as_float(tmat[t]), 0.f};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         Bp[k * T + t] = make_float4(B[(3 * k + 0) * T + t], B[(3 * k + 1) * T + t], B[(3 * k + 2) * T + t], w[k]);
 }
 
-cudaError_t launch_pack_tets(int T, const float *B, const float *V0, const int *tcell, float4 *Bp, cudaStream_t s) {
+cudaError_t launch_pack_tets(int T, const float *B, const float *V0, const int *tmat, float4 *Bp, cudaStream_t s) {
     if (T <= 0) return cudaSuccess;
-    k_pack_tets<<<(T + 255) / 256, 256, 0, s>>>(T, B, V0, tcell, Bp);
+    k_pack_tets<<<(T + 255) / 256, 256, 0, s>>>(T, B, V0, tmat, Bp);
+    return cudaGetLastError();
+}
+
+__global__ void k_shift_slots(int T, int from, int delta, int *tmat) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T && tmat[t] >= from) tmat[t] += delta;
+}
+
+cudaError_t launch_shift_slots(int T, int from, int delta, int *tmat, cudaStream_t s) {
+    if (T <= 0 || delta == 0) return cudaSuccess;
+    k_shift_slots<<<(T + 255) / 256, 256, 0, s>>>(T, from, delta, tmat);
     return cudaGetLastError();
 }
 

@@ -156,16 +156,20 @@ __device__ __forceinline__ void tet_grad(const float4 &w0, const float4 &w1, con
         for (int j = 0; j < 3; ++j) H[i][j] = A[i][0] * Bm[0][j] + A[i][1] * Bm[1][j] + A[i][2] * Bm[2][j];
 }
 
-// B, V0 and the tet's cell: three 16-byte loads from the packed rows when
-// the view has them, else eleven 4-byte loads from the separate arrays.
-__device__ __forceinline__ void load_tet_params(const MeshView &m, int t, float (&Bm)[3][3], float &V0, int &cell) {
+// Material slot of tet t.
+__device__ __forceinline__ int mat_slot(const MeshView &m, int t) { return __ldg((m.tmat ? m.tmat : m.tcell) + t); }
+
+// B, V0 and the tet's material slot: three 16-byte loads from the packed
+// rows when the view has them, else eleven 4-byte loads from the separate
+// arrays.
+__device__ __forceinline__ void load_tet_params(const MeshView &m, int t, float (&Bm)[3][3], float &V0, int &slot) {
     if (m.Bp) {
         const float4 r0 = __ldg(m.Bp + t), r1 = __ldg(m.Bp + m.T + t), r2 = __ldg(m.Bp + 2 * m.T + t);
         Bm[0][0] = r0.x; Bm[0][1] = r0.y; Bm[0][2] = r0.z;
         Bm[1][0] = r1.x; Bm[1][1] = r1.y; Bm[1][2] = r1.z;
         Bm[2][0] = r2.x; Bm[2][1] = r2.y; Bm[2][2] = r2.z;
         V0 = r0.w;
-        cell = __float_as_int(r1.w);
+        slot = __float_as_int(r1.w);
         return;
     }
 #pragma unroll
@@ -173,7 +177,7 @@ __device__ __forceinline__ void load_tet_params(const MeshView &m, int t, float 
 #pragma unroll
         for (int j = 0; j < 3; ++j) Bm[k][j] = __ldg(m.B + (3 * k + j) * m.T + t);
     V0 = __ldg(m.V0 + t);
-    cell = __ldg(m.tcell + t);
+    slot = mat_slot(m, t);
 }
 
 __device__ __forceinline__ void load_B(const MeshView &m, int t, float (&Bm)[3][3]) {

@@ -106,6 +106,15 @@ cf_status need_cells(cf_ctx *c) {
     return ensure_adjoint(c);
 }
 
+// The parameter gradients are per cell: a cell whose tets carry their own
+// materials has no single (mu, kappa, w) to differentiate.
+cf_status need_uniform_materials(cf_ctx *c) {
+    for (size_t i = 0; i < c->cells.size(); ++i)
+        if (c->cells[i].per_tet)
+            return fail(c, CF_ESTATE, "cell %zu has per-tet materials: parameter gradients are per cell", i);
+    return CF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -201,6 +210,7 @@ cf_status cf_tape_clear(cf_ctx *c) {
 
 cf_status cf_relax_adjoint(cf_ctx *c, const double *dF) {
     cf_status st = need_cells(c);
+    if (st == CF_OK) st = need_uniform_materials(c);
     if (st != CF_OK) return st;
     DeviceGuard dg(c->device);
     if (c->tape.empty()) return fail(c, CF_ESTATE, "no recorded cf_relax call left to reverse");
@@ -241,6 +251,7 @@ cf_status cf_relax_adjoint(cf_ctx *c, const double *dF) {
 
 cf_status cf_adjoint_gradients(cf_ctx *c, double *out) {
     cf_status st = need_cells(c);
+    if (st == CF_OK) st = need_uniform_materials(c);
     if (st != CF_OK) return st;
     DeviceGuard dg(c->device);
     if (!out) return fail(c, CF_EINVAL, "null output");
@@ -264,6 +275,7 @@ cf_status cf_force_jvp(cf_ctx *c, const double *v, double *out) {
 
 cf_status cf_force_param_vjp(cf_ctx *c, const double *lam, double *out) {
     cf_status st = need_cells(c);
+    if (st == CF_OK) st = need_uniform_materials(c);
     if (st != CF_OK) return st;
     DeviceGuard dg(c->device);
     if (!lam || !out) return fail(c, CF_EINVAL, "null array");

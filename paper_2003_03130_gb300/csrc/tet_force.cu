@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(256) k_energy(MeshView m, const float4 *__rest
         tet_grad(__ldg(u + a4.x), __ldg(u + a4.y), __ldg(u + a4.z), __ldg(u + a4.w), Bm, H);
         InvT<float> v;
         invariants_t(H, v);
-        const int c = __ldg(m.tcell + t);
-        const float4 mat = __ldg(m.mat + c);
+        const float4 mat = __ldg(m.mat + mat_slot(m, t));
         const float sm1 = expm1f(-(2.f / 3.f) * v.L);
         const float s2m1 = expm1f(-(4.f / 3.f) * v.L);
         const float s = 1.f + sm1, s2 = 1.f + s2m1;

@@ -84,7 +84,7 @@ def test_rigid_motion_has_no_force(m):
 def test_per_tet_balance(m):
     """Each tet's four corner forces sum to zero and exert no torque."""
     y = perturb(m.x, 0.15, 5)
-    fc = oracle.tet_forces(m.tets, m.B, m.V0, y - m.x, m.cell, m.mu, m.kappa, m.w)
+    fc = oracle.tet_forces(m.tets, m.B, m.V0, y - m.x, m.tmat, m.mu, m.kappa, m.w)
     scale = np.abs(fc).max()
     assert np.abs(fc.sum(1)).max() < 1e-13 * scale * 10
     torque = np.cross(y[m.tets], fc).sum(1)

@@ -16,6 +16,7 @@ Readings of the paper that fix these shapes:
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from typing import Optional
 
 import numpy as np
 
@@ -32,6 +33,9 @@ class Cell:
     mu: float
     kappa: float
     w: float
+    # optional materials per tet: region index [T] and one (mu, kappa, w) per region
+    regions: Optional[np.ndarray] = None
+    region_materials: Optional[list] = None
 
 
 @dataclass

@@ -89,3 +89,13 @@ def replicate_meshes(x: np.ndarray, tets: np.ndarray, offsets: np.ndarray):
     """Concatenate copies of one mesh shifted by ``offsets [n,3]``; returns a
     list of ``(x_i, tets)`` pairs (tets stay local to each copy)."""
     return [(x + o[None, :], tets) for o in np.asarray(offsets, np.float64)]
+
+
+def shell_regions(x, tets, r_inner, r_outer):
+    """Region of each tet by the distance of its centroid from the mesh's
+    centre: 0 inside r_inner (a nucleus), 2 beyond r_outer (a cortex), 1 in
+    between."""
+    x = np.asarray(x, np.float64)
+    c = x[np.asarray(tets)].mean(axis=1)
+    r = np.linalg.norm(c - x.mean(axis=0), axis=1)
+    return np.where(r < r_inner, 0, np.where(r > r_outer, 2, 1)).astype(np.int32)
