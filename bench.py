@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--box", default="512,256,256", help="lattice of the suspension workload")
     ap.add_argument("--delta", choices=("trilinear", "peskin4"), default="trilinear",
                     help="immersed-boundary delta kernel")
+    ap.add_argument("--fused", type=int, default=-1, choices=(-1, 0, 1),
+                    help="cell chain as one persistent launch (1) or two (0); -1: default / autotuner")
     ap.add_argument("--autotune-steps", type=int, default=20,
                     help="steps per launch-shape candidate of the autotuner in the warm-up (0: default shape)")
     ap.add_argument("--ca", type=float, default=0.2)
@@ -291,6 +293,8 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         ctx = P.cf_create(dev, stream.cuda_stream)
         ids = P.load_workload(ctx, wl)
+        if args.fused >= 0:
+            P.cf_set_launch_shape(ctx, {"fused": args.fused})
         P.cf_step(ctx, W)
         shape = P.cf_autotune(ctx, args.autotune_steps) if args.autotune_steps > 0 else P.cf_get_launch_shape(ctx)
         P.cf_prepare_steps(ctx, K)  # graph instantiation stays out of the timed region

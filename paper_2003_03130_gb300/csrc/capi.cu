@@ -66,6 +66,72 @@ cudaError_t clear_slot(const cf_ctx *c, const RegionSlot &r, cudaStream_t s) {
 }
 
 int near_grid(const cf_ctx *c) { return 8 * c->sms; }
+int chain_grid(const cf_ctx *c) { return 4 * c->sms; }
+
+// Work items of the fused cell chain: the region items over all vertices,
+// then the tet items of the cells in order, with the vertex-sum items of a
+// cell placed LAG items after its last tet item (by then its tets are most
+// likely done, so the sums rarely wait), then the remaining vertex-sum
+// items. Every item a vertex-sum item waits for comes before it.
+cf_status build_chain_items(cf_ctx *c) {
+    std::vector<int4> items;
+    // item sizes: small meshes keep every block busy, large ones keep the
+    // item count (one claim each) low
+    const int grid = chain_grid(c);
+    auto size_for = [&](int n, int lo, int hi) { return std::max(lo, std::min(hi, n / (2 * grid) / lo * lo)); };
+    const int RB = size_for(c->V, 256, 1024), TB = size_for(c->T, 256, 1024), GB = size_for(c->V, 64, 256);
+    const size_t LAG = 2 * (size_t)grid;
+    for (int v = 0; v < c->V; v += RB) items.push_back(make_int4(0, 0, v, std::min(c->V, v + RB)));
+    const int nregion = (int)items.size();
+    const int C = (int)c->cells.size();
+    std::vector<int> need(C, 0);
+    std::vector<size_t> last_tet(C, 0);
+    auto gathers = [&](int k) {
+        const CellInfo &ci = c->cells[k];
+        for (int v = ci.v_off; v < ci.v_off + ci.nv; v += GB)
+            items.push_back(make_int4(2, k, v, std::min(ci.v_off + ci.nv, v + GB)));
+    };
+    int next_sum = 0;  // first cell whose vertex sums are not placed yet
+    for (int k = 0; k < C; ++k) {
+        const CellInfo &ci = c->cells[k];
+        for (int t = ci.t_off; t < ci.t_off + ci.nt; t += TB) {
+            items.push_back(make_int4(1, k, t, std::min(ci.t_off + ci.nt, t + TB)));
+            ++need[k];
+            while (next_sum < k && items.size() >= last_tet[next_sum] + LAG) gathers(next_sum++);
+        }
+        last_tet[k] = items.size();
+    }
+    while (next_sum < C) gathers(next_sum++);
+    dfree(c->chain_items);
+    dfree(c->chain_need);
+    dfree(c->chain_ctr);
+    c->chain_nitems = 0;
+    CUDA_TRY(c, dalloc(&c->chain_items, items.size()));
+    CUDA_TRY(c, dalloc(&c->chain_need, std::max(C, 1)));
+    CUDA_TRY(c, dalloc(&c->chain_ctr, 2 + std::max(C, 1)));
+    CUDA_TRY(c, cudaMemcpyAsync(c->chain_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    if (C) CUDA_TRY(c, cudaMemcpyAsync(c->chain_need, need.data(), sizeof(int) * C, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+    c->chain_nitems = (int)items.size();
+    c->chain_nregion = nregion;
+    return CF_OK;
+}
+
+// K1 + K23 of one step on stream s: the fused persistent launch, or the two
+// separate kernels.
+cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, const RegionSlot &acc,
+                              const RegionSlot &use, cudaStream_t s) {
+    if (sh.fused) {
+        cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
+        if (e != cudaSuccess) return e;
+        return launch_cell_chain(m, c->u[p], c->u[1 - p], c->F, c->lp, acc, use.bits, c->d_err, c->chain_items,
+                                 c->chain_nitems, c->chain_nregion, c->chain_need, c->chain_ctr, chain_grid(c), s);
+    }
+    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &acc, use.bits);
+    if (e != cudaSuccess) return e;
+    return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
+}
 
 // Tile fields of the lattice parameters for tile shape k.
 void set_tiles(LbmParams &p, int k) {
@@ -116,9 +182,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
         CUDA_TRY(c, clear_slot(c, acc, sc));
-        CUDA_TRY(c, launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, sc, sh.tet_block, &acc,
-                                     use.bits));
-        CUDA_TRY(c, launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, sc, sh.gather_block));
+        CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, use, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c),
                                     c->seed + p, c->seed + 1 - p, sc));
@@ -299,6 +363,9 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->V0);
     dfree(c->tcell);
     dfree(c->tmat);
+    dfree(c->chain_items);
+    dfree(c->chain_need);
+    dfree(c->chain_ctr);
     dfree(c->origin);
     dfree(c->mat);
     dfree(c->csr_ptr);
@@ -563,7 +630,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
         c->cells.push_back(add[k]);
         if (cell_ids_out) cell_ids_out[k] = cell0 + k;
     }
-    return CF_OK;
+    return build_chain_items(c);
 }
 
 cf_status cf_mesh_init(cf_ctx *c, int32_t nv, const double *x_ref, int32_t nt, const int32_t *tets, const double *y0,
@@ -740,12 +807,13 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
                 e = clear_slot(c, accm, s);
-                if (e == cudaSuccess)
+                if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, use, s);
+                if (e == cudaSuccess && !sh.fused)
                     e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &accm,
                                          use.bits);
             }
-            cudaEventRecord(E[2], s);
-            if (cells && e == cudaSuccess)
+            cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
+            if (cells && e == cudaSuccess && !sh.fused)
                 e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
@@ -842,6 +910,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[3] = sh.tet_block;
     shape[4] = sh.gather_block;
     shape[5] = sh.interp_block;
+    shape[6] = sh.fused;
     return CF_OK;
 }
 
@@ -863,6 +932,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.tet_block = shape[3];
     sh.gather_block = shape[4];
     sh.interp_block = shape[5];
+    if (shape[6] != 0 && shape[6] != 1) return fail(c, CF_EINVAL, "fused must be 0 or 1");
+    sh.fused = shape[6];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -887,6 +958,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
         };
         const Knob knobs[] = {
             {&Shape::tile, {0, 1, 2, 3}, {1, 2, 3}},
+            {&Shape::fused, {0, 1}, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}, {0}},
             {&Shape::gather_block, {64, 128, 256}, {1}},
             {&Shape::interp_block, {64, 128, 256}, {4}},

@@ -1,0 +1,170 @@
+// Per-element bodies of the cell kernels, shared by the separate launches
+// (csrc/tet_force.cu, csrc/ibm.cu) and the fused persistent chain
+// (csrc/chain.cu): tet corner forces, the per-vertex region work, and the
+// vertex sum with its spread.
+#pragma once
+
+#include "mr.cuh"
+
+namespace cf {
+
+// Corner forces of tet t (Sec. 3.1): f^a = -V0 P B_a, f^4 = -(f^1 + f^2 + f^3).
+__device__ __forceinline__ void tet_corner_forces(const MeshView &m, const float4 *__restrict__ u, unsigned *err,
+                                                  int t) {
+    const int4 a4 = __ldg(m.tet + t);
+    float Bm[3][3], V0;
+    int cell;
+    load_tet_params(m, t, Bm, V0, cell);
+    float H[3][3];
+    tet_grad(__ldg(u + a4.x), __ldg(u + a4.y), __ldg(u + a4.z), __ldg(u + a4.w), Bm, H);
+    const float4 mat = __ldg(m.mat + cell);
+    InvT<float> v;
+    float P[3][3];
+    mr_stress(H, mat.x, mat.y, mat.z, v, P);
+    if (!(v.J > 0.f)) atomicOr(err, ERR_INVERTED);
+    float f[4][3];
+    corner_forces(P, Bm, V0, f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m.fc[a * m.T + t] = make_float4(f[a][0], f[a][1], f[a][2], 0.f);
+}
+
+// Zero the force field on the delta support of x + u_prev: every nonzero
+// entry of F was spread there in the previous step.
+template <int W>
+__device__ __forceinline__ void clear_support(const MeshView &m, const float4 *__restrict__ u_prev, float *F,
+                                              const LbmParams &lp, int v) {
+    Support sp;
+    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u_prev + v), lp.ny, sp)) return;  // nothing was spread
+    const int N = (int)lp.N;
+#pragma unroll
+    for (int dz = 0; dz < W; ++dz) {
+        const int Z = wrapi(sp.bz + dz, lp.nz);
+#pragma unroll
+        for (int dy = 0; dy < W; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < W; ++dx) {
+                const int n = wrapi(sp.bx + dx, lp.nx) + lp.nx * (sp.by + dy + lp.ny * Z);
+                F[n] = 0.f;
+                F[N + n] = 0.f;
+                F[2 * N + n] = 0.f;
+            }
+    }
+}
+
+// The per-vertex part of K1: clear last step's spread, add the next step's
+// region, check this step's region.
+template <int W>
+__device__ __forceinline__ void vertex_region(const MeshView &m, const float4 *__restrict__ u,
+                                              const float4 *__restrict__ u_prev, float *F, const LbmParams &lp,
+                                              int v, const RegionSlot &mark, const unsigned *__restrict__ bits_in,
+                                              unsigned *err) {
+    clear_support<W>(m, u_prev, F, lp, v);
+    Support s;
+    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s)) return;  // K23 reports it
+    if (mark.bits) mark_region<W>(s, lp, mark);
+    if (bits_in && !region_covers<W>(s, lp, bits_in)) atomicOr(err, ERR_MOVED);
+}
+
+// Corner-force load: from L2 (FC_L2) when the forces were written by other
+// blocks of the same launch, so that no stale L1 line is read.
+template <bool FC_L2>
+__device__ __forceinline__ float4 load_fc(const float4 *p) {
+    if constexpr (FC_L2)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// Vertex force of vertex v and, with do_spread, its spread onto F. Four lanes
+// per vertex (lane 0..3; every lane of the warp takes part in the shuffles,
+// `live` false for padding lanes): lane k sums the entries k, k+4, k+8, ...
+// of the incidence row, the four partial sums are combined by a fixed
+// shuffle tree (the same order every call: deterministic), and lane k
+// spreads onto its share of the support nodes.
+template <int W, bool FC_L2>
+__device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const float4 *__restrict__ u, float *F,
+                                                     const LbmParams &p, int do_spread, unsigned *err, int v,
+                                                     int lane, bool live) {
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (live) {
+        // the lane's entries e0 + lane, + 4, + 8, ... in groups of four: the
+        // index loads of a group, then its corner-force loads, are issued
+        // together; the sum still runs over the entries in ascending order
+        const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
+        for (int e = e0 + lane; e < e1; e += 16) {
+            int id[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) id[k] = e + 4 * k < e1 ? __ldg(m.csr_idx + e + 4 * k) : -1;
+            float4 c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                c[k] = id[k] >= 0 ? load_fc<FC_L2>(m.fc + (id[k] & 3) * m.T + (id[k] >> 2)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (id[k] >= 0) {
+                    fx += c[k].x;
+                    fy += c[k].y;
+                    fz += c[k].z;
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (live) {
+        if (lane == 0) {
+            m.fv[v] = make_float4(fx, fy, fz, 0.f);
+            if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
+        }
+        Support s;
+        if (!do_spread) {
+        } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+            if (lane == 0) atomicOr(err, ERR_DOMAIN);
+        } else {
+            const int N = (int)p.N;
+            float wx[W], wy[W], wz[W];
+            delta_weights<W>(s.fx, wx);
+            delta_weights<W>(s.fy, wy);
+            delta_weights<W>(s.fz, wz);
+            if constexpr (W == 2) {  // lane = (dz, dy), two nodes along x
+                const int dz = lane >> 1, dy = lane & 1;
+                const int Z = wrapi(s.bz + dz, p.nz);
+                const float wyz = wy[dy] * wz[dz];
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
+                    const float w = wx[dx] * wyz;
+                    atomicAdd(F + n, w * fx);
+                    atomicAdd(F + N + n, w * fy);
+                    atomicAdd(F + 2 * N + n, w * fz);
+                }
+            } else {  // lane = dz, a W x W plane
+                const int Z = wrapi(s.bz + lane, p.nz);
+                float wzl = wz[0];
+#pragma unroll
+                for (int k = 1; k < W; ++k) wzl = lane == k ? wz[k] : wzl;  // no local-memory indexing
+                int X[W];
+#pragma unroll
+                for (int dx = 0; dx < W; ++dx) X[dx] = wrapi(s.bx + dx, p.nx);
+#pragma unroll
+                for (int dy = 0; dy < W; ++dy) {
+                    const int row = p.nx * (s.by + dy + p.ny * Z);
+                    const float wyz = wy[dy] * wzl;
+#pragma unroll
+                    for (int dx = 0; dx < W; ++dx) {
+                        const int n = X[dx] + row;
+                        const float w = wx[dx] * wyz;
+                        atomicAdd(F + n, w * fx);
+                        atomicAdd(F + N + n, w * fy);
+                        atomicAdd(F + 2 * N + n, w * fz);
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace cf

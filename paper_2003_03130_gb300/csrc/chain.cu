@@ -1,0 +1,97 @@
+// K1 + K23 as one persistent launch over all cells (the batched form of the
+// cell chain): the per-vertex region work, the tet corner forces (Sec. 3.1)
+// and the vertex sums with their spread (Sec. 6), for cells of any size.
+//
+// Blocks take work items in a fixed order from one counter. A tet item never
+// waits; a vertex-sum item of cell c waits until every region item (they
+// clear last step's spread, which must precede any new spread) and every tet
+// item of cell c are done. The host orders the items so that every item an
+// item waits for comes before it; the block holding an earlier item is
+// therefore already running and never waits itself, so the waits end even
+// when blocks are not co-resident or other kernels share the GPU. Each wait
+// is still bounded: after kSpinLimit polls it sets ERR_WAIT and the block
+// skips the item. Vertex sums of early cells overlap the tet forces of later
+// ones, and one launch replaces two.
+#include "cell_ops.cuh"
+
+namespace cf {
+
+constexpr int kChainBlock = 256;
+constexpr long long kSpinLimit = 1LL << 24;  // with a 64 ns back-off: about a second
+
+__device__ __forceinline__ int load_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_count(const int *p, int target, unsigned *err) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        if (load_acquire(p) >= target) return true;
+        __nanosleep(64);
+    }
+    atomicOr(err, ERR_WAIT);
+    return false;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kChainBlock, 4)
+    k_cell_chain(MeshView m, const float4 *__restrict__ u, const float4 *__restrict__ u_prev, float *F,
+                 LbmParams lp, RegionSlot mark, const unsigned *__restrict__ bits_in, unsigned *err,
+                 const int4 *__restrict__ items, int nitems, int nregion, const int *__restrict__ need,
+                 int *counters) {
+    __shared__ int4 item;
+    __shared__ int ready;
+    int claim = 0;  // thread 0: the item claimed for the next round (claimed one round ahead)
+    if (threadIdx.x == 0) claim = atomicAdd(counters, 1);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = claim;
+            const int4 x = i < nitems ? items[i] : make_int4(-1, 0, 0, 0);
+            if (x.x >= 0) claim = atomicAdd(counters, 1);  // its latency hides under this item
+            int ok = 1;
+            if (x.x == 2) {
+                ok = wait_count(counters + 1, nregion, err) && wait_count(counters + 2 + x.y, need[x.y], err);
+                __threadfence();
+            }
+            item = x;
+            ready = ok;
+        }
+        __syncthreads();
+        const int4 x = item;
+        if (x.x < 0) break;
+        if (ready) {
+            if (x.x == 0) {
+                for (int v = x.z + threadIdx.x; v < x.w; v += kChainBlock)
+                    vertex_region<W>(m, u, u_prev, F, lp, v, mark, bits_in, err);
+            } else if (x.x == 1) {
+                for (int t = x.z + threadIdx.x; t < x.w; t += kChainBlock) tet_corner_forces(m, u, err, t);
+            } else {
+                for (int v0 = x.z; v0 < x.w; v0 += kChainBlock / 4) {  // the whole block takes each round
+                    const int v = v0 + (threadIdx.x >> 2);
+                    gather_spread_vertex<W, true>(m, u, F, lp, 1, err, v, threadIdx.x & 3, v < x.w);
+                }
+            }
+        }
+        __threadfence();  // this item's writes before its completion count
+        __syncthreads();
+        if (threadIdx.x == 0 && x.x != 2) atomicAdd(counters + (x.x == 0 ? 1 : 2 + x.y), 1);
+    }
+}
+
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, const float4 *u_prev, float *F,
+                              const LbmParams &lp, const RegionSlot &mark, const unsigned *bits_in, unsigned *err,
+                              const int4 *items, int nitems, int nregion, const int *need, int *counters, int blocks,
+                              cudaStream_t s) {
+    if (nitems == 0) return cudaSuccess;
+    const int g = blocks < nitems ? blocks : nitems;
+    if (lp.dw == 4)
+        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, bits_in, err, items, nitems, nregion,
+                                                   need, counters);
+    else
+        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, bits_in, err, items, nitems, nregion,
+                                                   need, counters);
+    return cudaGetLastError();
+}
+
+}  // namespace cf

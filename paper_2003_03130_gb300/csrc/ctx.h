@@ -36,6 +36,7 @@ constexpr int kNumTileShapes = 4;
 struct Shape {
     int tile = 0;  // index into kTileShapes
     int tet_block = 64, gather_block = 128, interp_block = 128;
+    int fused = 0;  // cell chain as one persistent launch (csrc/chain.cu) instead of two
 };
 
 }  // namespace cf
@@ -78,6 +79,10 @@ struct cf_ctx {
     int *tcell = nullptr, *origin = nullptr;
     int *tmat = nullptr;             // [T] material slot of each tet: its cell id, or a region slot
     std::vector<float4> rmats;       // region materials: slots ncells + i
+    // work items of the fused cell chain (csrc/chain.cu), rebuilt when cells are added
+    int4 *chain_items = nullptr;
+    int *chain_need = nullptr, *chain_ctr = nullptr;
+    int chain_nitems = 0, chain_nregion = 0;
     size_t mat_cap = 0;              // entries allocated in mat
     float4 *mat = nullptr;
     int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
@@ -199,6 +204,7 @@ cf_status consume_errors(cf_ctx *c) {
     if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
     if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
     if (h & ERR_MOVED) return fail(c, CF_EUNSTABLE, "a vertex moved a lattice spacing or more in one step");
+    if (h & ERR_WAIT) return fail(c, CF_ETIMEOUT, "a bounded wait in the fused cell chain gave up");
     return CF_OK;
 }
 

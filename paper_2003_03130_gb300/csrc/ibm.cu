@@ -21,7 +21,7 @@
 //   W = 2 lane (dz, dy, dx) its node, for W = 4 lane (dz, j) the rows
 //   dy = 2j, 2j + 1 of plane dz = 0..3) and the eight partial sums meet in a
 //   fixed shuffle tree.
-#include "internal.cuh"
+#include "cell_ops.cuh"
 
 namespace cf {
 
@@ -43,96 +43,12 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
     return cudaGetLastError();
 }
 
-// Four lanes per vertex: lane k sums the entries k, k+4, k+8, ... of the
-// incidence row, the four partial sums are combined by a fixed shuffle tree
-// (the same order every call: deterministic), and lane k spreads onto its
-// share of the support nodes.
 template <int W>
 __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F,
                                                           LbmParams p, int do_spread, unsigned *err) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = g >> 2, lane = g & 3;
-    const bool live = v < m.V;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (live) {
-        // the lane's entries e0 + lane, + 4, + 8, ... in groups of four: the
-        // index loads of a group, then its corner-force loads, are issued
-        // together; the sum still runs over the entries in ascending order
-        const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
-        for (int e = e0 + lane; e < e1; e += 16) {
-            int id[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) id[k] = e + 4 * k < e1 ? __ldg(m.csr_idx + e + 4 * k) : -1;
-            float4 c[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                c[k] = id[k] >= 0 ? m.fc[(id[k] & 3) * m.T + (id[k] >> 2)] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (id[k] >= 0) {
-                    fx += c[k].x;
-                    fy += c[k].y;
-                    fz += c[k].z;
-                }
-        }
-    }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-        fz += __shfl_xor_sync(0xffffffffu, fz, o);
-    }
-    if (live) {
-        if (lane == 0) {
-            m.fv[v] = make_float4(fx, fy, fz, 0.f);
-            if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
-        }
-        Support s;
-        if (!do_spread) {
-        } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
-            if (lane == 0) atomicOr(err, ERR_DOMAIN);
-        } else {
-            const int N = (int)p.N;
-            float wx[W], wy[W], wz[W];
-            delta_weights<W>(s.fx, wx);
-            delta_weights<W>(s.fy, wy);
-            delta_weights<W>(s.fz, wz);
-            if constexpr (W == 2) {  // lane = (dz, dy), two nodes along x
-                const int dz = lane >> 1, dy = lane & 1;
-                const int Z = wrapi(s.bz + dz, p.nz);
-                const float wyz = wy[dy] * wz[dz];
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
-                    const float w = wx[dx] * wyz;
-                    atomicAdd(F + n, w * fx);
-                    atomicAdd(F + N + n, w * fy);
-                    atomicAdd(F + 2 * N + n, w * fz);
-                }
-            } else {  // lane = dz, a W x W plane
-                const int Z = wrapi(s.bz + lane, p.nz);
-                float wzl = wz[0];
-#pragma unroll
-                for (int k = 1; k < W; ++k) wzl = lane == k ? wz[k] : wzl;  // no local-memory indexing
-                int X[W];
-#pragma unroll
-                for (int dx = 0; dx < W; ++dx) X[dx] = wrapi(s.bx + dx, p.nx);
-#pragma unroll
-                for (int dy = 0; dy < W; ++dy) {
-                    const int row = p.nx * (s.by + dy + p.ny * Z);
-                    const float wyz = wy[dy] * wzl;
-#pragma unroll
-                    for (int dx = 0; dx < W; ++dx) {
-                        const int n = X[dx] + row;
-                        const float w = wx[dx] * wyz;
-                        atomicAdd(F + n, w * fx);
-                        atomicAdd(F + N + n, w * fy);
-                        atomicAdd(F + 2 * N + n, w * fz);
-                    }
-                }
-            }
-        }
-    }
+    const int v = g >> 2;
+    gather_spread_vertex<W, false>(m, u, F, p, do_spread, err, v, g & 3, v < m.V);
 }
 
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,

@@ -26,6 +26,7 @@ enum : unsigned {
     ERR_NONFINITE = 1u << 1,  // NaN / Inf in a force or a displacement
     ERR_DOMAIN = 1u << 2,     // delta support outside 0 <= y <= ny-1
     ERR_MOVED = 1u << 3,      // a support node fell outside the step's force region
+    ERR_WAIT = 1u << 4,       // a bounded wait of the fused cell chain gave up
 };
 
 // ---------------------------------------------------------------- D3Q19
@@ -293,6 +294,17 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, c
 // a region slot (cleared by the caller).
 cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, const RegionSlot &r,
                                cudaStream_t s);
+// K1 + K23 fused (csrc/chain.cu): one persistent launch that runs the work
+// items of the cell chain in order: items[i] = (kind, cell, begin, end) with
+// kind 0 = per-vertex region work on vertices [begin, end), 1 = corner forces
+// of tets [begin, end) of `cell`, 2 = vertex sums + spread of vertices
+// [begin, end) of `cell`. A kind-2 item waits (bounded) until every kind-0
+// item and the need[cell] kind-1 items of its cell are done; counters
+// [2 + ncells] must be zero at launch.
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, const float4 *u_prev, float *F,
+                              const LbmParams &lp, const RegionSlot &mark, const unsigned *bits_in, unsigned *err,
+                              const int4 *items, int nitems, int nregion, const int *need, int *counters, int blocks,
+                              cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 // Every stream-collide launch reads the step's rounding seed from seed[0];

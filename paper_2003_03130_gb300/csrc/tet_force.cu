@@ -2,46 +2,9 @@
 // thread per tet, and the energy V_0 U per tet (K7, test support). The stress
 // evaluation (the cancellation-free form of the paper's chain rule) is in
 // mr.cuh.
-#include "mr.cuh"
+#include "cell_ops.cuh"
 
 namespace cf {
-
-// Zero the force field on the delta support of x + u_prev: every nonzero
-// entry of F was spread there in the previous step.
-template <int W>
-__device__ __forceinline__ void clear_support(const MeshView &m, const float4 *__restrict__ u_prev, float *F,
-                                              const LbmParams &lp, int v) {
-    Support sp;
-    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u_prev + v), lp.ny, sp)) return;  // nothing was spread
-    const int N = (int)lp.N;
-#pragma unroll
-    for (int dz = 0; dz < W; ++dz) {
-        const int Z = wrapi(sp.bz + dz, lp.nz);
-#pragma unroll
-        for (int dy = 0; dy < W; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < W; ++dx) {
-                const int n = wrapi(sp.bx + dx, lp.nx) + lp.nx * (sp.by + dy + lp.ny * Z);
-                F[n] = 0.f;
-                F[N + n] = 0.f;
-                F[2 * N + n] = 0.f;
-            }
-    }
-}
-
-// The per-vertex part of K1: clear last step's spread, add the next step's
-// region, check this step's region.
-template <int W>
-__device__ __forceinline__ void vertex_region(const MeshView &m, const float4 *__restrict__ u,
-                                              const float4 *__restrict__ u_prev, float *F, const LbmParams &lp,
-                                              int v, const RegionSlot &mark, const unsigned *__restrict__ bits_in,
-                                              unsigned *err) {
-    clear_support<W>(m, u_prev, F, lp, v);
-    Support s;
-    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s)) return;  // K23 reports it
-    if (mark.bits) mark_region<W>(s, lp, mark);
-    if (bits_in && !region_covers<W>(s, lp, bits_in)) atomicOr(err, ERR_MOVED);
-}
 
 __global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
                                                    int tet_blocks, const float4 *__restrict__ u_prev,
@@ -59,21 +22,7 @@ __global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
 
-    const int4 a4 = __ldg(m.tet + t);
-    float Bm[3][3], V0;
-    int cell;
-    load_tet_params(m, t, Bm, V0, cell);
-    float H[3][3];
-    tet_grad(__ldg(u + a4.x), __ldg(u + a4.y), __ldg(u + a4.z), __ldg(u + a4.w), Bm, H);
-    const float4 mat = __ldg(m.mat + cell);
-    InvT<float> v;
-    float P[3][3];
-    mr_stress(H, mat.x, mat.y, mat.z, v, P);
-    if (!(v.J > 0.f)) atomicOr(err, ERR_INVERTED);
-    float f[4][3];
-    corner_forces(P, Bm, V0, f);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) m.fc[a * m.T + t] = make_float4(f[a][0], f[a][1], f[a][2], 0.f);
+    tet_corner_forces(m, u, err, t);
 }
 
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
