@@ -193,23 +193,27 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *   [6]    1: the tet forces and the vertex sums + spread run as one
  *          persistent launch over work items of all cells, vertex sums of a
  *          cell starting as soon as its tets are done; 0 (default): two
- *          launches ([3] and [4] apply only then).
+ *          launches ([3] and [4] apply only then);
+ *   [7]    1: the near-field stream-collide runs in rows of 128 nodes over
+ *          the whole lattice, threads outside the region returning at once
+ *          (for regions that cover much of the lattice); 0 (default): blocks
+ *          stride over the region's tile list.
  * Block sizes are multiples of 32 in [32, 256].
  * No shape changes a computed value beyond the rounding order of the spread
  * (float atomics). cf_set_launch_shape applies from the next cf_step call;
  * CF_EINVAL for a value outside these sets. */
-#define CF_SHAPE_LEN 7
+#define CF_SHAPE_LEN 8
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
 /* Autotuner: picks the launch shape by timing the step kernels on the
  * context's own state. One knob at a time (tile shape, fused or separate
- * cell chain, tet-force, spread and interpolation block sizes), every
- * candidate runs
+ * cell chain, near-field form, tet-force, spread and interpolation block
+ * sizes), every candidate runs
  * steps_per_candidate (>= 1) coupled steps with CUDA events around each
  * kernel, and the candidate with the least summed time of the kernels the
  * knob shapes is kept. The simulation advances by those steps exactly as
- * under cf_step (15 candidates in all). A fluid-only context has nothing to
+ * under cf_step (17 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

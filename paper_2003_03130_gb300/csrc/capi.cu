@@ -184,8 +184,8 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         CUDA_TRY(c, clear_slot(c, acc, sc));
         CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, use, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c),
-                                    c->seed + p, c->seed + 1 - p, sc));
+        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
+                                    sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
@@ -821,8 +821,8 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                           : launch_lbm(c->f[p], c->f[1 - p], c->lp, c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[4], s);
             if (cells && e == cudaSuccess)
-                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.count, use.tiles, c->vel, near_grid(c),
-                                    c->seed + p, c->seed + 1 - p, s);
+                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
+                                    sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
             c->tstep += 1;
@@ -911,6 +911,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[4] = sh.gather_block;
     shape[5] = sh.interp_block;
     shape[6] = sh.fused;
+    shape[7] = sh.near_rows;
     return CF_OK;
 }
 
@@ -934,6 +935,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.interp_block = shape[5];
     if (shape[6] != 0 && shape[6] != 1) return fail(c, CF_EINVAL, "fused must be 0 or 1");
     sh.fused = shape[6];
+    if (shape[7] != 0 && shape[7] != 1) return fail(c, CF_EINVAL, "near_rows must be 0 or 1");
+    sh.near_rows = shape[7];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -959,6 +962,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
         const Knob knobs[] = {
             {&Shape::tile, {0, 1, 2, 3}, {1, 2, 3}},
             {&Shape::fused, {0, 1}, {0, 1}},
+            {&Shape::near_rows, {0, 1}, {3}},
             {&Shape::tet_block, {64, 128, 256}, {0}},
             {&Shape::gather_block, {64, 128, 256}, {1}},
             {&Shape::interp_block, {64, 128, 256}, {4}},

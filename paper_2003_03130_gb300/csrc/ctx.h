@@ -37,6 +37,7 @@ struct Shape {
     int tile = 0;  // index into kTileShapes
     int tet_block = 64, gather_block = 128, interp_block = 128;
     int fused = 0;  // cell chain as one persistent launch (csrc/chain.cu) instead of two
+    int near_rows = 0;  // near field in rows over the whole lattice instead of over the region's tile list
 };
 
 }  // namespace cf

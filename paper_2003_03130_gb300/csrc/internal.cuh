@@ -318,9 +318,12 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const un
 // with the force field, also storing u(t) there.
 cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
                            const unsigned *seed, cudaStream_t s);
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
-                            const int *tiles, float *vel, int blocks, const unsigned *seed, unsigned *next_seed,
-                            cudaStream_t s);
+// blocks > 0: that many blocks stride over the region's tile list;
+// blocks <= 0: rows of 128 nodes over the whole lattice, threads outside the
+// region return at once.
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned *bits,
+                            const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
+                            unsigned *next_seed, cudaStream_t s);
 // True for the device functions of the far-field kernels (to tell their graph
 // nodes apart).
 bool is_lbm_far_kernel(const void *fn);

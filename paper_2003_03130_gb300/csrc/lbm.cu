@@ -301,6 +301,28 @@ __global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *_
         lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
 }
 
+// The force region's nodes in rows of 128 along x over the whole lattice (the
+// far field's layout: y and z uniform over a block); threads outside the
+// region return at once. Cheaper per node than the list form when the region
+// is a large part of the lattice.
+template <class T>
+__global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin, T *__restrict__ fout,
+                                                       const float *__restrict__ F, LbmParams p,
+                                                       const unsigned *__restrict__ bits, float *__restrict__ vel,
+                                                       const unsigned *__restrict__ seed_in,
+                                                       unsigned *__restrict__ seed_out) {
+    const unsigned seed = *seed_in;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *seed_out = seed + 1u;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (!region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz))) return;
+    if (y > 0 && y < p.ny - 1)
+        lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel, seed);
+    else
+        lbm_node<T, true, true>(fin, fout, F, p, x, y, z, vel, seed);
+}
+
 // The force region's tiles from its list, with the force field; also stores
 // u(t) there. The grid is fixed when a step is captured while the region
 // moves with the cells, so blocks stride over the list's half tiles.
@@ -377,9 +399,16 @@ static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const 
 }
 
 template <class T>
-static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
-                          const int *tiles, float *vel, int blocks, const unsigned *seed, unsigned *next_seed,
-                          cudaStream_t s) {
+static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned *bits,
+                          const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
+                          unsigned *next_seed, cudaStream_t s) {
+    if (blocks <= 0) {  // rows over the whole lattice
+        const int bx = p.nx < 128 ? p.nx : 128;
+        dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+        k_lbm_near_rows<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, bits, vel,
+                                               seed, next_seed);
+        return cudaGetLastError();
+    }
     k_lbm_near<T><<<blocks, kTileBlock, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, count,
                                                 tiles, vel, seed, next_seed);
     return cudaGetLastError();
@@ -408,14 +437,14 @@ cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, cons
     }
 }
 
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const int *count,
-                            const int *tiles, float *vel, int blocks, const unsigned *seed, unsigned *next_seed,
-                            cudaStream_t s) {
+cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned *bits,
+                            const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
+                            unsigned *next_seed, cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return near_t<__half>(fin, fout, F, p, count, tiles, vel, blocks, seed, next_seed, s);
+        case POP_F16: return near_t<__half>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
         case POP_BF16:
-            return near_t<__nv_bfloat16>(fin, fout, F, p, count, tiles, vel, blocks, seed, next_seed, s);
-        default: return near_t<float>(fin, fout, F, p, count, tiles, vel, blocks, seed, next_seed, s);
+            return near_t<__nv_bfloat16>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
+        default: return near_t<float>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
     }
 }
 
