@@ -322,24 +322,21 @@ def run_ours(args):
         kms, near_nodes = P.cf_step_profiled(ctx, args.profile_steps)
 
         # end to end through the public API with host buffers: per step the
-        # positions go host -> device (pinned), one step, positions back
+        # positions go host -> device (pinned), one step, positions back, in
+        # one call with one wait (two pinned buffers take turns)
         nv = P.cf_cell_verts(ctx, P.CF_ALL_CELLS)
-        y_in = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
-        y_out = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
-        P.cf_get_positions(ctx, P.CF_ALL_CELLS, out=y_in)
+        ybuf = [torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        P.cf_get_positions(ctx, P.CF_ALL_CELLS, out=ybuf[0])
 
-        def e2e_step():
-            P.cf_set_positions(ctx, P.CF_ALL_CELLS, y_in)
-            P.cf_step(ctx, 1)
-            P.cf_get_positions(ctx, P.CF_ALL_CELLS, out=y_out)
-            y_in[...] = y_out
+        def e2e_step(k):
+            P.cf_step_exchange(ctx, 1, ybuf[k & 1], out=ybuf[(k + 1) & 1])
 
-        for _ in range(6):  # warm-up: the one-step graphs of every parity and region phase
-            e2e_step()
+        for k in range(6):  # warm-up: the one-step graphs of every parity and region phase
+            e2e_step(k)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        for k in range(args.e2e_steps):
+            e2e_step(k)
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{dev}")
         barrier()
         y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
@@ -406,7 +403,7 @@ def run_ours(args):
             "unit": "steps/s",
             "h2d_bytes_per_step": int(nv * 3 * 8),
             "d2h_bytes_per_step": int(nv * 3 * 8),
-            "api": "cf_set_positions + cf_step(1) + cf_get_positions (all cells), pinned host buffers",
+            "api": "cf_step_exchange: all positions in, 1 step, all positions out, one wait; pinned host buffers",
         },
         "clocks": clk,
     }

@@ -161,6 +161,14 @@ cf_status cf_step(cf_ctx *ctx, int32_t n);
  * cf_get_*). */
 cf_status cf_step_async(cf_ctx *ctx, int32_t n);
 
+/* One round trip for callers that drive the cells from the host: set the
+ * positions of all cells (y_in [V][3], every vertex in cell order as with
+ * CF_ALL_CELLS; NULL keeps them), advance n >= 0 steps as cf_step, then
+ * read the positions of all cells into y_out [V][3] (NULL skips it), with a
+ * single wait at the end. Errors as cf_set_positions, cf_step and
+ * cf_get_positions; CF_ESTATE without cells when y_in or y_out is given. */
+cf_status cf_step_exchange(cf_ctx *ctx, int32_t n, const double *y_in, double *y_out);
+
 /* Build, without running anything, every CUDA graph that cf_step or
  * cf_step_async of n steps from the current state would build on first use
  * (graph capture and instantiation take milliseconds; after this call the
@@ -197,23 +205,26 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *   [7]    1: the near-field stream-collide runs in rows of 128 nodes over
  *          the whole lattice, threads outside the region returning at once
  *          (for regions that cover much of the lattice); 0 (default): blocks
- *          stride over the region's tile list.
+ *          stride over the region's tile list;
+ *   [8]    1: the far field issues a node's loads before its region test
+ *          resolves (saves a round trip per far node, wastes the loads of
+ *          region nodes); 0 (default): region nodes return first.
  * Block sizes are multiples of 32 in [32, 256].
  * No shape changes a computed value beyond the rounding order of the spread
  * (float atomics). cf_set_launch_shape applies from the next cf_step call;
  * CF_EINVAL for a value outside these sets. */
-#define CF_SHAPE_LEN 8
+#define CF_SHAPE_LEN 9
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
 /* Autotuner: picks the launch shape by timing the step kernels on the
  * context's own state. One knob at a time (tile shape, fused or separate
- * cell chain, near-field form, tet-force, spread and interpolation block
- * sizes), every candidate runs
+ * cell chain, near-field form, far-field load order, tet-force, spread and
+ * interpolation block sizes), every candidate runs
  * steps_per_candidate (>= 1) coupled steps with CUDA events around each
  * kernel, and the candidate with the least summed time of the kernels the
  * knob shapes is kept. The simulation advances by those steps exactly as
- * under cf_step (17 candidates in all). A fluid-only context has nothing to
+ * under cf_step (19 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

@@ -57,6 +57,7 @@ def lib():
             "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_prepare_steps": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_step_exchange": ([vp, ctypes.c_int32, _d, _d], ctypes.c_int),
             "cf_get_launch_shape": ([vp, _i], ctypes.c_int),
             "cf_set_launch_shape": ([vp, _i], ctypes.c_int),
             "cf_autotune": ([vp, ctypes.c_int32, _i], ctypes.c_int),
@@ -253,13 +254,25 @@ def cf_step_async(ctx, n: int = 1):
     _check(ctx, lib().cf_step_async(ctx.handle, n))
 
 
+def cf_step_exchange(ctx, n: int, y_in=None, out=None):
+    """Set all positions from ``y_in`` [V,3] (or keep them when None),
+    advance n steps, and return all positions (into ``out`` when given),
+    with one wait."""
+    nv = lib().cf_cell_verts(ctx.handle, CF_ALL_CELLS)
+    yi = None if y_in is None else _f64(y_in).reshape(nv, 3)
+    yo = _out(out, (nv, 3))
+    _check(ctx, lib().cf_step_exchange(ctx.handle, n, _p(yi), _p(yo)))
+    return yo
+
+
 def cf_prepare_steps(ctx, n: int):
     """Instantiate the step graphs an n-step call would use, without running."""
     _check(ctx, lib().cf_prepare_steps(ctx.handle, n))
 
 
-CF_SHAPE_LEN = 8
-SHAPE_KEYS = ("tile_x", "tile_y", "tile_z", "tet_block", "gather_block", "interp_block", "fused", "near_rows")
+CF_SHAPE_LEN = 9
+SHAPE_KEYS = ("tile_x", "tile_y", "tile_z", "tet_block", "gather_block", "interp_block", "fused", "near_rows",
+              "far_spec")
 
 
 def cf_get_launch_shape(ctx):
@@ -284,7 +297,7 @@ def cf_set_launch_shape(ctx, shape):
 
 def cf_autotune(ctx, steps_per_candidate=20):
     """Time the launch-shape candidates on the context's own state (the
-    simulation advances 17 x steps_per_candidate steps) and keep the
+    simulation advances 19 x steps_per_candidate steps) and keep the
     fastest; returns the chosen shape."""
     out = np.zeros(CF_SHAPE_LEN, np.int32)
     _check(ctx, lib().cf_autotune(ctx.handle, steps_per_candidate, _p(out, _i)))

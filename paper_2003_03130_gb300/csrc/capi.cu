@@ -177,7 +177,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         const int p = p0 ^ (i & 1), s = (s0 + i) % 3;
         const RegionSlot use = region_slot(c, s), acc = accum_slot(c, s);
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sf));
+        CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
         if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
@@ -770,6 +770,29 @@ cf_status cf_step(cf_ctx *c, int32_t n) {
     return cf_synchronize(c);
 }
 
+cf_status cf_step_exchange(cf_ctx *c, int32_t n, const double *y_in, double *y_out) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
+    if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step_exchange needs cf_lbm_init first");
+    if ((y_in || y_out) && c->V == 0) return fail(c, CF_ESTATE, "no cells");
+    if (y_in) {
+        for (long long i = 0; i < 3LL * c->V; ++i)
+            if (!std::isfinite(y_in[i])) return fail(c, CF_EINVAL, "non-finite position");
+        CUDA_TRY(c, cudaMemcpyAsync(c->stage, y_in, sizeof(double) * 3 * c->V, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, launch_set_positions(c->stage, 0, c->V, c->xref64, c->u[c->cur], c->stream));
+    }
+    if (n > 0) {
+        cf_status st = schedule_steps(c, n, true);
+        if (st != CF_OK) return st;
+    }
+    if (y_out) {
+        CUDA_TRY(c, launch_get_positions(c->u[c->cur], c->xref64, 0, c->V, c->stage, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(y_out, c->stage, sizeof(double) * 3 * c->V, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return consume_errors(c);  // the one wait of the call
+}
+
 }  // extern "C"
 
 namespace {
@@ -817,7 +840,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                 e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
-                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, s)
+                e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, s)
                           : launch_lbm(c->f[p], c->f[1 - p], c->lp, c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[4], s);
             if (cells && e == cudaSuccess)
@@ -912,6 +935,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[5] = sh.interp_block;
     shape[6] = sh.fused;
     shape[7] = sh.near_rows;
+    shape[8] = sh.far_spec;
     return CF_OK;
 }
 
@@ -937,6 +961,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.fused = shape[6];
     if (shape[7] != 0 && shape[7] != 1) return fail(c, CF_EINVAL, "near_rows must be 0 or 1");
     sh.near_rows = shape[7];
+    if (shape[8] != 0 && shape[8] != 1) return fail(c, CF_EINVAL, "far_spec must be 0 or 1");
+    sh.far_spec = shape[8];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -963,6 +989,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::tile, {0, 1, 2, 3}, {1, 2, 3}},
             {&Shape::fused, {0, 1}, {0, 1}},
             {&Shape::near_rows, {0, 1}, {3}},
+            {&Shape::far_spec, {0, 1}, {2}},
             {&Shape::tet_block, {64, 128, 256}, {0}},
             {&Shape::gather_block, {64, 128, 256}, {1}},
             {&Shape::interp_block, {64, 128, 256}, {4}},

@@ -38,6 +38,7 @@ struct Shape {
     int tet_block = 64, gather_block = 128, interp_block = 128;
     int fused = 0;  // cell chain as one persistent launch (csrc/chain.cu) instead of two
     int near_rows = 0;  // near field in rows over the whole lattice instead of over the region's tile list
+    int far_spec = 0;   // far field issues its loads before the region test resolves
 };
 
 }  // namespace cf
@@ -181,16 +182,18 @@ MeshView view(const cf_ctx *c) {
 }
 
 // Wait for the stream by polling, giving up after the context's timeout.
+// The first 2 ms are spent polling (a step takes tens of microseconds, and a
+// sleeping host thread would add its wake-up latency to every call); after
+// that the thread sleeps 20 us between polls.
 cf_status wait_stream(cf_ctx *c) {
     auto t0 = std::chrono::steady_clock::now();
-    int spins = 0;
     for (;;) {
         cudaError_t e = cudaStreamQuery(c->stream);
         if (e == cudaSuccess) return CF_OK;
         if (e != cudaErrorNotReady) return fail(c, CF_ECUDA, "device work failed: %s", cudaGetErrorString(e));
         double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (dt > c->timeout_s) return fail(c, CF_ETIMEOUT, "device work did not finish within %.0f s", c->timeout_s);
-        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (dt > 2e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 

@@ -316,8 +316,9 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const un
 // nodes; threads in region tiles return at once), with no force-field read;
 // near = the region's tiles from its list (blocks stride over the list),
 // with the force field, also storing u(t) there.
+// spec: the far field issues a node's loads before its region test resolves.
 cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
-                           const unsigned *seed, cudaStream_t s);
+                           const unsigned *seed, bool spec, cudaStream_t s);
 // blocks > 0: that many blocks stride over the region's tile list;
 // blocks <= 0: rows of 128 nodes over the whole lattice, threads outside the
 // region return at once.

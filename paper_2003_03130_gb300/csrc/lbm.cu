@@ -201,10 +201,12 @@ __device__ __forceinline__ bool wall_pull(int y, int ny) {
 }
 
 // ---------------------------------------------------------------- one node
+// store = false: load and collide but write nothing (a node found, after its
+// loads were issued, to belong to the other part of the split).
 template <class T, bool WALL, bool HAS_F>
 __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restrict__ fout,
                                          const float *__restrict__ F, const LbmParams &p, int x, int y, int z,
-                                         float *__restrict__ vel, unsigned seed) {
+                                         float *__restrict__ vel, unsigned seed, bool store = true) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -232,6 +234,7 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         Fz += __ldg(F + 2 * N + n);
     }
     const float3 u = collide(d, Fx, Fy, Fz, p);
+    if (!store) return;
     if (vel) {  // u(t) of this step, for the interpolation at the vertices
         vel[n] = u.x;
         vel[N + n] = u.y;
@@ -286,19 +289,23 @@ constexpr int kTileBlock = kTileNodes / 2;
 // read), in rows of 128 nodes along x as in the fluid-only kernel, so that y
 // and z stay uniform over a block; a thread whose node lies in a region tile
 // returns at once.
-template <class T>
+// SPEC: the region test resolves while the populations load (a region
+// node's loads are wasted, a far node saves a round trip before its loads);
+// otherwise a region node returns before loading.
+template <class T, bool SPEC>
 __global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
                                                  const unsigned *__restrict__ bits,
                                                  const unsigned *__restrict__ seed_in) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
-    if (region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz))) return;
+    const bool region = region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz));
+    if (!SPEC && region) return;
     const unsigned seed = *seed_in;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
+        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed, !region);
     else
-        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed);
+        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed, !region);
 }
 
 // The force region's nodes in rows of 128 along x over the whole lattice (the
@@ -391,10 +398,13 @@ static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, const 
 
 template <class T>
 static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, const unsigned *seed,
-                         cudaStream_t s) {
+                         bool spec, cudaStream_t s) {
     const int bx = p.nx < 128 ? p.nx : 128;
     dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-    k_lbm_far<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, bits, seed);
+    if (spec)
+        k_lbm_far<T, true><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, bits, seed);
+    else
+        k_lbm_far<T, false><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, bits, seed);
     return cudaGetLastError();
 }
 
@@ -415,8 +425,9 @@ static cudaError_t near_t(const void *fin, void *fout, const float *F, const Lbm
 }
 
 bool is_lbm_far_kernel(const void *fn) {
-    return fn == (const void *)k_lbm_far<float> || fn == (const void *)k_lbm_far<__half> ||
-           fn == (const void *)k_lbm_far<__nv_bfloat16>;
+    return fn == (const void *)k_lbm_far<float, false> || fn == (const void *)k_lbm_far<__half, false> ||
+           fn == (const void *)k_lbm_far<__nv_bfloat16, false> || fn == (const void *)k_lbm_far<float, true> ||
+           fn == (const void *)k_lbm_far<__half, true> || fn == (const void *)k_lbm_far<__nv_bfloat16, true>;
 }
 
 cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const unsigned *seed, unsigned *next_seed,
@@ -429,11 +440,11 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const un
 }
 
 cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
-                           const unsigned *seed, cudaStream_t s) {
+                           const unsigned *seed, bool spec, cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return far_t<__half>(fin, fout, p, bits, seed, s);
-        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, bits, seed, s);
-        default: return far_t<float>(fin, fout, p, bits, seed, s);
+        case POP_F16: return far_t<__half>(fin, fout, p, bits, seed, spec, s);
+        case POP_BF16: return far_t<__nv_bfloat16>(fin, fout, p, bits, seed, spec, s);
+        default: return far_t<float>(fin, fout, p, bits, seed, spec, s);
     }
 }
 

@@ -378,3 +378,28 @@ def test_batch_init_names_the_failing_cell(P):
         P.cf_mesh_init_batch(ctx, [c.x_ref for c in cells], tets)
     assert e.value.name == "CF_EINVAL" and "cell 2, tet 5" in str(e.value)
     assert P.cf_cell_verts(ctx, 0) == 0  # nothing was added
+
+
+def test_step_exchange_equals_separate_calls(P):
+    """cf_step_exchange (positions in, n steps, positions out, one wait)
+    gives the oracle's positions, like cf_set_positions + cf_step +
+    cf_get_positions."""
+    wl = configs.small_shear()
+    y0 = wl.cells[0].y0
+    ctx = P.cf_create(0)
+    (cid,) = P.load_workload(ctx, wl)
+    y = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
+    for _ in range(4):
+        y = P.cf_step_exchange(ctx, 5, y)
+    y_none = P.cf_step_exchange(ctx, 0)  # no input, no step: the current positions
+    sim = oracle.Coupled(wl)
+    sim.step(20)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert np.array_equal(y_none, y)
+    from paper_2003_03130_gb300 import CellFSIError
+
+    bad = y.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(CellFSIError) as e:
+        P.cf_step_exchange(ctx, 1, bad)
+    assert e.value.name == "CF_EINVAL"
