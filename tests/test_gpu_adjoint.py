@@ -179,3 +179,26 @@ def test_fit_recovers_hidden_moduli(P):
     print("losses", losses[0], losses[-1], "mu", mu, "hidden", hm.mu)
     assert losses[-1] < 0.05 * losses[0]
     assert np.abs(mu / hm.mu - 1).max() < np.abs(1.0 / hm.mu - 1).max()
+
+
+def test_compression_full_size_matches_oracle(P):
+    """The 64-cell compression set at full size (8,256 tets per cell) with
+    the benchmark's hidden moduli, plate stiffness, time step, damping and
+    plate ramp: the first two strain levels, shortened to 40 damped steps
+    each, against the oracle."""
+    from paper_2003_03130_gb300.adjoint import Compression
+    from workloads import configs
+
+    cs = configs.compression_set()
+    cells = [Cell(c.x_ref, c.tets, c.y0, mu, ka, w)
+             for c, mu, ka, w in zip(cs.cells, cs.hidden_mu, cs.hidden_kappa, cs.hidden_w)]
+    m = oracle.Mesh(cells)
+    z_lo, radius = protocol_geometry(cells)
+    strains, steps = cs.strains[:2], 40
+    ctx, ids = setup(P, cells)
+    run = Compression(ctx, ids, m.x, z_lo, radius, strains, steps, cs.dt, cs.k_plate, cs.ramp, cs.damping)
+    F = run.run(m.mu, m.kappa, m.w, record=False)
+    F_ref, y_ref = cp.protocol(m, m.x, z_lo, radius, strains, steps, cs.dt, cs.k_plate, cs.ramp, cs.damping)
+    assert len(ids) == 64 and (F_ref > 0).all()
+    assert rel(F, F_ref) <= 1e-5
+    assert rel(P.cf_get_positions(ctx, P.CF_ALL_CELLS) - m.x, y_ref - m.x) <= 1e-5

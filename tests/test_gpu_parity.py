@@ -403,3 +403,31 @@ def test_step_exchange_equals_separate_calls(P):
     with pytest.raises(CellFSIError) as e:
         P.cf_step_exchange(ctx, 1, bad)
     assert e.value.name == "CF_EINVAL"
+
+
+def test_suspension_full_size(P):
+    """The 400-cell suspension at full size (512 x 256 x 256 lattice,
+    1.26 M vertices, 6.0 M tets) in the launch shape the autotuner picks for
+    it (32 x 2 x 4 tiles, near field in rows): every vertex displacement,
+    every vertex force and the whole velocity field after 2 coupled steps
+    against the oracle. The cells start off their rest shape (seeded
+    perturbation of up to 0.08 lattice units per coordinate), so that the
+    forces are not rounding noise."""
+    wl = configs.batched_channel()
+    for k, c in enumerate(wl.cells):
+        c.y0 = perturb(c.x_ref, 0.08, 1000 + k)
+    ctx = P.cf_create(0)
+    P.cf_set_launch_shape(ctx, {"tile_x": 32, "tile_y": 2, "tile_z": 4, "near_rows": 1})
+    ids = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 2)
+    y = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
+    f = P.cf_get_forces(ctx, P.CF_ALL_CELLS)
+    u = P.cf_get_velocity(ctx)
+    P.cf_destroy(ctx)
+    sim = oracle.Coupled(wl)
+    sim.step(2)
+    y0 = np.concatenate([c.y0 for c in wl.cells])
+    assert len(ids) == 400 and len(y) == 1261146
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(u, sim.fluid.u) <= TOL
