@@ -270,9 +270,9 @@ def cf_prepare_steps(ctx, n: int):
     _check(ctx, lib().cf_prepare_steps(ctx.handle, n))
 
 
-CF_SHAPE_LEN = 9
+CF_SHAPE_LEN = 10
 SHAPE_KEYS = ("tile_x", "tile_y", "tile_z", "tet_block", "gather_block", "interp_block", "fused", "near_rows",
-              "far_spec")
+              "far_spec", "tet_pairs")
 
 
 def cf_get_launch_shape(ctx):
@@ -297,7 +297,7 @@ def cf_set_launch_shape(ctx, shape):
 
 def cf_autotune(ctx, steps_per_candidate=20):
     """Time the launch-shape candidates on the context's own state (the
-    simulation advances 19 x steps_per_candidate steps) and keep the
+    simulation advances 21 x steps_per_candidate steps) and keep the
     fastest; returns the chosen shape."""
     out = np.zeros(CF_SHAPE_LEN, np.int32)
     _check(ctx, lib().cf_autotune(ctx.handle, steps_per_candidate, _p(out, _i)))

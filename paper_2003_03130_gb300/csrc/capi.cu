@@ -128,7 +128,8 @@ cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &
         return launch_cell_chain(m, c->u[p], c->u[1 - p], c->F, c->lp, acc, use.bits, c->d_err, c->chain_items,
                                  c->chain_nitems, c->chain_nregion, c->chain_need, c->chain_ctr, chain_grid(c), s);
     }
-    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &acc, use.bits);
+    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &acc, use.bits,
+                                     sh.tet_pairs);
     if (e != cudaSuccess) return e;
     return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
 }
@@ -833,7 +834,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                 if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, use, s);
                 if (e == cudaSuccess && !sh.fused)
                     e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &accm,
-                                         use.bits);
+                                         use.bits, sh.tet_pairs);
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)
@@ -936,6 +937,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[6] = sh.fused;
     shape[7] = sh.near_rows;
     shape[8] = sh.far_spec;
+    shape[9] = sh.tet_pairs;
     return CF_OK;
 }
 
@@ -963,6 +965,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.near_rows = shape[7];
     if (shape[8] != 0 && shape[8] != 1) return fail(c, CF_EINVAL, "far_spec must be 0 or 1");
     sh.far_spec = shape[8];
+    if (shape[9] != 0 && shape[9] != 1) return fail(c, CF_EINVAL, "tet_pairs must be 0 or 1");
+    sh.tet_pairs = shape[9];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -990,6 +994,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::fused, {0, 1}, {0, 1}},
             {&Shape::near_rows, {0, 1}, {3}},
             {&Shape::far_spec, {0, 1}, {2}},
+            {&Shape::tet_pairs, {0, 1}, {0}},
             {&Shape::tet_block, {64, 128, 256}, {0}},
             {&Shape::gather_block, {64, 128, 256}, {1}},
             {&Shape::interp_block, {64, 128, 256}, {4}},

@@ -8,24 +8,46 @@
 
 namespace cf {
 
-// Corner forces of tet t (Sec. 3.1): f^a = -V0 P B_a, f^4 = -(f^1 + f^2 + f^3).
-__device__ __forceinline__ void tet_corner_forces(const MeshView &m, const float4 *__restrict__ u, unsigned *err,
-                                                  int t) {
+// Everything the force of one tet reads: its four displacements, B, V0 and
+// its material.
+struct TetIn {
+    float4 w[4];
+    float Bm[3][3];
+    float V0;
+    float4 mat;
+};
+
+__device__ __forceinline__ void tet_load(const MeshView &m, const float4 *__restrict__ u, int t, TetIn &in) {
     const int4 a4 = __ldg(m.tet + t);
-    float Bm[3][3], V0;
-    int cell;
-    load_tet_params(m, t, Bm, V0, cell);
+    int slot;
+    load_tet_params(m, t, in.Bm, in.V0, slot);
+    in.w[0] = __ldg(u + a4.x);
+    in.w[1] = __ldg(u + a4.y);
+    in.w[2] = __ldg(u + a4.z);
+    in.w[3] = __ldg(u + a4.w);
+    in.mat = __ldg(m.mat + slot);
+}
+
+// Corner forces of tet t from its inputs (Sec. 3.1): f^a = -V0 P B_a,
+// f^4 = -(f^1 + f^2 + f^3).
+__device__ __forceinline__ void tet_forces_store(const MeshView &m, const TetIn &in, unsigned *err, int t) {
     float H[3][3];
-    tet_grad(__ldg(u + a4.x), __ldg(u + a4.y), __ldg(u + a4.z), __ldg(u + a4.w), Bm, H);
-    const float4 mat = __ldg(m.mat + cell);
+    tet_grad(in.w[0], in.w[1], in.w[2], in.w[3], in.Bm, H);
     InvT<float> v;
     float P[3][3];
-    mr_stress(H, mat.x, mat.y, mat.z, v, P);
+    mr_stress(H, in.mat.x, in.mat.y, in.mat.z, v, P);
     if (!(v.J > 0.f)) atomicOr(err, ERR_INVERTED);
     float f[4][3];
-    corner_forces(P, Bm, V0, f);
+    corner_forces(P, in.Bm, in.V0, f);
 #pragma unroll
     for (int a = 0; a < 4; ++a) m.fc[a * m.T + t] = make_float4(f[a][0], f[a][1], f[a][2], 0.f);
+}
+
+__device__ __forceinline__ void tet_corner_forces(const MeshView &m, const float4 *__restrict__ u, unsigned *err,
+                                                  int t) {
+    TetIn in;
+    tet_load(m, u, t, in);
+    tet_forces_store(m, in, err, t);
 }
 
 // Zero the force field on the delta support of x + u_prev: every nonzero

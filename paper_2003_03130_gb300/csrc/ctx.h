@@ -39,6 +39,7 @@ struct Shape {
     int fused = 0;  // cell chain as one persistent launch (csrc/chain.cu) instead of two
     int near_rows = 0;  // near field in rows over the whole lattice instead of over the region's tile list
     int far_spec = 0;   // far field issues its loads before the region test resolves
+    int tet_pairs = 0;  // two tets per thread in the force kernel
 };
 
 }  // namespace cf

@@ -275,9 +275,10 @@ cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cud
 // spread its forces), adds the tiles of the next step's force region (the
 // support of x + u grown by one node) to mark_out, and checks that the
 // support of x + u lies in the region bits_in (else ERR_MOVED).
+// pairs: two tets per thread (both tets' loads issued before either is computed).
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
                              const LbmParams *lp, cudaStream_t s, int block = 0, const RegionSlot *mark_out = nullptr,
-                             const unsigned *bits_in = nullptr);
+                             const unsigned *bits_in = nullptr, int pairs = 0);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
