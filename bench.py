@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=128, help="cubic lattice extent")
-    ap.add_argument("--workload", choices=("shear", "suspension", "compression"), default="shear",
-                    help="shear: one R = 16 cell in a 128^3 Couette box; suspension: 400 cells in a "
+    ap.add_argument("--workload", choices=("shear", "paperbox", "suspension", "compression"), default="shear",
+                    help="shear: one R = 16 cell in a 128^3 Couette box; paperbox: the same cell in the "
+                         "paper's 10 x 15 x 5 R box (160 x 240 x 80); suspension: 400 cells in a "
                          "512 x 256 x 256 channel; compression: fit the moduli of 64 cells to synthetic "
                          "force-strain curves with the adjoint")
     ap.add_argument("--fit-iters", type=int, default=10, help="Adam iterations of the compression fit")
@@ -77,6 +78,8 @@ def workload(args):
     if args.workload == "suspension":
         nx, ny, nz = (int(v) for v in args.box.split(","))
         wl = configs.batched_channel(ncells=args.cells, nx=nx, ny=ny, nz=nz)
+    elif args.workload == "paperbox":
+        wl = configs.paper_box_shear(ca=args.ca, w=args.w)
     else:
         wl = configs.production_shear(ca=args.ca, w=args.w, n=args.n)
     wl.delta = {"trilinear": 2, "peskin4": 4}[args.delta]

@@ -431,3 +431,16 @@ def test_suspension_full_size(P):
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(u, sim.fluid.u) <= TOL
+
+
+def test_paper_box_shear_full_size(P):
+    """The paper's shear box shape (10 x 15 x 5 R at R = 16: 160 x 240 x 80)
+    with a perturbed R = 16 cell: 3 coupled steps against the oracle."""
+    wl = configs.paper_box_shear()
+    cell = wl.cells[0]
+    cell.y0 = perturb(cell.x_ref, 0.08, 20030313)
+    y0 = cell.y0.copy()
+    ctx, sim, y, f = _coupled_pair(P, wl, 3)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL

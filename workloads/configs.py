@@ -101,6 +101,18 @@ def production_shear(ca: float = 0.2, w: float = 1.0, steps: int = 10000, n: int
     return Workload(f"shear_{n}^3_R16_Ca{ca}_w{w}", n, n, n, 1.0, -u_wall, u_wall, cells=[cell], steps=steps)
 
 
+def paper_box_shear(ca: float = 0.2, w: float = 0.5, steps: int = 10000) -> Workload:
+    """The paper's single-cell shear box, 10 x 15 x 5 cell radii (Sec. 6.1,
+    shear gradient along the 15 R axis), at R = 16: a 160 x 240 x 80 lattice
+    (3.07 M nodes) with the same R = 16 cell at the centre, walls at -/+0.05,
+    tau = 1; mu from Ca at this box's shear rate, kappa = 50 mu."""
+    nx, ny, nz, u_wall = 160, 240, 80, 0.05
+    mu = shear_modulus_for_ca(ca, 1.0, u_wall, ny)
+    cell = sphere_cell(16.0, 1.72, ((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0), mu, 50.0 * mu, w)
+    return Workload(f"shear_160x240x80_R16_Ca{ca}_w{w}", nx, ny, nz, 1.0, -u_wall, u_wall, cells=[cell],
+                    steps=steps)
+
+
 def precision_channel(steps: int = 2000, nx: int = 256, ny: int = 128, nz: int = 128) -> Workload:
     """Pressure-driven channel 256 x 128 x 128 (walls at rest, uniform body
     force for a centre-line velocity of 0.02 at tau = 1: g = 8 nu u_max / ny^2),
