@@ -330,6 +330,7 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
     }
     if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
         dalloc(&c->taylor_out, 10) != cudaSuccess || dalloc(&c->seed, 2) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(c->seed, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
         dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
         cf_destroy(c);
@@ -347,6 +348,7 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->d_err);
     dfree(c->d_status);
     dfree(c->seed);
+    if (c->h_err) cudaFreeHost(c->h_err);
     dfree(c->region);
     dfree(c->f[0]);
     dfree(c->f[1]);

@@ -59,6 +59,7 @@ struct cf_ctx {
     double timeout_s = 600.0;
 
     unsigned *d_err = nullptr;
+    unsigned *h_err = nullptr;  // pinned host copy of the error word (one wait per read)
     unsigned *seed = nullptr;  // rounding seeds of the two buffer parities (16-bit stochastic rounding)
     unsigned long long *d_status = nullptr;
 
@@ -200,11 +201,13 @@ cf_status wait_stream(cf_ctx *c) {
 
 // Read and clear the device error word.
 cf_status consume_errors(cf_ctx *c) {
-    unsigned h = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    // into pinned memory the copy stays asynchronous, so the read costs one
+    // wait instead of two
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
     cf_status s = wait_stream(c);
     if (s != CF_OK) return s;
+    const unsigned h = *c->h_err;
     if (h & ERR_INVERTED) return fail(c, CF_EINVERTED, "a tet reached det F <= 0");
     if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
     if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
