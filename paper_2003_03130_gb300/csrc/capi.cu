@@ -15,7 +15,8 @@
 // moves less than one spacing per step; K23 checks that the support of y^t
 // lies in it and raises CF_EUNSTABLE otherwise). A cf_step call is a
 // "first" step graph (region from the current positions, no K5 before it),
-// n - 1 pipelined step graphs and a final K5. Populations and displacements
+// n - 1 pipelined step graphs and a final K5; a one-step call is a single
+// graph with its K5. Populations and displacements
 // are double-buffered with one shared parity; each graph is captured once per
 // parity. F keeps the last step's force until the next step begins, so the
 // velocity of the last step can still be read.
@@ -44,7 +45,11 @@ namespace {
 // multiple of 3 (region slots), so a graph starts and ends in the same phase.
 constexpr int kChunk = 12;
 
-enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3 };
+// First: the first step of a call (its region from the current positions);
+// Mid: pipelined steps; Tail: K5 of the last step; Fluid: steps without
+// cells; Single: a whole one-step call, K5 included (it waits for the near
+// field only, so it overlaps the end of the far field).
+enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3, Single = 4 };
 
 // Region slots of step t (phase s = t % 3): the step's force region is slot
 // (s + 2) % 3 (filled by step t - 1, or from the current positions in the
@@ -167,7 +172,8 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         return CF_OK;
     }
     cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
-    if (kind == Kind::First) {
+    const bool first = kind == Kind::First || kind == Kind::Single;
+    if (first) {
         const RegionSlot use = region_slot(c, s0);
         CUDA_TRY(c, clear_slot(c, use, sf));
         CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, sf));
@@ -180,7 +186,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
         CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
-        if (!(kind == Kind::First && i == 0))  // K5 of the previous step (parity 1-p)
+        if (!(first && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
         CUDA_TRY(c, clear_slot(c, acc, sc));
         CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, use, sc));
@@ -188,6 +194,10 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
+    }
+    if (kind == Kind::Single) {  // K5 of this step (parity p0), after the near field in sc order
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sc, sh.interp_block));
+        CUDA_TRY(c, cudaEventRecord(ev_near[nsteps - 1], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_far[nsteps - 1], 0));
@@ -283,6 +293,14 @@ cf_status schedule_steps(cf_ctx *c, int32_t n, bool launch) {
             --left;
         }
     } else {
+        if (n == 1) {  // one graph for the whole call
+            st = launch_steps(c, Kind::Single, 1, launch);
+            if (!launch) {
+                c->cur = cur0;
+                c->tstep = t0;
+            }
+            return st;
+        }
         st = launch_steps(c, Kind::First, 1, launch);
         int left = n - 1;
         while (st == CF_OK && left >= kChunk) {
