@@ -382,7 +382,7 @@ def run_ours(args):
         "config": config_of(wl),
         "mlups": job_rate(wl.n_nodes * K, world, ms / 1e3) / 1e6,
         "tet_forces_per_s": job_rate(wl.n_tets * K, world, ms / 1e3),
-        "gpu_launches": 5 * K + 1,
+        "gpu_launches": (4 if shape.get("fused") else 5) * K + 1,  # far, K5, K1 (+K23), near; mark + final K5
         "launch_shape": shape,
         "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
         "kernel_share": dict(zip(KERNELS, [float(x) / step_ms_profiled for x in kms])),
