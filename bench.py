@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--fused", type=int, default=-1, choices=(-1, 0, 1),
                     help="cell chain as one persistent launch (1) or two (0); -1: default / autotuner")
     ap.add_argument("--tile", default="", help="force-region tile x,y,z (e.g. 32,2,4); default: autotuner's")
+    ap.add_argument("--shape", default="", help="launch-shape knobs set after the autotuner, e.g. far_pdl=1")
     ap.add_argument("--autotune-steps", type=int, default=20,
                     help="steps per launch-shape candidate of the autotuner in the warm-up (0: default shape)")
     ap.add_argument("--ca", type=float, default=0.2)
@@ -304,6 +305,9 @@ def run_ours(args):
             P.cf_set_launch_shape(ctx, {"tile_x": tx, "tile_y": ty, "tile_z": tz})
         P.cf_step(ctx, W)
         shape = P.cf_autotune(ctx, args.autotune_steps) if args.autotune_steps > 0 else P.cf_get_launch_shape(ctx)
+        if args.shape:  # explicit knobs after the autotuner (e.g. far_pdl, which it does not time)
+            P.cf_set_launch_shape(ctx, {k: int(v) for k, v in (kv.split("=") for kv in args.shape.split(","))})
+            shape = P.cf_get_launch_shape(ctx)
         P.cf_prepare_steps(ctx, K)  # graph instantiation stays out of the timed region
         barrier()
         torch.cuda.synchronize(dev)
