@@ -58,6 +58,8 @@ def parse():
                     help="immersed-boundary delta kernel")
     ap.add_argument("--fused", type=int, default=-1, choices=(-1, 0, 1),
                     help="cell chain as one persistent launch (1) or two (0); -1: default / autotuner")
+    ap.add_argument("--pop-format", choices=("f32", "f16", "bf16", "f16sr", "bf16sr"), default="f32",
+                    help="population storage (the collide is FP32 in every format)")
     ap.add_argument("--tile", default="", help="force-region tile x,y,z (e.g. 32,2,4); default: autotuner's")
     ap.add_argument("--shape", default="", help="launch-shape knobs set after the autotuner, e.g. far_pdl=1")
     ap.add_argument("--autotune-steps", type=int, default=20,
@@ -297,6 +299,7 @@ def run_ours(args):
 
     with torch.cuda.stream(stream):
         ctx = P.cf_create(dev, stream.cuda_stream)
+        P.cf_set_population_format(ctx, args.pop_format)
         ids = P.load_workload(ctx, wl)
         if args.fused >= 0:
             P.cf_set_launch_shape(ctx, {"fused": args.fused})
@@ -355,10 +358,12 @@ def run_ours(args):
     # single-cell box, the near field (force read, velocity written) when the
     # cells spread over the whole lattice
     far_nodes = wl.n_nodes - near_nodes
+    pop_b = POP_BYTES_PER_NODE // (1 if args.pop_format == "f32" else 2)  # 2-byte storage halves it
     if kms[2] >= kms[3]:
-        dom, units, per_unit, dom_ms = "k_lbm_far", far_nodes, POP_BYTES_PER_NODE, kms[2]
+        dom, units, per_unit, dom_ms = "k_lbm_far", far_nodes, pop_b, kms[2]
     else:
-        dom, units, per_unit, dom_ms = "k_lbm_near", near_nodes, NEAR_BYTES_PER_NODE, kms[3]
+        near_b = pop_b + NEAR_BYTES_PER_NODE - POP_BYTES_PER_NODE
+        dom, units, per_unit, dom_ms = "k_lbm_near", near_nodes, near_b, kms[3]
     alg_bytes = per_unit * units
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
     n_sup = support_nodes(y_now, (wl.nx, wl.ny, wl.nz))
@@ -368,7 +373,7 @@ def run_ours(args):
     tag = (f"{wl.nx}cubed" if wl.nx == wl.ny == wl.nz else f"{wl.nx}x{wl.ny}x{wl.nz}") + (
         f"_{len(wl.cells)}cells" if args.workload == "suspension" else "")
     tag = ("suspension_" if args.workload == "suspension" else "") + tag
-    traffic = traffic_record(dom, tag) if wl.delta == 2 else None
+    traffic = traffic_record(dom, tag) if wl.delta == 2 and args.pop_format == "f32" else None
     step_ms_profiled = float(sum(kms))
     out = {
         "metric": METRIC,
@@ -381,7 +386,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": {"f32": "f32", "f16": "f16", "bf16": "bf16", "f16sr": "f16 (stochastic rounding)",
+                  "bf16sr": "bf16 (stochastic rounding)"}[args.pop_format],
         "data": "synthetic (seeded sphere mesh, fluid at rest at t=0)",
         "config": config_of(wl),
         "mlups": job_rate(wl.n_nodes * K, world, ms / 1e3) / 1e6,
@@ -414,7 +420,8 @@ def run_ours(args):
         },
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear":
+    if (rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear"
+            and args.pop_format == "f32"):
         out["precision"] = precision_block(P, torch, dev, args.precision_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "shear":
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
