@@ -46,13 +46,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=128, help="cubic lattice extent")
-    ap.add_argument("--workload", choices=("shear", "paperbox", "suspension", "compression"), default="shear",
+    ap.add_argument("--workload", choices=("shear", "paperbox", "multicell", "suspension", "compression"),
+                    default="shear",
                     help="shear: one R = 16 cell in a 128^3 Couette box; paperbox: the same cell in the "
-                         "paper's 10 x 15 x 5 R box (160 x 240 x 80); suspension: 400 cells in a "
+                         "paper's 10 x 15 x 5 R box (160 x 240 x 80); multicell: 4 or 8 R = 16 cells "
+                         "(--phi 0.11 / 0.22) in the paper's 5 x 8 x 4 R sheared box; suspension: 400 cells in a "
                          "512 x 256 x 256 channel; compression: fit the moduli of 64 cells to synthetic "
                          "force-strain curves with the adjoint")
     ap.add_argument("--fit-iters", type=int, default=10, help="Adam iterations of the compression fit")
     ap.add_argument("--cells", type=int, default=400, help="cells of the suspension workload")
+    ap.add_argument("--phi", type=float, choices=(0.11, 0.22), default=0.22,
+                    help="volume fraction of the multicell workload (4 or 8 cells)")
     ap.add_argument("--box", default="512,256,256", help="lattice of the suspension workload")
     ap.add_argument("--delta", choices=("trilinear", "peskin4"), default="trilinear",
                     help="immersed-boundary delta kernel")
@@ -83,6 +87,8 @@ def workload(args):
         wl = configs.batched_channel(ncells=args.cells, nx=nx, ny=ny, nz=nz)
     elif args.workload == "paperbox":
         wl = configs.paper_box_shear(ca=args.ca, w=args.w)
+    elif args.workload == "multicell":
+        wl = configs.multicell_shear(ncells=4 if args.phi == 0.11 else 8, ca=args.ca, w=args.w)
     else:
         wl = configs.production_shear(ca=args.ca, w=args.w, n=args.n)
     wl.delta = {"trilinear": 2, "peskin4": 4}[args.delta]
@@ -350,6 +356,7 @@ def run_ours(args):
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{dev}")
         barrier()
         y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
+        mean_D = float(np.mean([P.cf_get_taylor(ctx, i)["D"] for i in ids])) if args.workload == "multicell" else None
         P.cf_destroy(ctx)
 
     steps_per_s = job_rate(K, world, ms / 1e3)
@@ -420,6 +427,8 @@ def run_ours(args):
         },
         "clocks": clk,
     }
+    if mean_D is not None:  # Taylor deformation averaged over the cells, after warm-up + timed steps
+        out["mean_taylor_D"] = mean_D
     if (rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear"
             and args.pop_format == "f32"):
         out["precision"] = precision_block(P, torch, dev, args.precision_steps)

@@ -444,3 +444,30 @@ def test_paper_box_shear_full_size(P):
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_multicell_shear_small(P):
+    """The paper's multiple-cell setup scaled to R = 6 (30 x 48 x 24 box, 4
+    cells at random positions, volume fraction 0.11): 40 coupled steps
+    against the oracle, cells perturbed off their rest shape."""
+    wl = configs.multicell_shear(ncells=4, R=6.0, h=1.3)
+    for k, c in enumerate(wl.cells):
+        c.y0 = perturb(c.x_ref, 0.08, 300 + k)
+    y0 = np.concatenate([c.y0 for c in wl.cells])
+    ctx, sim, y, f = _coupled_pair(P, wl, 40)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_multicell_shear_full_size(P):
+    """8 R = 16 cells in the 80 x 128 x 64 box (volume fraction 0.22), in the
+    benchmark's configuration: 3 coupled steps against the oracle."""
+    wl = configs.multicell_shear(ncells=8)
+    for k, c in enumerate(wl.cells):
+        c.y0 = perturb(c.x_ref, 0.08, 400 + k)
+    y0 = np.concatenate([c.y0 for c in wl.cells])
+    ctx, sim, y, f = _coupled_pair(P, wl, 3)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL

@@ -113,6 +113,39 @@ def paper_box_shear(ca: float = 0.2, w: float = 0.5, steps: int = 10000) -> Work
                     steps=steps)
 
 
+def multicell_shear(ncells: int = 8, R: float = 16.0, h: float = 1.72, ca: float = 0.2, w: float = 0.5,
+                    u_wall: float = 0.05, seed: int = 55, steps: int = 10000) -> Workload:
+    """The paper's multiple-cell setup (Sec. 6.3): ncells cells of radius R
+    at seeded random positions (no overlap, gap >= 2 lattice units, at least
+    R + 2 from the walls, periodic in x and z) in a 5 x 8 x 4 R box with
+    moving walls across its 8 R axis; 4 cells fill 11 % of the box, 8 cells
+    22 %. At R = 16 the box is 80 x 128 x 64. mu from Ca, kappa = 50 mu."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny, nz = int(round(5 * R)), int(round(8 * R)), int(round(4 * R))
+    L = np.array([nx, ny, nz], np.float64)
+    centres = []
+    for _ in range(ncells):
+        for _ in range(200000):
+            c = np.array([rng.uniform(0, nx), rng.uniform(R + 2.0, ny - 3.0 - R), rng.uniform(0, nz)])
+            ok = True
+            for o in centres:
+                d = np.abs(c - o)
+                d[[0, 2]] = np.minimum(d[[0, 2]], L[[0, 2]] - d[[0, 2]])
+                if np.sqrt((d * d).sum()) < 2 * R + 2.0:
+                    ok = False
+                    break
+            if ok:
+                break
+        else:
+            raise RuntimeError("could not place all cells")
+        centres.append(c)
+    mu = shear_modulus_for_ca(ca, 1.0, u_wall, ny)
+    x, tets = sphere_tet_mesh(R, h)
+    cells = [Cell(x_ref=x + c[None, :], tets=tets, y0=x + c[None, :], mu=mu, kappa=50.0 * mu, w=w) for c in centres]
+    return Workload(f"multicell_{nx}x{ny}x{nz}_{ncells}cells_R{R:g}_Ca{ca}", nx, ny, nz, 1.0, -u_wall, u_wall,
+                    cells=cells, steps=steps)
+
+
 def precision_channel(steps: int = 2000, nx: int = 256, ny: int = 128, nz: int = 128) -> Workload:
     """Pressure-driven channel 256 x 128 x 128 (walls at rest, uniform body
     force for a centre-line velocity of 0.02 at tau = 1: g = 8 nu u_max / ny^2),
