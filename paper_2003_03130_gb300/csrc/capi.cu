@@ -12,8 +12,8 @@
 // K5(t-1) -> K1(t) -> K23(t); after the join the near part updates the
 // region's tiles with the force field. The region of step t is the set of
 // tiles that meet the delta support of y^{t-1} grown by one node (a vertex
-// moves less than one spacing per step; K23 checks that the support of y^t
-// lies in it and raises CF_EUNSTABLE otherwise). A cf_step call is a
+// moves less than one spacing per step, so the support of y^t lies in it; K5
+// checks every move and raises CF_EUNSTABLE otherwise). A cf_step call is a
 // "first" step graph (region from the current positions, no K5 before it),
 // n - 1 pipelined step graphs and a final K5; a one-step call is a single
 // graph with its K5. Populations and displacements
@@ -126,14 +126,14 @@ cf_status build_chain_items(cf_ctx *c) {
 // K1 + K23 of one step on stream s: the fused persistent launch, or the two
 // separate kernels.
 cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, const RegionSlot &acc,
-                              const RegionSlot &use, cudaStream_t s) {
+                              cudaStream_t s) {
     if (sh.fused) {
         cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
         if (e != cudaSuccess) return e;
-        return launch_cell_chain(m, c->u[p], c->u[1 - p], c->F, c->lp, acc, use.bits, c->d_err, c->chain_items,
+        return launch_cell_chain(m, c->u[p], c->u[1 - p], c->F, c->lp, acc, c->d_err, c->chain_items,
                                  c->chain_nitems, c->chain_nregion, c->chain_need, c->chain_ctr, chain_grid(c), s);
     }
-    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &acc, use.bits,
+    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &acc,
                                      sh.tet_pairs);
     if (e != cudaSuccess) return e;
     return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
@@ -189,7 +189,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (!(first && i == 0))  // K5 of the previous step (parity 1-p)
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
         CUDA_TRY(c, clear_slot(c, acc, sc));
-        CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, use, sc));
+        CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
@@ -851,10 +851,10 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
                 e = clear_slot(c, accm, s);
-                if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, use, s);
+                if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, s);
                 if (e == cudaSuccess && !sh.fused)
                     e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &accm,
-                                         use.bits, sh.tet_pairs);
+                                         sh.tet_pairs);
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)

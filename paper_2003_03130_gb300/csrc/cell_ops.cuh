@@ -73,18 +73,22 @@ __device__ __forceinline__ void clear_support(const MeshView &m, const float4 *_
     }
 }
 
-// The per-vertex part of K1: clear last step's spread, add the next step's
-// region, check this step's region.
+// The per-vertex part of K1, two independent jobs: 0 clears last step's
+// spread (the support of x + u_prev), 1 adds the next step's region (the
+// support of x + u grown by one node). Whether this step's support lies in
+// this step's region follows from the step before moving every vertex by
+// less than one spacing, which K5 checks.
 template <int W>
-__device__ __forceinline__ void vertex_region(const MeshView &m, const float4 *__restrict__ u,
-                                              const float4 *__restrict__ u_prev, float *F, const LbmParams &lp,
-                                              int v, const RegionSlot &mark, const unsigned *__restrict__ bits_in,
-                                              unsigned *err) {
-    clear_support<W>(m, u_prev, F, lp, v);
+__device__ __forceinline__ void vertex_job(const MeshView &m, const float4 *__restrict__ u,
+                                           const float4 *__restrict__ u_prev, float *F, const LbmParams &lp, int v,
+                                           int job, const RegionSlot &mark) {
+    if (job == 0) {
+        clear_support<W>(m, u_prev, F, lp, v);
+        return;
+    }
     Support s;
-    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s)) return;  // K23 reports it
-    if (mark.bits) mark_region<W>(s, lp, mark);
-    if (bits_in && !region_covers<W>(s, lp, bits_in)) atomicOr(err, ERR_MOVED);
+    if (mark.bits && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s))  // else K23 reports it
+        mark_region<W>(s, lp, mark);
 }
 
 // Corner-force load: from L2 (FC_L2) when the forces were written by other

@@ -37,7 +37,7 @@ __device__ __forceinline__ bool wait_count(const int *p, int target, unsigned *e
 template <int W>
 __global__ void __launch_bounds__(kChainBlock, 4)
     k_cell_chain(MeshView m, const float4 *__restrict__ u, const float4 *__restrict__ u_prev, float *F,
-                 LbmParams lp, RegionSlot mark, const unsigned *__restrict__ bits_in, unsigned *err,
+                 LbmParams lp, RegionSlot mark, unsigned *err,
                  const int4 *__restrict__ items, int nitems, int nregion, const int *__restrict__ need,
                  int *counters) {
     __shared__ int4 item;
@@ -62,8 +62,10 @@ __global__ void __launch_bounds__(kChainBlock, 4)
         if (x.x < 0) break;
         if (ready) {
             if (x.x == 0) {
-                for (int v = x.z + threadIdx.x; v < x.w; v += kChainBlock)
-                    vertex_region<W>(m, u, u_prev, F, lp, v, mark, bits_in, err);
+                for (int v = x.z + threadIdx.x; v < x.w; v += kChainBlock) {
+                    vertex_job<W>(m, u, u_prev, F, lp, v, 0, mark);
+                    vertex_job<W>(m, u, u_prev, F, lp, v, 1, mark);
+                }
             } else if (x.x == 1) {
                 for (int t = x.z + threadIdx.x; t < x.w; t += kChainBlock) tet_corner_forces(m, u, err, t);
             } else {
@@ -80,16 +82,16 @@ __global__ void __launch_bounds__(kChainBlock, 4)
 }
 
 cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, const float4 *u_prev, float *F,
-                              const LbmParams &lp, const RegionSlot &mark, const unsigned *bits_in, unsigned *err,
+                              const LbmParams &lp, const RegionSlot &mark, unsigned *err,
                               const int4 *items, int nitems, int nregion, const int *need, int *counters, int blocks,
                               cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     const int g = blocks < nitems ? blocks : nitems;
     if (lp.dw == 4)
-        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, bits_in, err, items, nitems, nregion,
+        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, err, items, nitems, nregion,
                                                    need, counters);
     else
-        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, bits_in, err, items, nitems, nregion,
+        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, err, items, nitems, nregion,
                                                    need, counters);
     return cudaGetLastError();
 }

@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
     }
     const float4 un = make_float4(uc.x + vx, uc.y + vy, uc.z + vz, 0.f);
     if (!isfinite(un.x + un.y + un.z)) atomicOr(err, ERR_NONFINITE);
+    // the next step's force region holds this step's support grown by one
+    // node: a move of a spacing or more along an axis would leave it
+    if (!(fabsf(vx) < 1.f && fabsf(vy) < 1.f && fabsf(vz) < 1.f)) atomicOr(err, ERR_MOVED);
     u_next[v] = un;
 }
 

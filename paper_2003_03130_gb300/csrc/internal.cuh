@@ -237,16 +237,6 @@ __device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p
                   [&](int t) { region_add(r, t); });
 }
 
-// True if every support node of the vertex lies in a tile of the region.
-template <int W>
-__device__ __forceinline__ bool region_covers(const Support &s, const LbmParams &p,
-                                              const unsigned *__restrict__ bits) {
-    bool ok = true;
-    for_each_tile(p, s.bx, s.bx + W - 1, s.by, s.by + W - 1, s.bz, s.bz + W - 1,
-                  [&](int t) { ok = ok && region_has(bits, t); });
-    return ok;
-}
-
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch status.
 // Once per cell (Sec. 3.2): validate, orient, B = J^-1 and V_0 in FP64;
@@ -270,15 +260,14 @@ cudaError_t launch_get_positions(const float4 *u, const double *xref64, int v0, 
 cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cudaStream_t s);
 
 // K1: elastic corner forces of all tets at displacements u. When `u_prev` is
-// non-null the same launch also runs one thread per vertex that zeroes the
+// non-null the same launch also runs two threads per vertex: one zeroes the
 // force field on the delta support of x + u_prev (where the previous step
-// spread its forces), adds the tiles of the next step's force region (the
-// support of x + u grown by one node) to mark_out, and checks that the
-// support of x + u lies in the region bits_in (else ERR_MOVED).
+// spread its forces), the other adds the tiles of the next step's force
+// region (the support of x + u grown by one node) to mark_out.
 // pairs: two tets per thread (both tets' loads issued before either is computed).
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
                              const LbmParams *lp, cudaStream_t s, int block = 0, const RegionSlot *mark_out = nullptr,
-                             const unsigned *bits_in = nullptr, int pairs = 0);
+                             int pairs = 0);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
@@ -303,7 +292,7 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
 // item and the need[cell] kind-1 items of its cell are done; counters
 // [2 + ncells] must be zero at launch.
 cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, const float4 *u_prev, float *F,
-                              const LbmParams &lp, const RegionSlot &mark, const unsigned *bits_in, unsigned *err,
+                              const LbmParams &lp, const RegionSlot &mark, unsigned *err,
                               const int4 *items, int nitems, int nregion, const int *need, int *counters, int blocks,
                               cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
@@ -331,7 +320,9 @@ cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const L
 bool is_lbm_far_kernel(const void *fn);
 size_t pop_bytes(int fmt);
 // K5: velocity u(t) (stored by the near-field stream-collide) interpolated at
-// x + u_cur; u_next = u_cur + velocity.
+// x + u_cur; u_next = u_cur + velocity. A vertex that moves one lattice
+// spacing or more along an axis sets ERR_MOVED: the next step's force region
+// (this step's support grown by one node) would no longer hold its support.
 cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s, int block = 0);
 // Compression between plates and the adjoint (csrc/adjoint.cu).

@@ -8,15 +8,14 @@ namespace cf {
 
 __global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
                                                    int tet_blocks, const float4 *__restrict__ u_prev,
-                                                   float *__restrict__ F, LbmParams lp, RegionSlot mark,
-                                                   const unsigned *__restrict__ bits_in) {
-    if ((int)blockIdx.x >= tet_blocks) {
-        const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
-        if (v >= m.V) return;
+                                                   float *__restrict__ F, LbmParams lp, RegionSlot mark) {
+    if ((int)blockIdx.x >= tet_blocks) {  // two threads per vertex, one job each
+        const int i = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+        if ((i >> 1) >= m.V) return;
         if (lp.dw == 4)
-            vertex_region<4>(m, u, u_prev, F, lp, v, mark, bits_in, err);
+            vertex_job<4>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
         else
-            vertex_region<2>(m, u, u_prev, F, lp, v, mark, bits_in, err);
+            vertex_job<2>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
         return;
     }
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -30,15 +29,14 @@ __global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *
 // has in flight in this latency-bound kernel.
 __global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 *__restrict__ u, unsigned *err,
                                                      int tet_blocks, const float4 *__restrict__ u_prev,
-                                                     float *__restrict__ F, LbmParams lp, RegionSlot mark,
-                                                     const unsigned *__restrict__ bits_in) {
-    if ((int)blockIdx.x >= tet_blocks) {
-        const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
-        if (v >= m.V) return;
+                                                     float *__restrict__ F, LbmParams lp, RegionSlot mark) {
+    if ((int)blockIdx.x >= tet_blocks) {  // two threads per vertex, one job each
+        const int i = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+        if ((i >> 1) >= m.V) return;
         if (lp.dw == 4)
-            vertex_region<4>(m, u, u_prev, F, lp, v, mark, bits_in, err);
+            vertex_job<4>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
         else
-            vertex_region<2>(m, u, u_prev, F, lp, v, mark, bits_in, err);
+            vertex_job<2>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
         return;
     }
     const int t0 = 2 * blockIdx.x * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
@@ -52,19 +50,19 @@ __global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 
 
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
                              const LbmParams *lp, cudaStream_t s, int block, const RegionSlot *mark_out,
-                             const unsigned *bits_in, int pairs) {
+                             int pairs) {
     if (m.T == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 64;  // default: ~20k tets still give every SM blocks
     const int per = pairs ? 2 : 1;
     const int tb = (m.T + bs * per - 1) / (bs * per);
-    const int cb = (u_prev && F && lp) ? (m.V + bs - 1) / bs : 0;
+    const int cb = (u_prev && F && lp) ? (2 * m.V + bs - 1) / bs : 0;
     LbmParams p{};
     if (lp) p = *lp;
     const RegionSlot mark = (cb && mark_out) ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
     if (pairs)
-        k_tet_force2<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark, cb ? bits_in : nullptr);
+        k_tet_force2<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark);
     else
-        k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark, cb ? bits_in : nullptr);
+        k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark);
     return cudaGetLastError();
 }
 
