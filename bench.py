@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--pop-format", choices=("f32", "f16", "bf16", "f16sr", "bf16sr"), default="f32",
                     help="population storage (the collide is FP32 in every format)")
     ap.add_argument("--tile", default="", help="force-region tile x,y,z (e.g. 32,2,4); default: autotuner's")
-    ap.add_argument("--shape", default="", help="launch-shape knobs set after the autotuner, e.g. far_pdl=1")
+    ap.add_argument("--shape", default="", help="launch-shape knobs set after the autotuner, e.g. far_blocks=4")
     ap.add_argument("--autotune-steps", type=int, default=20,
                     help="steps per launch-shape candidate of the autotuner in the warm-up (0: default shape)")
     ap.add_argument("--ca", type=float, default=0.2)
@@ -314,7 +314,7 @@ def run_ours(args):
             P.cf_set_launch_shape(ctx, {"tile_x": tx, "tile_y": ty, "tile_z": tz})
         P.cf_step(ctx, W)
         shape = P.cf_autotune(ctx, args.autotune_steps) if args.autotune_steps > 0 else P.cf_get_launch_shape(ctx)
-        if args.shape:  # explicit knobs after the autotuner (e.g. far_pdl, which it does not time)
+        if args.shape:  # explicit knobs after the autotuner
             P.cf_set_launch_shape(ctx, {k: int(v) for k, v in (kv.split("=") for kv in args.shape.split(","))})
             shape = P.cf_get_launch_shape(ctx)
         P.cf_prepare_steps(ctx, K)  # graph instantiation stays out of the timed region

@@ -160,27 +160,38 @@ __device__ __forceinline__ void collide_pair(float (&d)[19], const WClass &k, fl
     d[B] = b;
 }
 
-// Moments and collision of one node, in place: d holds the pulled
-// populations on entry and the post-collision ones on exit. Returns u(t).
+// Moments and collision of one node, in place, in stored units: d holds the
+// pulled populations as stored (d_q times its class scale S) on entry and the
+// post-collision ones, scaled the same way, on exit. The moments sum each
+// weight class first and unscale the three sums; the collision constants are
+// those of the weights w S. S is a power of two, so both are exact
+// rescalings of the same operations on the unscaled values, and no
+// population is multiplied by its scale on load or store. Returns u(t).
+template <class T>
 __device__ __forceinline__ float3 collide(float (&d)[19], float Fx, float Fy, float Fz, const LbmParams &p) {
-    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) +
-                       ((d[8] + d[9]) + (d[10] + d[11])) + ((d[12] + d[13]) + (d[14] + d[15])) +
-                       ((d[16] + d[17]) + d[18]);
+    constexpr float s0 = pop_scale<T>(0), s1 = pop_scale<T>(1), s2 = pop_scale<T>(7);
+    const float face = ((d[1] + d[2]) + (d[3] + d[4])) + (d[5] + d[6]);
+    const float edge = ((d[7] + d[8]) + (d[9] + d[10])) + ((d[11] + d[12]) + (d[13] + d[14])) +
+                       ((d[15] + d[16]) + (d[17] + d[18]));
+    const float drho = fmaf(edge, 1.f / s2, fmaf(face, 1.f / s1, d[0] * (1.f / s0)));
     // x: +1 at 1, 15..18; -1 at 2, 7..10
-    const float jx = ((d[1] - d[2]) + (d[15] - d[7])) + ((d[16] - d[8]) + (d[17] - d[9])) + (d[18] - d[10]);
+    const float ex = ((d[15] - d[7]) + (d[16] - d[8])) + ((d[17] - d[9]) + (d[18] - d[10]));
     // y: +1 at 3, 10, 13, 14, 18; -1 at 4, 7, 11, 12, 15
-    const float jy = ((d[3] - d[4]) + (d[10] - d[7])) + ((d[13] - d[11]) + (d[14] - d[12])) + (d[18] - d[15]);
+    const float ey = ((d[10] - d[7]) + (d[13] - d[11])) + ((d[14] - d[12]) + (d[18] - d[15]));
     // z: +1 at 5, 9, 12, 14, 17; -1 at 6, 8, 11, 13, 16
-    const float jz = ((d[5] - d[6]) + (d[9] - d[8])) + ((d[12] - d[11]) + (d[14] - d[13])) + (d[17] - d[16]);
+    const float ez = ((d[9] - d[8]) + (d[12] - d[11])) + ((d[14] - d[13]) + (d[17] - d[16]));
+    const float jx = fmaf(ex, 1.f / s2, (d[1] - d[2]) * (1.f / s1));
+    const float jy = fmaf(ey, 1.f / s2, (d[3] - d[4]) * (1.f / s1));
+    const float jz = fmaf(ez, 1.f / s2, (d[5] - d[6]) * (1.f / s1));
     const float rho = 1.f + drho;
     const float ir = __frcp_rn(rho);
     const float ux = fmaf(0.5f, Fx, jx) * ir, uy = fmaf(0.5f, Fy, jy) * ir, uz = fmaf(0.5f, Fz, jz) * ir;
     const float usq15 = 1.5f * fmaf(ux, ux, fmaf(uy, uy, uz * uz));
     const float uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
     const float om = p.omega, g = p.guo, om1 = 1.f - om;
-    const WClass k0 = wclass(1.f / 3.f, drho, rho, usq15, uF, om, g);
-    const WClass k1 = wclass(1.f / 18.f, drho, rho, usq15, uF, om, g);
-    const WClass k2 = wclass(1.f / 36.f, drho, rho, usq15, uF, om, g);
+    const WClass k0 = wclass((1.f / 3.f) * s0, drho, rho, usq15, uF, om, g);
+    const WClass k1 = wclass((1.f / 18.f) * s1, drho, rho, usq15, uF, om, g);
+    const WClass k2 = wclass((1.f / 36.f) * s2, drho, rho, usq15, uF, om, g);
     d[0] = fmaf(om1, d[0], k0.c0);
     collide_pair<1>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
     collide_pair<3>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
@@ -221,10 +232,10 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         const int sy = y - cy(q);
         if (WALL && ((cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1))) {
             const float uw = cy(q) == 1 ? p.uw_lo : p.uw_hi;
-            d[q] = Pop<T>::ld(fin + opp(q) * N + n) * pop_unscale<T>(q);
-            if (cx(q) != 0) d[q] += (6.f * wq(q) * cx(q)) * uw;
+            d[q] = Pop<T>::ld(fin + opp(q) * N + n);
+            if (cx(q) != 0) d[q] += (6.f * wq(q) * cx(q) * pop_scale<T>(q)) * uw;
         } else {
-            d[q] = Pop<T>::ld(fin + q * N + sx + nx * (sy + ny * sz)) * pop_unscale<T>(q);
+            d[q] = Pop<T>::ld(fin + q * N + sx + nx * (sy + ny * sz));
         }
     }
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
@@ -233,7 +244,7 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         Fy += __ldg(F + N + n);
         Fz += __ldg(F + 2 * N + n);
     }
-    const float3 u = collide(d, Fx, Fy, Fz, p);
+    const float3 u = collide<T>(d, Fx, Fy, Fz, p);
     if (!store) return;
     if (vel) {  // u(t) of this step, for the interpolation at the vertices
         vel[n] = u.x;
@@ -248,13 +259,13 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
 #pragma unroll
             for (int q = 0; q < 19; ++q) {
                 const unsigned r = (h + (unsigned)q * 0x9e3779b9u) >> (32 - Pop<T>::kDropped);
-                Pop<T>::st_sr(fout + q * N + n, d[q] * pop_scale<T>(q), r & mask);
+                Pop<T>::st_sr(fout + q * N + n, d[q], r & mask);
             }
             return;
         }
     }
 #pragma unroll
-    for (int q = 0; q < 19; ++q) Pop<T>::st(fout + q * N + n, d[q] * pop_scale<T>(q));
+    for (int q = 0; q < 19; ++q) Pop<T>::st(fout + q * N + n, d[q]);
 }
 
 // ---------------------------------------------------------------- kernels

@@ -471,3 +471,37 @@ def test_multicell_shear_full_size(P):
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_contexts_in_two_host_threads(P):
+    """One context per host thread: two threads, each with its own context
+    and stream, capture and run their step graphs at the same time; both
+    end at the oracle's state."""
+    import threading
+
+    wl = configs.small_shear()
+    sim = oracle.Coupled(wl)
+    sim.step(30)
+    y0 = wl.cells[0].y0
+    out, errors = {}, []
+
+    def run(k):
+        try:
+            ctx = P.cf_create(0)
+            (cid,) = P.load_workload(ctx, wl)
+            for _ in range(3):
+                P.cf_step(ctx, 10)
+            out[k] = (P.cf_get_positions(ctx, cid), P.cf_get_velocity(ctx))
+            P.cf_destroy(ctx)
+        except Exception as e:  # reported below, in the test's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for y, u in out.values():
+        assert rel(y - y0, sim.y - y0) <= TOL
+        assert rel(u, sim.fluid.u) <= TOL
