@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled LBM-IBM steps/s & MLUPS (% HBM roofline); tet-forces/s; FP16 vs FP32 error"
 POP_BYTES_PER_NODE = 2 * 19 * 4  # read + write of 19 FP32 populations
 NEAR_BYTES_PER_NODE = POP_BYTES_PER_NODE + 12 + 12  # + force read, velocity written
+CONSUME_BYTES_PER_SUPPORT_NODE = 12  # the near field zeroes the force it read on the spread's support
 KERNELS = ("k_tet_force", "k_gather_spread", "k_lbm_far", "k_lbm_near", "k_interp_advect")
 
 
@@ -180,14 +181,16 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def support_nodes(y, dims):
-    """Number of distinct lattice nodes in the trilinear support of y."""
+def support_nodes(y, dims, width=2):
+    """Number of distinct lattice nodes in the delta support (width 2:
+    trilinear, 4: four-point) of y."""
     nx, ny, nz = dims
-    b = np.floor(y).astype(np.int64)
+    b = np.floor(y).astype(np.int64) - (width // 2 - 1)
     keys = []
-    for dz in (0, 1):
-        for dy in (0, 1):
-            for dx in (0, 1):
+    r = range(width)
+    for dz in r:
+        for dy in r:
+            for dx in r:
                 X = (b[:, 0] + dx) % nx
                 Y = b[:, 1] + dy
                 Z = (b[:, 2] + dz) % nz
@@ -366,14 +369,15 @@ def run_ours(args):
     # cells spread over the whole lattice
     far_nodes = wl.n_nodes - near_nodes
     pop_b = POP_BYTES_PER_NODE // (1 if args.pop_format == "f32" else 2)  # 2-byte storage halves it
+    n_sup = support_nodes(y_now, (wl.nx, wl.ny, wl.nz), wl.delta)
     if kms[2] >= kms[3]:
         dom, units, per_unit, dom_ms = "k_lbm_far", far_nodes, pop_b, kms[2]
+        alg_bytes = per_unit * units
     else:
         near_b = pop_b + NEAR_BYTES_PER_NODE - POP_BYTES_PER_NODE
         dom, units, per_unit, dom_ms = "k_lbm_near", near_nodes, near_b, kms[3]
-    alg_bytes = per_unit * units
+        alg_bytes = per_unit * units + CONSUME_BYTES_PER_SUPPORT_NODE * n_sup
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    n_sup = support_nodes(y_now, (wl.nx, wl.ny, wl.nz))
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))

@@ -87,7 +87,6 @@ cf_status build_chain_items(cf_ctx *c) {
     const int RB = size_for(c->V, 256, 1024), TB = size_for(c->T, 256, 1024), GB = size_for(c->V, 64, 256);
     const size_t LAG = 2 * (size_t)grid;
     for (int v = 0; v < c->V; v += RB) items.push_back(make_int4(0, 0, v, std::min(c->V, v + RB)));
-    const int nregion = (int)items.size();
     const int C = (int)c->cells.size();
     std::vector<int> need(C, 0);
     std::vector<size_t> last_tet(C, 0);
@@ -119,7 +118,6 @@ cf_status build_chain_items(cf_ctx *c) {
     if (C) CUDA_TRY(c, cudaMemcpyAsync(c->chain_need, need.data(), sizeof(int) * C, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
     c->chain_nitems = (int)items.size();
-    c->chain_nregion = nregion;
     return CF_OK;
 }
 
@@ -130,11 +128,10 @@ cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &
     if (sh.fused) {
         cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
         if (e != cudaSuccess) return e;
-        return launch_cell_chain(m, c->u[p], c->u[1 - p], c->F, c->lp, acc, c->d_err, c->chain_items,
-                                 c->chain_nitems, c->chain_nregion, c->chain_need, c->chain_ctr, chain_grid(c), s);
+        return launch_cell_chain(m, c->u[p], c->F, c->lp, acc, c->d_err, c->chain_items, c->chain_nitems,
+                                 c->chain_need, c->chain_ctr, chain_grid(c), s);
     }
-    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &acc,
-                                     sh.tet_pairs);
+    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, &c->lp, &acc, sh.tet_pairs);
     if (e != cudaSuccess) return e;
     return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
 }
@@ -282,6 +279,7 @@ cf_status schedule_steps(cf_ctx *c, int32_t n, bool launch) {
     const int cur0 = c->cur;
     const long long t0 = c->tstep;
     cf_status st = CF_OK;
+    if (launch && n > 0) c->macro_tile = c->T > 0 ? c->shape.tile : -1;
     if (c->T == 0) {
         int left = n;
         while (st == CF_OK && left >= kChunk) {
@@ -460,11 +458,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     CUDA_TRY(c, cudaMemsetAsync(c->vel, 0, sizeof(float) * 3 * (size_t)N, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->seed, 0, 2 * sizeof(unsigned), c->stream));  // rounding seeds restart
     c->lp = p;
-    // both displacement buffers must agree: the first step clears F on the
-    // support of the "previous" positions
-    if (c->V > 0)
-        CUDA_TRY(c, cudaMemcpyAsync(c->u[1 - c->cur], c->u[c->cur], sizeof(float4) * c->V, cudaMemcpyDeviceToDevice,
-                                    c->stream));
+    c->macro_tile = -1;
     c->lbm_ready = true;
     return wait_stream(c);
 }
@@ -833,6 +827,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
     const MeshView m = view(c);
     const bool cells = c->T > 0;
     cudaStream_t s = c->stream;
+    if (n > 0) c->macro_tile = cells ? sh.tile : -1;
     for (int done = 0; done < n && st == CF_OK;) {
         const int b = std::min(BATCH, n - done);
         cudaError_t e = cudaSuccess;
@@ -853,8 +848,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                 e = clear_slot(c, accm, s);
                 if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, s);
                 if (e == cudaSuccess && !sh.fused)
-                    e = launch_tet_force(m, c->u[p], c->d_err, c->u[1 - p], c->F, &c->lp, s, sh.tet_block, &accm,
-                                         sh.tet_pairs);
+                    e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, &c->lp, &accm, sh.tet_pairs);
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)
@@ -1054,7 +1048,7 @@ cf_status cf_compute_forces(cf_ctx *c) {
     DeviceGuard dg(c->device);
     if (c->T == 0) return fail(c, CF_ESTATE, "no cells");
     const MeshView m = view(c);
-    CUDA_TRY(c, launch_tet_force(m, c->u[c->cur], c->d_err, nullptr, nullptr, nullptr, c->stream));
+    CUDA_TRY(c, launch_tet_force(m, c->u[c->cur], c->d_err, c->stream));
     CUDA_TRY(c, launch_gather_spread(m, c->u[c->cur], nullptr, nullptr, c->d_err, c->stream));
     return consume_errors(c);
 }
@@ -1095,7 +1089,15 @@ static cf_status get_macro(cf_ctx *c, double *rho_out, double *u_out) {
     const size_t N = (size_t)c->lp.N;
     double *d;
     CUDA_TRY(c, dalloc(&d, u_out ? 3 * N : N));
-    cudaError_t e = launch_lbm_macro(c->f[c->cur], c->F, c->lp, u_out ? nullptr : d, u_out ? d : nullptr, c->stream);
+    // the last step's force region, in the tiling that step ran with
+    LbmParams q = c->lp;
+    const unsigned *bits = nullptr;
+    if (c->macro_tile >= 0 && c->tstep > 0) {
+        set_tiles(q, c->macro_tile);
+        bits = region_slot(c, (int)((c->tstep - 1) % 3)).bits;
+    }
+    cudaError_t e = launch_lbm_macro(c->f[c->cur], c->F, q, bits, c->vel, u_out ? nullptr : d, u_out ? d : nullptr,
+                                     c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(u_out ? u_out : rho_out, d, sizeof(double) * (u_out ? 3 * N : N), cudaMemcpyDeviceToHost,
                             c->stream);

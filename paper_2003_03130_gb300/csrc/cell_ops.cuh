@@ -1,6 +1,6 @@
 // Per-element bodies of the cell kernels, shared by the separate launches
 // (csrc/tet_force.cu, csrc/ibm.cu) and the fused persistent chain
-// (csrc/chain.cu): tet corner forces, the per-vertex region work, and the
+// (csrc/chain.cu): tet corner forces, the per-vertex region marking, and the
 // vertex sum with its spread.
 #pragma once
 
@@ -50,44 +50,17 @@ __device__ __forceinline__ void tet_corner_forces(const MeshView &m, const float
     tet_forces_store(m, in, err, t);
 }
 
-// Zero the force field on the delta support of x + u_prev: every nonzero
-// entry of F was spread there in the previous step.
-template <int W>
-__device__ __forceinline__ void clear_support(const MeshView &m, const float4 *__restrict__ u_prev, float *F,
-                                              const LbmParams &lp, int v) {
-    Support sp;
-    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u_prev + v), lp.ny, sp)) return;  // nothing was spread
-    const int N = (int)lp.N;
-#pragma unroll
-    for (int dz = 0; dz < W; ++dz) {
-        const int Z = wrapi(sp.bz + dz, lp.nz);
-#pragma unroll
-        for (int dy = 0; dy < W; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < W; ++dx) {
-                const int n = wrapi(sp.bx + dx, lp.nx) + lp.nx * (sp.by + dy + lp.ny * Z);
-                F[n] = 0.f;
-                F[N + n] = 0.f;
-                F[2 * N + n] = 0.f;
-            }
-    }
-}
-
-// The per-vertex part of K1, two independent jobs: 0 clears last step's
-// spread (the support of x + u_prev), 1 adds the next step's region (the
-// support of x + u grown by one node). Whether this step's support lies in
+// The per-vertex part of K1: add the next step's force region (the support
+// of x + u grown by one node) to mark. Whether this step's support lies in
 // this step's region follows from the step before moving every vertex by
-// less than one spacing, which K5 checks.
+// less than one spacing, which K5 checks. (Last step's spread needs no
+// clearing: the near-field stream-collide zeroes the force field where it
+// reads it.)
 template <int W>
-__device__ __forceinline__ void vertex_job(const MeshView &m, const float4 *__restrict__ u,
-                                           const float4 *__restrict__ u_prev, float *F, const LbmParams &lp, int v,
-                                           int job, const RegionSlot &mark) {
-    if (job == 0) {
-        clear_support<W>(m, u_prev, F, lp, v);
-        return;
-    }
+__device__ __forceinline__ void mark_vertex(const MeshView &m, const float4 *__restrict__ u, const LbmParams &lp,
+                                            int v, const RegionSlot &mark) {
     Support s;
-    if (mark.bits && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s))  // else K23 reports it
+    if (support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s))  // else K23 reports it
         mark_region<W>(s, lp, mark);
 }
 

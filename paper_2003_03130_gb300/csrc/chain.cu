@@ -1,11 +1,10 @@
 // K1 + K23 as one persistent launch over all cells (the batched form of the
-// cell chain): the per-vertex region work, the tet corner forces (Sec. 3.1)
+// cell chain): the per-vertex region marking, the tet corner forces (Sec. 3.1)
 // and the vertex sums with their spread (Sec. 6), for cells of any size.
 //
-// Blocks take work items in a fixed order from one counter. A tet item never
-// waits; a vertex-sum item of cell c waits until every region item (they
-// clear last step's spread, which must precede any new spread) and every tet
-// item of cell c are done. The host orders the items so that every item an
+// Blocks take work items in a fixed order from one counter. Tet and region
+// items never wait; a vertex-sum item of cell c waits until every tet item of
+// cell c is done. The host orders the items so that every item an
 // item waits for comes before it; the block holding an earlier item is
 // therefore already running and never waits itself, so the waits end even
 // when blocks are not co-resident or other kernels share the GPU. Each wait
@@ -36,10 +35,8 @@ __device__ __forceinline__ bool wait_count(const int *p, int target, unsigned *e
 
 template <int W>
 __global__ void __launch_bounds__(kChainBlock, 4)
-    k_cell_chain(MeshView m, const float4 *__restrict__ u, const float4 *__restrict__ u_prev, float *F,
-                 LbmParams lp, RegionSlot mark, unsigned *err,
-                 const int4 *__restrict__ items, int nitems, int nregion, const int *__restrict__ need,
-                 int *counters) {
+    k_cell_chain(MeshView m, const float4 *__restrict__ u, float *F, LbmParams lp, RegionSlot mark, unsigned *err,
+                 const int4 *__restrict__ items, int nitems, const int *__restrict__ need, int *counters) {
     __shared__ int4 item;
     __shared__ int ready;
     int claim = 0;  // thread 0: the item claimed for the next round (claimed one round ahead)
@@ -51,7 +48,7 @@ __global__ void __launch_bounds__(kChainBlock, 4)
             if (x.x >= 0) claim = atomicAdd(counters, 1);  // its latency hides under this item
             int ok = 1;
             if (x.x == 2) {
-                ok = wait_count(counters + 1, nregion, err) && wait_count(counters + 2 + x.y, need[x.y], err);
+                ok = wait_count(counters + 2 + x.y, need[x.y], err);
                 __threadfence();
             }
             item = x;
@@ -62,10 +59,7 @@ __global__ void __launch_bounds__(kChainBlock, 4)
         if (x.x < 0) break;
         if (ready) {
             if (x.x == 0) {
-                for (int v = x.z + threadIdx.x; v < x.w; v += kChainBlock) {
-                    vertex_job<W>(m, u, u_prev, F, lp, v, 0, mark);
-                    vertex_job<W>(m, u, u_prev, F, lp, v, 1, mark);
-                }
+                for (int v = x.z + threadIdx.x; v < x.w; v += kChainBlock) mark_vertex<W>(m, u, lp, v, mark);
             } else if (x.x == 1) {
                 for (int t = x.z + threadIdx.x; t < x.w; t += kChainBlock) tet_corner_forces(m, u, err, t);
             } else {
@@ -77,22 +71,19 @@ __global__ void __launch_bounds__(kChainBlock, 4)
         }
         __threadfence();  // this item's writes before its completion count
         __syncthreads();
-        if (threadIdx.x == 0 && x.x != 2) atomicAdd(counters + (x.x == 0 ? 1 : 2 + x.y), 1);
+        if (threadIdx.x == 0 && x.x == 1) atomicAdd(counters + 2 + x.y, 1);
     }
 }
 
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, const float4 *u_prev, float *F,
-                              const LbmParams &lp, const RegionSlot &mark, unsigned *err,
-                              const int4 *items, int nitems, int nregion, const int *need, int *counters, int blocks,
-                              cudaStream_t s) {
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float *F, const LbmParams &lp,
+                              const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
+                              int *counters, int blocks, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     const int g = blocks < nitems ? blocks : nitems;
     if (lp.dw == 4)
-        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, err, items, nitems, nregion,
-                                                   need, counters);
+        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters);
     else
-        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, u_prev, F, lp, mark, err, items, nitems, nregion,
-                                                   need, counters);
+        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters);
     return cudaGetLastError();
 }
 

@@ -86,7 +86,7 @@ struct cf_ctx {
     // work items of the fused cell chain (csrc/chain.cu), rebuilt when cells are added
     int4 *chain_items = nullptr;
     int *chain_need = nullptr, *chain_ctr = nullptr;
-    int chain_nitems = 0, chain_nregion = 0;
+    int chain_nitems = 0;
     size_t mat_cap = 0;              // entries allocated in mat
     float4 *mat = nullptr;
     int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
@@ -122,6 +122,8 @@ struct cf_ctx {
 
     int cur = 0;          // buffer parity of the next step
     long long tstep = 0;  // steps taken; tstep % 3 picks the region slots
+    int macro_tile = -1;  // tiling of the last step if it had cells (its region and u(t) there serve
+                          // cf_get_velocity); -1: no such step since cf_lbm_init
     std::map<int, cudaGraphExec_t> graphs;
 };
 

@@ -100,7 +100,7 @@ struct MeshView {
 //                   0 beyond.
 // The support of a point p on one axis is the W nodes lo + k, k = 0..W-1,
 // with lo = floor(p) - (W/2 - 1). Shared by the spread, the interpolation
-// and the clearing of F so that all three see exactly the same node set.
+// and the region marking so that all three see exactly the same node set.
 struct Support {
     int bx, by, bz;     // lower corner lo (absolute node, x and z not yet wrapped)
     float fx, fy, fz;   // p - floor(p) per axis, in [0, 1)
@@ -259,15 +259,13 @@ cudaError_t launch_get_positions(const float4 *u, const double *xref64, int v0, 
                                  cudaStream_t s);
 cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cudaStream_t s);
 
-// K1: elastic corner forces of all tets at displacements u. When `u_prev` is
-// non-null the same launch also runs two threads per vertex: one zeroes the
-// force field on the delta support of x + u_prev (where the previous step
-// spread its forces), the other adds the tiles of the next step's force
-// region (the support of x + u grown by one node) to mark_out.
+// K1: elastic corner forces of all tets at displacements u. With lp and
+// mark_out non-null the same launch also runs one thread per vertex that adds
+// the tiles of the next step's force region (the support of x + u grown by
+// one node) to mark_out.
 // pairs: two tets per thread (both tets' loads issued before either is computed).
-cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
-                             const LbmParams *lp, cudaStream_t s, int block = 0, const RegionSlot *mark_out = nullptr,
-                             int pairs = 0);
+cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, cudaStream_t s, int block = 0,
+                             const LbmParams *lp = nullptr, const RegionSlot *mark_out = nullptr, int pairs = 0);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
@@ -286,15 +284,13 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
                                cudaStream_t s);
 // K1 + K23 fused (csrc/chain.cu): one persistent launch that runs the work
 // items of the cell chain in order: items[i] = (kind, cell, begin, end) with
-// kind 0 = per-vertex region work on vertices [begin, end), 1 = corner forces
-// of tets [begin, end) of `cell`, 2 = vertex sums + spread of vertices
-// [begin, end) of `cell`. A kind-2 item waits (bounded) until every kind-0
-// item and the need[cell] kind-1 items of its cell are done; counters
-// [2 + ncells] must be zero at launch.
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, const float4 *u_prev, float *F,
-                              const LbmParams &lp, const RegionSlot &mark, unsigned *err,
-                              const int4 *items, int nitems, int nregion, const int *need, int *counters, int blocks,
-                              cudaStream_t s);
+// kind 0 = region marking of vertices [begin, end), 1 = corner forces of tets
+// [begin, end) of `cell`, 2 = vertex sums + spread of vertices [begin, end)
+// of `cell`. A kind-2 item waits (bounded) until the need[cell] kind-1 items
+// of its cell are done; counters[2 + ncells] must be zero at launch.
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float *F, const LbmParams &lp,
+                              const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
+                              int *counters, int blocks, cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 // Every stream-collide launch reads the step's rounding seed from seed[0];
@@ -305,14 +301,15 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const un
 // K4 split by the force region: far = the nodes outside it (rows of 128
 // nodes; threads in region tiles return at once), with no force-field read;
 // near = the region's tiles from its list (blocks stride over the list),
-// with the force field, also storing u(t) there.
+// with the force field, also storing u(t) there; it zeroes the force field
+// where it read a nonzero one, so that F is zero everywhere between steps.
 // spec: the far field issues a node's loads before its region test resolves.
 cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
                            const unsigned *seed, bool spec, cudaStream_t s);
 // blocks > 0: that many blocks stride over the region's tile list;
 // blocks <= 0: rows of 128 nodes over the whole lattice, threads outside the
 // region return at once.
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned *bits,
+cudaError_t launch_lbm_near(const void *fin, void *fout, float *F, const LbmParams &p, const unsigned *bits,
                             const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
                             unsigned *next_seed, cudaStream_t s);
 // True for the device functions of the far-field kernels (to tell their graph
@@ -346,7 +343,10 @@ cudaError_t launch_adj_step(const MeshView &m, const float4 *u, const float4 *jv
 cudaError_t launch_pack3(const double *in, int n, float4 *out, cudaStream_t s);
 
 cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s);
-cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, double *rho, double *u,
-                             cudaStream_t s);
+// rho and u(t) of every node after a step. u is u(t) as the near field
+// stored it (vel) on the last step's force region (bits, in the tiling of
+// p; null: no region), and from the populations and F elsewhere.
+cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, const unsigned *bits,
+                             const float *vel, double *rho, double *u, cudaStream_t s);
 
 }  // namespace cf

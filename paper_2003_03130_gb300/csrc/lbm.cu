@@ -216,7 +216,7 @@ __device__ __forceinline__ bool wall_pull(int y, int ny) {
 // loads were issued, to belong to the other part of the split).
 template <class T, bool WALL, bool HAS_F>
 __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restrict__ fout,
-                                         const float *__restrict__ F, const LbmParams &p, int x, int y, int z,
+                                         float *__restrict__ F, const LbmParams &p, int x, int y, int z,
                                          float *__restrict__ vel, unsigned seed, bool store = true) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
@@ -239,13 +239,21 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         }
     }
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
+    bool spread = false;
     if (HAS_F) {
-        Fx += __ldg(F + n);
-        Fy += __ldg(F + N + n);
-        Fz += __ldg(F + 2 * N + n);
+        const float ax = __ldcg(F + n), ay = __ldcg(F + N + n), az = __ldcg(F + 2 * N + n);
+        spread = ax != 0.f || ay != 0.f || az != 0.f;
+        Fx += ax;
+        Fy += ay;
+        Fz += az;
     }
     const float3 u = collide<T>(d, Fx, Fy, Fz, p);
     if (!store) return;
+    if (HAS_F && spread) {  // consumed: the next step spreads onto a zero field
+        F[n] = 0.f;
+        F[N + n] = 0.f;
+        F[2 * N + n] = 0.f;
+    }
     if (vel) {  // u(t) of this step, for the interpolation at the vertices
         vel[n] = u.x;
         vel[N + n] = u.y;
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *_
 // is a large part of the lattice.
 template <class T>
 __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin, T *__restrict__ fout,
-                                                       const float *__restrict__ F, LbmParams p,
+                                                       float *__restrict__ F, LbmParams p,
                                                        const unsigned *__restrict__ bits, float *__restrict__ vel,
                                                        const unsigned *__restrict__ seed_in,
                                                        unsigned *__restrict__ seed_out) {
@@ -346,7 +354,7 @@ __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin
 // moves with the cells, so blocks stride over the list's half tiles.
 template <class T>
 __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
-                                                            const float *__restrict__ F, LbmParams p,
+                                                            float *__restrict__ F, LbmParams p,
                                                             const int *__restrict__ count,
                                                             const int *__restrict__ tiles, float *__restrict__ vel,
                                                             const unsigned *__restrict__ seed_in,
@@ -368,11 +376,15 @@ __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict_
     }
 }
 
-// rho and u(t) on every node from post-collision populations and the force of
-// the same step: rho = 1 + sum d*_q, rho u = sum c_q d*_q - F/2 (the collision
-// adds exactly F to the momentum, and rho u = sum c_q d_q + F/2 before it).
+// rho and u(t) on every node after a step. On the last step's force region
+// (bits; null: none) u(t) is the value the near field stored (vel): the force
+// field there has been consumed. Elsewhere it follows from the post-collision
+// populations and the force of the same step: rho = 1 + sum d*_q,
+// rho u = sum c_q d*_q - F/2 (the collision adds exactly F to the momentum,
+// and rho u = sum c_q d_q + F/2 before it).
 template <class T>
-__global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, LbmParams p, double *rho, double *u) {
+__global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, LbmParams p,
+                        const unsigned *__restrict__ bits, const float *__restrict__ vel, double *rho, double *u) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = (int)p.N;
     if (n >= N) return;
@@ -385,14 +397,24 @@ __global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, Lb
         if (cy(q)) jy += cy(q) * d;
         if (cz(q)) jz += cz(q) * d;
     }
-    const float Fx = F[n] + p.gx, Fy = F[N + n] + p.gy, Fz = F[2 * N + n] + p.gz;
     const float r = 1.f + drho;
     if (rho) rho[n] = (double)r;
-    if (u) {
-        u[3 * (size_t)n + 0] = (double)((jx - 0.5f * Fx) / r);
-        u[3 * (size_t)n + 1] = (double)((jy - 0.5f * Fy) / r);
-        u[3 * (size_t)n + 2] = (double)((jz - 0.5f * Fz) / r);
+    if (!u) return;
+    const int x = n % p.nx, y = (n / p.nx) % p.ny, z = n / (p.nx * p.ny);
+    float ux, uy, uz;
+    if (bits && region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz))) {
+        ux = vel[n];
+        uy = vel[N + n];
+        uz = vel[2 * N + n];
+    } else {
+        const float Fx = F[n] + p.gx, Fy = F[N + n] + p.gy, Fz = F[2 * N + n] + p.gz;
+        ux = (jx - 0.5f * Fx) / r;
+        uy = (jy - 0.5f * Fy) / r;
+        uz = (jz - 0.5f * Fz) / r;
     }
+    u[3 * (size_t)n + 0] = (double)ux;
+    u[3 * (size_t)n + 1] = (double)uy;
+    u[3 * (size_t)n + 2] = (double)uz;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -420,7 +442,7 @@ static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const 
 }
 
 template <class T>
-static cudaError_t near_t(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned *bits,
+static cudaError_t near_t(const void *fin, void *fout, float *F, const LbmParams &p, const unsigned *bits,
                           const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
                           unsigned *next_seed, cudaStream_t s) {
     if (blocks <= 0) {  // rows over the whole lattice
@@ -459,7 +481,7 @@ cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, cons
     }
 }
 
-cudaError_t launch_lbm_near(const void *fin, void *fout, const float *F, const LbmParams &p, const unsigned *bits,
+cudaError_t launch_lbm_near(const void *fin, void *fout, float *F, const LbmParams &p, const unsigned *bits,
                             const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
                             unsigned *next_seed, cudaStream_t s) {
     switch (p.fmt) {
@@ -476,15 +498,18 @@ cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s) {
     return cudaMemsetAsync(f, 0, pop_bytes(p.fmt) * 19 * (size_t)p.N, s);
 }
 
-cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, double *rho, double *u,
-                             cudaStream_t s) {
+cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, const unsigned *bits,
+                             const float *vel, double *rho, double *u, cudaStream_t s) {
     const int blocks = (int)((p.N + 255) / 256);
     switch (p.fmt) {
-        case POP_F16: k_macro<__half><<<blocks, 256, 0, s>>>(static_cast<const __half *>(f), F, p, rho, u); break;
-        case POP_BF16:
-            k_macro<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(f), F, p, rho, u);
+        case POP_F16:
+            k_macro<__half><<<blocks, 256, 0, s>>>(static_cast<const __half *>(f), F, p, bits, vel, rho, u);
             break;
-        default: k_macro<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(f), F, p, rho, u);
+        case POP_BF16:
+            k_macro<__nv_bfloat16>
+                <<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(f), F, p, bits, vel, rho, u);
+            break;
+        default: k_macro<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(f), F, p, bits, vel, rho, u);
     }
     return cudaGetLastError();
 }

@@ -91,7 +91,7 @@ extern "C" cf_status cf_vertex_forces_static(int32_t nv, int32_t nt, const int32
     m.fc = a.corner;
     m.fv = reinterpret_cast<float4 *>(f);
     const float4 *u4 = reinterpret_cast<const float4 *>(u);
-    if (launch_tet_force(m, u4, a.err, nullptr, nullptr, nullptr, s) != cudaSuccess) return CF_ECUDA;
+    if (launch_tet_force(m, u4, a.err, s) != cudaSuccess) return CF_ECUDA;
     if (launch_gather_spread(m, u4, nullptr, nullptr, a.err, s) != cudaSuccess) return CF_ECUDA;
 
     unsigned h = 0;

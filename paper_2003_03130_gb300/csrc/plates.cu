@@ -87,7 +87,7 @@ cf_status upload_plates(cf_ctx *c, const std::vector<float> &zlo, const std::vec
 // forces at u into c->fv, then one damped step (u_in, v_in) -> (u_out, v_out)
 cf_status relax_step(cf_ctx *c, const MeshView &m, const float4 *u_in, const float4 *v_in, float4 *u_out,
                      float4 *v_out, float dt, float cd, float kp) {
-    CUDA_TRY(c, launch_tet_force(m, u_in, c->d_err, nullptr, nullptr, nullptr, c->stream));
+    CUDA_TRY(c, launch_tet_force(m, u_in, c->d_err, c->stream));
     CUDA_TRY(c, launch_gather_spread(m, u_in, nullptr, nullptr, c->d_err, c->stream));
     CUDA_TRY(c, launch_plate_step(m, u_in, v_in, c->fv, u_out, v_out, dt, cd, kp, c->zlo, c->zhi, c->d_err,
                                   c->stream));

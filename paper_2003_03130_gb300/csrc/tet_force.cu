@@ -6,16 +6,22 @@
 
 namespace cf {
 
+// Blocks past tet_blocks: one thread per vertex, marking the next step's
+// force region.
+__device__ __forceinline__ void mark_block(const MeshView &m, const float4 *__restrict__ u, const LbmParams &lp,
+                                           int tet_blocks, const RegionSlot &mark) {
+    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+    if (v >= m.V) return;
+    if (lp.dw == 4)
+        mark_vertex<4>(m, u, lp, v, mark);
+    else
+        mark_vertex<2>(m, u, lp, v, mark);
+}
+
 __global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
-                                                   int tet_blocks, const float4 *__restrict__ u_prev,
-                                                   float *__restrict__ F, LbmParams lp, RegionSlot mark) {
-    if ((int)blockIdx.x >= tet_blocks) {  // two threads per vertex, one job each
-        const int i = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
-        if ((i >> 1) >= m.V) return;
-        if (lp.dw == 4)
-            vertex_job<4>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
-        else
-            vertex_job<2>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
+                                                   int tet_blocks, LbmParams lp, RegionSlot mark) {
+    if ((int)blockIdx.x >= tet_blocks) {
+        mark_block(m, u, lp, tet_blocks, mark);
         return;
     }
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -28,15 +34,9 @@ __global__ void __launch_bounds__(256, 4) k_tet_force(MeshView m, const float4 *
 // loads are issued before either is computed, doubling the bytes a thread
 // has in flight in this latency-bound kernel.
 __global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 *__restrict__ u, unsigned *err,
-                                                     int tet_blocks, const float4 *__restrict__ u_prev,
-                                                     float *__restrict__ F, LbmParams lp, RegionSlot mark) {
-    if ((int)blockIdx.x >= tet_blocks) {  // two threads per vertex, one job each
-        const int i = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
-        if ((i >> 1) >= m.V) return;
-        if (lp.dw == 4)
-            vertex_job<4>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
-        else
-            vertex_job<2>(m, u, u_prev, F, lp, i >> 1, i & 1, mark);
+                                                     int tet_blocks, LbmParams lp, RegionSlot mark) {
+    if ((int)blockIdx.x >= tet_blocks) {
+        mark_block(m, u, lp, tet_blocks, mark);
         return;
     }
     const int t0 = 2 * blockIdx.x * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
@@ -48,21 +48,19 @@ __global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 
     if (t1 < m.T) tet_forces_store(m, b, err, t1);
 }
 
-cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, const float4 *u_prev, float *F,
-                             const LbmParams *lp, cudaStream_t s, int block, const RegionSlot *mark_out,
-                             int pairs) {
+cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, cudaStream_t s, int block,
+                             const LbmParams *lp, const RegionSlot *mark_out, int pairs) {
     if (m.T == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 64;  // default: ~20k tets still give every SM blocks
     const int per = pairs ? 2 : 1;
     const int tb = (m.T + bs * per - 1) / (bs * per);
-    const int cb = (u_prev && F && lp) ? (2 * m.V + bs - 1) / bs : 0;
-    LbmParams p{};
-    if (lp) p = *lp;
-    const RegionSlot mark = (cb && mark_out) ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
+    const int cb = (lp && mark_out) ? (m.V + bs - 1) / bs : 0;
+    const LbmParams p = lp ? *lp : LbmParams{};
+    const RegionSlot mark = cb ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
     if (pairs)
-        k_tet_force2<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark);
+        k_tet_force2<<<tb + cb, bs, 0, s>>>(m, u, err, tb, p, mark);
     else
-        k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, u_prev, F, p, mark);
+        k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, p, mark);
     return cudaGetLastError();
 }
 
