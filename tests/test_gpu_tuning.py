@@ -81,13 +81,33 @@ def test_autotune_advances_like_cf_step(P):
     assert shape["interp_block"] in (64, 128, 256) and shape["fused"] in (0, 1) and shape["near_rows"] in (0, 1)
     assert shape["far_spec"] in (0, 1) and shape["tet_pairs"] in (0, 1)
     assert P.cf_get_launch_shape(ctx) == shape
-    P.cf_step(ctx, 10)
     sim = oracle.Coupled(wl)
-    sim.step(52)
+    sim.step(42)
+    # the last timed candidate may have run another tiling than the chosen one
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+    P.cf_step(ctx, 10)
+    sim.step(10)
     y0 = np.concatenate([c.y0 for c in cells])
     y = np.concatenate([P.cf_get_positions(ctx, i) for i in ids])
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_velocity_readback_after_a_tile_change(P, reference_20):
+    """After a step the force field is consumed and u(t) on the step's force
+    region comes from the near field's store, looked up in the tiling that
+    step ran with, also when the shape changed since."""
+    wl, sim = reference_20
+    ctx = P.cf_create(0)
+    P.cf_set_launch_shape(ctx, {"tile_x": 32, "tile_y": 2, "tile_z": 4})
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 20)
+    u20 = P.cf_get_velocity(ctx)
+    assert rel(u20, sim.fluid.u) <= TOL
+    for tile in ((8, 8, 4), (16, 4, 4)):
+        P.cf_set_launch_shape(ctx, {"tile_x": tile[0], "tile_y": tile[1], "tile_z": tile[2]})
+        assert np.array_equal(P.cf_get_velocity(ctx), u20)
+    P.cf_destroy(ctx)
 
 
 def _cell(centre, seed, R=4.0, h=1.3):
