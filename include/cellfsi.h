@@ -219,14 +219,14 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
-/* Autotuner: picks the launch shape by timing the step kernels on the
+/* Autotuner: picks the launch shape by timing coupled steps on the
  * context's own state. One knob at a time (tile shape, fused or separate
  * cell chain, near-field form, far-field load order, tets per thread,
  * tet-force, spread and interpolation block sizes), every candidate runs
- * steps_per_candidate (>= 1) coupled steps with CUDA events around each
- * kernel, and the candidate with the least summed time of the kernels the
- * knob shapes is kept. The simulation advances by those steps exactly as
- * under cf_step (21 candidates in all). A fluid-only context has nothing to
+ * steps_per_candidate (>= 1) coupled steps exactly as cf_step runs them
+ * (the same step graphs, far field and cell chain overlapping), timed as a
+ * whole with CUDA events, and the fastest candidate is kept. The simulation
+ * advances by those steps exactly as under cf_step (21 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

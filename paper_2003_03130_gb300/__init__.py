@@ -296,8 +296,9 @@ def cf_set_launch_shape(ctx, shape):
 
 
 def cf_autotune(ctx, steps_per_candidate=20):
-    """Time the launch-shape candidates on the context's own state (the
-    simulation advances 21 x steps_per_candidate steps) and keep the
+    """Time the launch-shape candidates on the context's own state, each as
+    steps_per_candidate whole coupled steps run like cf_step (the
+    simulation advances 21 x steps_per_candidate steps), and keep the
     fastest; returns the chosen shape."""
     out = np.zeros(CF_SHAPE_LEN, np.int32)
     _check(ctx, lib().cf_autotune(ctx.handle, steps_per_candidate, _p(out, _i)))

@@ -918,6 +918,36 @@ cf_status region_nodes(cf_ctx *c, long long *out) {
     return CF_OK;
 }
 
+// Device time of n coupled steps with shape sh, run exactly as cf_step(n)
+// runs them (the same graphs, the two streams overlapping), the graphs
+// instantiated before the timed launch. Leaves sh as the context's shape.
+cf_status timed_call(cf_ctx *c, int n, const Shape &sh, double *ms) {
+    c->shape = sh;
+    set_tiles(c->lp, sh.tile);
+    drop_graphs(c);
+    cf_status st = schedule_steps(c, n, false);
+    if (st != CF_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    if (e == cudaSuccess) {
+        st = schedule_steps(c, n, true);
+        if (st == CF_OK) e = cudaEventRecord(e1, c->stream);
+    }
+    if (e == cudaSuccess && st == CF_OK) {
+        st = wait_stream(c);
+        float t = 0.f;
+        if (st == CF_OK) e = cudaEventElapsedTime(&t, e0, e1);
+        *ms = t;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != CF_OK) return st;
+    if (e != cudaSuccess) return fail(c, CF_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+    return consume_errors(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -994,42 +1024,40 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
     if (steps_per_candidate < 1) return fail(c, CF_EINVAL, "steps_per_candidate must be >= 1");
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_autotune needs cf_lbm_init first");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    drop_graphs(c);
     if (c->T > 0) {
-        // one knob at a time, the others at their best so far; a knob is
-        // judged by the kernels it shapes (slots of timed_steps' sums)
+        // one knob at a time, the others at their best so far; a candidate
+        // is judged by the time of whole pipelined steps, so that what the
+        // far field overlaps counts as it does in cf_step
         struct Knob {
             int Shape::*field;
             std::vector<int> cands;
-            std::vector<int> slots;
         };
         const Knob knobs[] = {
-            {&Shape::tile, {0, 1, 2, 3}, {1, 2, 3}},
-            {&Shape::fused, {0, 1}, {0, 1}},
-            {&Shape::near_rows, {0, 1}, {3}},
-            {&Shape::far_spec, {0, 1}, {2}},
-            {&Shape::tet_pairs, {0, 1}, {0}},
-            {&Shape::tet_block, {64, 128, 256}, {0}},
-            {&Shape::gather_block, {64, 128, 256}, {1}},
-            {&Shape::interp_block, {64, 128, 256}, {4}},
+            {&Shape::tile, {0, 1, 2, 3}},
+            {&Shape::fused, {0, 1}},
+            {&Shape::near_rows, {0, 1}},
+            {&Shape::far_spec, {0, 1}},
+            {&Shape::tet_pairs, {0, 1}},
+            {&Shape::tet_block, {64, 128, 256}},
+            {&Shape::gather_block, {64, 128, 256}},
+            {&Shape::interp_block, {64, 128, 256}},
         };
-        Shape best = c->shape;
+        const Shape start = c->shape;
+        Shape best = start;
         for (const Knob &k : knobs) {
             double tbest = 1e300;
             int vbest = best.*k.field;
             for (int v : k.cands) {
                 Shape sh = best;
                 sh.*k.field = v;
-                set_tiles(c->lp, sh.tile);
-                double acc[5];
-                cf_status st = timed_steps(c, steps_per_candidate, sh, acc);
-                if (st == CF_OK) st = consume_errors(c);
+                double t = 0.0;
+                const cf_status st = timed_call(c, steps_per_candidate, sh, &t);
                 if (st != CF_OK) {
-                    set_tiles(c->lp, c->shape.tile);
+                    c->shape = start;
+                    set_tiles(c->lp, start.tile);
+                    drop_graphs(c);
                     return st;
                 }
-                double t = 0.0;
-                for (int slot : k.slots) t += acc[slot];
                 if (t < tbest) {
                     tbest = t;
                     vbest = v;
@@ -1039,6 +1067,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
         }
         c->shape = best;
         set_tiles(c->lp, best.tile);
+        drop_graphs(c);
     }
     return shape_out ? cf_get_launch_shape(c, shape_out) : CF_OK;
 }
