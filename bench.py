@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coupled LBM-IBM steps/s & MLUPS (% HBM roofline); tet-forces/s; FP16 vs FP32 error"
 POP_BYTES_PER_NODE = 2 * 19 * 4  # read + write of 19 FP32 populations
-NEAR_BYTES_PER_NODE = POP_BYTES_PER_NODE + 12 + 12  # + force read, velocity written
-CONSUME_BYTES_PER_SUPPORT_NODE = 12  # the near field zeroes the force it read on the spread's support
+NEAR_BYTES_PER_NODE = POP_BYTES_PER_NODE + 16 + 16  # + force read, velocity written (float4 per node)
+CONSUME_BYTES_PER_SUPPORT_NODE = 16  # the near field zeroes the force it read on the spread's support
 KERNELS = ("k_tet_force", "k_gather_spread", "k_lbm_far", "k_lbm_near", "k_interp_advect")
 
 

@@ -448,14 +448,14 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
     CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
-    CUDA_TRY(c, dalloc(&c->F, 3 * (size_t)N));
-    CUDA_TRY(c, dalloc(&c->vel, 3 * (size_t)N));
+    CUDA_TRY(c, dalloc(&c->F, (size_t)N));
+    CUDA_TRY(c, dalloc(&c->vel, (size_t)N));
     CUDA_TRY(c, dalloc(&c->region, 3 * c->region_stride));
     CUDA_TRY(c, cudaMemsetAsync(c->region, 0, sizeof(unsigned) * 3 * c->region_stride, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float) * 3 * (size_t)N, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->vel, 0, sizeof(float) * 3 * (size_t)N, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float4) * (size_t)N, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->vel, 0, sizeof(float4) * (size_t)N, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->seed, 0, 2 * sizeof(unsigned), c->stream));  // rounding seeds restart
     c->lp = p;
     c->macro_tile = -1;

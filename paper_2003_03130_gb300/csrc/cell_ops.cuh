@@ -81,7 +81,7 @@ __device__ __forceinline__ float4 load_fc(const float4 *p) {
 // shuffle tree (the same order every call: deterministic), and lane k
 // spreads onto its share of the support nodes.
 template <int W, bool FC_L2>
-__device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const float4 *__restrict__ u, float *F,
+__device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const float4 *__restrict__ u, float4 *F,
                                                      const LbmParams &p, int do_spread, unsigned *err, int v,
                                                      int lane, bool live) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -123,7 +123,6 @@ __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const fl
         } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
             if (lane == 0) atomicOr(err, ERR_DOMAIN);
         } else {
-            const int N = (int)p.N;
             float wx[W], wy[W], wz[W];
             delta_weights<W>(s.fx, wx);
             delta_weights<W>(s.fy, wy);
@@ -136,9 +135,7 @@ __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const fl
                 for (int dx = 0; dx < 2; ++dx) {
                     const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
                     const float w = wx[dx] * wyz;
-                    atomicAdd(F + n, w * fx);
-                    atomicAdd(F + N + n, w * fy);
-                    atomicAdd(F + 2 * N + n, w * fz);
+                    atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
                 }
             } else {  // lane = dz, a W x W plane
                 const int Z = wrapi(s.bz + lane, p.nz);
@@ -156,9 +153,7 @@ __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const fl
                     for (int dx = 0; dx < W; ++dx) {
                         const int n = X[dx] + row;
                         const float w = wx[dx] * wyz;
-                        atomicAdd(F + n, w * fx);
-                        atomicAdd(F + N + n, w * fy);
-                        atomicAdd(F + 2 * N + n, w * fz);
+                        atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
                     }
                 }
             }

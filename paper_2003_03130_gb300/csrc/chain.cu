@@ -35,7 +35,7 @@ __device__ __forceinline__ bool wait_count(const int *p, int target, unsigned *e
 
 template <int W>
 __global__ void __launch_bounds__(kChainBlock, 4)
-    k_cell_chain(MeshView m, const float4 *__restrict__ u, float *F, LbmParams lp, RegionSlot mark, unsigned *err,
+    k_cell_chain(MeshView m, const float4 *__restrict__ u, float4 *F, LbmParams lp, RegionSlot mark, unsigned *err,
                  const int4 *__restrict__ items, int nitems, const int *__restrict__ need, int *counters) {
     __shared__ int4 item;
     __shared__ int ready;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kChainBlock, 4)
     }
 }
 
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float *F, const LbmParams &lp,
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
                               const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
                               int *counters, int blocks, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;

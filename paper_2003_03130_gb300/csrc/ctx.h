@@ -69,8 +69,8 @@ struct cf_ctx {
     int pop_format = CF_POP_F32;  // CF_POP_* storage of the populations (next cf_lbm_init)
     int delta_w = 2;           // delta kernel support width (next cf_lbm_init)
     void *f[2] = {nullptr, nullptr};
-    float *F = nullptr;
-    float *vel = nullptr;  // u(t) on the force region, [3][N]
+    float4 *F = nullptr;    // force field, (Fx, Fy, Fz, 0) per node
+    float4 *vel = nullptr;  // u(t) on the force region, (ux, uy, uz, 0) per node
 
     // cells
     int V = 0, T = 0;

@@ -44,14 +44,14 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
 }
 
 template <int W>
-__global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float *F,
+__global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float4 *F,
                                                           LbmParams p, int do_spread, unsigned *err) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = g >> 2;
     gather_spread_vertex<W, false>(m, u, F, p, do_spread, err, v, g & 3, v < m.V);
 }
 
-cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
+cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
                                  cudaStream_t s, int block) {
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
@@ -69,7 +69,7 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, c
 // Eight threads per vertex, each summing W^3 / 8 support nodes; the group of
 // eight combines its partial sums with shuffles.
 template <int W>
-__global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const float *__restrict__ vel, LbmParams p,
+__global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const float4 *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
                                                        unsigned *err) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,7 +83,6 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
         Support s;
         ok = support_of<W>(m.origin, __ldg(m.xr + v), uc, p.ny, s);
         if (ok) {
-            const int N = (int)p.N;
             float wx[W], wy[W], wz[W];
             delta_weights<W>(s.fx, wx);
             delta_weights<W>(s.fy, wy);
@@ -92,9 +91,10 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
                 const int dx = lane & 1, dy = (lane >> 1) & 1, dz = lane >> 2;
                 const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * wrapi(s.bz + dz, p.nz));
                 const float w = wx[dx] * wy[dy] * wz[dz];
-                vx = w * __ldg(vel + n);
-                vy = w * __ldg(vel + N + n);
-                vz = w * __ldg(vel + 2 * N + n);
+                const float4 q = __ldg(vel + n);
+                vx = w * q.x;
+                vy = w * q.y;
+                vz = w * q.z;
             } else {  // lane = (dz, row pair): plane dz = lane >> 1, rows dy = 2 (lane & 1) + {0, 1}
                 const int dz = lane >> 1, dy0 = 2 * (lane & 1);
                 const int Z = wrapi(s.bz + dz, p.nz);
@@ -107,9 +107,10 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
                     for (int dx = 0; dx < W; ++dx) {
                         const int n = wrapi(s.bx + dx, p.nx) + row;
                         const float w = wx[dx] * wyz;
-                        vx = fmaf(w, __ldg(vel + n), vx);
-                        vy = fmaf(w, __ldg(vel + N + n), vy);
-                        vz = fmaf(w, __ldg(vel + 2 * N + n), vz);
+                        const float4 q = __ldg(vel + n);
+                        vx = fmaf(w, q.x, vx);
+                        vy = fmaf(w, q.y, vy);
+                        vz = fmaf(w, q.z, vz);
                     }
                 }
             }
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
     u_next[v] = un;
 }
 
-cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
+cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s, int block) {
     if (m.V == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 128;

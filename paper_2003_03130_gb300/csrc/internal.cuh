@@ -1,12 +1,16 @@
 // Internal declarations of the GB300 cell/fluid library: device layouts,
 // kernel launchers and the D3Q19 lattice as compile-time constants.
 //
-// Device layout (structure of arrays throughout, so that consecutive threads
-// touch consecutive words):
+// Device layout (structure of arrays for the streams that consecutive
+// threads read word by word; float4 per node or vertex where a thread reads
+// all three components of one point):
 //   populations  f[q * N + n], q = 0..18, n = x + nx*(y + ny*z), stored as the
 //                deviation f_q - w_q from the rest equilibrium (keeps FP32
 //                rounding relative to the O(u) signal, not to O(w_q));
-//   force field  F[a * N + n], a = 0..2;
+//   force field  float4 F[n] = (Fx, Fy, Fz, 0): one vector atomic per node
+//                in the spread, one 16-byte load in the near field;
+//   u(t)         float4 vel[n] = (ux, uy, uz, 0) on the force region (one
+//                16-byte load per support node in the interpolation);
 //   vertices     float4 per vertex (one 16-byte load in the tet gathers):
 //                xr (FP32 x_ref relative to the cell's integer origin, .w =
 //                cell id), u (FP32 displacement y - x_ref), fv (force);
@@ -276,7 +280,7 @@ cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, do
                           cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
 // same threads spread their vertex force onto the lattice.
-cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float *F, const LbmParams *lp, unsigned *err,
+cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
                                  cudaStream_t s, int block = 0);
 // Add the force region of the positions x + u (support grown by one node) to
 // a region slot (cleared by the caller).
@@ -288,7 +292,7 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
 // [begin, end) of `cell`, 2 = vertex sums + spread of vertices [begin, end)
 // of `cell`. A kind-2 item waits (bounded) until the need[cell] kind-1 items
 // of its cell are done; counters[2 + ncells] must be zero at launch.
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float *F, const LbmParams &lp,
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
                               const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
                               int *counters, int blocks, cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
@@ -309,8 +313,8 @@ cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, cons
 // blocks > 0: that many blocks stride over the region's tile list;
 // blocks <= 0: rows of 128 nodes over the whole lattice, threads outside the
 // region return at once.
-cudaError_t launch_lbm_near(const void *fin, void *fout, float *F, const LbmParams &p, const unsigned *bits,
-                            const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
+cudaError_t launch_lbm_near(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
+                            const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
                             unsigned *next_seed, cudaStream_t s);
 // True for the device functions of the far-field kernels (to tell their graph
 // nodes apart).
@@ -320,7 +324,7 @@ size_t pop_bytes(int fmt);
 // x + u_cur; u_next = u_cur + velocity. A vertex that moves one lattice
 // spacing or more along an axis sets ERR_MOVED: the next step's force region
 // (this step's support grown by one node) would no longer hold its support.
-cudaError_t launch_interp_advect(const MeshView &m, const float *vel, const LbmParams &p, const float4 *u_cur,
+cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s, int block = 0);
 // Compression between plates and the adjoint (csrc/adjoint.cu).
 // out = J_el v at displacements u (vertex sums of the corner tangents; uses m.fc).
@@ -346,7 +350,7 @@ cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s);
 // rho and u(t) of every node after a step. u is u(t) as the near field
 // stored it (vel) on the last step's force region (bits, in the tiling of
 // p; null: no region), and from the populations and F elsewhere.
-cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, const unsigned *bits,
-                             const float *vel, double *rho, double *u, cudaStream_t s);
+cudaError_t launch_lbm_macro(const void *f, const float4 *F, const LbmParams &p, const unsigned *bits,
+                             const float4 *vel, double *rho, double *u, cudaStream_t s);
 
 }  // namespace cf

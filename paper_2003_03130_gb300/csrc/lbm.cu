@@ -216,8 +216,8 @@ __device__ __forceinline__ bool wall_pull(int y, int ny) {
 // loads were issued, to belong to the other part of the split).
 template <class T, bool WALL, bool HAS_F>
 __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restrict__ fout,
-                                         float *__restrict__ F, const LbmParams &p, int x, int y, int z,
-                                         float *__restrict__ vel, unsigned seed, bool store = true) {
+                                         float4 *__restrict__ F, const LbmParams &p, int x, int y, int z,
+                                         float4 *__restrict__ vel, unsigned seed, bool store = true) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -241,23 +241,17 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
     bool spread = false;
     if (HAS_F) {
-        const float ax = __ldcg(F + n), ay = __ldcg(F + N + n), az = __ldcg(F + 2 * N + n);
-        spread = ax != 0.f || ay != 0.f || az != 0.f;
-        Fx += ax;
-        Fy += ay;
-        Fz += az;
+        const float4 a = __ldcg(F + n);
+        spread = a.x != 0.f || a.y != 0.f || a.z != 0.f;
+        Fx += a.x;
+        Fy += a.y;
+        Fz += a.z;
     }
     const float3 u = collide<T>(d, Fx, Fy, Fz, p);
     if (!store) return;
-    if (HAS_F && spread) {  // consumed: the next step spreads onto a zero field
-        F[n] = 0.f;
-        F[N + n] = 0.f;
-        F[2 * N + n] = 0.f;
-    }
+    if (HAS_F && spread) F[n] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed: the next step spreads onto zeros
     if (vel) {  // u(t) of this step, for the interpolation at the vertices
-        vel[n] = u.x;
-        vel[N + n] = u.y;
-        vel[2 * N + n] = u.z;
+        vel[n] = make_float4(u.x, u.y, u.z, 0.f);
     }
     if constexpr (sizeof(T) == 2) {
         if (p.sr) {
@@ -333,8 +327,8 @@ __global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *_
 // is a large part of the lattice.
 template <class T>
 __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin, T *__restrict__ fout,
-                                                       float *__restrict__ F, LbmParams p,
-                                                       const unsigned *__restrict__ bits, float *__restrict__ vel,
+                                                       float4 *__restrict__ F, LbmParams p,
+                                                       const unsigned *__restrict__ bits, float4 *__restrict__ vel,
                                                        const unsigned *__restrict__ seed_in,
                                                        unsigned *__restrict__ seed_out) {
     const unsigned seed = *seed_in;
@@ -354,9 +348,9 @@ __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin
 // moves with the cells, so blocks stride over the list's half tiles.
 template <class T>
 __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
-                                                            float *__restrict__ F, LbmParams p,
+                                                            float4 *__restrict__ F, LbmParams p,
                                                             const int *__restrict__ count,
-                                                            const int *__restrict__ tiles, float *__restrict__ vel,
+                                                            const int *__restrict__ tiles, float4 *__restrict__ vel,
                                                             const unsigned *__restrict__ seed_in,
                                                             unsigned *__restrict__ seed_out) {
     const unsigned seed = *seed_in;
@@ -383,8 +377,8 @@ __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict_
 // rho u = sum c_q d*_q - F/2 (the collision adds exactly F to the momentum,
 // and rho u = sum c_q d_q + F/2 before it).
 template <class T>
-__global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, LbmParams p,
-                        const unsigned *__restrict__ bits, const float *__restrict__ vel, double *rho, double *u) {
+__global__ void k_macro(const T *__restrict__ f, const float4 *__restrict__ F, LbmParams p,
+                        const unsigned *__restrict__ bits, const float4 *__restrict__ vel, double *rho, double *u) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = (int)p.N;
     if (n >= N) return;
@@ -403,11 +397,13 @@ __global__ void k_macro(const T *__restrict__ f, const float *__restrict__ F, Lb
     const int x = n % p.nx, y = (n / p.nx) % p.ny, z = n / (p.nx * p.ny);
     float ux, uy, uz;
     if (bits && region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz))) {
-        ux = vel[n];
-        uy = vel[N + n];
-        uz = vel[2 * N + n];
+        const float4 q = vel[n];
+        ux = q.x;
+        uy = q.y;
+        uz = q.z;
     } else {
-        const float Fx = F[n] + p.gx, Fy = F[N + n] + p.gy, Fz = F[2 * N + n] + p.gz;
+        const float4 a = F[n];
+        const float Fx = a.x + p.gx, Fy = a.y + p.gy, Fz = a.z + p.gz;
         ux = (jx - 0.5f * Fx) / r;
         uy = (jy - 0.5f * Fy) / r;
         uz = (jz - 0.5f * Fz) / r;
@@ -442,8 +438,8 @@ static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const 
 }
 
 template <class T>
-static cudaError_t near_t(const void *fin, void *fout, float *F, const LbmParams &p, const unsigned *bits,
-                          const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
+static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
+                          const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
                           unsigned *next_seed, cudaStream_t s) {
     if (blocks <= 0) {  // rows over the whole lattice
         const int bx = p.nx < 128 ? p.nx : 128;
@@ -481,8 +477,8 @@ cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, cons
     }
 }
 
-cudaError_t launch_lbm_near(const void *fin, void *fout, float *F, const LbmParams &p, const unsigned *bits,
-                            const int *count, const int *tiles, float *vel, int blocks, const unsigned *seed,
+cudaError_t launch_lbm_near(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
+                            const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
                             unsigned *next_seed, cudaStream_t s) {
     switch (p.fmt) {
         case POP_F16: return near_t<__half>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
@@ -498,8 +494,8 @@ cudaError_t launch_lbm_init(void *f, const LbmParams &p, cudaStream_t s) {
     return cudaMemsetAsync(f, 0, pop_bytes(p.fmt) * 19 * (size_t)p.N, s);
 }
 
-cudaError_t launch_lbm_macro(const void *f, const float *F, const LbmParams &p, const unsigned *bits,
-                             const float *vel, double *rho, double *u, cudaStream_t s) {
+cudaError_t launch_lbm_macro(const void *f, const float4 *F, const LbmParams &p, const unsigned *bits,
+                             const float4 *vel, double *rho, double *u, cudaStream_t s) {
     const int blocks = (int)((p.N + 255) / 256);
     switch (p.fmt) {
         case POP_F16:
