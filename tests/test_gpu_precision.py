@@ -13,6 +13,9 @@
   7.3e-3, BF16 6.7e-2, FP16-SR 2.0e-6, BF16-SR 9.2e-5). Every 16-bit format
   but round-to-nearest BF16 meets the 1e-3 relative bound on D; stochastic
   rounding removes the stagnation of sub-ULP increments.
+* The steady Poiseuille profile at the magic tau (where the oracle is exact)
+  by format, and round-to-nearest against stochastic rounding in a channel
+  of height 128.
 """
 import numpy as np
 import pytest
@@ -76,6 +79,52 @@ def test_reduced_precision_fluid(P, fmt, tol):
     print(f"{fmt}: relative velocity error {err:.2e}")
     assert err <= tol
     assert abs((rho - 1.0).sum()) <= 1e-3 * rho.size ** 0.5
+
+
+def poiseuille_by_format(P, fmt, H=32, u_max=0.02, steps=12000):
+    """Body-force channel of height H at the magic tau = 1/2 + sqrt(3)/4,
+    where BGK with halfway bounce-back is exact (the oracle's pin): steady
+    profile against u(y) = g/(2 nu) (y + 1/2)(H - y - 1/2). 12,000 steps are
+    17 decay times H^2 / (pi^2 nu) of the slowest mode."""
+    tau = 0.5 + np.sqrt(3) / 4
+    nu = (tau - 0.5) / 3
+    g = 8 * nu * u_max / H**2
+    u, _ = fluid_run(P, fmt, 4, H, 4, tau, 0.0, 0.0, (g, 0.0, 0.0), steps)
+    y = np.arange(H)
+    exact = g / (2 * nu) * (y + 0.5) * (H - y - 0.5)
+    prof = u[:, :, :, 0].mean(axis=(0, 2))
+    spread = np.abs(u[:, :, :, 0] - prof[None, :, None]).max()  # the flow is uniform in x and z
+    return rel(prof, exact), spread / u_max
+
+
+@pytest.mark.parametrize("fmt,tol", [("f32", 3e-4), ("f16sr", 2e-3), ("bf16sr", 2e-2)])
+def test_poiseuille_profile_by_format(P, fmt, tol):
+    """FP32 meets the exact profile to its accumulated rounding (the same
+    algorithm emulated in FP64 ends 6e-8 from it, in FP32 3e-5; the GPU's
+    FP32 operation order measured 9e-5); stochastic rounding keeps the 16-bit
+    formats within a few units of their last place (2^-11 FP16, 2^-8 BF16)."""
+    err, spread = poiseuille_by_format(P, fmt)
+    print(f"{fmt}: Poiseuille profile error {err:.2e}, spread across x and z {spread:.1e}")
+    assert err <= tol
+    assert spread <= tol
+
+
+def test_stochastic_rounding_beats_nearest_in_a_wide_channel(P):
+    """In a channel of height 128 (u_max 0.02) the per-step increments of the
+    slow start-up fall below half an FP16 unit of the stored populations:
+    round-to-nearest loses them, stochastic rounding keeps them in
+    expectation. Profiles after 20,000 steps against FP32's."""
+    H, tau = 128, 1.0
+    nu = (tau - 0.5) / 3
+    g = 8 * nu * 0.02 / H**2
+    prof = {}
+    for fmt in ("f32", "f16", "f16sr"):
+        u, _ = fluid_run(P, fmt, 4, H, 4, tau, 0.0, 0.0, (g, 0.0, 0.0), 20000)
+        prof[fmt] = u[:, :, :, 0].mean(axis=(0, 2))
+    e_rn, e_sr = rel(prof["f16"], prof["f32"]), rel(prof["f16sr"], prof["f32"])
+    print(f"profile vs FP32 after 20,000 steps: f16 {e_rn:.2e}, f16sr {e_sr:.2e}")
+    assert e_sr <= 1e-3
+    assert e_sr < e_rn
 
 
 def sheared_cell():
