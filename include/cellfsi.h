@@ -165,8 +165,13 @@ cf_status cf_step_async(cf_ctx *ctx, int32_t n);
  * positions of all cells (y_in [V][3], every vertex in cell order as with
  * CF_ALL_CELLS; NULL keeps them), advance n >= 0 steps as cf_step, then
  * read the positions of all cells into y_out [V][3] (NULL skips it), with a
- * single wait at the end. Errors as cf_set_positions, cf_step and
- * cf_get_positions; CF_ESTATE without cells when y_in or y_out is given. */
+ * single wait at the end. Host buffers that are page-locked and mapped into
+ * the device's address space (cudaHostAlloc, cudaMallocHost, or registered
+ * as mapped) are read and written in place by the conversion kernels over
+ * the host link; other buffers go through a device staging copy. The caller
+ * keeps both buffers unchanged and unread until the call returns. Errors as
+ * cf_set_positions, cf_step and cf_get_positions; CF_ESTATE without cells
+ * when y_in or y_out is given. */
 cf_status cf_step_exchange(cf_ctx *ctx, int32_t n, const double *y_in, double *y_out);
 
 /* Build, without running anything, every CUDA graph that cf_step or

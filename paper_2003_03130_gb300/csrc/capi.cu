@@ -785,6 +785,17 @@ cf_status cf_step(cf_ctx *c, int32_t n) {
     return cf_synchronize(c);
 }
 
+// Device address of page-locked host memory that is mapped into the current
+// device's address space, else null (pageable memory, or no mapping).
+static void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not an error of the context
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 cf_status cf_step_exchange(cf_ctx *c, int32_t n, const double *y_in, double *y_out) {
     if (!c) return CF_EINVAL;
     DeviceGuard dg(c->device);
@@ -794,16 +805,26 @@ cf_status cf_step_exchange(cf_ctx *c, int32_t n, const double *y_in, double *y_o
     if (y_in) {
         for (long long i = 0; i < 3LL * c->V; ++i)
             if (!std::isfinite(y_in[i])) return fail(c, CF_EINVAL, "non-finite position");
-        CUDA_TRY(c, cudaMemcpyAsync(c->stage, y_in, sizeof(double) * 3 * c->V, cudaMemcpyHostToDevice, c->stream));
-        CUDA_TRY(c, launch_set_positions(c->stage, 0, c->V, c->xref64, c->u[c->cur], c->stream));
+        // mapped page-locked input: the conversion kernel reads it in place
+        // over the host link; otherwise it is staged by a copy
+        const double *src = static_cast<const double *>(mapped_host(y_in));
+        if (!src) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->stage, y_in, sizeof(double) * 3 * c->V, cudaMemcpyHostToDevice,
+                                        c->stream));
+            src = c->stage;
+        }
+        CUDA_TRY(c, launch_set_positions(src, 0, c->V, c->xref64, c->u[c->cur], c->stream));
     }
     if (n > 0) {
         cf_status st = schedule_steps(c, n, true);
         if (st != CF_OK) return st;
     }
     if (y_out) {
-        CUDA_TRY(c, launch_get_positions(c->u[c->cur], c->xref64, 0, c->V, c->stage, c->stream));
-        CUDA_TRY(c, cudaMemcpyAsync(y_out, c->stage, sizeof(double) * 3 * c->V, cudaMemcpyDeviceToHost, c->stream));
+        double *dst = static_cast<double *>(mapped_host(y_out));  // written in place when mapped
+        CUDA_TRY(c, launch_get_positions(c->u[c->cur], c->xref64, 0, c->V, dst ? dst : c->stage, c->stream));
+        if (!dst)
+            CUDA_TRY(c, cudaMemcpyAsync(y_out, c->stage, sizeof(double) * 3 * c->V, cudaMemcpyDeviceToHost,
+                                        c->stream));
     }
     return consume_errors(c);  // the one wait of the call
 }
