@@ -344,11 +344,29 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         }
         c->own_stream = true;
     }
-    if (dalloc(&c->d_err, 1) != cudaSuccess || dalloc(&c->d_status, 1) != cudaSuccess ||
-        dalloc(&c->taylor_out, 10) != cudaSuccess || dalloc(&c->seed, 2) != cudaSuccess ||
-        cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(c->seed, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
-        dalloc(&c->energy_out, 1) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+    int host_atomics = 0;
+    if (cudaDeviceGetAttribute(&host_atomics, cudaDevAttrHostNativeAtomicSupported, device) != cudaSuccess)
+        host_atomics = 0;
+    if (host_atomics && cudaHostAlloc((void **)&c->h_err, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess) {
+        *c->h_err = 0u;
+        if (cudaHostGetDevicePointer((void **)&c->d_err, c->h_err, 0) == cudaSuccess) {
+            c->err_mapped = true;
+        } else {
+            cudaGetLastError();
+            cudaFreeHost(c->h_err);
+            c->h_err = nullptr;
+            c->d_err = nullptr;
+        }
+    } else {
+        cudaGetLastError();
+        c->h_err = nullptr;
+    }
+    const bool err_ok =
+        c->err_mapped || (dalloc(&c->d_err, 1) == cudaSuccess && cudaMemset(c->d_err, 0, sizeof(unsigned)) == cudaSuccess &&
+                          cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) == cudaSuccess);
+    if (!err_ok || dalloc(&c->d_status, 1) != cudaSuccess || dalloc(&c->taylor_out, 10) != cudaSuccess ||
+        dalloc(&c->seed, 2) != cudaSuccess || cudaMemset(c->seed, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
+        dalloc(&c->energy_out, 1) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
     }
@@ -361,7 +379,7 @@ void cf_destroy(cf_ctx *c) {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
-    dfree(c->d_err);
+    if (!c->err_mapped) dfree(c->d_err);  // else the device address of h_err
     dfree(c->d_status);
     dfree(c->seed);
     if (c->h_err) cudaFreeHost(c->h_err);

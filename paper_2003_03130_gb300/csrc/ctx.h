@@ -58,8 +58,14 @@ struct cf_ctx {
     std::string err;
     double timeout_s = 600.0;
 
+    // The device error word: kernels atomicOr ERR_* bits into d_err. Where the
+    // device has native atomics on host memory, the word lives in mapped
+    // page-locked memory (h_err, with d_err its device address) and the host
+    // reads and clears it after a wait, with no copy on the stream; otherwise
+    // d_err is device memory and h_err its page-locked copy.
     unsigned *d_err = nullptr;
-    unsigned *h_err = nullptr;  // pinned host copy of the error word (one wait per read)
+    unsigned *h_err = nullptr;
+    bool err_mapped = false;
     unsigned *seed = nullptr;  // rounding seeds of the two buffer parities (16-bit stochastic rounding)
     unsigned long long *d_status = nullptr;
 
@@ -203,13 +209,24 @@ cf_status wait_stream(cf_ctx *c) {
 
 // Read and clear the device error word.
 cf_status consume_errors(cf_ctx *c) {
-    // into pinned memory the copy stays asynchronous, so the read costs one
-    // wait instead of two
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
-    cf_status s = wait_stream(c);
-    if (s != CF_OK) return s;
-    const unsigned h = *c->h_err;
+    unsigned h = 0;
+    if (c->err_mapped) {
+        // every kernel of the context has finished after the wait, and the
+        // word is written only by them
+        cf_status s = wait_stream(c);
+        if (s != CF_OK) return s;
+        volatile unsigned *w = c->h_err;
+        h = *w;
+        *w = 0u;
+    } else {
+        // into page-locked memory the copy stays asynchronous, so the read
+        // costs one wait instead of two
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+        cf_status s = wait_stream(c);
+        if (s != CF_OK) return s;
+        h = *c->h_err;
+    }
     if (h & ERR_INVERTED) return fail(c, CF_EINVERTED, "a tet reached det F <= 0");
     if (h & ERR_NONFINITE) return fail(c, CF_ENONFINITE, "non-finite force or position");
     if (h & ERR_DOMAIN) return fail(c, CF_EDOMAIN, "a vertex's delta support left 0 <= y <= ny-1");
