@@ -803,6 +803,19 @@ cf_status cf_step(cf_ctx *c, int32_t n) {
     return cf_synchronize(c);
 }
 
+// True if no value of y[0..n) is an infinity or a NaN (exponent bits all
+// set). Branch-free over the array, so the compiler vectorises it.
+static bool all_finite(const double *y, long long n) {
+    const uint64_t exp = 0x7ff0000000000000ull;
+    uint64_t bad = 0;
+    for (long long i = 0; i < n; ++i) {
+        uint64_t b;
+        std::memcpy(&b, y + i, sizeof b);
+        bad |= (uint64_t)((b & exp) == exp);
+    }
+    return bad == 0;
+}
+
 // Device address of page-locked host memory that is mapped into the current
 // device's address space, else null (pageable memory, or no mapping).
 static void *mapped_host(const void *p) {
@@ -821,8 +834,7 @@ cf_status cf_step_exchange(cf_ctx *c, int32_t n, const double *y_in, double *y_o
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_step_exchange needs cf_lbm_init first");
     if ((y_in || y_out) && c->V == 0) return fail(c, CF_ESTATE, "no cells");
     if (y_in) {
-        for (long long i = 0; i < 3LL * c->V; ++i)
-            if (!std::isfinite(y_in[i])) return fail(c, CF_EINVAL, "non-finite position");
+        if (!all_finite(y_in, 3LL * c->V)) return fail(c, CF_EINVAL, "non-finite position");
         // mapped page-locked input: the conversion kernel reads it in place
         // over the host link; otherwise it is staged by a copy
         const double *src = static_cast<const double *>(mapped_host(y_in));
@@ -1143,8 +1155,7 @@ cf_status cf_set_positions(cf_ctx *c, int32_t id, const double *y) {
     int v0, nv;
     if (!vertex_range(c, id, &v0, &nv) || !y) return fail(c, CF_EINVAL, "unknown cell or null input");
     DeviceGuard dg(c->device);
-    for (long long i = 0; i < 3LL * nv; ++i)
-        if (!std::isfinite(y[i])) return fail(c, CF_EINVAL, "non-finite position");
+    if (!all_finite(y, 3LL * nv)) return fail(c, CF_EINVAL, "non-finite position");
     CUDA_TRY(c, cudaMemcpyAsync(c->stage, y, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, launch_set_positions(c->stage, v0, nv, c->xref64, c->u[c->cur], c->stream));
     return wait_stream(c);
