@@ -37,6 +37,29 @@ METRIC = "coupled LBM-IBM steps/s & MLUPS (% HBM roofline); tet-forces/s; FP16 v
 POP_BYTES_PER_NODE = 2 * 19 * 4  # read + write of 19 FP32 populations
 NEAR_BYTES_PER_NODE = POP_BYTES_PER_NODE + 16 + 16  # + force read, velocity written (float4 per node)
 CONSUME_BYTES_PER_SUPPORT_NODE = 16  # the near field zeroes the force it read on the spread's support
+# cell kernels (FP32): per tet, K1 reads the int4 indices (16) and the packed B rows (48) and writes
+# four float4 corner forces (64); K23 reads four incidence entries (16) and the corner forces (64).
+# Per vertex, K1 reads xr and u (32); K23 reads the row bounds (8), xr and u (32), writes the vertex
+# force (16) and adds one float4 per support node into F (16 W^3).
+CELL_BYTES_PER_TET = 16 + 48 + 64 + 16 + 64
+CELL_BYTES_PER_VERTEX = 32 + 8 + 32 + 16
+
+
+def cell_bytes(n_tets, n_verts, width):
+    """Algorithmic bytes of the tet forces + vertex sums + spread of one step."""
+    return CELL_BYTES_PER_TET * n_tets + (CELL_BYTES_PER_VERTEX + 16 * width**3) * n_verts
+
+
+def cell_roofline(wl, kms, peak):
+    """Tet forces + vertex sums + spread by their CUDA-event times (kernel
+    slots 0 and 1): tets/s and the fraction of the HBM peak their algorithmic
+    bytes reach."""
+    s = (kms[0] + kms[1]) / 1e3
+    b = cell_bytes(wl.n_tets, wl.n_verts, wl.delta)
+    return {"kernels": "k_tet_force + k_gather_spread", "tets_per_s": wl.n_tets / s, "bound": "hbm",
+            "algorithmic_bytes_per_step": b, "achieved": b / s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": b / s / 1e9 / peak,
+            "bytes_model": f"{CELL_BYTES_PER_TET} B/tet + ({CELL_BYTES_PER_VERTEX} + 16 W^3) B/vertex"}
 KERNELS = ("k_tet_force", "k_gather_spread", "k_lbm_far", "k_lbm_near", "k_interp_advect")
 
 
@@ -470,6 +493,9 @@ def run_ours(args):
             "support_nodes": n_sup,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
         },
+        # the tet forces and vertex sums + spread against the same HBM peak (FP32 corner forces
+        # through HBM: the deterministic incidence-row gather)
+        "cell_roofline": cell_roofline(wl, kms, peak) if wl.n_tets else None,
         "e2e": {
             "value": job_rate(args.e2e_steps, world, e2e_s),
             "unit": "steps/s",
