@@ -251,6 +251,45 @@ def test_errors_are_status_codes(P):
     assert e.value.name == "CF_EDOMAIN"
 
 
+def test_empty_and_limit_inputs(P):
+    """Empty calls change nothing; inputs at or past the limits are status
+    codes before any device work, and a rejected call leaves the state as it
+    was."""
+    from paper_2003_03130_gb300 import CellFSIError
+
+    def rejects(name, f, *a):
+        with pytest.raises(CellFSIError) as e:
+            f(*a)
+        assert e.value.name == name
+
+    ctx = P.cf_create(0)
+    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 0, 8, 8, 1.0, 0.0, 0.0)
+    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 1024, 1024, 111, 1.0, 0.0, 0.0)  # 19 N >= 2^31
+    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 8, 8, 8, 1.0, 0.1, 0.0)  # Mach guard
+    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 8, 8, 8, 1.0, 0.0, 0.0, (np.inf, 0.0, 0.0))
+    cell = small_cell()
+    rejects("CF_EINVAL", P.cf_mesh_init, ctx, cell.x_ref[:3], cell.tets[:0])
+    rejects("CF_EINVAL", P.cf_mesh_init, ctx, cell.x_ref, cell.tets[:0])
+
+    wl = configs.small_shear()
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 3)
+    y, u = P.cf_get_positions(ctx, cid), P.cf_get_velocity(ctx)
+    P.cf_step(ctx, 0)
+    P.cf_step_exchange(ctx, 0)
+    assert np.array_equal(P.cf_get_positions(ctx, cid), y)
+    assert np.array_equal(P.cf_get_velocity(ctx), u)
+    rejects("CF_EINVAL", P.cf_step, ctx, -1)
+    for bad in (np.inf, -np.inf, np.nan):
+        yb = y.copy()
+        yb[-1, 2] = bad
+        rejects("CF_EINVAL", P.cf_set_positions, ctx, cid, yb)
+        rejects("CF_EINVAL", P.cf_step_exchange, ctx, 1, yb)
+    assert np.array_equal(P.cf_get_positions(ctx, cid), y)
+    assert np.array_equal(P.cf_get_velocity(ctx), u)
+    P.cf_destroy(ctx)
+
+
 # ---------------------------------------------------------------- orchestration
 
 def test_pipelined_steps_equal_single_steps_and_profiled_path(P):
