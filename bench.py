@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled LBM-IBM steps/s & MLUPS (% HBM roofline); tet-forces/s; FP16 vs FP32 error"
 POP_BYTES_PER_NODE = 2 * 19 * 4  # read + write of 19 FP32 populations
 NEAR_BYTES_PER_NODE = POP_BYTES_PER_NODE + 16 + 16  # + force read, velocity written (float4 per node)
+MULTICELL_R = 16.0  # cell radius of the multicell workload (its d_ref = 2R for the cell strain)
 CONSUME_BYTES_PER_SUPPORT_NODE = 16  # the near field zeroes the force it read on the spread's support
 # cell kernels (FP32): per tet, K1 reads the int4 indices (16) and the packed B rows (48) and writes
 # four float4 corner forces (64); K23 reads four incidence entries (16) and the corner forces (64).
@@ -112,7 +113,7 @@ def workload(args):
     elif args.workload == "paperbox":
         wl = configs.paper_box_shear(ca=args.ca, w=args.w)
     elif args.workload == "multicell":
-        wl = configs.multicell_shear(ncells=4 if args.phi == 0.11 else 8, ca=args.ca, w=args.w)
+        wl = configs.multicell_shear(ncells=4 if args.phi == 0.11 else 8, R=MULTICELL_R, ca=args.ca, w=args.w)
     else:
         wl = configs.production_shear(ca=args.ca, w=args.w, n=args.n)
     wl.delta = {"trilinear": 2, "peskin4": 4}[args.delta]
@@ -431,6 +432,8 @@ def run_ours(args):
         barrier()
         y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
         mean_D = float(np.mean([P.cf_get_taylor(ctx, i)["D"] for i in ids])) if args.workload == "multicell" else None
+        mean_strain = (float(np.mean([P.cf_get_cell_strain(ctx, i, 2 * MULTICELL_R)["strain"] for i in ids]))
+                       if args.workload == "multicell" else None)
         P.cf_destroy(ctx)
 
     steps_per_s = job_rate(K, world, ms / 1e3)
@@ -507,6 +510,7 @@ def run_ours(args):
     }
     if mean_D is not None:  # Taylor deformation averaged over the cells, after warm-up + timed steps
         out["mean_taylor_D"] = mean_D
+        out["mean_cell_strain"] = mean_strain  # (d_max - 2R) / 2R averaged over the cells
     if (rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear"
             and args.pop_format == "f32"):
         out["precision"] = precision_block(P, torch, dev, args.precision_steps)

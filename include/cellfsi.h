@@ -278,6 +278,14 @@ cf_status cf_get_energy(cf_ctx *ctx, int32_t cell_id, double *out);
  * cell volume. */
 cf_status cf_get_taylor(cf_ctx *ctx, int32_t cell_id, double *out);
 
+/* Cell strain (Sec. 6.1, Eq. for the net strain): out[0] = d_max, the
+ * largest distance between two vertices of the cell at the current positions
+ * (all pairs, on the device, in FP32 from the cell-relative positions),
+ * out[1] = (d_max - d_ref) / d_ref with d_ref the reference diameter (2R for a
+ * sphere of radius R). CF_EINVAL for an unknown cell, a null output or d_ref
+ * not positive and finite. */
+cf_status cf_get_cell_strain(cf_ctx *ctx, int32_t cell_id, double d_ref, double *out);
+
 /* Incidence rows of a cell: ptr[nv+1], idx[4 nt] with entries 4*t + c (t
  * local to the cell, ascending within each row). */
 cf_status cf_get_csr(cf_ctx *ctx, int32_t cell_id, int32_t *ptr, int32_t *idx);

@@ -72,6 +72,7 @@ def lib():
             "cf_get_energy": ([vp, ctypes.c_int32, _d], ctypes.c_int),
             "cf_get_csr": ([vp, ctypes.c_int32, _i, _i], ctypes.c_int),
             "cf_get_taylor": ([vp, ctypes.c_int32, _d], ctypes.c_int),
+            "cf_get_cell_strain": ([vp, ctypes.c_int32, ctypes.c_double, _d], ctypes.c_int),
             "cf_get_mesh": ([vp, ctypes.c_int32, _i, _d, _d], ctypes.c_int),
             "cf_cell_verts": ([vp, ctypes.c_int32], ctypes.c_int32),
             "cf_cell_tets": ([vp, ctypes.c_int32], ctypes.c_int32),
@@ -378,6 +379,14 @@ def cf_get_taylor(ctx, cell_id):
     out = np.zeros(10)
     _check(ctx, lib().cf_get_taylor(ctx.handle, cell_id, _p(out)))
     return dict(zip(TAYLOR_KEYS, out.tolist()))
+
+
+def cf_get_cell_strain(ctx, cell_id, d_ref):
+    """Cell strain (computed on the device): {"d_max": largest vertex-vertex
+    distance, "strain": (d_max - d_ref) / d_ref}."""
+    out = np.zeros(2)
+    _check(ctx, lib().cf_get_cell_strain(ctx.handle, cell_id, float(d_ref), _p(out)))
+    return {"d_max": float(out[0]), "strain": float(out[1])}
 
 
 def cf_get_csr(ctx, cell_id):

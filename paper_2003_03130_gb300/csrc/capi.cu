@@ -1215,6 +1215,24 @@ cf_status cf_get_taylor(cf_ctx *c, int32_t id, double *out) {
     return wait_stream(c);
 }
 
+cf_status cf_get_cell_strain(cf_ctx *c, int32_t id, double d_ref, double *out) {
+    const CellInfo *ci = cell_of(c, id);
+    if (!ci || !out) return fail(c, CF_EINVAL, "unknown cell or null output");
+    if (!(d_ref > 0.0) || !std::isfinite(d_ref)) return fail(c, CF_EINVAL, "d_ref must be positive and finite");
+    DeviceGuard dg(c->device);
+    unsigned *word = reinterpret_cast<unsigned *>(c->d_status);  // device scratch of the context
+    CUDA_TRY(c, launch_max_extent(view(c), c->u[c->cur], ci->v_off, ci->nv, word, c->stream));
+    unsigned bits = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&bits, word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    const cf_status s = wait_stream(c);
+    if (s != CF_OK) return s;
+    float d2;
+    std::memcpy(&d2, &bits, sizeof d2);
+    out[0] = std::sqrt((double)d2);
+    out[1] = (out[0] - d_ref) / d_ref;
+    return CF_OK;
+}
+
 cf_status cf_get_csr(cf_ctx *c, int32_t id, int32_t *ptr, int32_t *idx) {
     const CellInfo *ci = cell_of(c, id);
     if (!ci || !ptr || !idx) return fail(c, CF_EINVAL, "unknown cell or null output");

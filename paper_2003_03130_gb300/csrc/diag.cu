@@ -162,4 +162,53 @@ cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, do
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- cell strain
+// Largest distance between two vertices of a cell (the elongation d_max of
+// the cell strain, Sec. 6.1), by brute force over all pairs. Block b holds
+// vertex tile b and sweeps the tiles b, b+1, ... through shared memory, so
+// every pair meets once; the squared distances are reduced by a maximum,
+// which does not depend on the order, first per block, then across blocks by
+// atomicMax on the bit pattern (non-negative floats order like their bits).
+// Positions enter relative to the cell's integer origin.
+constexpr int kExtentBlock = 256;
+
+__global__ void __launch_bounds__(kExtentBlock) k_max_extent(MeshView m, const float4 *__restrict__ u, int v0,
+                                                             int nv, unsigned *out) {
+    __shared__ float3 tile[kExtentBlock];
+    __shared__ float red[kExtentBlock];
+    const int i = blockIdx.x * kExtentBlock + threadIdx.x;
+    const bool live = i < nv;
+    // a padding slot takes the cell's first vertex: its distances are real pairs
+    auto pos = [&](int k) {
+        const float4 xr = __ldg(m.xr + v0 + k), du = __ldg(u + v0 + k);
+        return make_float3(xr.x + du.x, xr.y + du.y, xr.z + du.z);
+    };
+    const float3 yi = pos(live ? i : 0);
+    float best = 0.f;
+    for (int jt = blockIdx.x; jt * kExtentBlock < nv; ++jt) {
+        const int j = jt * kExtentBlock + threadIdx.x;
+        __syncthreads();
+        tile[threadIdx.x] = pos(j < nv ? j : 0);
+        __syncthreads();
+        for (int k = 0; k < kExtentBlock; ++k) {
+            const float dx = tile[k].x - yi.x, dy = tile[k].y - yi.y, dz = tile[k].z - yi.z;
+            best = fmaxf(best, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+    }
+    red[threadIdx.x] = best;
+    __syncthreads();
+    for (int w = kExtentBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out, __float_as_uint(red[0]));
+}
+
+cudaError_t launch_max_extent(const MeshView &m, const float4 *u, int v0, int nv, unsigned *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess || nv <= 0) return e;
+    k_max_extent<<<(nv + kExtentBlock - 1) / kExtentBlock, kExtentBlock, 0, s>>>(m, u, v0, nv, out);
+    return cudaGetLastError();
+}
+
 }  // namespace cf

@@ -276,6 +276,9 @@ cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, do
 // K8: Taylor deformation of tets [t0, t1) at displacements u; out[10] (device)
 // = D, D from the printed squared expression, inclination (deg), a1, a2, a3,
 // theta1, theta2, theta3, volume. partial: 10 doubles per 256 tets.
+// Squared largest distance between two of the vertices [v0, v0 + nv) at
+// displacements u, as the bits of a float in *out (device).
+cudaError_t launch_max_extent(const MeshView &m, const float4 *u, int v0, int nv, unsigned *out, cudaStream_t s);
 cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the

@@ -376,6 +376,34 @@ def test_device_taylor_matches_oracle(P, stretch, angle):
         assert abs(got["inclination"] - ref["inclination"]) <= 1e-4
 
 
+def test_device_cell_strain_matches_oracle(P):
+    """cf_get_cell_strain (all vertex pairs on the device) against the
+    oracle's brute force on the same positions, for two cells of one context
+    stretched differently (several vertex tiles and a ragged last one)."""
+    from paper_2003_03130_gb300 import CellFSIError
+    from oracle import analysis
+
+    cell = configs.small_shear().cells[0]
+    R = 8.0
+    c = cell.x_ref.mean(0)
+    ctx = P.cf_create(0)
+    ids = []
+    for k, stretch in enumerate(((1.0, 1.0, 1.0), (1.6, 0.8, 0.9))):
+        shift = np.array([0.0, 0.0, 30.0 * k])
+        y = c + shift + (cell.x_ref - c) * np.asarray(stretch)
+        ids.append(P.cf_mesh_init(ctx, cell.x_ref + shift, cell.tets, y))
+    assert len(cell.x_ref) % 256 and len(cell.x_ref) > 512
+    for cid in ids:
+        got = P.cf_get_cell_strain(ctx, cid, 2 * R)
+        eps = analysis.cell_strain(P.cf_get_positions(ctx, cid), R)
+        assert abs(got["d_max"] - (eps + 1) * 2 * R) <= 1e-6 * 2 * R
+        assert abs(got["strain"] - eps) <= 1e-6
+    with pytest.raises(CellFSIError) as e:
+        P.cf_get_cell_strain(ctx, ids[0], 0.0)
+    assert e.value.name == "CF_EINVAL"
+    P.cf_destroy(ctx)
+
+
 # ---------------------------------------------------------------- batches
 
 def test_batch_init_matches_single_inits_and_oracle(P):

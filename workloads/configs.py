@@ -115,7 +115,7 @@ def paper_box_shear(ca: float = 0.2, w: float = 0.5, steps: int = 10000) -> Work
 
 def multicell_shear(ncells: int = 8, R: float = 16.0, h: float = 1.72, ca: float = 0.2, w: float = 0.5,
                     u_wall: float = 0.05, seed: int = 55, steps: int = 10000) -> Workload:
-    """The paper's multiple-cell setup (Sec. 6.3): ncells cells of radius R
+    """The paper's multiple-cell setup (Sec. 6.2): ncells cells of radius R
     at seeded random positions (no overlap, gap >= 2 lattice units, at least
     R + 2 from the walls, periodic in x and z) in a 5 x 8 x 4 R box with
     moving walls across its 8 R axis; 4 cells fill 11 % of the box, 8 cells
