@@ -1,0 +1,46 @@
+"""CPU tests of the benchmark's roofline arithmetic: the support-node count
+against a direct enumeration, and the byte models of the stream-collide and
+the cell kernels against hand counts."""
+import numpy as np
+
+import bench
+
+
+def test_support_nodes_counts_distinct_nodes():
+    # one point: W^3 nodes; two points one spacing apart in x share W^2 (W - 1)
+    y = np.array([[5.5, 6.25, 7.75]])
+    assert bench.support_nodes(y, (16, 16, 16), 2) == 8
+    assert bench.support_nodes(y, (16, 16, 16), 4) == 64
+    y2 = np.vstack([y, y + [1.0, 0.0, 0.0]])
+    assert bench.support_nodes(y2, (16, 16, 16), 2) == 8 + 4
+    assert bench.support_nodes(y2, (16, 16, 16), 4) == 64 + 16
+    # periodic wrap in x and z: a point at the upper seam
+    ys = np.array([[15.5, 3.0, 15.2]])
+    assert bench.support_nodes(ys, (16, 16, 16), 2) == 8
+
+
+def test_support_nodes_against_enumeration():
+    rng = np.random.default_rng(3)
+    dims = (12, 10, 9)
+    y = rng.uniform([0, 2, 0], [12, 7, 9], size=(40, 3))
+    for w in (2, 4):
+        nodes = set()
+        for p in y:
+            b = np.floor(p).astype(int) - (w // 2 - 1)
+            for dz in range(w):
+                for dy in range(w):
+                    for dx in range(w):
+                        nodes.add(((b[0] + dx) % dims[0], b[1] + dy, (b[2] + dz) % dims[2]))
+        assert bench.support_nodes(y, dims, w) == len(nodes)
+
+
+def test_byte_models():
+    # 19 FP32 populations read and written
+    assert bench.POP_BYTES_PER_NODE == 2 * 19 * 4
+    # near field: + float4 force read + float4 velocity store
+    assert bench.NEAR_BYTES_PER_NODE == 152 + 16 + 16
+    # per tet: int4 indices, 3 float4 B rows, 4 float4 corner forces written and read, 4 int32 entries
+    assert bench.CELL_BYTES_PER_TET == 16 + 3 * 16 + 2 * 4 * 16 + 4 * 4
+    # per vertex: xr + u (K1), row bounds, xr + u (K23), vertex force; plus one float4 per support node
+    assert bench.cell_bytes(0, 1, 2) == 32 + 8 + 32 + 16 + 8 * 16
+    assert bench.cell_bytes(10, 3, 4) == 10 * 208 + 3 * (88 + 64 * 16)
