@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle (test infrastructure only).
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package. It shares no code with the CUDA path:
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(its ``cpu_baseline`` and ``--impl reference``) may import this package. It shares no code with the CUDA path:
 the arithmetic lives in ``oracle.c`` (compiled with gcc into
 ``liboracle.so``) and in the plain numpy diagnostics of ``analysis.py``.
 
