@@ -21,6 +21,9 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#ifdef __CUDACC__
+#include <cooperative_groups.h>
+#endif
 
 namespace cf {
 
@@ -213,33 +216,59 @@ __host__ __device__ __forceinline__ TileRange tile_range(int lo, int hi, int n, 
     return r;
 }
 
-// Visit the tiles met by the node box [x0,x1] x [y0,y1] x [z0,z1] (x and z
-// unwrapped, y clamped to the lattice by the caller).
+// The tiles met by the node box [x0,x1] x [y0,y1] x [z0,z1] (x and z
+// unwrapped, y clamped to the lattice by the caller): n of them, the k-th
+// (x fastest) given by tile_of_box.
+struct TileBox {
+    TileRange rx, ry, rz;
+    int n;
+};
+
+__host__ __device__ __forceinline__ TileBox tile_box(const LbmParams &p, int x0, int x1, int y0, int y1, int z0,
+                                                     int z1) {
+    TileBox b;
+    b.rx = tile_range(x0, x1, p.nx, p.tlx, p.ntx, true);
+    b.ry = tile_range(y0, y1, p.ny, p.tly, p.nty, false);
+    b.rz = tile_range(z0, z1, p.nz, p.tlz, p.ntz, true);
+    b.n = b.rx.cnt * b.ry.cnt * b.rz.cnt;
+    return b;
+}
+
+__host__ __device__ __forceinline__ int tile_of_box(const LbmParams &p, const TileBox &b, int k) {
+    const int r = k / b.rx.cnt;
+    int tx = b.rx.t0 + (k - r * b.rx.cnt);
+    tx -= tx >= p.ntx ? p.ntx : 0;
+    int tz = b.rz.t0 + r / b.ry.cnt;
+    tz -= tz >= p.ntz ? p.ntz : 0;
+    return tile_index(p, tx, b.ry.t0 + r % b.ry.cnt, tz);
+}
+
+// Visit the tiles of the box, each once.
 template <class Fn>
 __host__ __device__ __forceinline__ void for_each_tile(const LbmParams &p, int x0, int x1, int y0, int y1, int z0, int z1,
                                               Fn &&fn) {
-    const TileRange rx = tile_range(x0, x1, p.nx, p.tlx, p.ntx, true);
-    const TileRange ry = tile_range(y0, y1, p.ny, p.tly, p.nty, false);
-    const TileRange rz = tile_range(z0, z1, p.nz, p.tlz, p.ntz, true);
-    for (int k = 0; k < rz.cnt; ++k) {
-        int tz = rz.t0 + k;
-        tz -= tz >= p.ntz ? p.ntz : 0;
-        for (int j = 0; j < ry.cnt; ++j)
-            for (int i = 0; i < rx.cnt; ++i) {
-                int tx = rx.t0 + i;
-                tx -= tx >= p.ntx ? p.ntx : 0;
-                fn(tile_index(p, tx, ry.t0 + j, tz));
-            }
-    }
+    const TileBox b = tile_box(p, x0, x1, y0, y1, z0, z1);
+    for (int k = 0; k < b.n; ++k) fn(tile_of_box(p, b, k));
 }
 
+#ifdef __CUDACC__
 // Add the tiles of the force region around one vertex: its support grown by
-// one node per side (y clamped to the lattice).
+// one node per side (y clamped to the lattice). Neighbouring vertices mostly
+// meet the same tiles, so the lanes of a warp that hold the same tile at the
+// same step elect one of them to add it: a region slot has few words, and
+// one atomic per warp and tile, instead of one per lane, keeps them from
+// serialising.
 template <int W>
 __device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, const RegionSlot &r) {
-    for_each_tile(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W,
-                  [&](int t) { region_add(r, t); });
+    namespace cg = cooperative_groups;
+    const TileBox b = tile_box(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W);
+    for (int k = 0; k < b.n; ++k) {
+        const int t = tile_of_box(p, b, k);
+        const cg::coalesced_group same = cg::labeled_partition(cg::coalesced_threads(), t);
+        if (same.thread_rank() == 0) region_add(r, t);
+    }
 }
+#endif
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch status.
