@@ -6,11 +6,12 @@
 
 namespace cf {
 
-// Blocks past tet_blocks: one thread per vertex, marking the next step's
-// force region.
+// The first mark_blocks blocks: one thread per vertex, marking the next
+// step's force region. They come first so that their short, latency-bound
+// work runs under the tets' rather than after it.
 __device__ __forceinline__ void mark_block(const MeshView &m, const float4 *__restrict__ u, const LbmParams &lp,
-                                           int tet_blocks, const RegionSlot &mark) {
-    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+                                           const RegionSlot &mark) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= m.V) return;
     if (lp.dw == 4)
         mark_vertex<4>(m, u, lp, v, mark);
@@ -23,12 +24,12 @@ __device__ __forceinline__ void mark_block(const MeshView &m, const float4 *__re
 // (tet forces of the 400-cell suspension 190.6 -> 178.5 us against 56
 // registers and four blocks).
 __global__ void __launch_bounds__(256, 6) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
-                                                   int tet_blocks, LbmParams lp, RegionSlot mark) {
-    if ((int)blockIdx.x >= tet_blocks) {
-        mark_block(m, u, lp, tet_blocks, mark);
+                                                   int mark_blocks, LbmParams lp, RegionSlot mark) {
+    if ((int)blockIdx.x < mark_blocks) {
+        mark_block(m, u, lp, mark);
         return;
     }
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (blockIdx.x - mark_blocks) * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
 
     tet_corner_forces(m, u, err, t);
@@ -38,12 +39,12 @@ __global__ void __launch_bounds__(256, 6) k_tet_force(MeshView m, const float4 *
 // loads are issued before either is computed, doubling the bytes a thread
 // has in flight in this latency-bound kernel.
 __global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 *__restrict__ u, unsigned *err,
-                                                     int tet_blocks, LbmParams lp, RegionSlot mark) {
-    if ((int)blockIdx.x >= tet_blocks) {
-        mark_block(m, u, lp, tet_blocks, mark);
+                                                     int mark_blocks, LbmParams lp, RegionSlot mark) {
+    if ((int)blockIdx.x < mark_blocks) {
+        mark_block(m, u, lp, mark);
         return;
     }
-    const int t0 = 2 * blockIdx.x * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
+    const int t0 = 2 * (blockIdx.x - mark_blocks) * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
     if (t0 >= m.T) return;
     TetIn a, b;
     tet_load(m, u, t0, a);
@@ -62,9 +63,9 @@ cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, 
     const LbmParams p = lp ? *lp : LbmParams{};
     const RegionSlot mark = cb ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
     if (pairs)
-        k_tet_force2<<<tb + cb, bs, 0, s>>>(m, u, err, tb, p, mark);
+        k_tet_force2<<<tb + cb, bs, 0, s>>>(m, u, err, cb, p, mark);
     else
-        k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, tb, p, mark);
+        k_tet_force<<<tb + cb, bs, 0, s>>>(m, u, err, cb, p, mark);
     return cudaGetLastError();
 }
 
