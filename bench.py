@@ -91,7 +91,7 @@ def parse():
                     help="population storage (the collide is FP32 in every format)")
     ap.add_argument("--tile", default="", help="force-region tile x,y,z (e.g. 32,2,4); default: autotuner's")
     ap.add_argument("--shape", default="", help="launch-shape knobs set after the autotuner, e.g. far_blocks=4")
-    ap.add_argument("--autotune-steps", type=int, default=20,
+    ap.add_argument("--autotune-steps", type=int, default=40,
                     help="steps per launch-shape candidate of the autotuner in the warm-up (0: default shape)")
     ap.add_argument("--ca", type=float, default=0.2)
     ap.add_argument("--w", type=float, default=0.5)
@@ -458,7 +458,9 @@ def run_ours(args):
     tag = (f"{wl.nx}cubed" if wl.nx == wl.ny == wl.nz else f"{wl.nx}x{wl.ny}x{wl.nz}") + (
         f"_{len(wl.cells)}cells" if args.workload == "suspension" else "")
     tag = ("suspension_" if args.workload == "suspension" else "") + tag
-    traffic = traffic_record(dom, tag) if wl.delta == 2 and args.pop_format == "f32" else None
+    # the ncu record of the same kernel form: the L2-normal form of the FP32 populations has its own
+    traffic = (traffic_record(dom, tag + ("_l2" if shape.get("pop_l2") else ""))
+               if wl.delta == 2 and args.pop_format == "f32" else None)
     step_ms_profiled = float(sum(kms))
     out = {
         "metric": METRIC,

@@ -215,23 +215,29 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *          resolves (saves a round trip per far node, wastes the loads of
  *          region nodes); 0 (default): region nodes return first;
  *   [9]    1: the force kernel computes two tets per thread, both tets'
- *          loads in flight before either is computed; 0 (default): one.
+ *          loads in flight before either is computed; 0 (default): one;
+ *   [10]   1: with FP32 populations the far and near fields cache them in
+ *          L2 at normal priority (for lattices whose stream-collide gains
+ *          more from L2 reuse than the cell kernels lose); 0 (default):
+ *          populations are streamed with evict-first hints, so that the
+ *          cells' data stays in L2.
  * Block sizes are multiples of 32 in [32, 256].
  * No shape changes a computed value beyond the rounding order of the spread
  * (float atomics). cf_set_launch_shape applies from the next cf_step call;
  * CF_EINVAL for a value outside these sets. */
-#define CF_SHAPE_LEN 10
+#define CF_SHAPE_LEN 11
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
 /* Autotuner: picks the launch shape by timing coupled steps on the
  * context's own state. One knob at a time (tile shape, fused or separate
  * cell chain, near-field form, far-field load order, tets per thread,
- * tet-force, spread and interpolation block sizes), every candidate runs
+ * tet-force, spread and interpolation block sizes, caching of FP32
+ * populations), every candidate runs
  * steps_per_candidate (>= 1) coupled steps exactly as cf_step runs them
  * (the same step graphs, far field and cell chain overlapping), timed as a
  * whole with CUDA events, and the fastest candidate is kept. The simulation
- * advances by those steps exactly as under cf_step (21 candidates in all). A fluid-only context has nothing to
+ * advances by those steps exactly as under cf_step (23 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

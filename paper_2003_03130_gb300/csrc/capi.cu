@@ -461,6 +461,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
         tmax = std::max(tmax, tiles_of(p));
     }
     set_tiles(p, c->shape.tile);
+    p.l2 = c->shape.pop_l2;
     c->region_bits_max = (tmax + 31) / 32;
     c->region_stride = (32 + c->region_bits_max + tmax + 31) / 32 * 32;
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
@@ -975,6 +976,7 @@ cf_status region_nodes(cf_ctx *c, long long *out) {
 cf_status timed_call(cf_ctx *c, int n, const Shape &sh, double *ms) {
     c->shape = sh;
     set_tiles(c->lp, sh.tile);
+    c->lp.l2 = sh.pop_l2;
     drop_graphs(c);
     cf_status st = schedule_steps(c, n, false);
     if (st != CF_OK) return st;
@@ -1033,6 +1035,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[7] = sh.near_rows;
     shape[8] = sh.far_spec;
     shape[9] = sh.tet_pairs;
+    shape[10] = sh.pop_l2;
     return CF_OK;
 }
 
@@ -1062,10 +1065,15 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.far_spec = shape[8];
     if (shape[9] != 0 && shape[9] != 1) return fail(c, CF_EINVAL, "tet_pairs must be 0 or 1");
     sh.tet_pairs = shape[9];
+    if (shape[10] != 0 && shape[10] != 1) return fail(c, CF_EINVAL, "pop_l2 must be 0 or 1");
+    sh.pop_l2 = shape[10];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
-    if (c->lbm_ready) set_tiles(c->lp, sh.tile);
+    if (c->lbm_ready) {
+        set_tiles(c->lp, sh.tile);
+        c->lp.l2 = sh.pop_l2;
+    }
     return CF_OK;
 }
 
@@ -1089,6 +1097,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::near_rows, {0, 1}},
             {&Shape::far_spec, {0, 1}},
             {&Shape::tet_pairs, {0, 1}},
+            {&Shape::pop_l2, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}},
             {&Shape::gather_block, {64, 128, 256}},
             {&Shape::interp_block, {64, 128, 256}},
@@ -1106,6 +1115,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
                 if (st != CF_OK) {
                     c->shape = start;
                     set_tiles(c->lp, start.tile);
+                    c->lp.l2 = start.pop_l2;
                     drop_graphs(c);
                     return st;
                 }
@@ -1118,6 +1128,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
         }
         c->shape = best;
         set_tiles(c->lp, best.tile);
+        c->lp.l2 = best.pop_l2;
         drop_graphs(c);
     }
     return shape_out ? cf_get_launch_shape(c, shape_out) : CF_OK;

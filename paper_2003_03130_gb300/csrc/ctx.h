@@ -40,6 +40,7 @@ struct Shape {
     int near_rows = 0;  // near field in rows over the whole lattice instead of over the region's tile list
     int far_spec = 0;   // far field issues its loads before the region test resolves
     int tet_pairs = 0;  // two tets per thread in the force kernel
+    int pop_l2 = 0;     // FP32 far and near fields cache populations in L2 instead of streaming them
 };
 
 }  // namespace cf

@@ -73,6 +73,8 @@ struct LbmParams {
     float uw_lo, uw_hi; // wall x velocities at y = -1/2 and y = ny - 1/2
     float gx, gy, gz;   // uniform body-force density
     int dw;             // delta kernel: support width 2 (trilinear) or 4 (Peskin)
+    int l2;             // FP32 far and near fields: populations cached in L2 at normal priority
+                        // (1) instead of streamed with evict-first hints (0)
     // force-region tiles of 2^tlx x 2^tly x 2^tlz = 256 nodes (x fastest;
     // the last tile of an axis may stick out of the lattice), ntx * nty * ntz
     // of them

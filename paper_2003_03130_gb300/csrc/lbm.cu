@@ -30,6 +30,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace cf {
@@ -45,19 +47,38 @@ namespace cf {
 template <class T>
 struct Pop;
 
+// FP32 also comes in an L2-normal form (CS false: loads and stores cached in
+// L2 with normal priority, not in L1), which keeps more of a large lattice's
+// populations in L2 between the far and near fields; the streaming form
+// protects the cell data instead. The launch shape picks one.
 template <>
 struct Pop<float> {
     static constexpr int kDropped = 0;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
-    static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
-    static __device__ __forceinline__ void st_sr(float *p, float v, unsigned) { __stcs(p, v); }
+    template <bool CS = true>
+    static __device__ __forceinline__ float ld(const float *p) {
+        return CS ? __ldcs(p) : __ldcg(p);
+    }
+    template <bool CS = true>
+    static __device__ __forceinline__ void st(float *p, float v) {
+        if (CS)
+            __stcs(p, v);
+        else
+            __stcg(p, v);
+    }
+    template <bool CS = true>
+    static __device__ __forceinline__ void st_sr(float *p, float v, unsigned) {
+        st<CS>(p, v);
+    }
 };
 
 template <>
 struct Pop<__half> {
     static constexpr int kDropped = 13;
+    template <bool CS = true>
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
+    template <bool CS = true>
     static __device__ __forceinline__ void st(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
+    template <bool CS = true>
     static __device__ __forceinline__ void st_sr(__half *p, float v, unsigned dither) {
         __stcs(p, __float2half_rz(__uint_as_float(__float_as_uint(v) + dither)));
     }
@@ -66,8 +87,11 @@ struct Pop<__half> {
 template <>
 struct Pop<__nv_bfloat16> {
     static constexpr int kDropped = 16;
+    template <bool CS = true>
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
+    template <bool CS = true>
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
+    template <bool CS = true>
     static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned dither) {
         __stcs(p, __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + dither)));
     }
@@ -214,7 +238,7 @@ __device__ __forceinline__ bool wall_pull(int y, int ny) {
 // ---------------------------------------------------------------- one node
 // store = false: load and collide but write nothing (a node found, after its
 // loads were issued, to belong to the other part of the split).
-template <class T, bool WALL, bool HAS_F>
+template <class T, bool WALL, bool HAS_F, bool CS = true>
 __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restrict__ fout,
                                          float4 *__restrict__ F, const LbmParams &p, int x, int y, int z,
                                          float4 *__restrict__ vel, unsigned seed, bool store = true) {
@@ -232,10 +256,10 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
         const int sy = y - cy(q);
         if (WALL && ((cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1))) {
             const float uw = cy(q) == 1 ? p.uw_lo : p.uw_hi;
-            d[q] = Pop<T>::ld(fin + opp(q) * N + n);
+            d[q] = Pop<T>::template ld<CS>(fin + opp(q) * N + n);
             if (cx(q) != 0) d[q] += (6.f * wq(q) * cx(q) * pop_scale<T>(q)) * uw;
         } else {
-            d[q] = Pop<T>::ld(fin + q * N + sx + nx * (sy + ny * sz));
+            d[q] = Pop<T>::template ld<CS>(fin + q * N + sx + nx * (sy + ny * sz));
         }
     }
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
@@ -261,13 +285,13 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
 #pragma unroll
             for (int q = 0; q < 19; ++q) {
                 const unsigned r = (h + (unsigned)q * 0x9e3779b9u) >> (32 - Pop<T>::kDropped);
-                Pop<T>::st_sr(fout + q * N + n, d[q], r & mask);
+                Pop<T>::template st_sr<CS>(fout + q * N + n, d[q], r & mask);
             }
             return;
         }
     }
 #pragma unroll
-    for (int q = 0; q < 19; ++q) Pop<T>::st(fout + q * N + n, d[q]);
+    for (int q = 0; q < 19; ++q) Pop<T>::template st<CS>(fout + q * N + n, d[q]);
 }
 
 // ---------------------------------------------------------------- kernels
@@ -305,7 +329,7 @@ constexpr int kTileBlock = kTileNodes / 2;
 // SPEC: the region test resolves while the populations load (a region
 // node's loads are wasted, a far node saves a round trip before its loads);
 // otherwise a region node returns before loading.
-template <class T, bool SPEC>
+template <class T, bool SPEC, bool CS = true>
 __global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
                                                  const unsigned *__restrict__ bits,
                                                  const unsigned *__restrict__ seed_in) {
@@ -316,16 +340,16 @@ __global__ void __launch_bounds__(128) k_lbm_far(const T *__restrict__ fin, T *_
     if (!SPEC && region) return;
     const unsigned seed = *seed_in;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<T, false, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed, !region);
+        lbm_node<T, false, false, CS>(fin, fout, nullptr, p, x, y, z, nullptr, seed, !region);
     else
-        lbm_node<T, true, false>(fin, fout, nullptr, p, x, y, z, nullptr, seed, !region);
+        lbm_node<T, true, false, CS>(fin, fout, nullptr, p, x, y, z, nullptr, seed, !region);
 }
 
 // The force region's nodes in rows of 128 along x over the whole lattice (the
 // far field's layout: y and z uniform over a block); threads outside the
 // region return at once. Cheaper per node than the list form when the region
 // is a large part of the lattice.
-template <class T>
+template <class T, bool CS = true>
 __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin, T *__restrict__ fout,
                                                        float4 *__restrict__ F, LbmParams p,
                                                        const unsigned *__restrict__ bits, float4 *__restrict__ vel,
@@ -338,15 +362,15 @@ __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin
     const int y = blockIdx.y, z = blockIdx.z;
     if (!region_has(bits, tile_index(p, x >> p.tlx, y >> p.tly, z >> p.tlz))) return;
     if (y > 0 && y < p.ny - 1)
-        lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel, seed);
+        lbm_node<T, false, true, CS>(fin, fout, F, p, x, y, z, vel, seed);
     else
-        lbm_node<T, true, true>(fin, fout, F, p, x, y, z, vel, seed);
+        lbm_node<T, true, true, CS>(fin, fout, F, p, x, y, z, vel, seed);
 }
 
 // The force region's tiles from its list, with the force field; also stores
 // u(t) there. The grid is fixed when a step is captured while the region
 // moves with the cells, so blocks stride over the list's half tiles.
-template <class T>
+template <class T, bool CS = true>
 __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
                                                             float4 *__restrict__ F, LbmParams p,
                                                             const int *__restrict__ count,
@@ -364,9 +388,9 @@ __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict_
         int x, y, z;
         if (!tile_node(p, tx, r % p.nty, r / p.nty, (w & 1) * kTileBlock + threadIdx.x, x, y, z)) continue;
         if (y > 0 && y < p.ny - 1)
-            lbm_node<T, false, true>(fin, fout, F, p, x, y, z, vel, seed);
+            lbm_node<T, false, true, CS>(fin, fout, F, p, x, y, z, vel, seed);
         else
-            lbm_node<T, true, true>(fin, fout, F, p, x, y, z, vel, seed);
+            lbm_node<T, true, true, CS>(fin, fout, F, p, x, y, z, vel, seed);
     }
 }
 
@@ -430,6 +454,17 @@ static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const 
                          bool spec, cudaStream_t s) {
     const int bx = p.nx < 128 ? p.nx : 128;
     dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+    if constexpr (std::is_same<T, float>::value) {
+        if (p.l2) {  // L2-normal form (FP32 only)
+            if (spec)
+                k_lbm_far<T, true, false><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p,
+                                                              bits, seed);
+            else
+                k_lbm_far<T, false, false><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p,
+                                                               bits, seed);
+            return cudaGetLastError();
+        }
+    }
     if (spec)
         k_lbm_far<T, true><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, bits, seed);
     else
@@ -441,6 +476,21 @@ template <class T>
 static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
                           const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
                           unsigned *next_seed, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (p.l2) {  // L2-normal form (FP32 only)
+            if (blocks <= 0) {
+                const int bx = p.nx < 128 ? p.nx : 128;
+                dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+                k_lbm_near_rows<T, false><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p,
+                                                              bits, vel, seed, next_seed);
+            } else {
+                k_lbm_near<T, false><<<blocks, kTileBlock, 0, s>>>(static_cast<const T *>(fin),
+                                                                   static_cast<T *>(fout), F, p, count, tiles, vel,
+                                                                   seed, next_seed);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (blocks <= 0) {  // rows over the whole lattice
         const int bx = p.nx < 128 ? p.nx : 128;
         dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
@@ -454,7 +504,8 @@ static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParam
 }
 
 bool is_lbm_far_kernel(const void *fn) {
-    return fn == (const void *)k_lbm_far<float, false> || fn == (const void *)k_lbm_far<__half, false> ||
+    return fn == (const void *)k_lbm_far<float, false, false> || fn == (const void *)k_lbm_far<float, true, false> ||
+           fn == (const void *)k_lbm_far<float, false> || fn == (const void *)k_lbm_far<__half, false> ||
            fn == (const void *)k_lbm_far<__nv_bfloat16, false> || fn == (const void *)k_lbm_far<float, true> ||
            fn == (const void *)k_lbm_far<__half, true> || fn == (const void *)k_lbm_far<__nv_bfloat16, true>;
 }
