@@ -148,8 +148,10 @@ def test_single_node_planes(P):
 
 # ---------------------------------------------------------------- coupled
 
-def _coupled_pair(P, wl, steps):
+def _coupled_pair(P, wl, steps, shape=None):
     ctx = P.cf_create(0)
+    if shape is not None:
+        P.cf_set_launch_shape(ctx, shape)
     ids = P.load_workload(ctx, wl)
     sim = oracle.Coupled(wl)
     P.cf_step(ctx, steps)
@@ -188,6 +190,25 @@ def test_production_shear_full_size(P):
     cell.y0 = perturb(cell.x_ref, 0.08, 20030313)  # min det F = 0.28 (0.16 inverts tets)
     y0 = cell.y0.copy()
     ctx, sim, y, f = _coupled_pair(P, wl, 3)
+    assert rel(y - y0, sim.y - y0) <= TOL
+    assert rel(f, sim.last_forces) <= TOL
+    assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
+
+
+def test_production_shear_full_size_in_the_tuned_shape(P):
+    """The same full-size comparison in the launch shape the benchmark's
+    autotuner picks for this workload (tuned on a context of its own, then
+    set on a fresh one)."""
+    wl = configs.production_shear(ca=0.2, w=0.5)
+    tune = P.cf_create(0)
+    P.load_workload(tune, wl)
+    shape = P.cf_autotune(tune, 20)
+    P.cf_destroy(tune)
+    cell = wl.cells[0]
+    cell.y0 = perturb(cell.x_ref, 0.08, 20030313)
+    y0 = cell.y0.copy()
+    ctx, sim, y, f = _coupled_pair(P, wl, 3, shape)
+    assert P.cf_get_launch_shape(ctx) == shape
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
