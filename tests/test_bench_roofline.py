@@ -44,3 +44,12 @@ def test_byte_models():
     # per vertex: xr + u (K1), row bounds, xr + u (K23), vertex force; plus one float4 per support node
     assert bench.cell_bytes(0, 1, 2) == 32 + 8 + 32 + 16 + 8 * 16
     assert bench.cell_bytes(10, 3, 4) == 10 * 208 + 3 * (88 + 64 * 16)
+
+
+def test_host_replicas_are_capped_by_cores_and_memory():
+    import os
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    assert 1 <= bench._host_replicas(32**3) <= cores
+    # a lattice whose oracle would not fit twice into any host's memory: one replica
+    assert bench._host_replicas(10**13) == 1
