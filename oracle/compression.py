@@ -5,12 +5,19 @@ repulsive force that keeps vertices out of the plates (Sec. 4.2; the form of
 that force is given only in the supplement). Reading used here: a one-sided
 harmonic penalty per vertex, E_plate = k/2 [(z_lo - z)_+^2 + (z - z_hi)_+^2],
 so f_plate,z = k (z_lo - z)_+ - k (z - z_hi)_+, and quasi-static relaxation
-by damped (gradient-flow) steps y <- y + dt (f_el(y) + f_plate(y)). The
-measured force is the top plate's, F = sum_v k (z_v - z_hi)_+.
+of unit-mass vertices by damped second-order steps
+    v <- c v + dt (f_el(y) + f_plate(y)),   y <- y + dt v,
+where the force is taken at the positions before the step and the position
+update uses the new velocity (c = 0 is the gradient flow
+y <- y + dt^2 (f_el + f_plate)). The measured force is the top plate's,
+F = sum_v k (z_v - z_hi)_+. The plate heights of a protocol come from the
+input generator ``workloads.configs.plate_schedule``.
 """
 from __future__ import annotations
 
 import numpy as np
+
+from workloads.configs import plate_schedule
 
 
 def plate_forces(y, k, z_lo, z_hi):
@@ -50,23 +57,6 @@ def relax(mesh, y, n, dt, k, z_lo, z_hi, v=None, c=0.0):
         v = c * v + dt * (mesh.forces(y) + plate_forces(y, k, zl, zh))
         y = y + dt * v
     return y, v
-
-
-def plate_schedule(z_lo, radius, strains, steps, ramp):
-    """Per strain level: the top plate moves from its previous height to
-    z_lo + 2 R (1 - s) in ``ramp`` equal moves of ``steps // (2 ramp)`` steps
-    each (a quasi-static approach), then holds for the remaining steps. Yields
-    (z_hi per cell, number of steps, measured) with measured True at the end
-    of a level; ramp = 0 jumps to the new height."""
-    z_lo, radius = np.asarray(z_lo, np.float64), np.asarray(radius, np.float64)
-    prev = z_lo + 2.0 * radius
-    for s in strains:
-        new = z_lo + 2.0 * radius * (1.0 - s)
-        n_move = steps // (2 * ramp) if ramp > 0 else 0
-        for r in range(1, ramp + 1):
-            yield prev + (new - prev) * (r / ramp), n_move, False
-        yield new, steps - ramp * n_move, True
-        prev = new
 
 
 def protocol(mesh, y0, z_lo, radius, strains, steps, dt, k, ramp=0, c=0.0):

@@ -13,24 +13,10 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+from workloads.configs import plate_schedule
+
 from . import (CF_ALL_CELLS, cf_adjoint_gradients, cf_plate_force, cf_plates_set, cf_relax, cf_relax_adjoint,
                cf_set_materials, cf_set_positions, cf_tape_clear)
-
-
-def plate_schedule(z_lo, radius, strains, steps, ramp):
-    """Per strain level: the top plate moves from its previous height to
-    z_lo + 2 R (1 - s) in ``ramp`` equal moves of ``steps // (2 ramp)`` steps
-    each (a quasi-static approach), then holds for the remaining steps. Yields
-    (z_hi per cell, number of steps, measured) with measured True at the end
-    of a level; ramp = 0 jumps to the new height."""
-    prev = z_lo + 2.0 * radius
-    for s in strains:
-        new = z_lo + 2.0 * radius * (1.0 - s)
-        n_move = steps // (2 * ramp) if ramp > 0 else 0
-        for r in range(1, ramp + 1):
-            yield prev + (new - prev) * (r / ramp), n_move, False
-        yield new, steps - ramp * n_move, True
-        prev = new
 
 
 class Compression:

@@ -244,6 +244,27 @@ def compression_set(ncells: int = 64, R: float = 10.0, h: float = 1.45, steps: i
     return CompressionSet(cells, mu, kappa, w, [0.1 * (i + 1) for i in range(8)], steps, 0.03, 0.95, 50.0, 10)
 
 
+def plate_schedule(z_lo, radius, strains, steps, ramp):
+    """Top-plate heights of a quasi-static compression protocol (Sec. 4.2:
+    the upper plate approaches step by step while the cell relaxes). Per
+    strain level s the plate moves from its previous height to
+    ``z_lo + 2 R (1 - s)`` in ``ramp`` equal moves of ``steps // (2 ramp)``
+    relaxation steps each, then holds for the rest of the level's ``steps``.
+    Yields ``(z_hi per cell, number of steps, measured)`` with ``measured``
+    True for the hold that ends a level; ``ramp = 0`` jumps to the new height
+    at once. The plate starts at ``z_lo + 2 R`` (touching an undeformed
+    sphere of radius R resting on the lower plate)."""
+    z_lo, radius = np.asarray(z_lo, np.float64), np.asarray(radius, np.float64)
+    prev = z_lo + 2.0 * radius
+    for s in strains:
+        new = z_lo + 2.0 * radius * (1.0 - s)
+        n_move = steps // (2 * ramp) if ramp > 0 else 0
+        for r in range(1, ramp + 1):
+            yield prev + (new - prev) * (r / ramp), n_move, False
+        yield new, steps - ramp * n_move, True
+        prev = new
+
+
 def random_displacements(cell: Cell, amplitude: float, seed: int) -> np.ndarray:
     """Positions of ``cell`` perturbed by ``amplitude * U(-1, 1)``."""
     return perturb(cell.x_ref, amplitude, seed)
