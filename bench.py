@@ -101,6 +101,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision-steps", type=int, default=12500,
                     help="steps of the storage-format comparison on the channel workload (0 = skip)")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of K steps each; value = K / median region time")
+    ap.add_argument("--suspension-steps", type=int, default=300,
+                    help="with the default shear workload: also time the 400-cell suspension "
+                         "(512 x 256 x 256) for this many steps per region (0 = skip)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="shear workload: run the 9 (Ca, w) cases of the production shear for "
+                         "--sweep-steps steps each and print the Taylor deformation, inclination and "
+                         "cell strain every 100 steps")
+    ap.add_argument("--sweep-steps", type=int, default=10000,
+                    help="steps per (Ca, w) case of the production-shear sweep (0 = skip it in the "
+                         "default run, which reports every 1,000th step)")
     return ap.parse_args()
 
 
@@ -354,6 +366,126 @@ def precision_block(P, torch, dev, steps):
     return out
 
 
+def timed_regions(P, torch, ctx, stream, dev, K, repeats, world, barrier):
+    """`repeats` timed regions of exactly K coupled steps, each bracketed by a
+    barrier and a device synchronisation, timed with CUDA events on the
+    launching stream; per region the slowest rank's time (ms)."""
+    out = []
+    for _ in range(max(1, repeats)):
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        P.cf_step_async(ctx, K)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        P.cf_synchronize(ctx)
+        ms = ev0.elapsed_time(ev1)
+        barrier()
+        out.append(max_over_ranks(ms, world, device=f"cuda:{dev}"))
+    return out
+
+
+def region_stats(ms, K):
+    return {"n": len(ms), "steps_per_region": K, "ms_per_step_median": statistics.median(ms) / K,
+            "ms_per_step_min": min(ms) / K, "ms_per_step_max": max(ms) / K}
+
+
+def stream_collide_roofline(wl, kms, near_nodes, y_now, pop_format, peak):
+    """The stream-collide part with the longer mean launch time (far field:
+    every node outside the force region, populations only; near field: the
+    region's nodes with the force read and u(t) written, plus the zeroing of
+    the consumed force on the spread's support): its algorithmic bytes over
+    its CUDA-event launch time."""
+    far_nodes = wl.n_nodes - near_nodes
+    pop_b = POP_BYTES_PER_NODE // (1 if pop_format == "f32" else 2)  # 2-byte storage halves it
+    n_sup = support_nodes(y_now, (wl.nx, wl.ny, wl.nz), wl.delta)
+    if kms[2] >= kms[3]:
+        dom, units, per_unit, dom_ms = "k_lbm_far", far_nodes, pop_b, kms[2]
+        alg_bytes = per_unit * units
+    else:
+        near_b = pop_b + NEAR_BYTES_PER_NODE - POP_BYTES_PER_NODE
+        dom, units, per_unit, dom_ms = "k_lbm_near", near_nodes, near_b, kms[3]
+        alg_bytes = per_unit * units + CONSUME_BYTES_PER_SUPPORT_NODE * n_sup
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "algorithmic_bytes_per_launch": alg_bytes, "units_per_launch": units,
+            "bytes_per_unit": per_unit, "near_region_nodes": near_nodes, "support_nodes": n_sup}
+
+
+def suspension_block(P, torch, dev, steps, peak):
+    """The 400-cell suspension (512 x 256 x 256 channel, 1.26 M vertices,
+    6.0 M tets, FP32): steps/s over three timed regions after the
+    autotuner, MLUPS, tet forces/s, the stream-collide roofline and the cell
+    kernels' roofline. GPU only (the oracle takes ~18 s per step here)."""
+    from workloads import configs
+
+    wl = configs.batched_channel()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ctx = P.cf_create(dev, stream.cuda_stream)
+        P.load_workload(ctx, wl)
+        P.cf_step(ctx, 10)
+        shape = P.cf_autotune(ctx, 20)
+        P.cf_prepare_steps(ctx, steps)
+        clocks = ClockSampler(dev)
+        clocks.start()
+        time.sleep(0.3)
+        ms = timed_regions(P, torch, ctx, stream, dev, steps, 3, 1, lambda: None)
+        clk = clocks.stop()
+        kms, near_nodes = P.cf_step_profiled(ctx, 50)
+        y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
+        P.cf_destroy(ctx)
+    med = statistics.median(ms) / 1e3
+    return {"workload": wl.name, "lattice": [wl.nx, wl.ny, wl.nz], "n_cells": len(wl.cells),
+            "n_verts": wl.n_verts, "n_tets": wl.n_tets, "steps_per_s": steps / med,
+            "mlups": wl.n_nodes * steps / med / 1e6, "tet_forces_per_s": wl.n_tets * steps / med,
+            "regions": region_stats(ms, steps), "launch_shape": shape,
+            "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
+            "roofline": stream_collide_roofline(wl, kms, near_nodes, y_now, "f32", peak),
+            "cell_roofline": cell_roofline(wl, kms, peak), "clocks": clk}
+
+
+SWEEP_CA = (0.05, 0.2, 0.5)
+SWEEP_W = (0.0, 0.5, 1.0)
+
+
+def shear_sweep(P, torch, dev, steps, every):
+    """The production shear (128^3, R = 16, kappa = 50 mu) for every
+    (Ca, w) in {0.05, 0.2, 0.5} x {0, 0.5, 1}: `steps` coupled steps each,
+    with the Taylor deformation D, its printed-expression variant, the
+    inclination and the net cell strain (d_max - 2R) / 2R every `every`
+    steps, and the steps/s of each run."""
+    from workloads import configs
+
+    out = []
+    stream = torch.cuda.Stream(dev)
+    for ca in SWEEP_CA:
+        for w in SWEEP_W:
+            wl = configs.production_shear(ca=ca, w=w)
+            with torch.cuda.stream(stream):
+                ctx = P.cf_create(dev, stream.cuda_stream)
+                (cid,) = P.load_workload(ctx, wl)
+                P.cf_prepare_steps(ctx, every)
+                rows, t_dev = [], 0.0
+                for k in range(0, steps, every):
+                    n = min(every, steps - k)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    P.cf_step_async(ctx, n)
+                    e1.record(stream)
+                    P.cf_synchronize(ctx)
+                    t_dev += e0.elapsed_time(e1)
+                    t = P.cf_get_taylor(ctx, cid)
+                    st = P.cf_get_cell_strain(ctx, cid, 2 * 16.0)
+                    rows.append([k + n, t["D"], t["D_literal"], t["inclination"], st["strain"]])
+                P.cf_destroy(ctx)
+            out.append({"ca": ca, "w": w, "mu": wl.cells[0].mu, "kappa": wl.cells[0].kappa,
+                        "steps_per_s": steps / (t_dev / 1e3),
+                        "columns": ["step", "D", "D_literal", "inclination_deg", "cell_strain"], "rows": rows})
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -393,21 +525,12 @@ def run_ours(args):
             P.cf_set_launch_shape(ctx, {k: int(v) for k, v in (kv.split("=") for kv in args.shape.split(","))})
             shape = P.cf_get_launch_shape(ctx)
         P.cf_prepare_steps(ctx, K)  # graph instantiation stays out of the timed region
-        barrier()
-        torch.cuda.synchronize(dev)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         clocks = ClockSampler(dev)
         clocks.start()
         time.sleep(0.3)
-        ev0.record(stream)
-        P.cf_step_async(ctx, K)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
+        region_ms = timed_regions(P, torch, ctx, stream, dev, K, args.repeats, world, barrier)
         clk = clocks.stop()
-        P.cf_synchronize(ctx)
-        ms = ev0.elapsed_time(ev1)
-        barrier()
-        ms = max_over_ranks(ms, world, device=f"cuda:{dev}")
+        ms = statistics.median(region_ms)
 
         # per-kernel durations: CUDA events around every launch, same stream
         kms, near_nodes = P.cf_step_profiled(ctx, args.profile_steps)
@@ -437,24 +560,14 @@ def run_ours(args):
         P.cf_destroy(ctx)
 
     steps_per_s = job_rate(K, world, ms / 1e3)
-    # dominant kernel: the stream-collide part that takes longer - the far
-    # field (every node outside the force region; populations only) in a
-    # single-cell box, the near field (force read, velocity written) when the
-    # cells spread over the whole lattice
-    far_nodes = wl.n_nodes - near_nodes
-    pop_b = POP_BYTES_PER_NODE // (1 if args.pop_format == "f32" else 2)  # 2-byte storage halves it
-    n_sup = support_nodes(y_now, (wl.nx, wl.ny, wl.nz), wl.delta)
-    if kms[2] >= kms[3]:
-        dom, units, per_unit, dom_ms = "k_lbm_far", far_nodes, pop_b, kms[2]
-        alg_bytes = per_unit * units
-    else:
-        near_b = pop_b + NEAR_BYTES_PER_NODE - POP_BYTES_PER_NODE
-        dom, units, per_unit, dom_ms = "k_lbm_near", near_nodes, near_b, kms[3]
-        alg_bytes = per_unit * units + CONSUME_BYTES_PER_SUPPORT_NODE * n_sup
-    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant kernel: the stream-collide part that takes longer - the far
+    # field in a single-cell box, the near field when the cells spread over
+    # the whole lattice
+    roof = stream_collide_roofline(wl, kms, near_nodes, y_now, args.pop_format, peak)
+    dom = roof["kernel"]
     tag = (f"{wl.nx}cubed" if wl.nx == wl.ny == wl.nz else f"{wl.nx}x{wl.ny}x{wl.nz}") + (
         f"_{len(wl.cells)}cells" if args.workload == "suspension" else "")
     tag = ("suspension_" if args.workload == "suspension" else "") + tag
@@ -483,21 +596,9 @@ def run_ours(args):
         "launch_shape": shape,
         "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
         "kernel_share": dict(zip(KERNELS, [float(x) / step_ms_profiled for x in kms])),
-        "roofline": {
-            "kernel": dom,
-            "bound": "hbm",
-            "achieved": achieved,
-            "peak": peak,
-            "unit": "GB/s",
-            "frac": achieved / peak,
-            "traffic": traffic,
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "units_per_launch": units,
-            "bytes_per_unit": per_unit,
-            "near_region_nodes": near_nodes,
-            "support_nodes": n_sup,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
-        },
+        "roofline": dict(roof, traffic=traffic,
+                         peak_source="MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"),
+        "regions": region_stats(region_ms, K),
         # the tet forces and vertex sums + spread against the same HBM peak (FP32 corner forces
         # through HBM: the deterministic incidence-row gather)
         "cell_roofline": cell_roofline(wl, kms, peak) if wl.n_tets else None,
@@ -516,6 +617,13 @@ def run_ours(args):
     if (rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear"
             and args.pop_format == "f32"):
         out["precision"] = precision_block(P, torch, dev, args.precision_steps)
+    default_shear = args.workload == "shear" and args.pop_format == "f32" and wl.delta == 2 and args.n == 128
+    if rank == 0 and world == 1 and default_shear and args.suspension_steps > 0:
+        out["suspension"] = suspension_block(P, torch, dev, args.suspension_steps, peak)
+    if rank == 0 and world == 1 and default_shear and args.sweep_steps > 0:
+        every = 100 if args.sweep else 1000
+        sweep = shear_sweep(P, torch, dev, args.sweep_steps, every)
+        out["shear_sweep"] = {"steps": args.sweep_steps, "every": every, "cases": sweep}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "shear":
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if world > 1:

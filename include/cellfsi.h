@@ -229,6 +229,19 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
+/* Bounds of the waits in the fused cell chain (launch shape [6] = 1). A
+ * vertex-sum work item waits for the completion count of its cell's tet
+ * items; the wait gives up after max_polls polls (default 2^24, each with a
+ * 64 ns back-off: about a second), and the step then returns CF_ETIMEOUT
+ * instead of hanging. extra_need > 0 raises every cell's required count by
+ * that much, so that no wait can succeed: a host-side way to make the waits
+ * run out and check that the call reports CF_ETIMEOUT and leaves the
+ * context usable (the paper has no counterpart: this exercises the
+ * library's failure detection). Defaults: cf_set_chain_wait(ctx, 1 << 24,
+ * 0). Applies from the next step call. CF_EINVAL for max_polls < 1 or
+ * extra_need < 0. */
+cf_status cf_set_chain_wait(cf_ctx *ctx, int64_t max_polls, int32_t extra_need);
+
 /* Autotuner: picks the launch shape by timing coupled steps on the
  * context's own state. One knob at a time (tile shape, fused or separate
  * cell chain, near-field form, far-field load order, tets per thread,
@@ -337,12 +350,21 @@ cf_status cf_plate_force(cf_ctx *ctx, double *out);
  * (dL/dy, dL/dv and the accumulated parameter gradients). */
 cf_status cf_tape_clear(cf_ctx *ctx);
 
+/* Generation of the context's tape, *out: a counter that grows every time
+ * the tape is emptied (cf_tape_clear, or cells added since the last
+ * relaxation). A caller that records a forward pass and reverses it later
+ * (an autograd function) keeps the generation of its forward and checks it
+ * before the reverse pass: a different value means the tape now holds
+ * another forward. */
+cf_status cf_tape_generation(cf_ctx *ctx, int64_t *out);
+
 /* Reverse the most recent recorded cf_relax call not yet reversed: dF[ncells]
  * is dL/dF for the plate forces at the end of that call. Adds the call's
  * contribution to dL/d(mu, kappa, w) per cell (accumulated in double) and
  * carries dL/dy back to its start (recomputing positions from the
  * checkpoints). Reverse the calls last to first. CF_ESTATE if the tape is
- * empty. */
+ * empty, or if some cell's material differs from the one the recorded call
+ * ran with (the reverse pass would differentiate another forward). */
 cf_status cf_relax_adjoint(cf_ctx *ctx, const double *dF);
 
 /* Accumulated dL/d(mu, kappa, w) per cell, out[ncells][3]. */
@@ -401,11 +423,16 @@ const char *cf_last_error(const cf_ctx *ctx);
  * CF_EINVERTED / CF_ENONFINITE as cf_compute_forces; CF_ECUDA on a runtime
  * error. Indices are not validated here (cf_mesh_init validates them).
  *
- * The first call on each device looks up the static array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. Every call shares the one array: calls that
- * overlap on the GPU (several streams or host threads at once) race and
- * must be serialised by the caller. Each call overwrites the scratch it reads.
+ * The first call on each device (and again the first call after the
+ * device's CUDA context was destroyed and created anew, e.g. by
+ * cudaDeviceReset) looks up the static array's device address
+ * (cudaGetSymbolAddress, with that device current). Every call copies the
+ * material from host memory, reads the error word back and synchronises
+ * the stream, so no call may be made while its stream is being captured
+ * into a CUDA graph. Every call shares the one array: calls that overlap on
+ * the GPU (several streams or host threads at once) race and must be
+ * serialised by the caller. Each call clears the error word and overwrites
+ * the scratch it reads.
  * ------------------------------------------------------------------------ */
 #define CF_STATIC_MAX_TETS 65536
 cf_status cf_vertex_forces_static(int32_t nv, int32_t nt, const int32_t *tets, const float *B, const float *V0,

@@ -61,6 +61,7 @@ def lib():
             "cf_get_launch_shape": ([vp, _i], ctypes.c_int),
             "cf_set_launch_shape": ([vp, _i], ctypes.c_int),
             "cf_autotune": ([vp, ctypes.c_int32, _i], ctypes.c_int),
+            "cf_set_chain_wait": ([vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int),
             "cf_synchronize": ([vp], ctypes.c_int),
             "cf_compute_forces": ([vp], ctypes.c_int),
             "cf_step_profiled": ([vp, ctypes.c_int32, _d, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -81,6 +82,7 @@ def lib():
             "cf_relax": ([vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
             "cf_plate_force": ([vp, _d], ctypes.c_int),
             "cf_tape_clear": ([vp], ctypes.c_int),
+            "cf_tape_generation": ([vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
             "cf_relax_adjoint": ([vp, _d], ctypes.c_int),
             "cf_adjoint_gradients": ([vp, _d], ctypes.c_int),
             "cf_force_jvp": ([vp, _d, _d], ctypes.c_int),
@@ -306,6 +308,12 @@ def cf_autotune(ctx, steps_per_candidate=20):
     return dict(zip(SHAPE_KEYS, (int(v) for v in out)))
 
 
+def cf_set_chain_wait(ctx, max_polls=1 << 24, extra_need=0):
+    """Bounds of the fused cell chain's waits; extra_need > 0 makes every
+    wait unreachable (tests of the CF_ETIMEOUT path)."""
+    _check(ctx, lib().cf_set_chain_wait(ctx.handle, int(max_polls), int(extra_need)))
+
+
 def cf_synchronize(ctx):
     _check(ctx, lib().cf_synchronize(ctx.handle))
 
@@ -440,6 +448,12 @@ def cf_plate_force(ctx):
 
 def cf_tape_clear(ctx):
     _check(ctx, lib().cf_tape_clear(ctx.handle))
+
+
+def cf_tape_generation(ctx):
+    out = ctypes.c_int64(0)
+    _check(ctx, lib().cf_tape_generation(ctx.handle, ctypes.byref(out)))
+    return int(out.value)
 
 
 def cf_relax_adjoint(ctx, dF):

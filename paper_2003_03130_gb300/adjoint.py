@@ -16,7 +16,7 @@ import torch
 from workloads.configs import plate_schedule
 
 from . import (CF_ALL_CELLS, cf_adjoint_gradients, cf_plate_force, cf_plates_set, cf_relax, cf_relax_adjoint,
-               cf_set_materials, cf_set_positions, cf_tape_clear)
+               cf_set_materials, cf_set_positions, cf_tape_clear, cf_tape_generation)
 
 
 class Compression:
@@ -57,15 +57,21 @@ class CompressionCurve(torch.autograd.Function):
     def forward(fctx, mu, kappa, w, run: Compression):
         F = run.run(mu.detach().cpu().numpy(), kappa.detach().cpu().numpy(), w.detach().cpu().numpy(), record=True)
         fctx.run = run
+        # the tape lives in the library's context: remember which recording is this forward's
+        fctx.tape_gen = cf_tape_generation(run.ctx)
+        fctx.measured = list(run.measured)
         return torch.as_tensor(F, dtype=torch.float64)
 
     @staticmethod
     def backward(fctx, dF):
         run = fctx.run
+        if cf_tape_generation(run.ctx) != fctx.tape_gen or run.measured != fctx.measured:
+            raise RuntimeError("the context's tape was cleared or re-recorded after this forward pass "
+                               "(another CompressionCurve forward ran on the same context before this backward)")
         dF = dF.detach().cpu().numpy()
         level = dF.shape[1]
         zero = np.zeros(dF.shape[0])
-        for measured in reversed(run.measured):  # recorded cf_relax calls, last first
+        for measured in reversed(fctx.measured):  # recorded cf_relax calls, last first
             if measured:
                 level -= 1
                 cf_relax_adjoint(run.ctx, np.ascontiguousarray(dF[:, level]))

@@ -106,6 +106,7 @@ cf_status build_chain_items(cf_ctx *c) {
         last_tet[k] = items.size();
     }
     while (next_sum < C) gathers(next_sum++);
+    for (int &n : need) n += c->chain_extra_need;
     dfree(c->chain_items);
     dfree(c->chain_need);
     dfree(c->chain_ctr);
@@ -129,7 +130,7 @@ cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &
         cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
         if (e != cudaSuccess) return e;
         return launch_cell_chain(m, c->u[p], c->F, c->lp, acc, c->d_err, c->chain_items, c->chain_nitems,
-                                 c->chain_need, c->chain_ctr, chain_grid(c), s);
+                                 c->chain_need, c->chain_ctr, chain_grid(c), c->chain_spin_limit, s);
     }
     cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, &c->lp, &acc, sh.tet_pairs);
     if (e != cudaSuccess) return e;
@@ -1075,6 +1076,17 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
         c->lp.l2 = sh.pop_l2;
     }
     return CF_OK;
+}
+
+cf_status cf_set_chain_wait(cf_ctx *c, int64_t max_polls, int32_t extra_need) {
+    if (!c) return CF_EINVAL;
+    DeviceGuard dg(c->device);
+    if (max_polls < 1 || extra_need < 0) return fail(c, CF_EINVAL, "need max_polls >= 1 and extra_need >= 0");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph with the old arguments in flight
+    drop_graphs(c);
+    c->chain_spin_limit = max_polls;
+    c->chain_extra_need = extra_need;
+    return c->cells.empty() ? CF_OK : build_chain_items(c);
 }
 
 cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out) {

@@ -8,7 +8,8 @@
 // item waits for comes before it; the block holding an earlier item is
 // therefore already running and never waits itself, so the waits end even
 // when blocks are not co-resident or other kernels share the GPU. Each wait
-// is still bounded: after kSpinLimit polls it sets ERR_WAIT and the block
+// is still bounded: after spin_limit polls (a launch argument, by default
+// 2^24 with a 64 ns back-off, about a second) it sets ERR_WAIT and the block
 // skips the item. Vertex sums of early cells overlap the tet forces of later
 // ones, and one launch replaces two.
 #include "cell_ops.cuh"
@@ -16,7 +17,6 @@
 namespace cf {
 
 constexpr int kChainBlock = 256;
-constexpr long long kSpinLimit = 1LL << 24;  // with a 64 ns back-off: about a second
 
 __device__ __forceinline__ int load_acquire(const int *p) {
     int v;
@@ -24,8 +24,8 @@ __device__ __forceinline__ int load_acquire(const int *p) {
     return v;
 }
 
-__device__ __forceinline__ bool wait_count(const int *p, int target, unsigned *err) {
-    for (long long i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool wait_count(const int *p, int target, long long spin_limit, unsigned *err) {
+    for (long long i = 0; i < spin_limit; ++i) {
         if (load_acquire(p) >= target) return true;
         __nanosleep(64);
     }
@@ -36,7 +36,8 @@ __device__ __forceinline__ bool wait_count(const int *p, int target, unsigned *e
 template <int W>
 __global__ void __launch_bounds__(kChainBlock, 4)
     k_cell_chain(MeshView m, const float4 *__restrict__ u, float4 *F, LbmParams lp, RegionSlot mark, unsigned *err,
-                 const int4 *__restrict__ items, int nitems, const int *__restrict__ need, int *counters) {
+                 const int4 *__restrict__ items, int nitems, const int *__restrict__ need, int *counters,
+                 long long spin_limit) {
     __shared__ int4 item;
     __shared__ int ready;
     int claim = 0;  // thread 0: the item claimed for the next round (claimed one round ahead)
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(kChainBlock, 4)
             if (x.x >= 0) claim = atomicAdd(counters, 1);  // its latency hides under this item
             int ok = 1;
             if (x.x == 2) {
-                ok = wait_count(counters + 2 + x.y, need[x.y], err);
+                ok = wait_count(counters + 2 + x.y, need[x.y], spin_limit, err);
                 __threadfence();
             }
             item = x;
@@ -77,13 +78,15 @@ __global__ void __launch_bounds__(kChainBlock, 4)
 
 cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
                               const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
-                              int *counters, int blocks, cudaStream_t s) {
+                              int *counters, int blocks, long long spin_limit, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     const int g = blocks < nitems ? blocks : nitems;
     if (lp.dw == 4)
-        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters);
+        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters,
+                                                                spin_limit);
     else
-        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters);
+        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters,
+                                                                spin_limit);
     return cudaGetLastError();
 }
 

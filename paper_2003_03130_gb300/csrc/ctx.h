@@ -94,6 +94,8 @@ struct cf_ctx {
     int4 *chain_items = nullptr;
     int *chain_need = nullptr, *chain_ctr = nullptr;
     int chain_nitems = 0;
+    long long chain_spin_limit = 1LL << 24;  // polls before a wait of the fused chain gives up
+    int chain_extra_need = 0;                // added to every cell's need count (cf_set_chain_wait)
     size_t mat_cap = 0;              // entries allocated in mat
     float4 *mat = nullptr;
     int *csr_ptr = nullptr, *csr_idx = nullptr, *csr_cursor = nullptr;
@@ -114,11 +116,13 @@ struct cf_ctx {
         float dt, c, kp;
         std::vector<float> zlo, zhi;
         int ck0, nck;  // checkpoints ck0 .. ck0 + nck - 1: steps 0, S, 2S, ..., and the end state
+        std::vector<float4> mats;  // the cells' materials the call ran with
     };
     float k_plate = 0.f;
     std::vector<float> zlo_h, zhi_h;   // current plates per cell
     float *zlo = nullptr, *zhi = nullptr;
     std::vector<TapeEntry> tape;
+    long long tape_gen = 0;            // bumped whenever the tape is emptied (cf_tape_clear, new cells)
     std::vector<float4 *> ckpt;        // device checkpoints: positions then velocities, 2 V float4 each
     int ck_used = 0;
     float4 *vel_r = nullptr;           // relaxation velocities [V]

@@ -324,11 +324,12 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
 // items of the cell chain in order: items[i] = (kind, cell, begin, end) with
 // kind 0 = region marking of vertices [begin, end), 1 = corner forces of tets
 // [begin, end) of `cell`, 2 = vertex sums + spread of vertices [begin, end)
-// of `cell`. A kind-2 item waits (bounded) until the need[cell] kind-1 items
-// of its cell are done; counters[2 + ncells] must be zero at launch.
+// of `cell`. A kind-2 item waits until the need[cell] kind-1 items of its
+// cell are done, giving up after spin_limit polls (ERR_WAIT);
+// counters[2 + ncells] must be zero at launch.
 cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
                               const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
-                              int *counters, int blocks, cudaStream_t s);
+                              int *counters, int blocks, long long spin_limit, cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 // Every stream-collide launch reads the step's rounding seed from seed[0];

@@ -9,8 +9,14 @@
 // the library until the process exits.
 //
 // Host code cannot use the name of a __device__ array as a device address,
-// so the first call on each device looks the addresses up with
-// cudaGetSymbolAddress (with that device current) and caches them.
+// so the set-up looks the addresses up with cudaGetSymbolAddress, with the
+// device current, and caches them per device. The cache is keyed on the
+// unique id of the device's current CUDA context (cuCtxGetId, reached
+// through the runtime's driver entry points): if the context is destroyed
+// (cudaDeviceReset) and created again, the module is loaded anew, its arrays
+// may move, and the next call looks them up again. Without that driver
+// entry point every call looks them up.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,6 +37,7 @@ static __device__ __align__(256) unsigned g_err[1];                        // de
 
 struct StaticAddr {
     bool ready = false;
+    unsigned long long ctx_id = 0;  // context the addresses belong to
     float4 *corner = nullptr;
     int *tcell = nullptr;
     float4 *mat = nullptr;
@@ -40,17 +47,51 @@ struct StaticAddr {
 StaticAddr g_addr[kMaxDevices];
 std::mutex g_lock;
 
-// Once per device, with that device current.
+using CtxGetCurrent = CUresult (*)(CUcontext *);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrent g_get_current = nullptr;
+CtxGetId g_get_id = nullptr;
+std::once_flag g_entry_once;
+
+// Unique id of the calling thread's current context; false if the driver
+// entry points are unavailable or no context is current.
+bool current_context_id(unsigned long long *id) {
+    std::call_once(g_entry_once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 4000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            g_get_current = reinterpret_cast<CtxGetCurrent>(a);
+            g_get_id = reinterpret_cast<CtxGetId>(b);
+        }
+        cudaGetLastError();  // a failed lookup leaves no sticky state behind
+    });
+    if (!g_get_current || !g_get_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Set-up once per device and context, with that device current.
 cf_status static_setup(int dev, StaticAddr &out) {
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);  // false before the runtime made a context current
     std::lock_guard<std::mutex> lk(g_lock);
     StaticAddr &a = g_addr[dev];
-    if (!a.ready) {
+    if (!a.ready || !have_id || a.ctx_id != id) {
+        a.ready = false;
         if (cudaGetSymbolAddress((void **)&a.corner, g_corner) != cudaSuccess ||
             cudaGetSymbolAddress((void **)&a.tcell, g_tcell) != cudaSuccess ||
             cudaGetSymbolAddress((void **)&a.mat, g_mat) != cudaSuccess ||
             cudaGetSymbolAddress((void **)&a.err, g_err) != cudaSuccess)
             return CF_ECUDA;
-        a.ready = true;
+        // the lookups made the device's context current if none was: the
+        // addresses belong to that context
+        have_id = current_context_id(&id);
+        a.ctx_id = id;
+        a.ready = have_id;  // without an id, look up again next call
     }
     out = a;
     return CF_OK;

@@ -22,6 +22,7 @@ void free_adjoint(cf_ctx *c) {
     c->ckpt.clear();
     c->ck_used = 0;
     c->tape.clear();
+    ++c->tape_gen;
     dfree(c->vel_r);
     dfree(c->lam);
     dfree(c->lamv);
@@ -159,6 +160,7 @@ cf_status cf_relax(cf_ctx *c, int32_t n, double dt, double damping, int32_t reco
         e.zhi = c->zhi_h;
         e.ck0 = c->ck_used;
         e.nck = (n - 1) / kTapeStride + 2;
+        for (const CellInfo &ci : c->cells) e.mats.push_back(ci.mat);
         while ((int)c->ckpt.size() < e.ck0 + e.nck) {
             float4 *p = nullptr;
             CUDA_TRY(c, dalloc(&p, 2 * (size_t)c->V));
@@ -200,6 +202,7 @@ cf_status cf_tape_clear(cf_ctx *c) {
     if (st != CF_OK) return st;
     DeviceGuard dg(c->device);
     c->tape.clear();
+    ++c->tape_gen;
     c->ck_used = 0;
     CUDA_TRY(c, cudaMemsetAsync(c->vel_r, 0, sizeof(float4) * c->V, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->lam, 0, sizeof(float4) * c->V, c->stream));
@@ -217,6 +220,11 @@ cf_status cf_relax_adjoint(cf_ctx *c, const double *dF) {
     if (!dF) return fail(c, CF_EINVAL, "null dF");
     const cf_ctx::TapeEntry e = c->tape.back();
     const int C = (int)c->cells.size();
+    for (int k = 0; k < C; ++k) {
+        const float4 a = e.mats[k], b = c->cells[k].mat;
+        if (a.x != b.x || a.y != b.y || a.z != b.z || a.w != b.w)
+            return fail(c, CF_ESTATE, "cell %d: materials changed since the recorded cf_relax call", k);
+    }
     const MeshView m = view(c);
     st = upload_plates(c, e.zlo, e.zhi);
     if (st != CF_OK) return st;
@@ -247,6 +255,12 @@ cf_status cf_relax_adjoint(cf_ctx *c, const double *dF) {
     st = upload_plates(c, c->zlo_h, c->zhi_h);
     if (st != CF_OK) return st;
     return consume_errors(c);
+}
+
+cf_status cf_tape_generation(cf_ctx *c, int64_t *out) {
+    if (!c || !out) return CF_EINVAL;
+    *out = c->tape_gen;
+    return CF_OK;
 }
 
 cf_status cf_adjoint_gradients(cf_ctx *c, double *out) {

@@ -202,3 +202,38 @@ def test_compression_full_size_matches_oracle(P):
     assert len(ids) == 64 and (F_ref > 0).all()
     assert rel(F, F_ref) <= 1e-5
     assert rel(P.cf_get_positions(ctx, P.CF_ALL_CELLS) - m.x, y_ref - m.x) <= 1e-5
+
+
+def test_backward_refuses_a_tape_of_another_forward(P):
+    """The tape lives in the context: a second forward on the same context
+    re-records it, so the first forward's backward must refuse instead of
+    reversing the wrong recording; and a material changed after a recorded
+    relaxation makes its reverse pass a state error."""
+    torch = pytest.importorskip("torch")
+    from paper_2003_03130_gb300.adjoint import Compression, CompressionCurve
+
+    cells = two_cells()
+    m = oracle.Mesh(cells)
+    z_lo, radius = protocol_geometry(cells)
+    ctx, ids = setup(P, cells)
+    run = Compression(ctx, ids, m.x, z_lo, radius, STRAINS[:2], 20, DT, KP, RAMP, 0.8)
+    th = [torch.tensor(getattr(m, a), dtype=torch.float64, requires_grad=True) for a in ("mu", "kappa", "w")]
+    F1 = CompressionCurve.apply(*th, run)
+    g0 = P.cf_tape_generation(ctx)
+    F2 = CompressionCurve.apply(th[0] * 1.1, th[1], th[2], run)
+    assert P.cf_tape_generation(ctx) > g0
+    with pytest.raises(RuntimeError):
+        F1.sum().backward(retain_graph=True)
+    F2.sum().backward()  # its own tape: fine
+    assert all(t.grad is not None and torch.isfinite(t.grad).all() for t in th)
+
+    # materials changed between a recorded relaxation and its reverse pass
+    P.cf_tape_clear(ctx)
+    P.cf_plates_set(ctx, KP, z_lo, z_lo + 2 * radius * 0.9)
+    P.cf_relax(ctx, 10, DT, 0.8, record=True)
+    P.cf_set_material(ctx, ids[1], 0.9, 15.0, 0.2)
+    with pytest.raises(P.CellFSIError) as e:
+        P.cf_relax_adjoint(ctx, np.ones(2))
+    assert e.value.name == "CF_ESTATE"
+    P.cf_set_material(ctx, ids[1], cells[1].mu, cells[1].kappa, cells[1].w)  # back as recorded
+    P.cf_relax_adjoint(ctx, np.ones(2))

@@ -164,3 +164,35 @@ def test_invalid_shapes_are_status_codes(P):
         P.cf_autotune(ctx, 0)
     assert e.value.name == "CF_EINVAL"
     P.cf_destroy(ctx)
+
+
+def test_fused_chain_wait_runs_out_with_a_timeout_status(P):
+    """The fused cell chain's waits are bounded. With every cell's required
+    tet-item count raised out of reach (a host-side setting: nothing on the
+    device ever meets it) and a limit of 1,000 polls, a step returns
+    CF_ETIMEOUT promptly instead of hanging; with the defaults restored the
+    same context steps again and its forces match the oracle."""
+    import time
+
+    wl = configs.small_shear()
+    ctx = P.cf_create(0)
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_set_launch_shape(ctx, {"fused": 1})
+    P.cf_step(ctx, 2)
+    P.cf_set_chain_wait(ctx, 1000, 1)
+    t0 = time.perf_counter()
+    with pytest.raises(P.CellFSIError) as e:
+        P.cf_step(ctx, 1)
+    assert e.value.name == "CF_ETIMEOUT"
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(P.CellFSIError) as e:
+        P.cf_set_chain_wait(ctx, 0, 0)
+    assert e.value.name == "CF_EINVAL"
+    P.cf_set_chain_wait(ctx)
+    P.cf_set_positions(ctx, cid, wl.cells[0].y0)
+    P.cf_step(ctx, 3)
+    P.cf_compute_forces(ctx)
+    y = P.cf_get_positions(ctx, cid)
+    ref = oracle.Mesh(wl.cells).forces(y)
+    assert rel(P.cf_get_forces(ctx, cid), ref) <= TOL
+    P.cf_destroy(ctx)
