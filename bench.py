@@ -467,21 +467,27 @@ def shear_sweep(P, torch, dev, steps, every):
                 ctx = P.cf_create(dev, stream.cuda_stream)
                 (cid,) = P.load_workload(ctx, wl)
                 P.cf_prepare_steps(ctx, every)
-                rows, t_dev = [], 0.0
+                rows, t_dev, done, error = [], 0.0, 0, None
                 for k in range(0, steps, every):
                     n = min(every, steps - k)
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                     P.cf_step_async(ctx, n)
                     e1.record(stream)
-                    P.cf_synchronize(ctx)
+                    try:
+                        P.cf_synchronize(ctx)
+                    except P.CellFSIError as e:  # e.g. a tet inverted: reported, the other cases still run
+                        error = f"{e.name} within steps {k + 1}-{k + n}: {e}"
+                        break
                     t_dev += e0.elapsed_time(e1)
+                    done = k + n
                     t = P.cf_get_taylor(ctx, cid)
                     st = P.cf_get_cell_strain(ctx, cid, 2 * 16.0)
                     rows.append([k + n, t["D"], t["D_literal"], t["inclination"], st["strain"]])
                 P.cf_destroy(ctx)
             out.append({"ca": ca, "w": w, "mu": wl.cells[0].mu, "kappa": wl.cells[0].kappa,
-                        "steps_per_s": steps / (t_dev / 1e3),
+                        "steps_done": done, "error": error,
+                        "steps_per_s": done / (t_dev / 1e3) if t_dev > 0 else None,
                         "columns": ["step", "D", "D_literal", "inclination_deg", "cell_strain"], "rows": rows})
     return out
 

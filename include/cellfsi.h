@@ -214,8 +214,11 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *   [8]    1: the far field issues a node's loads before its region test
  *          resolves (saves a round trip per far node, wastes the loads of
  *          region nodes); 0 (default): region nodes return first;
- *   [9]    1: the force kernel computes two tets per thread, both tets'
- *          loads in flight before either is computed; 0 (default): one;
+ *   [9]    form of the force kernel: 0 (default) one thread per tet; 1 two
+ *          tets per thread, both tets' loads in flight before either is
+ *          computed; 2 four lanes per tet (one corner each, the tet's
+ *          deformation gradient and corner forces shared by shuffles: more
+ *          threads for meshes too small to fill the GPU);
  *   [10]   1: with FP32 populations the far and near fields cache them in
  *          L2 at normal priority (for lattices whose stream-collide gains
  *          more from L2 reuse than the cell kernels lose); 0 (default):
@@ -250,7 +253,7 @@ cf_status cf_set_chain_wait(cf_ctx *ctx, int64_t max_polls, int32_t extra_need);
  * steps_per_candidate (>= 1) coupled steps exactly as cf_step runs them
  * (the same step graphs, far field and cell chain overlapping), timed as a
  * whole with CUDA events, and the fastest candidate is kept. The simulation
- * advances by those steps exactly as under cf_step (23 candidates in all). A fluid-only context has nothing to
+ * advances by those steps exactly as under cf_step (24 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

@@ -73,20 +73,19 @@ cudaError_t clear_slot(const cf_ctx *c, const RegionSlot &r, cudaStream_t s) {
 int near_grid(const cf_ctx *c) { return 8 * c->sms; }
 int chain_grid(const cf_ctx *c) { return 4 * c->sms; }
 
-// Work items of the fused cell chain: the region items over all vertices,
-// then the tet items of the cells in order, with the vertex-sum items of a
-// cell placed LAG items after its last tet item (by then its tets are most
-// likely done, so the sums rarely wait), then the remaining vertex-sum
-// items. Every item a vertex-sum item waits for comes before it.
+// Work items of the fused cell chain: the tet items of the cells in order,
+// with the vertex-sum items of a cell placed LAG items after its last tet
+// item (by then its tets are most likely done, so the sums rarely wait),
+// then the remaining vertex-sum items. Every item a vertex-sum item waits
+// for comes before it.
 cf_status build_chain_items(cf_ctx *c) {
     std::vector<int4> items;
     // item sizes: small meshes keep every block busy, large ones keep the
     // item count (one claim each) low
     const int grid = chain_grid(c);
     auto size_for = [&](int n, int lo, int hi) { return std::max(lo, std::min(hi, n / (2 * grid) / lo * lo)); };
-    const int RB = size_for(c->V, 256, 1024), TB = size_for(c->T, 256, 1024), GB = size_for(c->V, 64, 256);
+    const int TB = size_for(c->T, 256, 1024), GB = size_for(c->V, 64, 256);
     const size_t LAG = 2 * (size_t)grid;
-    for (int v = 0; v < c->V; v += RB) items.push_back(make_int4(0, 0, v, std::min(c->V, v + RB)));
     const int C = (int)c->cells.size();
     std::vector<int> need(C, 0);
     std::vector<size_t> last_tet(C, 0);
@@ -124,15 +123,14 @@ cf_status build_chain_items(cf_ctx *c) {
 
 // K1 + K23 of one step on stream s: the fused persistent launch, or the two
 // separate kernels.
-cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, const RegionSlot &acc,
-                              cudaStream_t s) {
+cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, cudaStream_t s) {
     if (sh.fused) {
         cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
         if (e != cudaSuccess) return e;
-        return launch_cell_chain(m, c->u[p], c->F, c->lp, acc, c->d_err, c->chain_items, c->chain_nitems,
-                                 c->chain_need, c->chain_ctr, chain_grid(c), c->chain_spin_limit, s);
+        return launch_cell_chain(m, c->u[p], c->F, c->lp, c->d_err, c->chain_items, c->chain_nitems, c->chain_need,
+                                 c->chain_ctr, chain_grid(c), c->chain_spin_limit, s);
     }
-    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, &c->lp, &acc, sh.tet_pairs);
+    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form);
     if (e != cudaSuccess) return e;
     return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
 }
@@ -153,7 +151,10 @@ void set_tiles(LbmParams &p, int k) {
 //   far(t)   after far(t-1) [sf order] and near(t-1)
 //   K5(t-1) -> K1(t) -> K23(t) after near(t-1) [sc order]
 //   near(t)  after K23(t) [sc order] and far(t-1) (it reads far nodes' halo)
-// so near(t) and the cell chain overlap far(t).
+// so near(t) and the cell chain overlap far(t). K5(t-1), which computes
+// y^t, also marks the region of step t + 1 (its slot is cleared just
+// before); the first step of a call marks both its own region and the next
+// one from the current positions.
 cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaStream_t sf, cudaStream_t sc,
                         cudaEvent_t *ev) {
     const MeshView m = view(c);
@@ -172,9 +173,10 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
     const bool first = kind == Kind::First || kind == Kind::Single;
     if (first) {
-        const RegionSlot use = region_slot(c, s0);
+        const RegionSlot use = region_slot(c, s0), acc = accum_slot(c, s0);
         CUDA_TRY(c, clear_slot(c, use, sf));
-        CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, sf));
+        CUDA_TRY(c, clear_slot(c, acc, sf));
+        CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, acc, sf));
     }
     CUDA_TRY(c, cudaEventRecord(fork, sf));
     CUDA_TRY(c, cudaStreamWaitEvent(sc, fork, 0));
@@ -184,10 +186,12 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
         CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
-        if (!(first && i == 0))  // K5 of the previous step (parity 1-p)
-            CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block));
-        CUDA_TRY(c, clear_slot(c, acc, sc));
-        CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, sc));
+        if (!(first && i == 0)) {  // K5 of the previous step (parity 1-p), marking this step's acc slot
+            CUDA_TRY(c, clear_slot(c, acc, sc));
+            CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block,
+                                             acc));
+        }
+        CUDA_TRY(c, launch_chain_step(c, m, p, sh, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
@@ -397,6 +401,7 @@ void cf_destroy(cf_ctx *c) {
     dfree(c->xref64);
     dfree(c->tet);
     dfree(c->B);
+    dfree(c->B64);
     dfree(c->Bp);
     dfree(c->V0);
     dfree(c->tcell);
@@ -541,7 +546,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     int *tin = nullptr;
     auto cleanup = [&]() {
         dfree(n.xr); dfree(n.u[0]); dfree(n.u[1]); dfree(n.fv); dfree(n.fc); dfree(n.xref64); dfree(n.tet);
-        dfree(n.B); dfree(n.Bp); dfree(n.V0); dfree(n.tcell); dfree(n.tmat); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
+        dfree(n.B); dfree(n.B64); dfree(n.Bp); dfree(n.V0); dfree(n.tcell); dfree(n.tmat); dfree(n.origin); dfree(n.mat); dfree(n.csr_ptr);
         dfree(n.csr_idx); dfree(n.csr_cursor); dfree(n.energy_partial); dfree(n.stage); dfree(n.taylor_partial);
         dfree(x64); dfree(y64); dfree(tin);
     };
@@ -562,6 +567,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     TRY_N(dalloc(&n.xref64, 3 * (size_t)V1));
     TRY_N(dalloc(&n.tet, T1));
     TRY_N(dalloc(&n.B, 9 * (size_t)T1));
+    TRY_N(dalloc(&n.B64, 9 * (size_t)T1));
     TRY_N(dalloc(&n.Bp, 3 * (size_t)T1));
     TRY_N(dalloc(&n.V0, T1));
     TRY_N(dalloc(&n.tcell, T1));
@@ -585,6 +591,8 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
         TRY_N(cudaMemcpyAsync(n.xref64, c->xref64, sizeof(double) * 3 * c->V, cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpyAsync(n.tet, c->tet, sizeof(int4) * c->T, cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpy2DAsync(n.B, sizeof(float) * T1, c->B, sizeof(float) * c->T, sizeof(float) * c->T, 9,
+                                cudaMemcpyDeviceToDevice, s));
+        TRY_N(cudaMemcpy2DAsync(n.B64, sizeof(double) * T1, c->B64, sizeof(double) * c->T, sizeof(double) * c->T, 9,
                                 cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpyAsync(n.V0, c->V0, sizeof(float) * c->T, cudaMemcpyDeviceToDevice, s));
         TRY_N(cudaMemcpyAsync(n.tcell, c->tcell, sizeof(int) * c->T, cudaMemcpyDeviceToDevice, s));
@@ -610,7 +618,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     TRY_N(cudaMemsetAsync(c->d_status, 0xff, sizeof(unsigned long long), s));
     for (int k = 0; k < ncells; ++k)
         TRY_N(launch_mesh_prepare(x64 + 3 * voff[k], nv[k], tin + 4 * toff[k], nt[k], add[k].v_off, add[k].t_off,
-                                  (int)toff[k], T1, cell0 + k, n.tet, n.B, n.V0, n.tcell, c->d_status, s));
+                                  (int)toff[k], T1, cell0 + k, n.tet, n.B, n.B64, n.V0, n.tcell, c->d_status, s));
     unsigned long long st = 0;
     TRY_N(cudaMemcpyAsync(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
     TRY_N(cudaStreamSynchronize(s));
@@ -645,6 +653,7 @@ cf_status cf_mesh_init_batch(cf_ctx *c, int32_t ncells, const int32_t *nv, const
     std::swap(c->xref64, n.xref64);
     std::swap(c->tet, n.tet);
     std::swap(c->B, n.B);
+    std::swap(c->B64, n.B64);
     std::swap(c->Bp, n.Bp);
     std::swap(c->V0, n.V0);
     std::swap(c->tcell, n.tcell);
@@ -889,19 +898,20 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             const int sph = (int)((c->tstep) % 3);
             const RegionSlot use = region_slot(c, sph), accm = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
-            if (cells && t == 0) {  // region of the first step: not timed
+            if (cells && t == 0) {  // regions of the first step and the next: not timed
                 e = clear_slot(c, use, s);
-                if (e == cudaSuccess) e = launch_mark_region(m, c->u[p], c->lp, use, s);
+                if (e == cudaSuccess) e = clear_slot(c, accm, s);
+                if (e == cudaSuccess) e = launch_mark_region(m, c->u[p], c->lp, use, accm, s);
             }
+            if (cells && t > 0 && e == cudaSuccess) e = clear_slot(c, accm, s);
             cudaEventRecord(E[0], s);
             if (cells && t > 0 && e == cudaSuccess)
-                e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s, sh.interp_block);
+                e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s, sh.interp_block,
+                                         accm);
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
-                e = clear_slot(c, accm, s);
-                if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, s);
-                if (e == cudaSuccess && !sh.fused)
-                    e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, &c->lp, &accm, sh.tet_pairs);
+                if (sh.fused) e = launch_chain_step(c, m, p, sh, s);
+                else e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form);
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)
@@ -1035,7 +1045,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[6] = sh.fused;
     shape[7] = sh.near_rows;
     shape[8] = sh.far_spec;
-    shape[9] = sh.tet_pairs;
+    shape[9] = sh.tet_form;
     shape[10] = sh.pop_l2;
     return CF_OK;
 }
@@ -1064,8 +1074,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.near_rows = shape[7];
     if (shape[8] != 0 && shape[8] != 1) return fail(c, CF_EINVAL, "far_spec must be 0 or 1");
     sh.far_spec = shape[8];
-    if (shape[9] != 0 && shape[9] != 1) return fail(c, CF_EINVAL, "tet_pairs must be 0 or 1");
-    sh.tet_pairs = shape[9];
+    if (shape[9] < 0 || shape[9] > 2) return fail(c, CF_EINVAL, "tet_form must be 0, 1 or 2");
+    sh.tet_form = shape[9];
     if (shape[10] != 0 && shape[10] != 1) return fail(c, CF_EINVAL, "pop_l2 must be 0 or 1");
     sh.pop_l2 = shape[10];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
@@ -1108,7 +1118,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::fused, {0, 1}},
             {&Shape::near_rows, {0, 1}},
             {&Shape::far_spec, {0, 1}},
-            {&Shape::tet_pairs, {0, 1}},
+            {&Shape::tet_form, {0, 1, 2}},
             {&Shape::pop_l2, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}},
             {&Shape::gather_block, {64, 128, 256}},

@@ -1,7 +1,6 @@
 // Per-element bodies of the cell kernels, shared by the separate launches
 // (csrc/tet_force.cu, csrc/ibm.cu) and the fused persistent chain
-// (csrc/chain.cu): tet corner forces, the per-vertex region marking, and the
-// vertex sum with its spread.
+// (csrc/chain.cu): tet corner forces, and the vertex sum with its spread.
 #pragma once
 
 #include "mr.cuh"
@@ -35,7 +34,10 @@ __device__ __forceinline__ void tet_forces_store(const MeshView &m, const TetIn 
     tet_grad(in.w[0], in.w[1], in.w[2], in.w[3], in.Bm, H);
     InvT<float> v;
     float P[3][3];
-    mr_stress(H, in.mat.x, in.mat.y, in.mat.z, v, P);
+    invariants_t(H, v);
+    if (needs_fp64_volume(m, in.mat))
+        set_volume_change(v, (float)volume_change64(m.B64, m.T, t, in.w[0], in.w[1], in.w[2], in.w[3]));
+    mr_stress_inv(H, in.mat.x, in.mat.y, in.mat.z, v, P);
     if (!(v.J > 0.f)) atomicOr(err, ERR_INVERTED);
     float f[4][3];
     corner_forces(P, in.Bm, in.V0, f);
@@ -48,20 +50,6 @@ __device__ __forceinline__ void tet_corner_forces(const MeshView &m, const float
     TetIn in;
     tet_load(m, u, t, in);
     tet_forces_store(m, in, err, t);
-}
-
-// The per-vertex part of K1: add the next step's force region (the support
-// of x + u grown by one node) to mark. Whether this step's support lies in
-// this step's region follows from the step before moving every vertex by
-// less than one spacing, which K5 checks. (Last step's spread needs no
-// clearing: the near-field stream-collide zeroes the force field where it
-// reads it.)
-template <int W>
-__device__ __forceinline__ void mark_vertex(const MeshView &m, const float4 *__restrict__ u, const LbmParams &lp,
-                                            int v, const RegionSlot &mark) {
-    Support s;
-    if (support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s))  // else K23 reports it
-        mark_region<W>(s, lp, mark);
 }
 
 // Corner-force load: from L2 (FC_L2) when the forces were written by other

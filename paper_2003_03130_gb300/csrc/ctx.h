@@ -39,7 +39,7 @@ struct Shape {
     int fused = 0;  // cell chain as one persistent launch (csrc/chain.cu) instead of two
     int near_rows = 0;  // near field in rows over the whole lattice instead of over the region's tile list
     int far_spec = 0;   // far field issues its loads before the region test resolves
-    int tet_pairs = 0;  // two tets per thread in the force kernel
+    int tet_form = 0;   // force kernel: one thread per tet (0), two tets per thread (1), four lanes per tet (2)
     int pop_l2 = 0;     // FP32 far and near fields cache populations in L2 instead of streaming them
 };
 
@@ -86,6 +86,7 @@ struct cf_ctx {
     double *xref64 = nullptr;
     int4 *tet = nullptr;
     float *B = nullptr, *V0 = nullptr;
+    double *B64 = nullptr;  // B in FP64 [9][T] (J - 1 of nearly incompressible tets)
     float4 *Bp = nullptr;  // packed B / V0 / cell rows for the force kernel, [3][T]
     int *tcell = nullptr, *origin = nullptr;
     int *tmat = nullptr;             // [T] material slot of each tet: its cell id, or a region slot
@@ -184,6 +185,7 @@ MeshView view(const cf_ctx *c) {
     m.origin = c->origin;
     m.tet = c->tet;
     m.B = c->B;
+    m.B64 = c->B64;
     m.Bp = c->Bp;
     m.V0 = c->V0;
     m.tcell = c->tcell;

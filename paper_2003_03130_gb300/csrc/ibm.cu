@@ -20,26 +20,38 @@
 //   the support of y^t); each lane sums W^3 / 8 nodes in a fixed order (for
 //   W = 2 lane (dz, dy, dx) its node, for W = 4 lane (dz, j) the rows
 //   dy = 2j, 2j + 1 of plane dz = 0..3) and the eight partial sums meet in a
-//   fixed shuffle tree.
+//   fixed shuffle tree. The eight lanes then hold y^{t+1} and add the tiles
+//   of its support grown by one node to the force region of step t + 2 (a
+//   vertex moves less than a spacing per step, so that region holds the
+//   support of y^{t+2}), each lane taking its share of the tiles.
 #include "cell_ops.cuh"
 
 namespace cf {
 
+// The force region of the current positions, into one or two slots (the
+// first step of a call needs both its own region and the next step's, and
+// the positions have not moved in between). Eight lanes per vertex share its
+// tiles.
 template <int W>
 __global__ void __launch_bounds__(256) k_mark_region(MeshView m, const float4 *__restrict__ u, LbmParams p,
-                                                     RegionSlot r) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+                                                     RegionSlot r, RegionSlot r2) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = g >> 3, lane = g & 7;
     Support s;
-    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) mark_region<W>(s, p, r);
+    if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+        mark_region<W>(s, p, r, lane, 8);
+        if (r2.bits) mark_region<W>(s, p, r2, lane, 8);
+    }
 }
 
 cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, const RegionSlot &r,
-                               cudaStream_t s) {
+                               const RegionSlot &r2, cudaStream_t s) {
     if (m.V == 0) return cudaSuccess;
+    const int blocks = (int)((8LL * m.V + 255) / 256);
     if (p.dw == 4)
-        k_mark_region<4><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, r);
+        k_mark_region<4><<<blocks, 256, 0, s>>>(m, u, p, r, r2);
     else
-        k_mark_region<2><<<(m.V + 255) / 256, 256, 0, s>>>(m, u, p, r);
+        k_mark_region<2><<<blocks, 256, 0, s>>>(m, u, p, r, r2);
     return cudaGetLastError();
 }
 
@@ -71,17 +83,18 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, 
 template <int W>
 __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const float4 *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
-                                                       unsigned *err) {
+                                                       unsigned *err, RegionSlot mark) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = g >> 3, lane = g & 7;
     const bool live = v < m.V;
-    float4 uc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 uc = make_float4(0.f, 0.f, 0.f, 0.f), xr = uc;
     float vx = 0.f, vy = 0.f, vz = 0.f;
     bool ok = false;
     if (live) {
         uc = __ldg(u_cur + v);
+        xr = __ldg(m.xr + v);
         Support s;
-        ok = support_of<W>(m.origin, __ldg(m.xr + v), uc, p.ny, s);
+        ok = support_of<W>(m.origin, xr, uc, p.ny, s);
         if (ok) {
             float wx[W], wy[W], wz[W];
             delta_weights<W>(s.fx, wx);
@@ -122,13 +135,18 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
         vy += __shfl_xor_sync(0xffffffffu, vy, o);
         vz += __shfl_xor_sync(0xffffffffu, vz, o);
     }
-    if (!live || lane != 0) return;
+    if (!live) return;
+    const float4 un = make_float4(uc.x + vx, uc.y + vy, uc.z + vz, 0.f);
+    if (mark.bits && ok) {  // the region of step t + 2 (an invalid support is K23's to report)
+        Support s2;
+        if (support_of<W>(m.origin, xr, un, p.ny, s2)) mark_region<W>(s2, p, mark, lane, 8);
+    }
+    if (lane != 0) return;
     if (!ok) {
         atomicOr(err, ERR_DOMAIN);
         u_next[v] = uc;
         return;
     }
-    const float4 un = make_float4(uc.x + vx, uc.y + vy, uc.z + vz, 0.f);
     if (!isfinite(un.x + un.y + un.z)) atomicOr(err, ERR_NONFINITE);
     // the next step's force region holds this step's support grown by one
     // node: a move of a spacing or more along an axis would leave it
@@ -137,15 +155,15 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
 }
 
 cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
-                                 float4 *u_next, unsigned *err, cudaStream_t s, int block) {
+                                 float4 *u_next, unsigned *err, cudaStream_t s, int block, const RegionSlot &mark) {
     if (m.V == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 128;
     const long long threads = 8LL * m.V;
     const int blocks = (int)((threads + bs - 1) / bs);
     if (p.dw == 4)
-        k_interp_advect<4><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err);
+        k_interp_advect<4><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
     else
-        k_interp_advect<2><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err);
+        k_interp_advect<2><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
     return cudaGetLastError();
 }
 

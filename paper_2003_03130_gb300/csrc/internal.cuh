@@ -15,7 +15,8 @@
 //                xr (FP32 x_ref relative to the cell's integer origin, .w =
 //                cell id), u (FP32 displacement y - x_ref), fv (force);
 //                xref64 [V][3] FP64 for exact host round trips;
-//   tets         int4 tet[t], B[(3k + j) * T + t], V0[t], tcell[t];
+//   tets         int4 tet[t], B[(3k + j) * T + t] (FP32, and FP64 in B64), V0[t],
+//                tcell[t];
 //   corner force float4 fc[c * T + t].
 #pragma once
 
@@ -88,6 +89,7 @@ struct MeshView {
     const int *origin;     // [3 * ncells], integer origin of each cell
     const int4 *tet;       // [T]: global vertex indices, corner 3 = vertex 4
     const float *B;        // [9][T]: B[(3k + j) * T + t] = (J^-1)_kj
+    const double *B64;     // [9][T] or null: the same in FP64 (J - 1 of nearly incompressible tets)
     const float4 *Bp;      // [3][T] or null: row k of B with .w = V0, cell id (int bits), 0 for k = 0, 1, 2
     const float *V0;       // [T]
     const int *tcell;      // [T]: cell of each tet
@@ -175,10 +177,11 @@ __host__ __device__ __forceinline__ bool region_has(const unsigned *__restrict__
 }
 
 // Add tile t: the first thread to set its bit appends it to the list. The
-// plain read skips the atomic for the (many) tiles already in.
+// read from L2 (where the atomics land; an L1 line could be stale) skips the
+// atomic for the (many) tiles already in.
 __device__ __forceinline__ void region_add(const RegionSlot &r, int t) {
     const unsigned bit = 1u << (t & 31);
-    if (r.bits[t >> 5] & bit) return;
+    if (__ldcg(r.bits + (t >> 5)) & bit) return;
     if (!(atomicOr(r.bits + (t >> 5), bit) & bit)) r.tiles[atomicAdd(r.count, 1)] = t;
 }
 
@@ -255,16 +258,19 @@ __host__ __device__ __forceinline__ void for_each_tile(const LbmParams &p, int x
 
 #ifdef __CUDACC__
 // Add the tiles of the force region around one vertex: its support grown by
-// one node per side (y clamped to the lattice). Neighbouring vertices mostly
-// meet the same tiles, so the lanes of a warp that hold the same tile at the
-// same step elect one of them to add it: a region slot has few words, and
-// one atomic per warp and tile, instead of one per lane, keeps them from
-// serialising.
+// one node per side (y clamped to the lattice). `nlanes` lanes may share a
+// vertex, lane `lane` taking the tiles lane, lane + nlanes, ... of its box,
+// so that a vertex's tiles are added in parallel rather than one after
+// another. Neighbouring vertices mostly meet the same tiles, so the lanes of
+// a warp that hold the same tile at the same step elect one of them to add
+// it: a region slot has few words, and one atomic per warp and tile, instead
+// of one per lane, keeps them from serialising.
 template <int W>
-__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, const RegionSlot &r) {
+__device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p, const RegionSlot &r, int lane = 0,
+                                            int nlanes = 1) {
     namespace cg = cooperative_groups;
     const TileBox b = tile_box(p, s.bx - 1, s.bx + W, max(s.by - 1, 0), min(s.by + W, p.ny - 1), s.bz - 1, s.bz + W);
-    for (int k = 0; k < b.n; ++k) {
+    for (int k = lane; k < b.n; k += nlanes) {
         const int t = tile_of_box(p, b, k);
         const cg::coalesced_group same = cg::labeled_partition(cg::coalesced_threads(), t);
         if (same.thread_rank() == 0) region_add(r, t);
@@ -278,8 +284,8 @@ __device__ __forceinline__ void mark_region(const Support &s, const LbmParams &p
 // *status receives min over failing tets of ((t_report + t) << 8 | code),
 // code 1 = index out of range, 2 = repeated vertex, 3 = degenerate.
 cudaError_t launch_mesh_prepare(const double *x64, int nv, const int *tets_in, int nt, int v_off, int t_off,
-                                int t_report, int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
-                                unsigned long long *status, cudaStream_t s);
+                                int t_report, int T, int cell, int4 *tet, float *B, double *B64, float *V0,
+                                int *tcell, unsigned long long *status, cudaStream_t s);
 cudaError_t launch_vertex_prepare(const double *x64, const double *y64, int nv, int v_off, int cell,
                                   const int *origin_host3, float4 *xr, float4 *u0, float4 *u1, double *xref64,
                                   cudaStream_t s);
@@ -294,13 +300,12 @@ cudaError_t launch_get_positions(const float4 *u, const double *xref64, int v0, 
                                  cudaStream_t s);
 cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cudaStream_t s);
 
-// K1: elastic corner forces of all tets at displacements u. With lp and
-// mark_out non-null the same launch also runs one thread per vertex that adds
-// the tiles of the next step's force region (the support of x + u grown by
-// one node) to mark_out.
-// pairs: two tets per thread (both tets' loads issued before either is computed).
+// K1: elastic corner forces of all tets at displacements u. form 0: one
+// thread per tet; 1: two tets per thread (both tets' loads issued before
+// either is computed); 2: four lanes per tet (needs the packed rows m.Bp,
+// else one thread per tet).
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, cudaStream_t s, int block = 0,
-                             const LbmParams *lp = nullptr, const RegionSlot *mark_out = nullptr, int pairs = 0);
+                             int form = 0);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
@@ -317,19 +322,19 @@ cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, do
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
                                  cudaStream_t s, int block = 0);
 // Add the force region of the positions x + u (support grown by one node) to
-// a region slot (cleared by the caller).
+// a region slot, and to a second one if r2.bits is not null (both cleared by
+// the caller).
 cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmParams &p, const RegionSlot &r,
-                               cudaStream_t s);
+                               const RegionSlot &r2, cudaStream_t s);
 // K1 + K23 fused (csrc/chain.cu): one persistent launch that runs the work
 // items of the cell chain in order: items[i] = (kind, cell, begin, end) with
-// kind 0 = region marking of vertices [begin, end), 1 = corner forces of tets
-// [begin, end) of `cell`, 2 = vertex sums + spread of vertices [begin, end)
-// of `cell`. A kind-2 item waits until the need[cell] kind-1 items of its
-// cell are done, giving up after spin_limit polls (ERR_WAIT);
-// counters[2 + ncells] must be zero at launch.
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
-                              const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
-                              int *counters, int blocks, long long spin_limit, cudaStream_t s);
+// kind 1 = corner forces of tets [begin, end) of `cell`, 2 = vertex sums +
+// spread of vertices [begin, end) of `cell`. A kind-2 item waits until the
+// need[cell] kind-1 items of its cell are done, giving up after spin_limit
+// polls (ERR_WAIT); counters[2 + ncells] must be zero at launch.
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp, unsigned *err,
+                              const int4 *items, int nitems, const int *need, int *counters, int blocks,
+                              long long spin_limit, cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 // Every stream-collide launch reads the step's rounding seed from seed[0];
@@ -359,8 +364,12 @@ size_t pop_bytes(int fmt);
 // x + u_cur; u_next = u_cur + velocity. A vertex that moves one lattice
 // spacing or more along an axis sets ERR_MOVED: the next step's force region
 // (this step's support grown by one node) would no longer hold its support.
+// With mark.bits not null the same threads add the force region of the new
+// positions (the support of x + u_next grown by one node: the region of the
+// step after next) to `mark`, cleared by the caller.
 cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
-                                 float4 *u_next, unsigned *err, cudaStream_t s, int block = 0);
+                                 float4 *u_next, unsigned *err, cudaStream_t s, int block = 0,
+                                 const RegionSlot &mark = RegionSlot{nullptr, nullptr, nullptr});
 // Compression between plates and the adjoint (csrc/adjoint.cu).
 // out = J_el v at displacements u (vertex sums of the corner tangents; uses m.fc).
 cudaError_t launch_force_jvp(const MeshView &m, const float4 *u, const float4 *v, float4 *out, unsigned *err,

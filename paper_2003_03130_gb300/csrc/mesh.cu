@@ -2,15 +2,15 @@
 // reference coordinates and are computed once), vertex incidence rows for the
 // deterministic vertex-force sum, and host <-> device conversions of
 // positions and forces. The precompute runs in FP64 on the device and stores
-// FP32.
+// FP32 (B also in FP64, for the volume term of nearly incompressible tets).
 #include "internal.cuh"
 
 namespace cf {
 
 // One thread per tet of the new cell.
 __global__ void k_mesh_prepare(const double *__restrict__ x64, int nv, const int *__restrict__ tets_in, int nt,
-                               int v_off, int t_off, int t_report, int T, int cell, int4 *tet, float *B, float *V0,
-                               int *tcell, unsigned long long *status) {
+                               int v_off, int t_off, int t_report, int T, int cell, int4 *tet, float *B,
+                               double *B64, float *V0, int *tcell, unsigned long long *status) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     int a[4];
@@ -73,17 +73,21 @@ __global__ void k_mesh_prepare(const double *__restrict__ x64, int nv, const int
     Bi[2][2] = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
     const int tg = t_off + t;
     for (int k = 0; k < 3; ++k)
-        for (int j = 0; j < 3; ++j) B[(3 * k + j) * T + tg] = (float)(Bi[k][j] / det);
+        for (int j = 0; j < 3; ++j) {
+            const double b = Bi[k][j] / det;
+            B[(3 * k + j) * T + tg] = (float)b;
+            B64[(3 * k + j) * T + tg] = b;
+        }
     V0[tg] = (float)(det / 6.0);
     tet[tg] = make_int4(a[0] + v_off, a[1] + v_off, a[2] + v_off, a[3] + v_off);
     tcell[tg] = cell;
 }
 
 cudaError_t launch_mesh_prepare(const double *x64, int nv, const int *tets_in, int nt, int v_off, int t_off,
-                                int t_report, int T, int cell, int4 *tet, float *B, float *V0, int *tcell,
-                                unsigned long long *status, cudaStream_t s) {
-    k_mesh_prepare<<<(nt + 127) / 128, 128, 0, s>>>(x64, nv, tets_in, nt, v_off, t_off, t_report, T, cell, tet, B, V0,
-                                                    tcell, status);
+                                int t_report, int T, int cell, int4 *tet, float *B, double *B64, float *V0,
+                                int *tcell, unsigned long long *status, cudaStream_t s) {
+    k_mesh_prepare<<<(nt + 127) / 128, 128, 0, s>>>(x64, nv, tets_in, nt, v_off, t_off, t_report, T, cell, tet, B,
+                                                    B64, V0, tcell, status);
     return cudaGetLastError();
 }
 

@@ -96,11 +96,11 @@ __device__ __forceinline__ void invariants_t(const S (&H)[3][3], InvT<S> &v) {
     v.L = m_log1p(v.j);
 }
 
-// P = dU/dF for F = I + H and moduli (mu1, mu2, kappa); v gets the invariants.
+// P = dU/dF for F = I + H, moduli (mu1, mu2, kappa) and the invariants v of
+// H (invariants_t; the caller may replace j, J and L by a more accurate J - 1).
 template <class S>
-__device__ __forceinline__ void mr_stress(const S (&H)[3][3], float mu1, float mu2, float kappa, InvT<S> &v,
-                                          S (&P)[3][3]) {
-    invariants_t(H, v);
+__device__ __forceinline__ void mr_stress_inv(const S (&H)[3][3], float mu1, float mu2, float kappa,
+                                              const InvT<S> &v, S (&P)[3][3]) {
     const S s = m_exp(-(2.f / 3.f) * v.L);  // J^-2/3
     const S s2 = s * s;                     // J^-4/3
     const S TC = 3.f + v.e;
@@ -130,6 +130,72 @@ __device__ __forceinline__ void mr_stress(const S (&H)[3][3], float mu1, float m
             if (i == l) p = p + sigma + beta * v.t;
             P[i][l] = p;
         }
+}
+
+// P = dU/dF for F = I + H and moduli (mu1, mu2, kappa); v gets the invariants.
+template <class S>
+__device__ __forceinline__ void mr_stress(const S (&H)[3][3], float mu1, float mu2, float kappa, InvT<S> &v,
+                                          S (&P)[3][3]) {
+    invariants_t(H, v);
+    mr_stress_inv(H, mu1, mu2, kappa, v, P);
+}
+
+// Nearly incompressible tets (kappa >= kStiffVolume (mu1 + mu2), Poisson
+// ratio 0.495 and above) take J - 1 in FP64. The volume term kappa (J - 1)
+// multiplies any rounding of J - 1 by kappa: under a nearly isochoric
+// deformation J - 1 is small against |H|, and J - 1 from the FP32 B and
+// FP32 products carries errors of ~1e-7 |H|, which reach the forces
+// amplified by kappa / mu (measured: 7e-5 relative at kappa = 2,000 mu in
+// simple shear). In FP64, from the FP32 displacements (exact in FP64) and the
+// FP64 B of the precompute, J - 1 is exact to ~1e-16 |H|; the rest of the
+// stress stays FP32.
+constexpr float kStiffVolume = 100.f;
+
+__device__ __forceinline__ bool needs_fp64_volume(const MeshView &m, float4 mat) {
+    return m.B64 != nullptr && mat.z >= kStiffVolume * (mat.x + mat.y);
+}
+
+// J - 1 = tr H + ((tr H)^2 - tr H^2) / 2 + det H in FP64 with H = A B, A from
+// the column differences a_k = w_k - w_4 (k = 1..3, exact in FP64), B from
+// B64 ([9][T]).
+__device__ __forceinline__ double volume_change64_body(const double *__restrict__ B64, int T, int t, float4 w0,
+                                                       float4 w1, float4 w2, float4 w3) {
+    const double A[3][3] = {{(double)w0.x - w3.x, (double)w1.x - w3.x, (double)w2.x - w3.x},
+                            {(double)w0.y - w3.y, (double)w1.y - w3.y, (double)w2.y - w3.y},
+                            {(double)w0.z - w3.z, (double)w1.z - w3.z, (double)w2.z - w3.z}};
+    double Bm[3][3], H[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Bm[k][j] = __ldg(B64 + (size_t)(3 * k + j) * T + t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) H[i][j] = A[i][0] * Bm[0][j] + A[i][1] * Bm[1][j] + A[i][2] * Bm[2][j];
+    const double tr = H[0][0] + H[1][1] + H[2][2];
+    double tr2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tr2 += H[i][k] * H[k][i];
+    const double det = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
+                       H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                       H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+    return tr + 0.5 * (tr * tr - tr2) + det;
+}
+
+// The same as a called function, for kernels whose FP32 path the FP64
+// registers would otherwise crowd (one thread per tet).
+static __device__ __noinline__ double volume_change64(const double *__restrict__ B64, int T, int t, float4 w0, float4 w1,
+                                               float4 w2, float4 w3) {
+    return volume_change64_body(B64, T, t, w0, w1, w2, w3);
+}
+
+// Replace J - 1 (and J, log J) of v by j.
+__device__ __forceinline__ void set_volume_change(InvT<float> &v, float j) {
+    v.j = j;
+    v.J = 1.f + j;
+    v.L = log1pf(j);
 }
 
 // Corner forces f^a_i = -V_0 sum_l P_il B_al (a = 1..3), f^4 = -(f^1 + f^2 + f^3)

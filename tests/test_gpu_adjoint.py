@@ -228,12 +228,13 @@ def test_backward_refuses_a_tape_of_another_forward(P):
     assert all(t.grad is not None and torch.isfinite(t.grad).all() for t in th)
 
     # materials changed between a recorded relaxation and its reverse pass
+    P.cf_set_materials(ctx, ids, m.mu, m.kappa, m.w)
     P.cf_tape_clear(ctx)
     P.cf_plates_set(ctx, KP, z_lo, z_lo + 2 * radius * 0.9)
     P.cf_relax(ctx, 10, DT, 0.8, record=True)
-    P.cf_set_material(ctx, ids[1], 0.9, 15.0, 0.2)
+    P.cf_set_material(ctx, ids[1], 0.9 * m.mu[1], m.kappa[1], m.w[1])
     with pytest.raises(P.CellFSIError) as e:
         P.cf_relax_adjoint(ctx, np.ones(2))
     assert e.value.name == "CF_ESTATE"
-    P.cf_set_material(ctx, ids[1], cells[1].mu, cells[1].kappa, cells[1].w)  # back as recorded
+    P.cf_set_material(ctx, ids[1], m.mu[1], m.kappa[1], m.w[1])  # back as recorded
     P.cf_relax_adjoint(ctx, np.ones(2))

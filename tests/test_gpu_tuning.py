@@ -80,7 +80,7 @@ def test_autotune_advances_like_cf_step(P):
     assert (shape["tile_x"], shape["tile_y"], shape["tile_z"]) in TILES
     assert shape["tet_block"] in (64, 128, 256) and shape["gather_block"] in (64, 128, 256)
     assert shape["interp_block"] in (64, 128, 256) and shape["fused"] in (0, 1) and shape["near_rows"] in (0, 1)
-    assert shape["far_spec"] in (0, 1) and shape["tet_pairs"] in (0, 1) and shape["pop_l2"] in (0, 1)
+    assert shape["far_spec"] in (0, 1) and shape["tet_form"] in (0, 1, 2) and shape["pop_l2"] in (0, 1)
     assert P.cf_get_launch_shape(ctx) == shape
     sim = oracle.Coupled(wl)
     sim.step(46)

@@ -114,7 +114,7 @@ def test_static_entry_point_near_capacity(P):
     cid = P.cf_mesh_init(ctx, x, t, None)
     buf = CallerBuffers(P, torch, ctx, cid, x)
     for seed, (mu, kappa, w) in ((5, (1e-3, 5e-2, 0.3)), (6, (4e-4, 2e-2, 0.9))):
-        y = perturb(x, 0.2, seed)
+        y = perturb(x, 0.05, seed)
         got = buf.forces(P, y, mu, kappa, w)
         assert np.isfinite(got).all()
         assert _rel(got, _oracle_forces(x, t, y, mu, kappa, w)) <= TOL
