@@ -73,19 +73,21 @@ cudaError_t clear_slot(const cf_ctx *c, const RegionSlot &r, cudaStream_t s) {
 int near_grid(const cf_ctx *c) { return 8 * c->sms; }
 int chain_grid(const cf_ctx *c) { return 4 * c->sms; }
 
-// Work items of the fused cell chain: the tet items of the cells in order,
-// with the vertex-sum items of a cell placed LAG items after its last tet
-// item (by then its tets are most likely done, so the sums rarely wait),
-// then the remaining vertex-sum items. Every item a vertex-sum item waits
-// for comes before it.
+// Work items of the fused cell chain: the region items over all vertices
+// (skipped by the kernel when the interpolation marks the region), then the
+// tet items of the cells in order, with the vertex-sum items of a cell
+// placed LAG items after its last tet item (by then its tets are most likely
+// done, so the sums rarely wait), then the remaining vertex-sum items. Every
+// item a vertex-sum item waits for comes before it.
 cf_status build_chain_items(cf_ctx *c) {
     std::vector<int4> items;
     // item sizes: small meshes keep every block busy, large ones keep the
     // item count (one claim each) low
     const int grid = chain_grid(c);
     auto size_for = [&](int n, int lo, int hi) { return std::max(lo, std::min(hi, n / (2 * grid) / lo * lo)); };
-    const int TB = size_for(c->T, 256, 1024), GB = size_for(c->V, 64, 256);
+    const int RB = size_for(c->V, 256, 1024), TB = size_for(c->T, 256, 1024), GB = size_for(c->V, 64, 256);
     const size_t LAG = 2 * (size_t)grid;
+    for (int v = 0; v < c->V; v += RB) items.push_back(make_int4(0, 0, v, std::min(c->V, v + RB)));
     const int C = (int)c->cells.size();
     std::vector<int> need(C, 0);
     std::vector<size_t> last_tet(C, 0);
@@ -122,15 +124,19 @@ cf_status build_chain_items(cf_ctx *c) {
 }
 
 // K1 + K23 of one step on stream s: the fused persistent launch, or the two
-// separate kernels.
-cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, cudaStream_t s) {
+// separate kernels. Unless the interpolation marks the regions (mark_k5),
+// K1 marks the next step's region into acc.
+cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, const RegionSlot &acc,
+                              cudaStream_t s) {
+    const RegionSlot none{nullptr, nullptr, nullptr};
     if (sh.fused) {
         cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
         if (e != cudaSuccess) return e;
-        return launch_cell_chain(m, c->u[p], c->F, c->lp, c->d_err, c->chain_items, c->chain_nitems, c->chain_need,
-                                 c->chain_ctr, chain_grid(c), c->chain_spin_limit, s);
+        return launch_cell_chain(m, c->u[p], c->F, c->lp, sh.mark_k5 ? none : acc, c->d_err, c->chain_items,
+                                 c->chain_nitems, c->chain_need, c->chain_ctr, chain_grid(c), c->chain_spin_limit, s);
     }
-    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form);
+    cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form, sh.mark_k5 ? nullptr : &c->lp,
+                                     sh.mark_k5 ? nullptr : &acc);
     if (e != cudaSuccess) return e;
     return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
 }
@@ -145,16 +151,25 @@ void set_tiles(LbmParams &p, int k) {
     p.ntz = (p.nz + (1 << p.tlz) - 1) >> p.tlz;
 }
 
+// The lattice fields that follow the launch shape: tiles, L2 caching of
+// FP32 populations, node pairs of the 16-bit formats.
+void shape_to_lbm(LbmParams &p, const Shape &sh) {
+    set_tiles(p, sh.tile);
+    p.l2 = sh.pop_l2;
+    p.pairs = sh.pop_pairs;
+}
+
 // Enqueue `nsteps` steps starting at parity p0 and phase s0 on two streams:
 // sf carries the far-field stream-collide, sc the cell chain and the near
 // field. ev holds 2 * nsteps + 1 events for the cross-stream dependencies:
 //   far(t)   after far(t-1) [sf order] and near(t-1)
 //   K5(t-1) -> K1(t) -> K23(t) after near(t-1) [sc order]
 //   near(t)  after K23(t) [sc order] and far(t-1) (it reads far nodes' halo)
-// so near(t) and the cell chain overlap far(t). K5(t-1), which computes
-// y^t, also marks the region of step t + 1 (its slot is cleared just
-// before); the first step of a call marks both its own region and the next
-// one from the current positions.
+// so near(t) and the cell chain overlap far(t). The region of step t + 1
+// (the support of y^t grown by one node) is marked by K1(t) or, with the
+// launch shape's mark_k5, by K5(t-1), which computes y^t; the first step of
+// a call marks its own region from the current positions (and, with
+// mark_k5, the next one too).
 cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaStream_t sf, cudaStream_t sc,
                         cudaEvent_t *ev) {
     const MeshView m = view(c);
@@ -172,11 +187,12 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     }
     cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
     const bool first = kind == Kind::First || kind == Kind::Single;
+    const RegionSlot none{nullptr, nullptr, nullptr};
     if (first) {
         const RegionSlot use = region_slot(c, s0), acc = accum_slot(c, s0);
         CUDA_TRY(c, clear_slot(c, use, sf));
-        CUDA_TRY(c, clear_slot(c, acc, sf));
-        CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, acc, sf));
+        if (sh.mark_k5) CUDA_TRY(c, clear_slot(c, acc, sf));
+        CUDA_TRY(c, launch_mark_region(m, c->u[p0], c->lp, use, sh.mark_k5 ? acc : none, sf));
     }
     CUDA_TRY(c, cudaEventRecord(fork, sf));
     CUDA_TRY(c, cudaStreamWaitEvent(sc, fork, 0));
@@ -186,12 +202,13 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[i - 1], 0));
         CUDA_TRY(c, launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, sf));
         CUDA_TRY(c, cudaEventRecord(ev_far[i], sf));
-        if (!(first && i == 0)) {  // K5 of the previous step (parity 1-p), marking this step's acc slot
-            CUDA_TRY(c, clear_slot(c, acc, sc));
+        if (!(first && i == 0)) {  // K5 of the previous step (parity 1-p), with mark_k5 marking acc
+            if (sh.mark_k5) CUDA_TRY(c, clear_slot(c, acc, sc));
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block,
-                                             acc));
+                                             sh.mark_k5 ? acc : none));
         }
-        CUDA_TRY(c, launch_chain_step(c, m, p, sh, sc));
+        if (!sh.mark_k5) CUDA_TRY(c, clear_slot(c, acc, sc));
+        CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
@@ -466,8 +483,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
         set_tiles(p, k);
         tmax = std::max(tmax, tiles_of(p));
     }
-    set_tiles(p, c->shape.tile);
-    p.l2 = c->shape.pop_l2;
+    shape_to_lbm(p, c->shape);
     c->region_bits_max = (tmax + 31) / 32;
     c->region_stride = (32 + c->region_bits_max + tmax + 31) / 32 * 32;
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
@@ -898,20 +914,24 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             const int sph = (int)((c->tstep) % 3);
             const RegionSlot use = region_slot(c, sph), accm = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
-            if (cells && t == 0) {  // regions of the first step and the next: not timed
+            const RegionSlot none{nullptr, nullptr, nullptr};
+            if (cells && t == 0) {  // region of the first step (and, with mark_k5, the next): not timed
                 e = clear_slot(c, use, s);
-                if (e == cudaSuccess) e = clear_slot(c, accm, s);
-                if (e == cudaSuccess) e = launch_mark_region(m, c->u[p], c->lp, use, accm, s);
+                if (e == cudaSuccess && sh.mark_k5) e = clear_slot(c, accm, s);
+                if (e == cudaSuccess) e = launch_mark_region(m, c->u[p], c->lp, use, sh.mark_k5 ? accm : none, s);
             }
-            if (cells && t > 0 && e == cudaSuccess) e = clear_slot(c, accm, s);
+            if (cells && t > 0 && sh.mark_k5 && e == cudaSuccess) e = clear_slot(c, accm, s);
             cudaEventRecord(E[0], s);
             if (cells && t > 0 && e == cudaSuccess)
                 e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s, sh.interp_block,
-                                         accm);
+                                         sh.mark_k5 ? accm : none);
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
-                if (sh.fused) e = launch_chain_step(c, m, p, sh, s);
-                else e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form);
+                if (!sh.mark_k5) e = clear_slot(c, accm, s);
+                if (e == cudaSuccess && sh.fused) e = launch_chain_step(c, m, p, sh, accm, s);
+                if (e == cudaSuccess && !sh.fused)
+                    e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form,
+                                         sh.mark_k5 ? nullptr : &c->lp, sh.mark_k5 ? nullptr : &accm);
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)
@@ -986,8 +1006,7 @@ cf_status region_nodes(cf_ctx *c, long long *out) {
 // instantiated before the timed launch. Leaves sh as the context's shape.
 cf_status timed_call(cf_ctx *c, int n, const Shape &sh, double *ms) {
     c->shape = sh;
-    set_tiles(c->lp, sh.tile);
-    c->lp.l2 = sh.pop_l2;
+    shape_to_lbm(c->lp, sh);
     drop_graphs(c);
     cf_status st = schedule_steps(c, n, false);
     if (st != CF_OK) return st;
@@ -1047,6 +1066,8 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[8] = sh.far_spec;
     shape[9] = sh.tet_form;
     shape[10] = sh.pop_l2;
+    shape[11] = sh.pop_pairs;
+    shape[12] = sh.mark_k5;
     return CF_OK;
 }
 
@@ -1078,13 +1099,14 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.tet_form = shape[9];
     if (shape[10] != 0 && shape[10] != 1) return fail(c, CF_EINVAL, "pop_l2 must be 0 or 1");
     sh.pop_l2 = shape[10];
+    if (shape[11] != 0 && shape[11] != 1) return fail(c, CF_EINVAL, "pop_pairs must be 0 or 1");
+    sh.pop_pairs = shape[11];
+    if (shape[12] != 0 && shape[12] != 1) return fail(c, CF_EINVAL, "mark_k5 must be 0 or 1");
+    sh.mark_k5 = shape[12];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
-    if (c->lbm_ready) {
-        set_tiles(c->lp, sh.tile);
-        c->lp.l2 = sh.pop_l2;
-    }
+    if (c->lbm_ready) shape_to_lbm(c->lp, sh);
     return CF_OK;
 }
 
@@ -1120,6 +1142,8 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::far_spec, {0, 1}},
             {&Shape::tet_form, {0, 1, 2}},
             {&Shape::pop_l2, {0, 1}},
+            {&Shape::pop_pairs, {1, 0}},
+            {&Shape::mark_k5, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}},
             {&Shape::gather_block, {64, 128, 256}},
             {&Shape::interp_block, {64, 128, 256}},
@@ -1136,8 +1160,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
                 const cf_status st = timed_call(c, steps_per_candidate, sh, &t);
                 if (st != CF_OK) {
                     c->shape = start;
-                    set_tiles(c->lp, start.tile);
-                    c->lp.l2 = start.pop_l2;
+                    shape_to_lbm(c->lp, start);
                     drop_graphs(c);
                     return st;
                 }
@@ -1149,8 +1172,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             best.*k.field = vbest;
         }
         c->shape = best;
-        set_tiles(c->lp, best.tile);
-        c->lp.l2 = best.pop_l2;
+        shape_to_lbm(c->lp, best);
         drop_graphs(c);
     }
     return shape_out ? cf_get_launch_shape(c, shape_out) : CF_OK;

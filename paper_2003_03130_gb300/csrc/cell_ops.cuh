@@ -1,6 +1,7 @@
 // Per-element bodies of the cell kernels, shared by the separate launches
 // (csrc/tet_force.cu, csrc/ibm.cu) and the fused persistent chain
-// (csrc/chain.cu): tet corner forces, and the vertex sum with its spread.
+// (csrc/chain.cu): tet corner forces, the per-vertex region marking, and the
+// vertex sum with its spread.
 #pragma once
 
 #include "mr.cuh"
@@ -50,6 +51,18 @@ __device__ __forceinline__ void tet_corner_forces(const MeshView &m, const float
     TetIn in;
     tet_load(m, u, t, in);
     tet_forces_store(m, in, err, t);
+}
+
+// The per-vertex part of K1 when it marks the region: add the next step's
+// force region (the support of x + u grown by one node) to mark. Whether this
+// step's support lies in this step's region follows from the step before
+// moving every vertex by less than one spacing, which K5 checks.
+template <int W>
+__device__ __forceinline__ void mark_vertex(const MeshView &m, const float4 *__restrict__ u, const LbmParams &lp,
+                                            int v, const RegionSlot &mark) {
+    Support s;
+    if (support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), lp.ny, s))  // else K23 reports it
+        mark_region<W>(s, lp, mark);
 }
 
 // Corner-force load: from L2 (FC_L2) when the forces were written by other

@@ -1,9 +1,10 @@
 // K1 + K23 as one persistent launch over all cells (the batched form of the
-// cell chain): the tet corner forces (Sec. 3.1) and the vertex sums with
-// their spread (Sec. 6), for cells of any size.
+// cell chain): the per-vertex region marking (unless the interpolation of the
+// step before marks the region), the tet corner forces (Sec. 3.1) and the
+// vertex sums with their spread (Sec. 6), for cells of any size.
 //
-// Blocks take work items in a fixed order from one counter. Tet items never
-// wait; a vertex-sum item of cell c waits until every tet item of
+// Blocks take work items in a fixed order from one counter. Tet and region
+// items never wait; a vertex-sum item of cell c waits until every tet item of
 // cell c is done. The host orders the items so that every item an
 // item waits for comes before it; the block holding an earlier item is
 // therefore already running and never waits itself, so the waits end even
@@ -35,7 +36,7 @@ __device__ __forceinline__ bool wait_count(const int *p, int target, long long s
 
 template <int W>
 __global__ void __launch_bounds__(kChainBlock, 4)
-    k_cell_chain(MeshView m, const float4 *__restrict__ u, float4 *F, LbmParams lp, unsigned *err,
+    k_cell_chain(MeshView m, const float4 *__restrict__ u, float4 *F, LbmParams lp, RegionSlot mark, unsigned *err,
                  const int4 *__restrict__ items, int nitems, const int *__restrict__ need, int *counters,
                  long long spin_limit) {
     __shared__ int4 item;
@@ -59,7 +60,10 @@ __global__ void __launch_bounds__(kChainBlock, 4)
         const int4 x = item;
         if (x.x < 0) break;
         if (ready) {
-            if (x.x == 1) {
+            if (x.x == 0) {
+                if (mark.bits)
+                    for (int v = x.z + threadIdx.x; v < x.w; v += kChainBlock) mark_vertex<W>(m, u, lp, v, mark);
+            } else if (x.x == 1) {
                 for (int t = x.z + threadIdx.x; t < x.w; t += kChainBlock) tet_corner_forces(m, u, err, t);
             } else {
                 for (int v0 = x.z; v0 < x.w; v0 += kChainBlock / 4) {  // the whole block takes each round
@@ -74,15 +78,15 @@ __global__ void __launch_bounds__(kChainBlock, 4)
     }
 }
 
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp, unsigned *err,
-                              const int4 *items, int nitems, const int *need, int *counters, int blocks,
-                              long long spin_limit, cudaStream_t s) {
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
+                              const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
+                              int *counters, int blocks, long long spin_limit, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     const int g = blocks < nitems ? blocks : nitems;
     if (lp.dw == 4)
-        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, F, lp, err, items, nitems, need, counters, spin_limit);
+        k_cell_chain<4><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters, spin_limit);
     else
-        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, F, lp, err, items, nitems, need, counters, spin_limit);
+        k_cell_chain<2><<<g, kChainBlock, 0, s>>>(m, u, F, lp, mark, err, items, nitems, need, counters, spin_limit);
     return cudaGetLastError();
 }
 

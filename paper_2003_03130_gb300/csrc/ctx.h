@@ -41,6 +41,9 @@ struct Shape {
     int far_spec = 0;   // far field issues its loads before the region test resolves
     int tet_form = 0;   // force kernel: one thread per tet (0), two tets per thread (1), four lanes per tet (2)
     int pop_l2 = 0;     // FP32 far and near fields cache populations in L2 instead of streaming them
+    int pop_pairs = 1;  // 16-bit formats, nx even: two nodes per thread in the row-form stream-collide
+    int mark_k5 = 0;    // the interpolation (eight lanes per vertex) marks the region of the step after next,
+                        // instead of the force launch (one thread per vertex) the next step's
 };
 
 }  // namespace cf

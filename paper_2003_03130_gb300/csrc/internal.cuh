@@ -76,6 +76,7 @@ struct LbmParams {
     int dw;             // delta kernel: support width 2 (trilinear) or 4 (Peskin)
     int l2;             // FP32 far and near fields: populations cached in L2 at normal priority
                         // (1) instead of streamed with evict-first hints (0)
+    int pairs;          // 16-bit formats, nx even: two nodes per thread in the row-form kernels
     // force-region tiles of 2^tlx x 2^tly x 2^tlz = 256 nodes (x fastest;
     // the last tile of an axis may stick out of the lattice), ntx * nty * ntz
     // of them
@@ -177,11 +178,12 @@ __host__ __device__ __forceinline__ bool region_has(const unsigned *__restrict__
 }
 
 // Add tile t: the first thread to set its bit appends it to the list. The
-// read from L2 (where the atomics land; an L1 line could be stale) skips the
-// atomic for the (many) tiles already in.
+// plain read skips the atomic for the (many) tiles already in (a stale L1
+// line can only miss a bit set during this launch: then the atomic finds it
+// set and nothing is appended).
 __device__ __forceinline__ void region_add(const RegionSlot &r, int t) {
     const unsigned bit = 1u << (t & 31);
-    if (__ldcg(r.bits + (t >> 5)) & bit) return;
+    if (r.bits[t >> 5] & bit) return;
     if (!(atomicOr(r.bits + (t >> 5), bit) & bit)) r.tiles[atomicAdd(r.count, 1)] = t;
 }
 
@@ -303,9 +305,12 @@ cudaError_t launch_get_forces(const float4 *fv, int v0, int nv, double *out, cud
 // K1: elastic corner forces of all tets at displacements u. form 0: one
 // thread per tet; 1: two tets per thread (both tets' loads issued before
 // either is computed); 2: four lanes per tet (needs the packed rows m.Bp,
-// else one thread per tet).
+// else one thread per tet). With lp and mark_out non-null the same launch
+// also runs one thread per vertex (blocks at the front) that adds the
+// tiles of the next step's force region (the support of x + u grown by one
+// node) to mark_out.
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, cudaStream_t s, int block = 0,
-                             int form = 0);
+                             int form = 0, const LbmParams *lp = nullptr, const RegionSlot *mark_out = nullptr);
 // Per-tet V_0 U of tets [t0, t1) reduced in a fixed order into *out (double).
 cudaError_t launch_energy(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
@@ -328,13 +333,15 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
                                const RegionSlot &r2, cudaStream_t s);
 // K1 + K23 fused (csrc/chain.cu): one persistent launch that runs the work
 // items of the cell chain in order: items[i] = (kind, cell, begin, end) with
-// kind 1 = corner forces of tets [begin, end) of `cell`, 2 = vertex sums +
-// spread of vertices [begin, end) of `cell`. A kind-2 item waits until the
-// need[cell] kind-1 items of its cell are done, giving up after spin_limit
-// polls (ERR_WAIT); counters[2 + ncells] must be zero at launch.
-cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp, unsigned *err,
-                              const int4 *items, int nitems, const int *need, int *counters, int blocks,
-                              long long spin_limit, cudaStream_t s);
+// kind 0 = region marking of vertices [begin, end) into mark (skipped when
+// mark.bits is null), 1 = corner forces of tets [begin, end) of `cell`, 2 =
+// vertex sums + spread of vertices [begin, end) of `cell`. A kind-2 item
+// waits until the need[cell] kind-1 items of its cell are done, giving up
+// after spin_limit polls (ERR_WAIT); counters[2 + ncells] must be zero at
+// launch.
+cudaError_t launch_cell_chain(const MeshView &m, const float4 *u, float4 *F, const LbmParams &lp,
+                              const RegionSlot &mark, unsigned *err, const int4 *items, int nitems, const int *need,
+                              int *counters, int blocks, long long spin_limit, cudaStream_t s);
 // K4: pull stream + BGK collide with Guo forcing, fin -> fout, every node, no
 // force field (fluid-only runs). Population buffers are in the format p.fmt.
 // Every stream-collide launch reads the step's rounding seed from seed[0];

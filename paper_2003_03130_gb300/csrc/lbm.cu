@@ -23,7 +23,9 @@
 //
 // One node per thread: 19 independent coalesced loads per node (x-shifted
 // rows are off by one word; neighbouring warps share the lines in L2), the
-// collide, 19 coalesced stores. The whole-lattice and far-field kernels take
+// collide, 19 coalesced stores. The 16-bit formats also come in a pair form
+// (two x-neighbours per thread, 32-bit population access, packed FP32
+// collide; see "node pairs" below). The whole-lattice and far-field kernels take
 // rows of 128 nodes along x; with cells the lattice is also cut into tiles of
 // 256 nodes (x fastest), the unit of the force region, and the near field
 // runs two blocks of 128 threads per region tile.
@@ -294,6 +296,238 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
     for (int q = 0; q < 19; ++q) Pop<T>::template st<CS>(fout + q * N + n, d[q]);
 }
 
+// ---------------------------------------------------------------- node pairs
+// 16-bit storage, two neighbouring nodes (x0, x0 + 1) per thread, x0 even
+// (nx even): one 32-bit load or store moves a population of both nodes, and
+// the collide runs on packed FP32 pairs (f32x2 arithmetic, sm_100 and
+// later), so that a thread issues about half the instructions per node of
+// the one-node form (which is bound by instruction issue at 2 bytes per
+// population, not by HBM). A pull along x (c_x = +1: from x - 1; c_x = -1:
+// from x + 1) straddles two aligned pairs of the source row: both are loaded
+// (the second lies in the same L1/L2 sectors as a neighbouring thread's) and
+// the middle two values are taken with one byte permute. Both nodes of a
+// pair lie in the same force-region tile (tiles are at least 8 nodes wide
+// in x).
+__device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+
+// c . v for a lattice vector whose first nonzero component is +1 (only
+// nonzero components enter).
+template <int a, int b, int c>
+__device__ __forceinline__ float2 cdot2(float2 x, float2 y, float2 z) {
+    static_assert(a > 0 || (a == 0 && b > 0) || (a == 0 && b == 0 && c > 0), "first component must be +1");
+    if constexpr (a != 0 && b != 0) return b > 0 ? add2(x, y) : sub2(x, y);
+    else if constexpr (a != 0 && c != 0) return c > 0 ? add2(x, z) : sub2(x, z);
+    else if constexpr (b != 0 && c != 0) return c > 0 ? add2(y, z) : sub2(y, z);
+    else if constexpr (a != 0) return x;
+    else if constexpr (b != 0) return y;
+    else return z;
+}
+
+__host__ __device__ constexpr int first_nonzero(int q) { return cx(q) != 0 ? cx(q) : cy(q) != 0 ? cy(q) : cz(q); }
+
+struct WClass2 {
+    float2 c0, e45, o3;
+    float g9, g3;
+};
+
+__device__ __forceinline__ WClass2 wclass2(float w, float2 drho, float2 rho, float2 usq15, float2 uF, float om, float g) {
+    WClass2 k;
+    const float2 wr = mul2(f2(w), rho);
+    k.c0 = fma2(f2(-3.f * g * w), uF, mul2(f2(om), sub2(mul2(f2(w), drho), mul2(wr, usq15))));
+    k.e45 = mul2(f2(4.5f * om), wr);
+    k.o3 = mul2(f2(3.f * om), wr);
+    k.g9 = 9.f * g * w;
+    k.g3 = 3.f * g * w;
+    return k;
+}
+
+// The pair (A, opp(A)) of both nodes, as collide_pair, with the sign of c
+// chosen so that its first nonzero component is +1 (P is even in c, Q odd).
+template <int A>
+__device__ __forceinline__ void collide_pair2(float2 (&d)[19], const WClass2 &k, float2 om1, float2 ux, float2 uy,
+                                              float2 uz, float2 Fx, float2 Fy, float2 Fz) {
+    constexpr int Ap = first_nonzero(A) > 0 ? A : opp(A), Bp = opp(Ap);
+    const float2 cu = cdot2<cx(Ap), cy(Ap), cz(Ap)>(ux, uy, uz);
+    const float2 cF = cdot2<cx(Ap), cy(Ap), cz(Ap)>(Fx, Fy, Fz);
+    const float2 P = fma2(cu, fma2(f2(k.g9), cF, mul2(k.e45, cu)), k.c0);
+    const float2 Q = fma2(k.o3, cu, mul2(f2(k.g3), cF));
+    const float2 a = fma2(om1, d[Ap], add2(P, Q));
+    const float2 b = fma2(om1, d[Bp], sub2(P, Q));
+    d[Ap] = a;
+    d[Bp] = b;
+}
+
+// collide<T> for two nodes at once (the same operations per node, in packed
+// arithmetic); returns u(t) of both.
+template <class T>
+__device__ __forceinline__ void collide2(float2 (&d)[19], float2 Fx, float2 Fy, float2 Fz, const LbmParams &p,
+                                         float2 &ux, float2 &uy, float2 &uz) {
+    constexpr float s0 = pop_scale<T>(0), s1 = pop_scale<T>(1), s2 = pop_scale<T>(7);
+    const float2 face = add2(add2(add2(d[1], d[2]), add2(d[3], d[4])), add2(d[5], d[6]));
+    const float2 edge = add2(add2(add2(add2(d[7], d[8]), add2(d[9], d[10])), add2(add2(d[11], d[12]), add2(d[13], d[14]))),
+                             add2(add2(d[15], d[16]), add2(d[17], d[18])));
+    const float2 drho = fma2(edge, f2(1.f / s2), fma2(face, f2(1.f / s1), mul2(d[0], f2(1.f / s0))));
+    const float2 ex = add2(add2(sub2(d[15], d[7]), sub2(d[16], d[8])), add2(sub2(d[17], d[9]), sub2(d[18], d[10])));
+    const float2 ey = add2(add2(sub2(d[10], d[7]), sub2(d[13], d[11])), add2(sub2(d[14], d[12]), sub2(d[18], d[15])));
+    const float2 ez = add2(add2(sub2(d[9], d[8]), sub2(d[12], d[11])), add2(sub2(d[14], d[13]), sub2(d[17], d[16])));
+    const float2 jx = fma2(ex, f2(1.f / s2), mul2(sub2(d[1], d[2]), f2(1.f / s1)));
+    const float2 jy = fma2(ey, f2(1.f / s2), mul2(sub2(d[3], d[4]), f2(1.f / s1)));
+    const float2 jz = fma2(ez, f2(1.f / s2), mul2(sub2(d[5], d[6]), f2(1.f / s1)));
+    const float2 rho = add2(f2(1.f), drho);
+    const float2 ir = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
+    ux = mul2(fma2(f2(0.5f), Fx, jx), ir);
+    uy = mul2(fma2(f2(0.5f), Fy, jy), ir);
+    uz = mul2(fma2(f2(0.5f), Fz, jz), ir);
+    const float2 usq15 = mul2(f2(1.5f), fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+    const float2 uF = fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)));
+    const float om = p.omega, g = p.guo;
+    const float2 om1 = f2(1.f - om);
+    const WClass2 k0 = wclass2((1.f / 3.f) * s0, drho, rho, usq15, uF, om, g);
+    const WClass2 k1 = wclass2((1.f / 18.f) * s1, drho, rho, usq15, uF, om, g);
+    const WClass2 k2 = wclass2((1.f / 36.f) * s2, drho, rho, usq15, uF, om, g);
+    d[0] = fma2(om1, d[0], k0.c0);
+    collide_pair2<1>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<3>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<5>(d, k1, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<7>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<8>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<9>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<10>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<11>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+    collide_pair2<12>(d, k2, om1, ux, uy, uz, Fx, Fy, Fz);
+}
+
+// 32-bit pair access: the raw bits of two 16-bit populations (lower half =
+// the even node), their FP32 values, and the rounded or stochastically
+// rounded conversion back.
+__device__ __forceinline__ unsigned ld_pair(const void *p) { return __ldcs(static_cast<const unsigned *>(p)); }
+__device__ __forceinline__ void st_pair(void *p, unsigned v) { __stcs(static_cast<unsigned *>(p), v); }
+
+template <class T>
+__device__ __forceinline__ float2 unpack2(unsigned w);
+template <>
+__device__ __forceinline__ float2 unpack2<__half>(unsigned w) {
+    return make_float2(__half2float(__ushort_as_half((unsigned short)(w & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(w >> 16))));
+}
+template <>
+__device__ __forceinline__ float2 unpack2<__nv_bfloat16>(unsigned w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+// Round to nearest: one packing conversion for both values.
+template <class T>
+__device__ __forceinline__ unsigned pack2_rn(float2 v);
+template <>
+__device__ __forceinline__ unsigned pack2_rn<__half>(float2 v) {
+    unsigned d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.y), "f"(v.x));
+    return d;
+}
+template <>
+__device__ __forceinline__ unsigned pack2_rn<__nv_bfloat16>(float2 v) {
+    unsigned d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.y), "f"(v.x));
+    return d;
+}
+
+// Stochastic rounding as in Pop<T>::st_sr, both values at once: the dither
+// bits below the last kept mantissa bit (dlo for the even node, dhi for the
+// odd one) are added to each FP32 pattern, then both are truncated (round
+// toward zero) in one packing conversion.
+template <class T>
+__device__ __forceinline__ unsigned pack2_sr(float2 v, unsigned dlo, unsigned dhi) {
+    const float hi = __uint_as_float(__float_as_uint(v.y) + dhi), lo = __uint_as_float(__float_as_uint(v.x) + dlo);
+    unsigned d;
+    if constexpr (std::is_same<T, __half>::value)
+        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// Nodes (x0, x0 + 1) of row (y, z): pull, collide, store, as lbm_node.
+template <class T, bool WALL, bool HAS_F>
+__device__ __forceinline__ void lbm_pair(const T *__restrict__ fin, T *__restrict__ fout, float4 *__restrict__ F,
+                                         const LbmParams &p, int x0, int y, int z, float4 *__restrict__ vel,
+                                         unsigned seed) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int N = (int)p.N;
+    const int xm = x0 == 0 ? nx - 2 : x0 - 2, xp = x0 + 2 == nx ? 0 : x0 + 2;  // neighbouring pairs
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const int n0 = x0 + nx * (y + ny * z);
+
+    float2 d[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z);
+        const int sy = y - cy(q);
+        if (WALL && ((cy(q) == 1 && y == 0) || (cy(q) == -1 && y == ny - 1))) {
+            const float uw = cy(q) == 1 ? p.uw_lo : p.uw_hi;
+            d[q] = unpack2<T>(ld_pair(fin + opp(q) * N + n0));
+            if (cx(q) != 0) d[q] = add2(d[q], f2((6.f * wq(q) * cx(q) * pop_scale<T>(q)) * uw));
+        } else {
+            const T *row = fin + q * N + nx * (sy + ny * sz);
+            unsigned w;
+            if (cx(q) == 1)
+                w = __byte_perm(ld_pair(row + xm), ld_pair(row + x0), 0x5432);  // (x0 - 1, x0)
+            else if (cx(q) == -1)
+                w = __byte_perm(ld_pair(row + x0), ld_pair(row + xp), 0x5432);  // (x0 + 1, x0 + 2)
+            else
+                w = ld_pair(row + x0);
+            d[q] = unpack2<T>(w);
+        }
+    }
+    float2 Fx = f2(p.gx), Fy = f2(p.gy), Fz = f2(p.gz);
+    bool spread0 = false, spread1 = false;
+    if (HAS_F) {
+        const float4 a = __ldcg(F + n0), b = __ldcg(F + n0 + 1);
+        spread0 = a.x != 0.f || a.y != 0.f || a.z != 0.f;
+        spread1 = b.x != 0.f || b.y != 0.f || b.z != 0.f;
+        Fx = add2(Fx, make_float2(a.x, b.x));
+        Fy = add2(Fy, make_float2(a.y, b.y));
+        Fz = add2(Fz, make_float2(a.z, b.z));
+    }
+    float2 ux, uy, uz;
+    collide2<T>(d, Fx, Fy, Fz, p, ux, uy, uz);
+    if (HAS_F) {  // consumed: the next step spreads onto zeros
+        if (spread0) F[n0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (spread1) F[n0 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (vel) {
+        vel[n0] = make_float4(ux.x, uy.x, uz.x, 0.f);
+        vel[n0 + 1] = make_float4(ux.y, uy.y, uz.y, 0.f);
+    }
+    if (p.sr) {
+        // random bits per pair and population: the Weyl step h + q 0x9e3779b9
+        // of a per-pair hash; its top K bits dither the odd node, the next K
+        // bits the even node (K = dropped mantissa bits). A non-finite node
+        // (any NaN input makes its u NaN) converts without dither.
+        constexpr int K = Pop<T>::kDropped;
+        constexpr unsigned low = (1u << K) - 1u;
+        const unsigned h = mix32((unsigned)n0 ^ mix32(seed));
+        const unsigned m_lo = isfinite(ux.x + uy.x + uz.x) ? low : 0u, m_hi = isfinite(ux.y + uy.y + uz.y) ? low : 0u;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const unsigned r = h + (unsigned)q * 0x9e3779b9u;
+            st_pair(fout + q * N + n0, pack2_sr<T>(d[q], (r >> (32 - 2 * K)) & m_lo, (r >> (32 - K)) & m_hi));
+        }
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 19; ++q) st_pair(fout + q * N + n0, pack2_rn<T>(d[q]));
+}
+
 // ---------------------------------------------------------------- kernels
 // Whole lattice, no force field (fluid-only runs).
 template <class T>
@@ -394,6 +628,72 @@ __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict_
     }
 }
 
+// ---------------------------------------------------------------- pair kernels
+// The 16-bit storage formats with nx even: the whole-lattice, far-field and
+// row-form near-field kernels with two nodes per thread (lbm_pair), rows of
+// up to 64 pairs per block so that y and z stay uniform over a block.
+template <class T>
+__global__ void __launch_bounds__(64) k_lbm_pairs(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
+                                                  const unsigned *__restrict__ seed_in,
+                                                  unsigned *__restrict__ seed_out) {
+    const unsigned seed = *seed_in;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *seed_out = seed + 1u;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (y > 0 && y < p.ny - 1)
+        lbm_pair<T, false, false>(fin, fout, nullptr, p, x0, y, z, nullptr, seed);
+    else
+        lbm_pair<T, true, false>(fin, fout, nullptr, p, x0, y, z, nullptr, seed);
+}
+
+template <class T>
+__global__ void __launch_bounds__(64) k_lbm_far_pairs(const T *__restrict__ fin, T *__restrict__ fout, LbmParams p,
+                                                      const unsigned *__restrict__ bits,
+                                                      const unsigned *__restrict__ seed_in) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (region_has(bits, tile_index(p, x0 >> p.tlx, y >> p.tly, z >> p.tlz))) return;
+    const unsigned seed = *seed_in;
+    if (y > 0 && y < p.ny - 1)
+        lbm_pair<T, false, false>(fin, fout, nullptr, p, x0, y, z, nullptr, seed);
+    else
+        lbm_pair<T, true, false>(fin, fout, nullptr, p, x0, y, z, nullptr, seed);
+}
+
+template <class T>
+__global__ void __launch_bounds__(64) k_lbm_near_pairs(const T *__restrict__ fin, T *__restrict__ fout,
+                                                       float4 *__restrict__ F, LbmParams p,
+                                                       const unsigned *__restrict__ bits, float4 *__restrict__ vel,
+                                                       const unsigned *__restrict__ seed_in,
+                                                       unsigned *__restrict__ seed_out) {
+    const unsigned seed = *seed_in;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *seed_out = seed + 1u;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= p.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (!region_has(bits, tile_index(p, x0 >> p.tlx, y >> p.tly, z >> p.tlz))) return;
+    if (y > 0 && y < p.ny - 1)
+        lbm_pair<T, false, true>(fin, fout, F, p, x0, y, z, vel, seed);
+    else
+        lbm_pair<T, true, true>(fin, fout, F, p, x0, y, z, vel, seed);
+}
+
+// Grid of the pair kernels: up to 64 pairs per block along x.
+static dim3 pair_grid(const LbmParams &p, int &bx) {
+    const int pairs = p.nx / 2;
+    bx = pairs < 64 ? pairs : 64;
+    return dim3((pairs + bx - 1) / bx, p.ny, p.nz);
+}
+
+// The pair form applies to 16-bit storage with nx even, when the launch
+// shape asks for it.
+template <class T>
+static bool use_pairs(const LbmParams &p) {
+    return sizeof(T) == 2 && p.pairs && p.nx % 2 == 0;
+}
+
 // rho and u(t) on every node after a step. On the last step's force region
 // (bits; null: none) u(t) is the value the near field stored (vel): the force
 // field there has been consumed. Elsewhere it follows from the post-collision
@@ -443,6 +743,14 @@ size_t pop_bytes(int fmt) { return fmt == POP_F32 ? 4 : 2; }
 template <class T>
 static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, const unsigned *seed, unsigned *next_seed,
                          cudaStream_t s) {
+    if constexpr (sizeof(T) == 2) {
+        if (use_pairs<T>(p)) {
+            int bx;
+            const dim3 grid = pair_grid(p, bx);
+            k_lbm_pairs<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, seed, next_seed);
+            return cudaGetLastError();
+        }
+    }
     const int bx = p.nx < 128 ? p.nx : 128;
     dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
     k_lbm<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, seed, next_seed);
@@ -452,6 +760,14 @@ static cudaError_t lbm_t(const void *fin, void *fout, const LbmParams &p, const 
 template <class T>
 static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const unsigned *bits, const unsigned *seed,
                          bool spec, cudaStream_t s) {
+    if constexpr (sizeof(T) == 2) {
+        if (use_pairs<T>(p)) {
+            int bx;
+            const dim3 grid = pair_grid(p, bx);
+            k_lbm_far_pairs<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), p, bits, seed);
+            return cudaGetLastError();
+        }
+    }
     const int bx = p.nx < 128 ? p.nx : 128;
     dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
     if constexpr (std::is_same<T, float>::value) {
@@ -491,6 +807,15 @@ static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParam
             return cudaGetLastError();
         }
     }
+    if constexpr (sizeof(T) == 2) {
+        if (blocks <= 0 && use_pairs<T>(p)) {  // rows over the whole lattice, two nodes per thread
+            int bx;
+            const dim3 grid = pair_grid(p, bx);
+            k_lbm_near_pairs<T><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, bits,
+                                                     vel, seed, next_seed);
+            return cudaGetLastError();
+        }
+    }
     if (blocks <= 0) {  // rows over the whole lattice
         const int bx = p.nx < 128 ? p.nx : 128;
         dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
@@ -504,7 +829,8 @@ static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParam
 }
 
 bool is_lbm_far_kernel(const void *fn) {
-    return fn == (const void *)k_lbm_far<float, false, false> || fn == (const void *)k_lbm_far<float, true, false> ||
+    return fn == (const void *)k_lbm_far_pairs<__half> || fn == (const void *)k_lbm_far_pairs<__nv_bfloat16> ||
+           fn == (const void *)k_lbm_far<float, false, false> || fn == (const void *)k_lbm_far<float, true, false> ||
            fn == (const void *)k_lbm_far<float, false> || fn == (const void *)k_lbm_far<__half, false> ||
            fn == (const void *)k_lbm_far<__nv_bfloat16, false> || fn == (const void *)k_lbm_far<float, true> ||
            fn == (const void *)k_lbm_far<__half, true> || fn == (const void *)k_lbm_far<__nv_bfloat16, true>;

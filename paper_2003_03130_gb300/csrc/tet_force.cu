@@ -7,12 +7,31 @@
 
 namespace cf {
 
-// Six blocks of 256 per SM (40 registers, a 16-byte spill): this latency-
+// Region marking in the force launch: the first mark_blocks blocks run one
+// thread per vertex, marking the next step's force region. They come first
+// so that their short, latency-bound work runs under the tets' rather than
+// after it.
+__device__ __forceinline__ bool mark_block(const MeshView &m, const float4 *__restrict__ u, const LbmParams &lp,
+                                           const RegionSlot &mark, int mark_blocks) {
+    if ((int)blockIdx.x >= mark_blocks) return false;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < m.V) {
+        if (lp.dw == 4)
+            mark_vertex<4>(m, u, lp, v, mark);
+        else
+            mark_vertex<2>(m, u, lp, v, mark);
+    }
+    return true;
+}
+
+// Six blocks of 256 per SM (40 registers, a small spill): this latency-
 // bound kernel gains more from the extra resident warps than the spill costs
 // (tet forces of the 400-cell suspension 190.6 -> 178.5 us against 56
 // registers and four blocks).
-__global__ void __launch_bounds__(256, 6) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256, 6) k_tet_force(MeshView m, const float4 *__restrict__ u, unsigned *err,
+                                                   int mark_blocks, LbmParams lp, RegionSlot mark) {
+    if (mark_block(m, u, lp, mark, mark_blocks)) return;
+    const int t = (blockIdx.x - mark_blocks) * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
     tet_corner_forces(m, u, err, t);
 }
@@ -20,8 +39,10 @@ __global__ void __launch_bounds__(256, 6) k_tet_force(MeshView m, const float4 *
 // Two tets per thread, t and t + blockDim (coalesced either way): both tets'
 // loads are issued before either is computed, doubling the bytes a thread
 // has in flight in this latency-bound kernel.
-__global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 *__restrict__ u, unsigned *err) {
-    const int t0 = 2 * blockIdx.x * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
+__global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 *__restrict__ u, unsigned *err,
+                                                     int mark_blocks, LbmParams lp, RegionSlot mark) {
+    if (mark_block(m, u, lp, mark, mark_blocks)) return;
+    const int t0 = 2 * (blockIdx.x - mark_blocks) * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
     if (t0 >= m.T) return;
     TetIn a, b;
     tet_load(m, u, t0, a);
@@ -39,9 +60,11 @@ __global__ void __launch_bounds__(256, 2) k_tet_force2(MeshView m, const float4 
 // f^4 = -(f^1 + f^2 + f^3) from a second shuffle tree; each lane stores its
 // corner. Every lane of a warp takes part in the shuffles (tets past the end
 // compute on zeros and store nothing). Needs the packed rows (m.Bp).
-__global__ void __launch_bounds__(256, 4) k_tet_force4(MeshView m, const float4 *__restrict__ u, unsigned *err) {
+__global__ void __launch_bounds__(256, 4) k_tet_force4(MeshView m, const float4 *__restrict__ u, unsigned *err,
+                                                      int mark_blocks, LbmParams lp, RegionSlot mark) {
     constexpr unsigned kAll = 0xffffffffu;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mark_block(m, u, lp, mark, mark_blocks)) return;
+    const int g = (blockIdx.x - mark_blocks) * blockDim.x + threadIdx.x;
     const int t = g >> 2, k = g & 3, lead = (threadIdx.x & 31) & ~3;
     const bool live = t < m.T;
     float4 w = make_float4(0.f, 0.f, 0.f, 0.f), b = w, mat = w;
@@ -107,20 +130,23 @@ __global__ void __launch_bounds__(256, 4) k_tet_force4(MeshView m, const float4 
 }
 
 cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, cudaStream_t s, int block,
-                             int form) {
+                             int form, const LbmParams *lp, const RegionSlot *mark_out) {
     if (m.T == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 64;  // default: ~20k tets still give every SM blocks
+    const int cb = (lp && mark_out) ? (m.V + bs - 1) / bs : 0;
+    const LbmParams p = lp ? *lp : LbmParams{};
+    const RegionSlot mark = cb ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
     if (form == 2 && m.Bp) {
         const long long threads = 4LL * m.T;
-        k_tet_force4<<<(int)((threads + bs - 1) / bs), bs, 0, s>>>(m, u, err);
+        k_tet_force4<<<cb + (int)((threads + bs - 1) / bs), bs, 0, s>>>(m, u, err, cb, p, mark);
         return cudaGetLastError();
     }
     const int per = form == 1 ? 2 : 1;
     const int tb = (m.T + bs * per - 1) / (bs * per);
     if (per == 2)
-        k_tet_force2<<<tb, bs, 0, s>>>(m, u, err);
+        k_tet_force2<<<cb + tb, bs, 0, s>>>(m, u, err, cb, p, mark);
     else
-        k_tet_force<<<tb, bs, 0, s>>>(m, u, err);
+        k_tet_force<<<cb + tb, bs, 0, s>>>(m, u, err, cb, p, mark);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 """GPU: population storage formats.
 
 * Row-edge shapes (nx = 2; a partial block; two blocks per row) in FP32 and
-  FP16.
+  FP16 (in FP16 the pair form: nx = 2 is one pair whose x-neighbours are
+  itself).
 * FP16 / BF16 storage of the deviations f_q - w_q (power-of-two scaled,
   collide in FP32), rounded to nearest or stochastically (f16sr, bf16sr),
   against the FP64 oracle: velocity fields and the Taylor deformation of a
@@ -42,9 +43,10 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
 
 
-def fluid_run(P, fmt, nx, ny, nz, tau, lo, hi, g, steps):
+def fluid_run(P, fmt, nx, ny, nz, tau, lo, hi, g, steps, pairs=1):
     ctx = P.cf_create(0)
     P.cf_set_population_format(ctx, fmt)
+    P.cf_set_launch_shape(ctx, {"pop_pairs": pairs})
     P.cf_lbm_init(ctx, nx, ny, nz, tau, lo, hi, g)
     P.cf_step(ctx, steps)
     return P.cf_get_velocity(ctx), P.cf_get_density(ctx)
@@ -70,13 +72,16 @@ def test_row_edge_shapes(P, dims):
     assert rel(u16, fl.u) <= 5e-3
 
 
+@pytest.mark.parametrize("pairs", [1, 0])
 @pytest.mark.parametrize("fmt,tol", [("f16", 5e-3), ("bf16", 8e-2), ("f16sr", 5e-4), ("bf16sr", 4e-3)])
-def test_reduced_precision_fluid(P, fmt, tol):
+def test_reduced_precision_fluid(P, fmt, tol, pairs):
+    """Both forms of the 16-bit stream-collide (two nodes per thread with
+    packed arithmetic, and one node per thread) at the format's error."""
     args = (16, 24, 8, 0.8, -0.02, 0.02, (2e-6, 0.0, 0.0), 600)
-    u, rho = fluid_run(P, fmt, *args)
+    u, rho = fluid_run(P, fmt, *args, pairs=pairs)
     fl = oracle_fluid(*args)
     err = rel(u, fl.u)
-    print(f"{fmt}: relative velocity error {err:.2e}")
+    print(f"{fmt} pairs={pairs}: relative velocity error {err:.2e}")
     assert err <= tol
     assert abs((rho - 1.0).sum()) <= 1e-3 * rho.size ** 0.5
 
@@ -162,6 +167,27 @@ def test_taylor_deformation_by_format(P, sheared_oracle, fmt, tol):
     assert abs(D - D_ref) <= tol * D_ref
 
 
+@pytest.mark.parametrize("fmt,tol", [("f16", 1e-3), ("f16sr", 2e-5), ("bf16sr", 2e-4)])
+@pytest.mark.parametrize("near_rows", [0, 1])
+def test_taylor_deformation_pair_and_single_forms(P, sheared_oracle, fmt, tol, near_rows):
+    """The sheared cell with the 16-bit stream-collide in both forms (node
+    pairs / one node per thread) and both near-field forms (tile list / rows
+    over the lattice, the row form also in pairs): every far, near and
+    whole-lattice launch path of the 16-bit formats against the oracle."""
+    wl, y_ref, D_ref = sheared_oracle
+    for pairs in (1, 0):
+        ctx = P.cf_create(0)
+        P.cf_set_population_format(ctx, fmt)
+        P.cf_set_launch_shape(ctx, {"pop_pairs": pairs, "near_rows": near_rows})
+        (cid,) = P.load_workload(ctx, wl)
+        P.cf_step(ctx, 800)
+        y = P.cf_get_positions(ctx, cid)
+        D = analysis.taylor(y, oracle.Mesh(wl.cells).tets)["D"]
+        print(f"{fmt} pairs={pairs} near_rows={near_rows}: rel err D {abs(D - D_ref) / D_ref:.2e}")
+        assert abs(D - D_ref) <= tol * D_ref
+        P.cf_destroy(ctx)
+
+
 def test_stochastic_rounding_keeps_small_increments(P):
     """A weak body force in a channel at rest: per step each population
     changes by far less than half an FP16 unit in the last place, so
@@ -186,15 +212,17 @@ def test_stochastic_rounding_is_reproducible_and_seeded_per_step(P):
     a hash of node, direction and a per-step seed); the seed advances every
     step, also across separate cf_step calls."""
     args = (16, 24, 8, 0.8, -0.02, 0.02, (2e-6, 0.0, 0.0))
-    runs = []
-    for split in ((300,), (100, 1, 199)):
-        ctx = P.cf_create(0)
-        P.cf_set_population_format(ctx, "f16sr")
-        P.cf_lbm_init(ctx, *args)
-        for n in split:
-            P.cf_step(ctx, n)
-        runs.append(P.cf_get_velocity(ctx))
-    assert np.array_equal(runs[0], runs[1])
+    for pairs in (1, 0):
+        runs = []
+        for split in ((300,), (100, 1, 199)):
+            ctx = P.cf_create(0)
+            P.cf_set_population_format(ctx, "f16sr")
+            P.cf_set_launch_shape(ctx, {"pop_pairs": pairs})
+            P.cf_lbm_init(ctx, *args)
+            for n in split:
+                P.cf_step(ctx, n)
+            runs.append(P.cf_get_velocity(ctx))
+        assert np.array_equal(runs[0], runs[1])
 
 
 def test_format_is_validated(P):
