@@ -233,12 +233,18 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *          the force kernel of the step before, one extra thread per vertex
  *          running under the tets; 1 by the interpolation two steps before,
  *          right after it moves the vertices, its eight lanes per vertex
- *          sharing the vertex's tiles (a shorter chain for small meshes).
+ *          sharing the vertex's tiles (a shorter chain for small meshes);
+ *   [13]   1: the spread is staged in shared memory: a block of 256
+ *          consecutive vertices accumulates its forces in the bounding box
+ *          of their supports, then adds each node that received force to
+ *          the lattice with one atomic (for the four-point kernel, whose
+ *          supports overlap a dozen-fold); 0 (default): one atomic per
+ *          vertex and support node.
  * Block sizes are multiples of 32 in [32, 256].
  * No shape changes a computed value beyond the rounding order of the spread
  * (float atomics). cf_set_launch_shape applies from the next cf_step call;
  * CF_EINVAL for a value outside these sets. */
-#define CF_SHAPE_LEN 13
+#define CF_SHAPE_LEN 14
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
@@ -259,12 +265,12 @@ cf_status cf_set_chain_wait(cf_ctx *ctx, int64_t max_polls, int32_t extra_need);
  * context's own state. One knob at a time (tile shape, fused or separate
  * cell chain, near-field form, far-field load order, force-kernel form,
  * caching of FP32 populations, node pairs of 16-bit populations, where the
- * region is marked, tet-force, spread and interpolation block sizes), every
- * candidate runs
+ * region is marked, staged spread, tet-force, spread and interpolation block
+ * sizes), every candidate runs
  * steps_per_candidate (>= 1) coupled steps exactly as cf_step runs them
  * (the same step graphs, far field and cell chain overlapping), timed as a
  * whole with CUDA events, and the fastest candidate is kept. The simulation
- * advances by those steps exactly as under cf_step (28 candidates in all). A fluid-only context has nothing to
+ * advances by those steps exactly as under cf_step (30 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

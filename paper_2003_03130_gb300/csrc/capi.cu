@@ -138,7 +138,7 @@ cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &
     cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form, sh.mark_k5 ? nullptr : &c->lp,
                                      sh.mark_k5 ? nullptr : &acc);
     if (e != cudaSuccess) return e;
-    return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
+    return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block, sh.staged);
 }
 
 // Tile fields of the lattice parameters for tile shape k.
@@ -391,6 +391,10 @@ cf_status cf_create(cf_ctx **out, int device, void *cuda_stream) {
         dalloc(&c->energy_out, 1) != cudaSuccess) {
         cf_destroy(c);
         return CF_ENOMEM;
+    }
+    if (prepare_staged_spread() != cudaSuccess) {
+        cf_destroy(c);
+        return CF_ECUDA;
     }
     *out = c;
     return CF_OK;
@@ -935,7 +939,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)
-                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block);
+                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block, sh.staged);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
                 e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, s)
@@ -1068,6 +1072,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[10] = sh.pop_l2;
     shape[11] = sh.pop_pairs;
     shape[12] = sh.mark_k5;
+    shape[13] = sh.staged;
     return CF_OK;
 }
 
@@ -1103,6 +1108,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.pop_pairs = shape[11];
     if (shape[12] != 0 && shape[12] != 1) return fail(c, CF_EINVAL, "mark_k5 must be 0 or 1");
     sh.mark_k5 = shape[12];
+    if (shape[13] != 0 && shape[13] != 1) return fail(c, CF_EINVAL, "staged must be 0 or 1");
+    sh.staged = shape[13];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -1144,6 +1151,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::pop_l2, {0, 1}},
             {&Shape::pop_pairs, {1, 0}},
             {&Shape::mark_k5, {0, 1}},
+            {&Shape::staged, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}},
             {&Shape::gather_block, {64, 128, 256}},
             {&Shape::interp_block, {64, 128, 256}},

@@ -75,17 +75,15 @@ __device__ __forceinline__ float4 load_fc(const float4 *p) {
         return *p;
 }
 
-// Vertex force of vertex v and, with do_spread, its spread onto F. Four lanes
-// per vertex (lane 0..3; every lane of the warp takes part in the shuffles,
-// `live` false for padding lanes): lane k sums the entries k, k+4, k+8, ...
-// of the incidence row, the four partial sums are combined by a fixed
-// shuffle tree (the same order every call: deterministic), and lane k
-// spreads onto its share of the support nodes.
-template <int W, bool FC_L2>
-__device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const float4 *__restrict__ u, float4 *F,
-                                                     const LbmParams &p, int do_spread, unsigned *err, int v,
-                                                     int lane, bool live) {
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+// Vertex force of vertex v by four lanes (lane 0..3; every lane of the warp
+// takes part in the shuffles, `live` false for padding lanes): lane k sums
+// the entries k, k+4, k+8, ... of the incidence row, and the four partial
+// sums are combined by a fixed shuffle tree (the same order every call:
+// deterministic). Every lane of the group ends with the sum.
+template <bool FC_L2>
+__device__ __forceinline__ void gather_vertex(const MeshView &m, int v, int lane, bool live, float &fx, float &fy,
+                                              float &fz) {
+    fx = fy = fz = 0.f;
     if (live) {
         // the lane's entries e0 + lane, + 4, + 8, ... in groups of four: the
         // index loads of a group, then its corner-force loads, are issued
@@ -114,52 +112,61 @@ __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const fl
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
         fz += __shfl_xor_sync(0xffffffffu, fz, o);
     }
-    if (live) {
-        if (lane == 0) {
-            m.fv[v] = make_float4(fx, fy, fz, 0.f);
-            if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
-        }
-        Support s;
-        if (!do_spread) {
-        } else if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
-            if (lane == 0) atomicOr(err, ERR_DOMAIN);
-        } else {
-            float wx[W], wy[W], wz[W];
-            delta_weights<W>(s.fx, wx);
-            delta_weights<W>(s.fy, wy);
-            delta_weights<W>(s.fz, wz);
-            if constexpr (W == 2) {  // lane = (dz, dy), two nodes along x
-                const int dz = lane >> 1, dy = lane & 1;
-                const int Z = wrapi(s.bz + dz, p.nz);
-                const float wyz = wy[dy] * wz[dz];
+}
+
+// The spread of one vertex's force (fx, fy, fz) onto its support s, lane
+// `lane` of four taking its share of the support nodes: for W = 2 lane
+// (dz, dy) the two nodes of its x row, for W = 4 lane dz the W x W plane.
+// sink(X, Y, Z, w) receives each node with x and z not yet wrapped and its
+// weight w.
+template <int W, class Sink>
+__device__ __forceinline__ void spread_vertex(const Support &s, int lane, Sink &&sink) {
+    float wx[W], wy[W], wz[W];
+    delta_weights<W>(s.fx, wx);
+    delta_weights<W>(s.fy, wy);
+    delta_weights<W>(s.fz, wz);
+    if constexpr (W == 2) {
+        const int dz = lane >> 1, dy = lane & 1;
+        const float wyz = wy[dy] * wz[dz];
 #pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * Z);
-                    const float w = wx[dx] * wyz;
-                    atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
-                }
-            } else {  // lane = dz, a W x W plane
-                const int Z = wrapi(s.bz + lane, p.nz);
-                float wzl = wz[0];
+        for (int dx = 0; dx < 2; ++dx) sink(s.bx + dx, s.by + dy, s.bz + dz, wx[dx] * wyz);
+    } else {
+        float wzl = wz[0];
 #pragma unroll
-                for (int k = 1; k < W; ++k) wzl = lane == k ? wz[k] : wzl;  // no local-memory indexing
-                int X[W];
+        for (int k = 1; k < W; ++k) wzl = lane == k ? wz[k] : wzl;  // no local-memory indexing
 #pragma unroll
-                for (int dx = 0; dx < W; ++dx) X[dx] = wrapi(s.bx + dx, p.nx);
+        for (int dy = 0; dy < W; ++dy) {
+            const float wyz = wy[dy] * wzl;
 #pragma unroll
-                for (int dy = 0; dy < W; ++dy) {
-                    const int row = p.nx * (s.by + dy + p.ny * Z);
-                    const float wyz = wy[dy] * wzl;
-#pragma unroll
-                    for (int dx = 0; dx < W; ++dx) {
-                        const int n = X[dx] + row;
-                        const float w = wx[dx] * wyz;
-                        atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
-                    }
-                }
-            }
+            for (int dx = 0; dx < W; ++dx) sink(s.bx + dx, s.by + dy, s.bz + lane, wx[dx] * wyz);
         }
     }
+}
+
+// Vertex force of vertex v (four lanes, see gather_vertex) and, with
+// do_spread, its spread onto F with one float4 atomic per support node.
+template <int W, bool FC_L2>
+__device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const float4 *__restrict__ u, float4 *F,
+                                                     const LbmParams &p, int do_spread, unsigned *err, int v,
+                                                     int lane, bool live) {
+    float fx, fy, fz;
+    gather_vertex<FC_L2>(m, v, lane, live, fx, fy, fz);
+    if (!live) return;
+    if (lane == 0) {
+        m.fv[v] = make_float4(fx, fy, fz, 0.f);
+        if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
+    }
+    if (!do_spread) return;
+    Support s;
+    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+        if (lane == 0) atomicOr(err, ERR_DOMAIN);
+        return;
+    }
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    spread_vertex<W>(s, lane, [&](int X, int Y, int Z, float w) {
+        const int n = wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz));
+        atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
+    });
 }
 
 }  // namespace cf

@@ -44,6 +44,7 @@ struct Shape {
     int pop_pairs = 1;  // 16-bit formats, nx even: two nodes per thread in the row-form stream-collide
     int mark_k5 = 0;    // the interpolation (eight lanes per vertex) marks the region of the step after next,
                         // instead of the force launch (one thread per vertex) the next step's
+    int staged = 0;     // the spread accumulates a block of vertices in shared memory before its global atomics
 };
 
 }  // namespace cf

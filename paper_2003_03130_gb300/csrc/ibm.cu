@@ -24,6 +24,8 @@
 //   of its support grown by one node to the force region of step t + 2 (a
 //   vertex moves less than a spacing per step, so that region holds the
 //   support of y^{t+2}), each lane taking its share of the tiles.
+#include <climits>
+
 #include "cell_ops.cuh"
 
 namespace cf {
@@ -55,6 +57,90 @@ cudaError_t launch_mark_region(const MeshView &m, const float4 *u, const LbmPara
     return cudaGetLastError();
 }
 
+// K2+K3 with the spread staged in shared memory (launch shape: staged
+// spread). A block takes 256 consecutive vertices (neighbours in the mesh's
+// vertex order, so close in space), finds the bounding box of their delta
+// supports, accumulates their spread into that box in shared memory (float
+// atomics there), and adds each box node that received force to F with one
+// float4 atomic. For the four-point kernel a vertex touches 64 nodes and a
+// node receives about a dozen contributions, so the global atomics drop
+// several-fold; for the trilinear kernel (8 nodes per vertex, ~2 per node)
+// staging saves little. A box larger than kStageNodes (vertices of two
+// cells, or a strongly stretched cell) falls back to global atomics for that
+// block. The vertex sums are those of k_gather_spread (same order).
+constexpr int kStageVerts = 256;
+constexpr int kStageNodes = 6144;  // 3 x 24 KB of shared memory
+
+template <int W>
+__global__ void __launch_bounds__(256) k_gather_spread_staged(MeshView m, const float4 *__restrict__ u, float4 *F,
+                                                              LbmParams p, unsigned *err) {
+    extern __shared__ float stage[];  // [3][kStageNodes]: Fx, Fy, Fz of the box
+    __shared__ int lo[3], hi[3];
+    const int v0 = blockIdx.x * kStageVerts;
+    if (threadIdx.x < 3) {
+        lo[threadIdx.x] = INT_MAX;
+        hi[threadIdx.x] = INT_MIN;
+    }
+    __syncthreads();
+    {  // bounding box of the block's supports (lower corners; the box adds W - 1)
+        const int v = v0 + threadIdx.x;
+        Support s;
+        if (v < m.V && support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+            atomicMin(lo + 0, s.bx);
+            atomicMin(lo + 1, s.by);
+            atomicMin(lo + 2, s.bz);
+            atomicMax(hi + 0, s.bx);
+            atomicMax(hi + 1, s.by);
+            atomicMax(hi + 2, s.bz);
+        }
+    }
+    __syncthreads();
+    const int bx = hi[0] - lo[0] + W, by = hi[1] - lo[1] + W, bz = hi[2] - lo[2] + W;
+    const bool staged = lo[0] != INT_MAX && (long long)bx * by * bz <= kStageNodes;
+    const int vol = staged ? bx * by * bz : 0;
+    for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) stage[(i / vol) * kStageNodes + i % vol] = 0.f;
+    __syncthreads();
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int lane = threadIdx.x & 3;
+    for (int k = threadIdx.x >> 2; k < kStageVerts; k += blockDim.x >> 2) {
+        const int v = v0 + k;
+        const bool live = v < m.V;
+        float fx, fy, fz;
+        gather_vertex<false>(m, v, lane, live, fx, fy, fz);
+        if (!live) continue;
+        if (lane == 0) {
+            m.fv[v] = make_float4(fx, fy, fz, 0.f);
+            if (!isfinite(fx + fy + fz)) atomicOr(err, ERR_NONFINITE);
+        }
+        Support s;
+        if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
+            if (lane == 0) atomicOr(err, ERR_DOMAIN);
+            continue;
+        }
+        if (staged) {
+            spread_vertex<W>(s, lane, [&](int X, int Y, int Z, float w) {
+                const int i = (X - lo[0]) + bx * ((Y - lo[1]) + by * (Z - lo[2]));
+                atomicAdd(stage + i, w * fx);
+                atomicAdd(stage + kStageNodes + i, w * fy);
+                atomicAdd(stage + 2 * kStageNodes + i, w * fz);
+            });
+        } else {
+            spread_vertex<W>(s, lane, [&](int X, int Y, int Z, float w) {
+                const int n = wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz));
+                atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
+            });
+        }
+    }
+    if (!staged) return;
+    __syncthreads();
+    for (int i = threadIdx.x; i < vol; i += blockDim.x) {
+        const float a = stage[i], b = stage[kStageNodes + i], c = stage[2 * kStageNodes + i];
+        if (a == 0.f && b == 0.f && c == 0.f) continue;
+        const int X = lo[0] + i % bx, Y = lo[1] + (i / bx) % by, Z = lo[2] + i / (bx * by);
+        atomicAdd(F + wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz)), make_float4(a, b, c, 0.f));
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const float4 *__restrict__ u, float4 *F,
                                                           LbmParams p, int do_spread, unsigned *err) {
@@ -63,11 +149,30 @@ __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const floa
     gather_spread_vertex<W, false>(m, u, F, p, do_spread, err, v, g & 3, v < m.V);
 }
 
+// The staged spread's box takes more than the default 48 KB of dynamic
+// shared memory: opt in once per context, outside any stream capture.
+cudaError_t prepare_staged_spread() {
+    const int smem = (int)(3 * sizeof(float) * kStageNodes);
+    cudaError_t e = cudaFuncSetAttribute(k_gather_spread_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gather_spread_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, int block) {
+                                 cudaStream_t s, int block, int staged) {
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
+    if (staged && F && lp) {
+        const int blocks = (m.V + kStageVerts - 1) / kStageVerts;
+        const size_t smem = 3 * sizeof(float) * kStageNodes;
+        if (p.dw == 4)
+            k_gather_spread_staged<4><<<blocks, 256, smem, s>>>(m, u, F, p, err);
+        else
+            k_gather_spread_staged<2><<<blocks, 256, smem, s>>>(m, u, F, p, err);
+        return cudaGetLastError();
+    }
     const int bs = block > 0 ? block : 128;
     const long long threads = 4LL * m.V;
     const int blocks = (int)((threads + bs - 1) / bs), spread = (F && lp) ? 1 : 0;

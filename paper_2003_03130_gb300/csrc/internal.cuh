@@ -323,9 +323,14 @@ cudaError_t launch_max_extent(const MeshView &m, const float4 *u, int v0, int nv
 cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, double *partial, double *out,
                           cudaStream_t s);
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
-// same threads spread their vertex force onto the lattice.
+// same threads spread their vertex force onto the lattice, directly with
+// global atomics or (staged) through a shared-memory box per block of
+// vertices.
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, int block = 0);
+                                 cudaStream_t s, int block = 0, int staged = 0);
+// Shared-memory opt-in of the staged spread (once per context, before any
+// capture).
+cudaError_t prepare_staged_spread();
 // Add the force region of the positions x + u (support grown by one node) to
 // a region slot, and to a second one if r2.bits is not null (both cleared by
 // the caller).

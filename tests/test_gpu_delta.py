@@ -35,8 +35,10 @@ def cell_at(centre, R=4.0, h=1.3, mu=2e-3, kappa=0.2, w=0.6, seed=8):
     return Cell(x, t, perturb(x, 0.1, seed), mu, kappa, w)
 
 
-def pair(P, wl, steps, mode="pipelined"):
+def pair(P, wl, steps, mode="pipelined", shape=None):
     ctx = P.cf_create(0)
+    if shape:
+        P.cf_set_launch_shape(ctx, shape)
     ids = P.load_workload(ctx, wl)
     if mode == "pipelined":
         P.cf_step(ctx, steps)
@@ -52,11 +54,14 @@ def pair(P, wl, steps, mode="pipelined"):
     return ctx, sim, y, f
 
 
-def test_small_shear_peskin(P):
+@pytest.mark.parametrize("staged", [0, 1])
+def test_small_shear_peskin(P, staged):
+    """Both spread forms: one atomic per vertex and node, and the
+    shared-memory staged spread."""
     wl = configs.small_shear()
     wl.delta = 4
     y0 = wl.cells[0].y0
-    ctx, sim, y, f = pair(P, wl, 60)
+    ctx, sim, y, f = pair(P, wl, 60, shape={"staged": staged})
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
@@ -74,33 +79,41 @@ def test_peskin_every_launch_path(P, mode):
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
 
 
-def test_peskin_across_the_periodic_seam(P):
+@pytest.mark.parametrize("staged", [0, 1])
+def test_peskin_across_the_periodic_seam(P, staged):
+    """The staged spread's box is in unwrapped coordinates; its flush wraps
+    across the seams."""
     cell = cell_at((0.3, 12.0, 23.6))
     wl = Workload("seam", 24, 24, 24, 1.0, -0.02, 0.02, cells=[cell], delta=4)
-    ctx, sim, y, _ = pair(P, wl, 25)
+    ctx, sim, y, _ = pair(P, wl, 25, shape={"staged": staged})
     assert rel(y - cell.y0, sim.y - cell.y0) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
 
 
-def test_peskin_ragged_box_two_cells_body_force(P):
+@pytest.mark.parametrize("staged", [0, 1])
+def test_peskin_ragged_box_two_cells_body_force(P, staged):
+    """Two cells: the staged spread's block that holds vertices of both has a
+    box too large for shared memory and takes the global atomics."""
     cells = [cell_at((9.3, 8.7, 10.1), w=0.7, seed=5),
              cell_at((28.2, 17.4, 7.9), R=3.5, h=1.2, mu=1e-3, kappa=0.3, w=0.2, seed=6)]
     wl = Workload("ragged", 41, 27, 19, 0.9, -0.015, 0.02, body_force=(2e-6, 0.0, -1e-6), cells=cells, delta=4)
     y0 = np.concatenate([c.y0 for c in cells])
-    ctx, sim, y, f = pair(P, wl, 40)
+    ctx, sim, y, f = pair(P, wl, 40, shape={"staged": staged})
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
 
 
-def test_peskin_production_shear_full_size(P):
-    """128^3, R = 16 cell (~20k tets) in the benchmark's launch configuration."""
+@pytest.mark.parametrize("staged", [0, 1])
+def test_peskin_production_shear_full_size(P, staged):
+    """128^3, R = 16 cell (~20k tets) in the benchmark's launch configuration,
+    both spread forms."""
     wl = configs.production_shear(ca=0.2, w=0.5)
     wl.delta = 4
     cell = wl.cells[0]
     cell.y0 = perturb(cell.x_ref, 0.08, 20030313)
     y0 = cell.y0.copy()
-    ctx, sim, y, f = pair(P, wl, 3)
+    ctx, sim, y, f = pair(P, wl, 3, shape={"staged": staged})
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
