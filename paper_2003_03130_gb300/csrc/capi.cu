@@ -58,16 +58,13 @@ enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3, Single = 4 };
 // steps back may still read it.
 size_t tiles_of(const LbmParams &p) { return (size_t)p.ntx * p.nty * p.ntz; }
 
-RegionSlot slot_at(cf_ctx *c, int k) {
-    unsigned *base = c->region + c->region_stride * k;
-    return RegionSlot{base + 32, (int *)base, (int *)(base + 32 + c->region_bits_max)};
-}
+RegionSlot slot_at(cf_ctx *c, int k) { return RegionSlot{c->region + c->region_stride * k}; }
 RegionSlot region_slot(cf_ctx *c, int s) { return slot_at(c, (s + 2) % 3); }
 RegionSlot accum_slot(cf_ctx *c, int s) { return slot_at(c, s); }
 
-// Empty a slot: its count and the bitset of the current tiling.
+// Empty a slot: the bitset of the current tiling.
 cudaError_t clear_slot(const cf_ctx *c, const RegionSlot &r, cudaStream_t s) {
-    return cudaMemsetAsync(r.count, 0, sizeof(unsigned) * (32 + (tiles_of(c->lp) + 31) / 32), s);
+    return cudaMemsetAsync(r.bits, 0, sizeof(unsigned) * ((tiles_of(c->lp) + 31) / 32), s);
 }
 
 int near_grid(const cf_ctx *c) { return 8 * c->sms; }
@@ -128,7 +125,7 @@ cf_status build_chain_items(cf_ctx *c) {
 // K1 marks the next step's region into acc.
 cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &sh, const RegionSlot &acc,
                               cudaStream_t s) {
-    const RegionSlot none{nullptr, nullptr, nullptr};
+    const RegionSlot none{nullptr};
     if (sh.fused) {
         cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, sizeof(int) * (2 + c->cells.size()), s);
         if (e != cudaSuccess) return e;
@@ -187,7 +184,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     }
     cudaEvent_t fork = ev[0], *ev_far = ev + 1, *ev_near = ev + 1 + nsteps;
     const bool first = kind == Kind::First || kind == Kind::Single;
-    const RegionSlot none{nullptr, nullptr, nullptr};
+    const RegionSlot none{nullptr};
     if (first) {
         const RegionSlot use = region_slot(c, s0), acc = accum_slot(c, s0);
         CUDA_TRY(c, clear_slot(c, use, sf));
@@ -210,7 +207,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (!sh.mark_k5) CUDA_TRY(c, clear_slot(c, acc, sc));
         CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
-        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
+        CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, c->vel,
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
@@ -489,7 +486,9 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     }
     shape_to_lbm(p, c->shape);
     c->region_bits_max = (tmax + 31) / 32;
-    c->region_stride = (32 + c->region_bits_max + tmax + 31) / 32 * 32;
+    c->region_stride = (c->region_bits_max + 31) / 32 * 32;
+    if (prepare_near_field((long long)c->region_bits_max) != cudaSuccess)
+        return fail(c, CF_ECUDA, "shared-memory opt-in of the near field failed");
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
     CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
@@ -918,7 +917,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             const int sph = (int)((c->tstep) % 3);
             const RegionSlot use = region_slot(c, sph), accm = accum_slot(c, sph);
             cudaEvent_t *E = &ev[NE * i];
-            const RegionSlot none{nullptr, nullptr, nullptr};
+            const RegionSlot none{nullptr};
             if (cells && t == 0) {  // region of the first step (and, with mark_k5, the next): not timed
                 e = clear_slot(c, use, s);
                 if (e == cudaSuccess && sh.mark_k5) e = clear_slot(c, accm, s);
@@ -946,7 +945,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
                           : launch_lbm(c->f[p], c->f[1 - p], c->lp, c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[4], s);
             if (cells && e == cudaSuccess)
-                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, use.count, use.tiles, c->vel,
+                e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, c->vel,
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
@@ -987,21 +986,20 @@ cf_status region_nodes(cf_ctx *c, long long *out) {
     if (c->T == 0 || c->tstep == 0) return CF_OK;
     const LbmParams &p = c->lp;
     const RegionSlot last = region_slot(c, (int)((c->tstep - 1) % 3));
-    int cnt = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(&cnt, last.count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    const size_t nw = (tiles_of(p) + 31) / 32;
+    std::vector<unsigned> h(nw);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), last.bits, sizeof(unsigned) * nw, cudaMemcpyDeviceToHost, c->stream));
     cf_status st = wait_stream(c);
-    if (st != CF_OK || cnt <= 0) return st;
-    std::vector<int> h(cnt);
-    CUDA_TRY(c, cudaMemcpyAsync(h.data(), last.tiles, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream));
-    st = wait_stream(c);
     if (st != CF_OK) return st;
     const int tx = 1 << p.tlx, ty = 1 << p.tly, tz = 1 << p.tlz;
-    for (int t : h) {
-        const int ix = t % p.ntx, iy = (t / p.ntx) % p.nty, iz = t / (p.ntx * p.nty);
-        const long long ex = std::min(tx, p.nx - ix * tx), ey = std::min(ty, p.ny - iy * ty),
-                        ez = std::min(tz, p.nz - iz * tz);
-        *out += ex * ey * ez;
-    }
+    for (size_t j = 0; j < nw; ++j)
+        for (unsigned w = h[j]; w; w &= w - 1u) {
+            const long long t = 32 * (long long)j + __builtin_ctz(w);
+            const long long ix = t % p.ntx, iy = (t / p.ntx) % p.nty, iz = t / ((long long)p.ntx * p.nty);
+            const long long ex = std::min<long long>(tx, p.nx - ix * tx), ey = std::min<long long>(ty, p.ny - iy * ty),
+                            ez = std::min<long long>(tz, p.nz - iz * tz);
+            *out += ex * ey * ez;
+        }
     return CF_OK;
 }
 

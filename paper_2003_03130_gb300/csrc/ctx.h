@@ -108,8 +108,9 @@ struct cf_ctx {
     double *stage = nullptr;  // [3 V] doubles for host <-> device vertex arrays
     double *taylor_partial = nullptr, *taylor_out = nullptr;
 
-    // force regions: three slots of region_stride words, each [count, 31
-    // words of padding, bitset over the tiles, tile list]
+    // force regions: three slots of region_stride words, each the bitset over
+    // the tiles of the current tiling (region_bits_max words for the tiling
+    // with the most tiles)
     unsigned *region = nullptr;
     size_t region_stride = 0, region_bits_max = 0;
     Shape shape;

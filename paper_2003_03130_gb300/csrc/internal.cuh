@@ -160,31 +160,28 @@ __host__ __device__ __forceinline__ int wrapi(int i, int n) {
 }
 
 // Force region of a step: the set of tiles that hold a node that may carry
-// force in that step, as a bitset over the tiles plus the list of the set's
-// tiles (in no particular order) and its length. A step's region holds every
+// force in that step, as a bitset over the tiles. A step's region holds every
 // tile that meets the delta support of a vertex grown by one node per side
 // (a vertex moves less than one spacing per step, so the support at the next
 // step stays inside). Nodes outside the region see no force.
 constexpr int kTileNodes = 256;
 
 struct RegionSlot {
-    unsigned *bits;  // [ceil(tiles / 32)], followed by the count
-    int *count;
-    int *tiles;      // [tiles]
+    unsigned *bits;  // [ceil(tiles / 32)]
 };
 
 __host__ __device__ __forceinline__ bool region_has(const unsigned *__restrict__ bits, int t) {
     return (bits[t >> 5] >> (t & 31)) & 1u;
 }
 
-// Add tile t: the first thread to set its bit appends it to the list. The
-// plain read skips the atomic for the (many) tiles already in (a stale L1
-// line can only miss a bit set during this launch: then the atomic finds it
-// set and nothing is appended).
+// Add tile t: an atomic OR whose result is not used (a reduction the thread
+// does not wait for), skipped for the (many) tiles whose bit a plain read
+// already shows (a stale L1 line can only miss a bit set during this launch,
+// which costs one redundant reduction).
 __device__ __forceinline__ void region_add(const RegionSlot &r, int t) {
     const unsigned bit = 1u << (t & 31);
     if (r.bits[t >> 5] & bit) return;
-    if (!(atomicOr(r.bits + (t >> 5), bit) & bit)) r.tiles[atomicAdd(r.count, 1)] = t;
+    atomicOr(r.bits + (t >> 5), bit);
 }
 
 __host__ __device__ __forceinline__ int tile_index(const LbmParams &p, int tx, int ty, int tz) {
@@ -356,18 +353,21 @@ cudaError_t launch_lbm(const void *fin, void *fout, const LbmParams &p, const un
                        cudaStream_t s);
 // K4 split by the force region: far = the nodes outside it (rows of 128
 // nodes; threads in region tiles return at once), with no force-field read;
-// near = the region's tiles from its list (blocks stride over the list),
-// with the force field, also storing u(t) there; it zeroes the force field
-// where it read a nonzero one, so that F is zero everywhere between steps.
-// spec: the far field issues a node's loads before its region test resolves.
+// near = the region's tiles (blocks stride over the set bits of its
+// bitset), with the force field, also storing u(t) there; it zeroes the
+// force field where it read a nonzero one, so that F is zero everywhere
+// between steps. spec: the far field issues a node's loads before its
+// region test resolves.
 cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, const unsigned *bits,
                            const unsigned *seed, bool spec, cudaStream_t s);
-// blocks > 0: that many blocks stride over the region's tile list;
-// blocks <= 0: rows of 128 nodes over the whole lattice, threads outside the
-// region return at once.
+// blocks > 0: that many blocks stride over the region's tiles (the set bits
+// of its bitset); blocks <= 0: rows of 128 nodes over the whole lattice,
+// threads outside the region return at once.
 cudaError_t launch_lbm_near(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
-                            const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
-                            unsigned *next_seed, cudaStream_t s);
+                            float4 *vel, int blocks, const unsigned *seed, unsigned *next_seed, cudaStream_t s);
+// Shared-memory opt-in of the list-form near field (its per-block running
+// counts of the region bitset; once per context, before any capture).
+cudaError_t prepare_near_field(long long max_words);
 // True for the device functions of the far-field kernels (to tell their graph
 // nodes apart).
 bool is_lbm_far_kernel(const void *fn);
@@ -381,7 +381,7 @@ size_t pop_bytes(int fmt);
 // step after next) to `mark`, cleared by the caller.
 cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s, int block = 0,
-                                 const RegionSlot &mark = RegionSlot{nullptr, nullptr, nullptr});
+                                 const RegionSlot &mark = RegionSlot{nullptr});
 // Compression between plates and the adjoint (csrc/adjoint.cu).
 // out = J_el v at displacements u (vertex sums of the corner tangents; uses m.fc).
 cudaError_t launch_force_jvp(const MeshView &m, const float4 *u, const float4 *v, float4 *out, unsigned *err,

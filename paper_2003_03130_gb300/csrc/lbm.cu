@@ -28,7 +28,7 @@
 // collide; see "node pairs" below). The whole-lattice and far-field kernels take
 // rows of 128 nodes along x; with cells the lattice is also cut into tiles of
 // 256 nodes (x fastest), the unit of the force region, and the near field
-// runs two blocks of 128 threads per region tile.
+// runs half a tile of the region per block and work item.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -441,18 +441,20 @@ __device__ __forceinline__ unsigned pack2_rn<__nv_bfloat16>(float2 v) {
     return d;
 }
 
-// Stochastic rounding as in Pop<T>::st_sr, both values at once: the dither
-// bits below the last kept mantissa bit (dlo for the even node, dhi for the
-// odd one) are added to each FP32 pattern, then both are truncated (round
-// toward zero) in one packing conversion.
+// Stochastic rounding of both values by the hardware conversion (cvt.rs,
+// sm_100a and later): each value rounds away from zero with probability
+// equal to the dropped fraction of its last kept unit, the odd node's value
+// drawing on the upper 16 bits of r, the even node's on the lower 16 (of
+// which FP16 uses 13). Measured on GB300: a value 0.7 (0.3) of a unit above
+// a representable one rounds up with frequency 0.7002 (0.3002) over 2^20
+// random words, in both formats.
 template <class T>
-__device__ __forceinline__ unsigned pack2_sr(float2 v, unsigned dlo, unsigned dhi) {
-    const float hi = __uint_as_float(__float_as_uint(v.y) + dhi), lo = __uint_as_float(__float_as_uint(v.x) + dlo);
+__device__ __forceinline__ unsigned pack2_sr(float2 v, unsigned r) {
     unsigned d;
     if constexpr (std::is_same<T, __half>::value)
-        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.y), "f"(v.x), "r"(r));
     else
-        asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.y), "f"(v.x), "r"(r));
     return d;
 }
 
@@ -510,18 +512,10 @@ __device__ __forceinline__ void lbm_pair(const T *__restrict__ fin, T *__restric
     }
     if (p.sr) {
         // random bits per pair and population: the Weyl step h + q 0x9e3779b9
-        // of a per-pair hash; its top K bits dither the odd node, the next K
-        // bits the even node (K = dropped mantissa bits). A non-finite node
-        // (any NaN input makes its u NaN) converts without dither.
-        constexpr int K = Pop<T>::kDropped;
-        constexpr unsigned low = (1u << K) - 1u;
+        // of a per-pair hash of the node and the step's seed
         const unsigned h = mix32((unsigned)n0 ^ mix32(seed));
-        const unsigned m_lo = isfinite(ux.x + uy.x + uz.x) ? low : 0u, m_hi = isfinite(ux.y + uy.y + uz.y) ? low : 0u;
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const unsigned r = h + (unsigned)q * 0x9e3779b9u;
-            st_pair(fout + q * N + n0, pack2_sr<T>(d[q], (r >> (32 - 2 * K)) & m_lo, (r >> (32 - K)) & m_hi));
-        }
+        for (int q = 0; q < 19; ++q) st_pair(fout + q * N + n0, pack2_sr<T>(d[q], h + (unsigned)q * 0x9e3779b9u));
         return;
     }
 #pragma unroll
@@ -601,23 +595,58 @@ __global__ void __launch_bounds__(128) k_lbm_near_rows(const T *__restrict__ fin
         lbm_node<T, true, true, CS>(fin, fout, F, p, x, y, z, vel, seed);
 }
 
-// The force region's tiles from its list, with the force field; also stores
-// u(t) there. The grid is fixed when a step is captured while the region
-// moves with the cells, so blocks stride over the list's half tiles.
+// The force region's tiles, with the force field; also stores u(t) there.
+// The grid is fixed when a step is captured while the region moves with the
+// cells, so blocks stride over the region's half tiles. The tiles are the
+// set bits of the region bitset: every block first forms, in shared memory,
+// the running count of set bits before each bitset word (nwords + 1
+// entries); the k-th tile of the region is then found by a binary search
+// over those counts and a scan of one word.
 template <class T, bool CS = true>
 __global__ void __launch_bounds__(kTileBlock, 8) k_lbm_near(const T *__restrict__ fin, T *__restrict__ fout,
                                                             float4 *__restrict__ F, LbmParams p,
-                                                            const int *__restrict__ count,
-                                                            const int *__restrict__ tiles, float4 *__restrict__ vel,
+                                                            const unsigned *__restrict__ bits, int nwords,
+                                                            float4 *__restrict__ vel,
                                                             const unsigned *__restrict__ seed_in,
                                                             unsigned *__restrict__ seed_out) {
+    extern __shared__ int before[];  // [nwords + 1]: set bits in the words before word j
+    __shared__ int warp_sum[kTileBlock / 32];
     const unsigned seed = *seed_in;
     if ((blockIdx.x | threadIdx.x) == 0) *seed_out = seed + 1u;
-    const int halves = 2 * *count;
-    int next = blockIdx.x < halves ? tiles[blockIdx.x >> 1] : 0;
+    // running counts: thread i takes a contiguous chunk of words
+    const int chunk = (nwords + kTileBlock - 1) / kTileBlock, w0 = threadIdx.x * chunk;
+    int mine = 0;
+    for (int j = w0; j < w0 + chunk && j < nwords; ++j) mine += __popc(bits[j]);
+    int incl = mine;  // inclusive scan over the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int k = 0; k < wid; ++k) base += warp_sum[k];
+    int run = base + incl - mine;
+    for (int j = w0; j < w0 + chunk && j < nwords; ++j) {
+        before[j] = run;
+        run += __popc(bits[j]);
+    }
+    if (threadIdx.x == kTileBlock - 1) before[nwords] = run;
+    __syncthreads();
+    const int halves = 2 * before[nwords];
     for (int w = blockIdx.x; w < halves; w += gridDim.x) {
-        const int tile = next;  // the next iteration's tile index loads under this one's populations
-        if (w + (int)gridDim.x < halves) next = tiles[(w + gridDim.x) >> 1];
+        const int rank = w >> 1;
+        int lo = 0, hi = nwords - 1;  // the last word j with before[j] <= rank
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (before[mid] <= rank) lo = mid;
+            else hi = mid - 1;
+        }
+        unsigned word = bits[lo];
+        for (int k = rank - before[lo]; k > 0; --k) word &= word - 1u;  // drop the lower set bits
+        const int tile = 32 * lo + __ffs(word) - 1;
         const int tx = tile % p.ntx, r = tile / p.ntx;
         int x, y, z;
         if (!tile_node(p, tx, r % p.nty, r / p.nty, (w & 1) * kTileBlock + threadIdx.x, x, y, z)) continue;
@@ -790,8 +819,9 @@ static cudaError_t far_t(const void *fin, void *fout, const LbmParams &p, const 
 
 template <class T>
 static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
-                          const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
-                          unsigned *next_seed, cudaStream_t s) {
+                          float4 *vel, int blocks, const unsigned *seed, unsigned *next_seed, cudaStream_t s) {
+    const int nwords = (int)(((long long)p.ntx * p.nty * p.ntz + 31) / 32);
+    const size_t smem = sizeof(int) * ((size_t)nwords + 1);
     if constexpr (std::is_same<T, float>::value) {
         if (p.l2) {  // L2-normal form (FP32 only)
             if (blocks <= 0) {
@@ -800,9 +830,9 @@ static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParam
                 k_lbm_near_rows<T, false><<<grid, bx, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p,
                                                               bits, vel, seed, next_seed);
             } else {
-                k_lbm_near<T, false><<<blocks, kTileBlock, 0, s>>>(static_cast<const T *>(fin),
-                                                                   static_cast<T *>(fout), F, p, count, tiles, vel,
-                                                                   seed, next_seed);
+                k_lbm_near<T, false><<<blocks, kTileBlock, smem, s>>>(static_cast<const T *>(fin),
+                                                                      static_cast<T *>(fout), F, p, bits, nwords, vel,
+                                                                      seed, next_seed);
             }
             return cudaGetLastError();
         }
@@ -823,9 +853,22 @@ static cudaError_t near_t(const void *fin, void *fout, float4 *F, const LbmParam
                                                seed, next_seed);
         return cudaGetLastError();
     }
-    k_lbm_near<T><<<blocks, kTileBlock, 0, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, count,
-                                                tiles, vel, seed, next_seed);
+    k_lbm_near<T><<<blocks, kTileBlock, smem, s>>>(static_cast<const T *>(fin), static_cast<T *>(fout), F, p, bits,
+                                                   nwords, vel, seed, next_seed);
     return cudaGetLastError();
+}
+
+// Every list-form near-field kernel may take up to 4 (max_words + 1) bytes
+// of dynamic shared memory.
+cudaError_t prepare_near_field(long long max_words) {
+    const int smem = (int)(sizeof(int) * (max_words + 1));
+    if (smem <= 48 * 1024) return cudaSuccess;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_lbm_near<float, true>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lbm_near<float, false>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lbm_near<__half, true>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lbm_near<__nv_bfloat16, true>, a, smem);
+    return e;
 }
 
 bool is_lbm_far_kernel(const void *fn) {
@@ -855,13 +898,11 @@ cudaError_t launch_lbm_far(const void *fin, void *fout, const LbmParams &p, cons
 }
 
 cudaError_t launch_lbm_near(const void *fin, void *fout, float4 *F, const LbmParams &p, const unsigned *bits,
-                            const int *count, const int *tiles, float4 *vel, int blocks, const unsigned *seed,
-                            unsigned *next_seed, cudaStream_t s) {
+                            float4 *vel, int blocks, const unsigned *seed, unsigned *next_seed, cudaStream_t s) {
     switch (p.fmt) {
-        case POP_F16: return near_t<__half>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
-        case POP_BF16:
-            return near_t<__nv_bfloat16>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
-        default: return near_t<float>(fin, fout, F, p, bits, count, tiles, vel, blocks, seed, next_seed, s);
+        case POP_F16: return near_t<__half>(fin, fout, F, p, bits, vel, blocks, seed, next_seed, s);
+        case POP_BF16: return near_t<__nv_bfloat16>(fin, fout, F, p, bits, vel, blocks, seed, next_seed, s);
+        default: return near_t<float>(fin, fout, F, p, bits, vel, blocks, seed, next_seed, s);
     }
 }
 

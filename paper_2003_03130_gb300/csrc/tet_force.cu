@@ -135,7 +135,7 @@ cudaError_t launch_tet_force(const MeshView &m, const float4 *u, unsigned *err, 
     const int bs = block > 0 ? block : 64;  // default: ~20k tets still give every SM blocks
     const int cb = (lp && mark_out) ? (m.V + bs - 1) / bs : 0;
     const LbmParams p = lp ? *lp : LbmParams{};
-    const RegionSlot mark = cb ? *mark_out : RegionSlot{nullptr, nullptr, nullptr};
+    const RegionSlot mark = cb ? *mark_out : RegionSlot{nullptr};
     if (form == 2 && m.Bp) {
         const long long threads = 4LL * m.T;
         k_tet_force4<<<cb + (int)((threads + bs - 1) / bs), bs, 0, s>>>(m, u, err, cb, p, mark);
