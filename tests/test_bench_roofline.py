@@ -53,3 +53,38 @@ def test_host_replicas_are_capped_by_cores_and_memory():
     assert 1 <= bench._host_replicas(32**3) <= cores
     # a lattice whose oracle would not fit twice into any host's memory: one replica
     assert bench._host_replicas(10**13) == 1
+
+
+def test_region_statistics_take_the_median_of_the_regions():
+    st = bench.region_stats([3.0, 1.0, 2.0, 10.0, 2.5], 20)
+    assert st["n"] == 5 and st["steps_per_region"] == 20
+    assert st["ms_per_step_median"] == 2.5 / 20
+    assert st["ms_per_step_min"] == 1.0 / 20 and st["ms_per_step_max"] == 10.0 / 20
+
+
+class _WL:
+    nx, ny, nz, delta = 16, 16, 16, 2
+    n_nodes = 16 ** 3
+
+
+def test_stream_collide_roofline_picks_the_longer_part_and_counts_its_bytes():
+    y = np.array([[5.5, 6.25, 7.75], [9.2, 8.1, 3.3]])
+    n_sup = bench.support_nodes(y, (16, 16, 16), 2)
+    # far field longer: 152 B per node outside the region (FP32), 76 with 16-bit storage
+    r = bench.stream_collide_roofline(_WL, [0, 0, 0.05, 0.01, 0], 1000, y, "f32", 6000.0)
+    assert r["kernel"] == "k_lbm_far" and r["units_per_launch"] == 16 ** 3 - 1000
+    assert r["algorithmic_bytes_per_launch"] == 152 * (16 ** 3 - 1000)
+    assert abs(r["achieved"] - 152 * (16 ** 3 - 1000) / 0.05e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    r16 = bench.stream_collide_roofline(_WL, [0, 0, 0.05, 0.01, 0], 1000, y, "f16sr", 6000.0)
+    assert r16["bytes_per_unit"] == 76
+    # near field longer: 184 B per region node (+16 B per support node whose force is zeroed)
+    r = bench.stream_collide_roofline(_WL, [0, 0, 0.01, 0.05, 0], 1000, y, "f32", 6000.0)
+    assert r["kernel"] == "k_lbm_near" and r["units_per_launch"] == 1000
+    assert r["algorithmic_bytes_per_launch"] == 184 * 1000 + 16 * n_sup
+    r16 = bench.stream_collide_roofline(_WL, [0, 0, 0.01, 0.05, 0], 1000, y, "bf16", 6000.0)
+    assert r16["bytes_per_unit"] == 76 + 32
+
+
+def test_sweep_cases_cover_the_capillary_numbers_and_weights():
+    assert bench.SWEEP_CA == (0.05, 0.2, 0.5) and bench.SWEEP_W == (0.0, 0.5, 1.0)

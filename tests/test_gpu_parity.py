@@ -651,12 +651,12 @@ def test_suspension_full_size(P):
 
 def test_paper_box_shear_full_size(P):
     """The paper's shear box shape (10 x 15 x 5 R at R = 16: 160 x 240 x 80)
-    with a perturbed R = 16 cell: 3 coupled steps against the oracle."""
+    with a perturbed R = 16 cell: 50 coupled steps against the oracle."""
     wl = configs.paper_box_shear()
     cell = wl.cells[0]
     cell.y0 = perturb(cell.x_ref, 0.08, 20030313)
     y0 = cell.y0.copy()
-    ctx, sim, y, f = _coupled_pair(P, wl, 3)
+    ctx, sim, y, f = _coupled_pair(P, wl, 50)
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
@@ -680,12 +680,12 @@ def test_multicell_shear_small(P):
 
 def test_multicell_shear_full_size(P):
     """8 R = 16 cells in the 80 x 128 x 64 box (volume fraction 0.22), in the
-    benchmark's configuration: 3 coupled steps against the oracle."""
+    benchmark's configuration: 50 coupled steps against the oracle."""
     wl = configs.multicell_shear(ncells=8)
     for k, c in enumerate(wl.cells):
         c.y0 = perturb(c.x_ref, 0.08, 400 + k)
     y0 = np.concatenate([c.y0 for c in wl.cells])
-    ctx, sim, y, f = _coupled_pair(P, wl, 3)
+    ctx, sim, y, f = _coupled_pair(P, wl, 50)
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
