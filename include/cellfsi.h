@@ -128,7 +128,12 @@ cf_status cf_mesh_init_batch(cf_ctx *ctx, int32_t ncells, const int32_t *nv, con
 
 /* Mooney-Rivlin material of one cell (Sec. 2): shear modulus mu >= 0, bulk
  * modulus kappa >= 0 and ratio w in [0, 1], with mu_1 = w mu and
- * mu_2 = (1 - w) mu; w = 1 is neo-Hookean. */
+ * mu_2 = (1 - w) mu; w = 1 is neo-Hookean. A nearly incompressible material,
+ * kappa >= 100 mu (Poisson ratio 0.495 and above), has the volume change
+ * J - 1 of its tets evaluated in FP64 (from the FP32 displacements and an
+ * FP64 copy of B kept from the set-up): the volume term kappa (J - 1)
+ * amplifies any rounding of J - 1 by kappa / mu. The rest of the force is
+ * FP32. */
 cf_status cf_set_material(cf_ctx *ctx, int32_t cell_id, double mu, double kappa, double w);
 
 /* Materials of several cells at once: ids[ncells], mu, kappa, w as in
