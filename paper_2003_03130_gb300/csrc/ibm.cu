@@ -184,8 +184,10 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, 
 }
 
 // Eight threads per vertex, each summing W^3 / 8 support nodes; the group of
-// eight combines its partial sums with shuffles.
-template <int W>
+// eight combines its partial sums with shuffles. MARK: the lanes also mark the
+// region of the step after next (a separate instantiation, so that the form
+// without marking keeps its lower register count: 30 against 48).
+template <int W, bool MARK>
 __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const float4 *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
                                                        unsigned *err, RegionSlot mark) {
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
     }
     if (!live) return;
     const float4 un = make_float4(uc.x + vx, uc.y + vy, uc.z + vz, 0.f);
-    if (mark.bits && ok) {  // the region of step t + 2 (an invalid support is K23's to report)
+    if (MARK && ok) {  // the region of step t + 2 (an invalid support is K23's to report)
         Support s2;
         if (support_of<W>(m.origin, xr, un, p.ny, s2)) mark_region<W>(s2, p, mark, lane, 8);
     }
@@ -265,10 +267,18 @@ cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const Lbm
     const int bs = block > 0 ? block : 128;
     const long long threads = 8LL * m.V;
     const int blocks = (int)((threads + bs - 1) / bs);
-    if (p.dw == 4)
-        k_interp_advect<4><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
-    else
-        k_interp_advect<2><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+    const bool mk = mark.bits != nullptr;
+    if (p.dw == 4) {
+        if (mk)
+            k_interp_advect<4, true><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+        else
+            k_interp_advect<4, false><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+    } else {
+        if (mk)
+            k_interp_advect<2, true><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+        else
+            k_interp_advect<2, false><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+    }
     return cudaGetLastError();
 }
 
