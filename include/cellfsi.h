@@ -80,6 +80,24 @@ void cf_destroy(cf_ctx *ctx);
 enum { CF_POP_F32 = 0, CF_POP_F16 = 1, CF_POP_BF16 = 2, CF_POP_F16_SR = 3, CF_POP_BF16_SR = 4 };
 cf_status cf_set_population_format(cf_ctx *ctx, int32_t format);
 
+/* How the spread accumulates the force field, from the next cf_lbm_init on.
+ * CF_SPREAD_FLOAT (default): one float4 atomic add per vertex and support
+ * node; the field is exact up to the order of those additions, so two runs
+ * can differ by rounding, and a chaotic flow amplifies that. CF_SPREAD_FIXED:
+ * the field is held in 64-bit fixed point (units of 2^-48 per component),
+ * each contribution is its FP32 value scaled by 2^48 and rounded once, and
+ * the integer sums are exact whatever the order: every run, launch shape
+ * (tiles, block sizes, near-field form, where the region is marked) and
+ * schedule (pipelined, one step per call, profiled) gives bit-identical
+ * results; the force kernel's form (tets per thread, lanes per tet) still
+ * changes its rounding. Costs 8 more bytes per node of the field (24 instead
+ * of 16), three 64-bit reductions per support node instead of one vector
+ * one, and disables the staged spread. |F| must stay below 2^15 per
+ * component. Not a paper feature: a service for reproducible runs. */
+#define CF_SPREAD_FLOAT 0
+#define CF_SPREAD_FIXED 1
+cf_status cf_set_spread(cf_ctx *ctx, int32_t mode);
+
 /* Immersed-boundary delta kernel for the spreading of vertex forces and the
  * interpolation of the fluid velocity (the paper does not name its kernel),
  * from the next cf_lbm_init on: delta_h(r) = phi(r_x) phi(r_y) phi(r_z) with

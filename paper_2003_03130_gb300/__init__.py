@@ -47,6 +47,7 @@ def lib():
             "cf_destroy": ([vp], None),
             "cf_set_population_format": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_set_delta": ([vp, ctypes.c_int32], ctypes.c_int),
+            "cf_set_spread": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_lbm_init": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, _d], ctypes.c_int),
             "cf_mesh_init": ([vp, ctypes.c_int32, _d, ctypes.c_int32, _i, _d, _i], ctypes.c_int),
@@ -191,6 +192,17 @@ def cf_set_delta(ctx, kernel):
     2 or 4) or "trilinear" / "peskin4"; applies at the next cf_lbm_init."""
     kernel = DELTAS.get(kernel, kernel)
     _check(ctx, lib().cf_set_delta(ctx.handle, int(kernel)))
+
+
+CF_SPREAD_FLOAT, CF_SPREAD_FIXED = 0, 1
+SPREADS = {"float": CF_SPREAD_FLOAT, "fixed": CF_SPREAD_FIXED}
+
+
+def cf_set_spread(ctx, mode):
+    """``mode``: CF_SPREAD_FLOAT / CF_SPREAD_FIXED or "float" / "fixed" (the
+    deterministic fixed-point force field); applies at the next cf_lbm_init."""
+    mode = SPREADS.get(mode, mode)
+    _check(ctx, lib().cf_set_spread(ctx.handle, int(mode)))
 
 
 def cf_lbm_init(ctx, nx, ny, nz, tau, u_wall_lo_x, u_wall_hi_x, body_force=None):

@@ -478,6 +478,7 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     p.gy = g ? (float)g[1] : 0.f;
     p.gz = g ? (float)g[2] : 0.f;
     p.dw = c->delta_w;
+    p.det = c->spread_fixed;
     // region slots sized for the largest tile count of any tile shape
     size_t tmax = 0;
     for (int k = 0; k < kNumTileShapes; ++k) {
@@ -492,13 +493,15 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
     CUDA_TRY(c, cudaMalloc(&c->f[1], pop));
-    CUDA_TRY(c, dalloc(&c->F, (size_t)N));
+    // float4 per node, or long long [3][N] for the deterministic spread
+    const size_t f_units = p.det ? (3 * (size_t)N + 1) / 2 : (size_t)N;
+    CUDA_TRY(c, dalloc(&c->F, f_units));
     CUDA_TRY(c, dalloc(&c->vel, (size_t)N));
     CUDA_TRY(c, dalloc(&c->region, 3 * c->region_stride));
     CUDA_TRY(c, cudaMemsetAsync(c->region, 0, sizeof(unsigned) * 3 * c->region_stride, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[0], p, c->stream));
     CUDA_TRY(c, launch_lbm_init(c->f[1], p, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float4) * (size_t)N, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->F, 0, sizeof(float4) * f_units, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->vel, 0, sizeof(float4) * (size_t)N, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->seed, 0, 2 * sizeof(unsigned), c->stream));  // rounding seeds restart
     c->lp = p;
@@ -513,6 +516,13 @@ cf_status cf_set_population_format(cf_ctx *c, int32_t format) {
         format != CF_POP_BF16_SR)
         return fail(c, CF_EINVAL, "unknown population format %d", format);
     c->pop_format = format;
+    return CF_OK;
+}
+
+cf_status cf_set_spread(cf_ctx *c, int32_t mode) {
+    if (!c) return CF_EINVAL;
+    if (mode != CF_SPREAD_FLOAT && mode != CF_SPREAD_FIXED) return fail(c, CF_EINVAL, "unknown spread mode %d", mode);
+    c->spread_fixed = mode == CF_SPREAD_FIXED;
     return CF_OK;
 }
 

@@ -144,7 +144,8 @@ __device__ __forceinline__ void spread_vertex(const Support &s, int lane, Sink &
 }
 
 // Vertex force of vertex v (four lanes, see gather_vertex) and, with
-// do_spread, its spread onto F with one float4 atomic per support node.
+// do_spread, its spread onto F with one atomic per support node (one float4
+// reduction, or three fixed-point ones with the deterministic spread).
 template <int W, bool FC_L2>
 __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const float4 *__restrict__ u, float4 *F,
                                                      const LbmParams &p, int do_spread, unsigned *err, int v,
@@ -165,7 +166,7 @@ __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const fl
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     spread_vertex<W>(s, lane, [&](int X, int Y, int Z, float w) {
         const int n = wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz));
-        atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
+        force_add(F, p, n, w * fx, w * fy, w * fz);
     });
 }
 

@@ -79,8 +79,9 @@ struct cf_ctx {
     LbmParams lp{};
     int pop_format = CF_POP_F32;  // CF_POP_* storage of the populations (next cf_lbm_init)
     int delta_w = 2;           // delta kernel support width (next cf_lbm_init)
+    int spread_fixed = 0;      // deterministic (fixed-point) spread (next cf_lbm_init)
     void *f[2] = {nullptr, nullptr};
-    float4 *F = nullptr;    // force field, (Fx, Fy, Fz, 0) per node
+    float4 *F = nullptr;    // force field, (Fx, Fy, Fz, 0) per node, or fixed point long long [3][N]
     float4 *vel = nullptr;  // u(t) on the force region, (ux, uy, uz, 0) per node
 
     // cells

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_gather_spread_staged(MeshView m, const 
         } else {
             spread_vertex<W>(s, lane, [&](int X, int Y, int Z, float w) {
                 const int n = wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz));
-                atomicAdd(F + n, make_float4(w * fx, w * fy, w * fz, 0.f));
+                force_add(F, p, n, w * fx, w * fy, w * fz);
             });
         }
     }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_gather_spread_staged(MeshView m, const 
         const float a = stage[i], b = stage[kStageNodes + i], c = stage[2 * kStageNodes + i];
         if (a == 0.f && b == 0.f && c == 0.f) continue;
         const int X = lo[0] + i % bx, Y = lo[1] + (i / bx) % by, Z = lo[2] + i / (bx * by);
-        atomicAdd(F + wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz)), make_float4(a, b, c, 0.f));
+        force_add(F, p, wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz)), a, b, c);
     }
 }
 
@@ -164,7 +164,7 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, 
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
-    if (staged && F && lp) {
+    if (staged && F && lp && !p.det) {  // shared-memory float sums would depend on their order
         const int blocks = (m.V + kStageVerts - 1) / kStageVerts;
         const size_t smem = 3 * sizeof(float) * kStageNodes;
         if (p.dw == 4)

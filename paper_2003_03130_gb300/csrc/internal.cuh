@@ -8,7 +8,10 @@
 //                deviation f_q - w_q from the rest equilibrium (keeps FP32
 //                rounding relative to the O(u) signal, not to O(w_q));
 //   force field  float4 F[n] = (Fx, Fy, Fz, 0): one vector atomic per node
-//                in the spread, one 16-byte load in the near field;
+//                in the spread, one 16-byte load in the near field; with the
+//                deterministic spread the same buffer holds long long
+//                Fi[3][N], the components in fixed point (units of 2^-48):
+//                integer additions are exact and independent of their order;
 //   u(t)         float4 vel[n] = (ux, uy, uz, 0) on the force region (one
 //                16-byte load per support node in the interpolation);
 //   vertices     float4 per vertex (one 16-byte load in the tet gathers):
@@ -77,6 +80,7 @@ struct LbmParams {
     int l2;             // FP32 far and near fields: populations cached in L2 at normal priority
                         // (1) instead of streamed with evict-first hints (0)
     int pairs;          // 16-bit formats, nx even: two nodes per thread in the row-form kernels
+    int det;            // deterministic spread: the force field in fixed point, long long [3][N]
     // force-region tiles of 2^tlx x 2^tly x 2^tlz = 256 nodes (x fastest;
     // the last tile of an axis may stick out of the lattice), ntx * nty * ntz
     // of them
@@ -153,6 +157,55 @@ __device__ __forceinline__ void delta_weights<4>(float f, float (&w)[4]) {
     w[2] = 0.125f * (1.f + 2.f * f + q);
     w[3] = 0.125f * (1.f + 2.f * f - q);
 }
+
+// ---------------------------------------------------------------- force field access
+// The force field is float4 per node, or (p.det) fixed point: component k of
+// node n is the integer Fi[k * N + n] in units of 2^-48. A contribution is
+// converted by one rounding of its FP32 value scaled by 2^48 (exact for
+// values above 2^-24 in magnitude, which FP32 already carries at that
+// resolution); the sum of the integers is exact whatever the order of the
+// atomics, so every run, launch shape and schedule spreads the same field.
+// |F| must stay below 2^15 per component (far beyond any stable run).
+constexpr float kFixScale = 281474976710656.0f;  // 2^48
+constexpr double kFixUnit = 1.0 / 281474976710656.0;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void force_add(float4 *F, const LbmParams &p, long long n, float ax, float ay, float az) {
+    if (p.det) {
+        unsigned long long *Fi = reinterpret_cast<unsigned long long *>(F);
+        atomicAdd(Fi + n, (unsigned long long)__float2ll_rn(ax * kFixScale));
+        atomicAdd(Fi + p.N + n, (unsigned long long)__float2ll_rn(ay * kFixScale));
+        atomicAdd(Fi + 2 * p.N + n, (unsigned long long)__float2ll_rn(az * kFixScale));
+    } else {
+        atomicAdd(F + n, make_float4(ax, ay, az, 0.f));
+    }
+}
+
+// The force at node n (read through L2); *nonzero tells whether any component is.
+__device__ __forceinline__ float4 force_at(const float4 *F, const LbmParams &p, long long n, bool &nonzero) {
+    if (p.det) {
+        const long long *Fi = reinterpret_cast<const long long *>(F);
+        const long long x = __ldcg(Fi + n), y = __ldcg(Fi + p.N + n), z = __ldcg(Fi + 2 * p.N + n);
+        nonzero = (x | y | z) != 0;
+        return make_float4((float)((double)x * kFixUnit), (float)((double)y * kFixUnit), (float)((double)z * kFixUnit),
+                           0.f);
+    }
+    const float4 a = __ldcg(F + n);
+    nonzero = a.x != 0.f || a.y != 0.f || a.z != 0.f;
+    return a;
+}
+
+__device__ __forceinline__ void force_clear(float4 *F, const LbmParams &p, long long n) {
+    if (p.det) {
+        long long *Fi = reinterpret_cast<long long *>(F);
+        Fi[n] = 0;
+        Fi[p.N + n] = 0;
+        Fi[2 * p.N + n] = 0;
+    } else {
+        F[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+#endif
 
 __host__ __device__ __forceinline__ int wrapi(int i, int n) {
     const int r = i % n;

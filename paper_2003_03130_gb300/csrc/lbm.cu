@@ -267,15 +267,14 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
     float Fx = p.gx, Fy = p.gy, Fz = p.gz;
     bool spread = false;
     if (HAS_F) {
-        const float4 a = __ldcg(F + n);
-        spread = a.x != 0.f || a.y != 0.f || a.z != 0.f;
+        const float4 a = force_at(F, p, n, spread);
         Fx += a.x;
         Fy += a.y;
         Fz += a.z;
     }
     const float3 u = collide<T>(d, Fx, Fy, Fz, p);
     if (!store) return;
-    if (HAS_F && spread) F[n] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed: the next step spreads onto zeros
+    if (HAS_F && spread) force_clear(F, p, n);  // consumed: the next step spreads onto zeros
     if (vel) {  // u(t) of this step, for the interpolation at the vertices
         vel[n] = make_float4(u.x, u.y, u.z, 0.f);
     }
@@ -493,9 +492,7 @@ __device__ __forceinline__ void lbm_pair(const T *__restrict__ fin, T *__restric
     float2 Fx = f2(p.gx), Fy = f2(p.gy), Fz = f2(p.gz);
     bool spread0 = false, spread1 = false;
     if (HAS_F) {
-        const float4 a = __ldcg(F + n0), b = __ldcg(F + n0 + 1);
-        spread0 = a.x != 0.f || a.y != 0.f || a.z != 0.f;
-        spread1 = b.x != 0.f || b.y != 0.f || b.z != 0.f;
+        const float4 a = force_at(F, p, n0, spread0), b = force_at(F, p, n0 + 1, spread1);
         Fx = add2(Fx, make_float2(a.x, b.x));
         Fy = add2(Fy, make_float2(a.y, b.y));
         Fz = add2(Fz, make_float2(a.z, b.z));
@@ -503,8 +500,8 @@ __device__ __forceinline__ void lbm_pair(const T *__restrict__ fin, T *__restric
     float2 ux, uy, uz;
     collide2<T>(d, Fx, Fy, Fz, p, ux, uy, uz);
     if (HAS_F) {  // consumed: the next step spreads onto zeros
-        if (spread0) F[n0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (spread1) F[n0 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (spread0) force_clear(F, p, n0);
+        if (spread1) force_clear(F, p, n0 + 1);
     }
     if (vel) {
         vel[n0] = make_float4(ux.x, uy.x, uz.x, 0.f);
@@ -758,7 +755,8 @@ __global__ void k_macro(const T *__restrict__ f, const float4 *__restrict__ F, L
         uy = q.y;
         uz = q.z;
     } else {
-        const float4 a = F[n];
+        bool nonzero;
+        const float4 a = force_at(F, p, n, nonzero);
         const float Fx = a.x + p.gx, Fy = a.y + p.gy, Fz = a.z + p.gz;
         ux = (jx - 0.5f * Fx) / r;
         uy = (jy - 0.5f * Fy) / r;
