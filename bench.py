@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--box", default="512,256,256", help="lattice of the suspension workload")
     ap.add_argument("--delta", choices=("trilinear", "peskin4"), default="trilinear",
                     help="immersed-boundary delta kernel")
+    ap.add_argument("--spread", choices=("float", "fixed"), default="float",
+                    help="force-field accumulation: float atomics, or the deterministic fixed-point field")
     ap.add_argument("--fused", type=int, default=-1, choices=(-1, 0, 1),
                     help="cell chain as one persistent launch (1) or two (0); -1: default / autotuner")
     ap.add_argument("--pop-format", choices=("f32", "f16", "bf16", "f16sr", "bf16sr"), default="f32",
@@ -519,6 +521,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         ctx = P.cf_create(dev, stream.cuda_stream)
         P.cf_set_population_format(ctx, args.pop_format)
+        P.cf_set_spread(ctx, args.spread)
         ids = P.load_workload(ctx, wl)
         if args.fused >= 0:
             P.cf_set_launch_shape(ctx, {"fused": args.fused})
@@ -594,6 +597,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"f32": "f32", "f16": "f16", "bf16": "bf16", "f16sr": "f16 (stochastic rounding)",
                   "bf16sr": "bf16 (stochastic rounding)"}[args.pop_format],
+        "spread": args.spread,
         "data": "synthetic (seeded sphere mesh, fluid at rest at t=0)",
         "config": config_of(wl),
         "mlups": job_rate(wl.n_nodes * K, world, ms / 1e3) / 1e6,
@@ -623,7 +627,8 @@ def run_ours(args):
     if (rank == 0 and world == 1 and args.precision_steps > 0 and args.workload == "shear"
             and args.pop_format == "f32"):
         out["precision"] = precision_block(P, torch, dev, args.precision_steps)
-    default_shear = args.workload == "shear" and args.pop_format == "f32" and wl.delta == 2 and args.n == 128
+    default_shear = (args.workload == "shear" and args.pop_format == "f32" and wl.delta == 2 and args.n == 128
+                     and args.spread == "float")
     if rank == 0 and world == 1 and default_shear and args.suspension_steps > 0:
         out["suspension"] = suspension_block(P, torch, dev, args.suspension_steps, peak)
     if rank == 0 and world == 1 and default_shear and args.sweep_steps > 0:
