@@ -80,11 +80,13 @@ def run(P, wl, steps, shape=None, mode="pipelined", spread="fixed", fmt="f32"):
     return y, u, rho
 
 
-def same_state(a, b):
-    """Bit-identical positions and populations; velocities to rounding."""
+def same_state(a, b, utol=1e-6):
+    """Bit-identical positions and populations; velocities to rounding (of
+    FP32, or of the 16-bit storage, whose populations give the readback
+    outside the force region)."""
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[2], b[2])
-    assert rel(a[1], b[1]) <= 1e-6
+    assert rel(a[1], b[1]) <= utol
 
 
 def test_fixed_spread_matches_oracle(P):
@@ -132,7 +134,7 @@ def test_fixed_spread_with_stochastic_rounding_is_bit_identical(P):
     a = run(P, wl, 40, shape={"near_rows": 1, "pop_pairs": 1}, fmt="f16sr")
     b = run(P, wl, 40, shape={"tile_x": 32, "tile_y": 2, "tile_z": 4, "near_rows": 1, "pop_pairs": 1},
             fmt="f16sr")
-    same_state(a, b)
+    same_state(a, b, utol=1e-4)
 
 
 def test_spread_mode_is_validated(P):
