@@ -198,10 +198,11 @@ cf_status cf_step_async(cf_ctx *ctx, int32_t n);
 cf_status cf_step_exchange(cf_ctx *ctx, int32_t n, const double *y_in, double *y_out);
 
 /* Build, without running anything, every CUDA graph that cf_step or
- * cf_step_async of n steps from the current state would build on first use
- * (graph capture and instantiation take milliseconds; after this call the
- * n-step call only launches). Positions, populations and the step counter
- * are unchanged. CF_ESTATE before cf_lbm_init, CF_EINVAL for n < 0. */
+ * cf_step_async of n steps would build on first use, from the current state
+ * and from every other buffer parity and region phase (the step counter
+ * modulo 2 and 3), so that repeated n-step calls only launch (graph capture
+ * and instantiation take milliseconds). Positions, populations and the step
+ * counter are unchanged. CF_ESTATE before cf_lbm_init, CF_EINVAL for n < 0. */
 cf_status cf_prepare_steps(cf_ctx *ctx, int32_t n);
 
 /* Wait for the context's stream (polling, with the host timeout) and return

@@ -44,11 +44,15 @@ namespace {
 // Steps per graph in the steady part of cf_step: even (buffer parity) and a
 // multiple of 3 (region slots), so a graph starts and ends in the same phase.
 constexpr int kChunk = 12;
+// Calls of up to this many steps run as one graph (first step, the rest and
+// the last K5); longer ones as the first step, chunks, one graph for the
+// remainder and the last K5. Every graph boundary joins the two streams.
+constexpr int kWhole = 24;
 
 // First: the first step of a call (its region from the current positions);
 // Mid: pipelined steps; Tail: K5 of the last step; Fluid: steps without
-// cells; Single: a whole one-step call, K5 included (it waits for the near
-// field only, so it overlaps the end of the far field).
+// cells; Single: a whole call of up to kWhole steps, the last K5 included
+// (it waits for the near field only, so it overlaps the end of the far field).
 enum class Kind { First = 0, Mid = 1, Tail = 2, Fluid = 3, Single = 4 };
 
 // Region slots of step t (phase s = t % 3): the step's force region is slot
@@ -211,8 +215,9 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
                                     sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
-    if (kind == Kind::Single) {  // K5 of this step (parity p0), after the near field in sc order
-        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sc, sh.interp_block));
+    if (kind == Kind::Single) {  // K5 of the last step, after its near field in sc order
+        const int pl = p0 ^ ((nsteps - 1) & 1);
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[pl], c->u[1 - pl], c->d_err, sc, sh.interp_block));
         CUDA_TRY(c, cudaEventRecord(ev_near[nsteps - 1], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
@@ -290,9 +295,9 @@ cf_status launch_steps(cf_ctx *c, Kind kind, int nsteps, bool launch = true) {
     return CF_OK;
 }
 
-// The graphs of n steps from the current state: the first step, chunks of
-// kChunk, single steps, then K5 of the last step (with cells); or chunks of
-// fluid-only steps. launch = false instantiates them without running and
+// The graphs of n steps from the current state: with cells one graph for up
+// to kWhole steps, else the first step, chunks of kChunk, the remainder,
+// then K5 of the last step; or chunks of fluid-only steps and the remainder. launch = false instantiates them without running and
 // leaves the state as it was.
 cf_status schedule_steps(cf_ctx *c, int32_t n, bool launch) {
     const int cur0 = c->cur;
@@ -305,13 +310,10 @@ cf_status schedule_steps(cf_ctx *c, int32_t n, bool launch) {
             st = launch_steps(c, Kind::Fluid, kChunk, launch);
             left -= kChunk;
         }
-        while (st == CF_OK && left > 0) {
-            st = launch_steps(c, Kind::Fluid, 1, launch);
-            --left;
-        }
+        if (st == CF_OK && left > 0) st = launch_steps(c, Kind::Fluid, left, launch);
     } else {
-        if (n == 1) {  // one graph for the whole call
-            st = launch_steps(c, Kind::Single, 1, launch);
+        if (n <= kWhole) {  // one graph for the whole call
+            st = launch_steps(c, Kind::Single, n, launch);
             if (!launch) {
                 c->cur = cur0;
                 c->tstep = t0;
@@ -324,10 +326,7 @@ cf_status schedule_steps(cf_ctx *c, int32_t n, bool launch) {
             st = launch_steps(c, Kind::Mid, kChunk, launch);
             left -= kChunk;
         }
-        while (st == CF_OK && left > 0) {
-            st = launch_steps(c, Kind::Mid, 1, launch);
-            --left;
-        }
+        if (st == CF_OK && left > 0) st = launch_steps(c, Kind::Mid, left, launch);
         cudaGraphExec_t g;
         if (st == CF_OK) st = get_graph(c, Kind::Tail, c->cur ^ 1, 0, 1, &g);  // parity of the last step
         if (st == CF_OK && launch) CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
@@ -828,7 +827,19 @@ cf_status cf_prepare_steps(cf_ctx *c, int32_t n) {
     if (n < 0) return fail(c, CF_EINVAL, "n must be >= 0");
     if (!c->lbm_ready) return fail(c, CF_ESTATE, "cf_prepare_steps needs cf_lbm_init first");
     if (n == 0) return CF_OK;
-    return schedule_steps(c, n, false);
+    // the graphs depend on the buffer parity and the region phase: build them
+    // for all six states, then put the state back
+    const int cur0 = c->cur;
+    const long long t0 = c->tstep;
+    cf_status st = CF_OK;
+    for (int k = 0; k < 6 && st == CF_OK; ++k) {
+        c->cur = (cur0 + k) & 1;
+        c->tstep = t0 - t0 % 3 + k % 3;
+        st = schedule_steps(c, n, false);
+    }
+    c->cur = cur0;
+    c->tstep = t0;
+    return st;
 }
 
 cf_status cf_synchronize(cf_ctx *c) {

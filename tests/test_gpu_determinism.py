@@ -68,6 +68,9 @@ def run(P, wl, steps, shape=None, mode="pipelined", spread="fixed", fmt="f32"):
     ids = P.load_workload(ctx, wl)
     if mode == "pipelined":
         P.cf_step(ctx, steps)
+    elif mode == "split":  # two calls of odd lengths, each one graph
+        P.cf_step(ctx, 17)
+        P.cf_step(ctx, steps - 17)
     elif mode == "single":
         for _ in range(steps):
             P.cf_step(ctx, 1)
@@ -115,12 +118,13 @@ def test_fixed_spread_is_bit_identical_across_launch_shapes(P, delta):
 
 
 def test_fixed_spread_is_bit_identical_across_schedules(P):
+    """40 steps as one call (the first step, three 12-step graphs, a 3-step
+    remainder and the last K5), as calls of 17 and 23 steps (one graph each),
+    one step per call, and the profiled path."""
     wl = configs.small_shear()
-    a = run(P, wl, 24, mode="pipelined")
-    b = run(P, wl, 24, mode="single")
-    c = run(P, wl, 24, mode="profiled")
-    for r in (b, c):
-        same_state(r, a)
+    a = run(P, wl, 40, mode="pipelined")
+    for mode in ("split", "single", "profiled"):
+        same_state(run(P, wl, 40, mode=mode), a)
 
 
 def test_fixed_spread_with_stochastic_rounding_is_bit_identical(P):
