@@ -58,7 +58,7 @@ def lib():
             "cf_step": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_step_async": ([vp, ctypes.c_int32], ctypes.c_int),
             "cf_prepare_steps": ([vp, ctypes.c_int32], ctypes.c_int),
-            "cf_step_exchange": ([vp, ctypes.c_int32, _d, _d], ctypes.c_int),
+            "cf_step_exchange": ([vp, ctypes.c_int32, vp, vp], ctypes.c_int),  # addresses: the per-step call
             "cf_get_launch_shape": ([vp, _i], ctypes.c_int),
             "cf_set_launch_shape": ([vp, _i], ctypes.c_int),
             "cf_autotune": ([vp, ctypes.c_int32, _i], ctypes.c_int),
@@ -273,10 +273,16 @@ def cf_step_exchange(ctx, n: int, y_in=None, out=None):
     """Set all positions from ``y_in`` [V,3] (or keep them when None),
     advance n steps, and return all positions (into ``out`` when given),
     with one wait."""
-    nv = lib().cf_cell_verts(ctx.handle, CF_ALL_CELLS)
-    yi = None if y_in is None else _f64(y_in).reshape(nv, 3)
+    L = lib()
+    nv = L.cf_cell_verts(ctx.handle, CF_ALL_CELLS)
+    pi = None
+    if y_in is not None:
+        yi = _f64(y_in)
+        if yi.size != 3 * nv:
+            raise ValueError(f"y_in must hold {nv} x 3 positions")
+        pi = yi.ctypes.data
     yo = _out(out, (nv, 3))
-    _check(ctx, lib().cf_step_exchange(ctx.handle, n, _p(yi), _p(yo)))
+    _check(ctx, L.cf_step_exchange(ctx.handle, n, pi, yo.ctypes.data))
     return yo
 
 
