@@ -46,9 +46,33 @@ CELL_BYTES_PER_TET = 16 + 48 + 64 + 16 + 64
 CELL_BYTES_PER_VERTEX = 32 + 8 + 32 + 16
 
 
+# interpolation + advection: per vertex xr and u read (32), u written (16), and the velocity (float4)
+# of each support node read (16 W^3)
+INTERP_BYTES_PER_VERTEX = 32 + 16
+
+
 def cell_bytes(n_tets, n_verts, width):
     """Algorithmic bytes of the tet forces + vertex sums + spread of one step."""
     return CELL_BYTES_PER_TET * n_tets + (CELL_BYTES_PER_VERTEX + 16 * width**3) * n_verts
+
+
+def step_roofline(wl, roof, pop_format, ms_per_step, peak):
+    """The whole step against the HBM peak: the algorithmic bytes of every
+    kernel of one step (far and near stream-collide, tet forces, vertex sums
+    + spread, interpolation + advection) over the measured time per step."""
+    pop_b = POP_BYTES_PER_NODE // (1 if pop_format == "f32" else 2)
+    near_nodes, n_sup = roof["near_region_nodes"], roof["support_nodes"]
+    parts = {
+        "far": pop_b * (wl.n_nodes - near_nodes),
+        "near": (pop_b + NEAR_BYTES_PER_NODE - POP_BYTES_PER_NODE) * near_nodes
+        + CONSUME_BYTES_PER_SUPPORT_NODE * n_sup,
+        "cells": cell_bytes(wl.n_tets, wl.n_verts, wl.delta) if wl.n_tets else 0,
+        "interp": (INTERP_BYTES_PER_VERTEX + 16 * wl.delta**3) * wl.n_verts,
+    }
+    total = sum(parts.values())
+    achieved = total / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "algorithmic_bytes_per_step": total, "parts": parts, "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak}
 
 
 def cell_roofline(wl, kms, peak):
@@ -442,13 +466,14 @@ def suspension_block(P, torch, dev, steps, peak):
         y_now = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
         P.cf_destroy(ctx)
     med = statistics.median(ms) / 1e3
+    roof = stream_collide_roofline(wl, kms, near_nodes, y_now, "f32", peak)
     return {"workload": wl.name, "lattice": [wl.nx, wl.ny, wl.nz], "n_cells": len(wl.cells),
             "n_verts": wl.n_verts, "n_tets": wl.n_tets, "steps_per_s": steps / med,
             "mlups": wl.n_nodes * steps / med / 1e6, "tet_forces_per_s": wl.n_tets * steps / med,
             "regions": region_stats(ms, steps), "launch_shape": shape,
             "kernel_ms": dict(zip(KERNELS, [float(x) for x in kms])),
-            "roofline": stream_collide_roofline(wl, kms, near_nodes, y_now, "f32", peak),
-            "cell_roofline": cell_roofline(wl, kms, peak), "clocks": clk}
+            "roofline": roof, "cell_roofline": cell_roofline(wl, kms, peak),
+            "step_roofline": step_roofline(wl, roof, "f32", med * 1e3 / steps, peak), "clocks": clk}
 
 
 SWEEP_CA = (0.05, 0.2, 0.5)
@@ -615,6 +640,7 @@ def run_ours(args):
         # the tet forces and vertex sums + spread against the same HBM peak (FP32 corner forces
         # through HBM: the deterministic incidence-row gather)
         "cell_roofline": cell_roofline(wl, kms, peak) if wl.n_tets else None,
+        "step_roofline": step_roofline(wl, roof, args.pop_format, ms / K, peak),
         "e2e": {
             "value": job_rate(args.e2e_steps, world, e2e_s),
             "unit": "steps/s",

@@ -88,3 +88,21 @@ def test_stream_collide_roofline_picks_the_longer_part_and_counts_its_bytes():
 
 def test_sweep_cases_cover_the_capillary_numbers_and_weights():
     assert bench.SWEEP_CA == (0.05, 0.2, 0.5) and bench.SWEEP_W == (0.0, 0.5, 1.0)
+
+
+def test_step_roofline_adds_every_kernel_of_the_step():
+    class WL(_WL):
+        n_tets, n_verts = 100, 30
+
+    roof = {"near_region_nodes": 1000, "support_nodes": 50}
+    r = bench.step_roofline(WL, roof, "f32", 0.02, 6000.0)
+    far = 152 * (16 ** 3 - 1000)
+    near = 184 * 1000 + 16 * 50
+    cells = 100 * 208 + 30 * (88 + 8 * 16)
+    interp = 30 * (48 + 8 * 16)
+    assert r["parts"] == {"far": far, "near": near, "cells": cells, "interp": interp}
+    assert r["algorithmic_bytes_per_step"] == far + near + cells + interp
+    assert abs(r["frac"] - (far + near + cells + interp) / 0.02e-3 / 1e9 / 6000.0) < 1e-12
+    # 16-bit storage halves the population bytes only
+    r16 = bench.step_roofline(WL, roof, "f16sr", 0.02, 6000.0)
+    assert r16["parts"]["far"] == far // 2 and r16["parts"]["near"] == near - 76 * 1000

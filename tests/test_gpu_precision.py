@@ -188,6 +188,48 @@ def test_taylor_deformation_pair_and_single_forms(P, sheared_oracle, fmt, tol, n
         P.cf_destroy(ctx)
 
 
+@pytest.fixture(scope="module")
+def channel_oracle():
+    """The precision workload at full size (256 x 128 x 128 channel with a
+    body force, one R = 16 cell off the centre plane), 30 coupled steps of
+    the FP64 oracle from rest."""
+    from workloads import configs
+
+    wl = configs.precision_channel()
+    sim = oracle.Coupled(wl)
+    sim.step(30)
+    return wl, sim.y.copy(), sim.fluid.u.copy()
+
+
+@pytest.mark.parametrize("fmt,tol_u,tol_y", [("f32", 1e-5, 1e-5), ("f16", 2e-2, 2e-2), ("f16sr", 2e-2, 2e-2),
+                                             ("bf16", 2e-1, 2e-1), ("bf16sr", 2e-1, 2e-1)])
+def test_precision_channel_full_size_by_format(P, channel_oracle, fmt, tol_u, tol_y):
+    """Every storage format on the full-size precision workload against the
+    FP64 oracle (not against FP32): velocity field, the velocity on the
+    nodes around the cell and the cell's displacement after 30 steps."""
+    wl, y_ref, u_ref = channel_oracle
+    ctx = P.cf_create(0)
+    P.cf_set_population_format(ctx, fmt)
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, 30)
+    y, u = P.cf_get_positions(ctx, cid), P.cf_get_velocity(ctx)
+    P.cf_destroy(ctx)
+    x0 = wl.cells[0].y0
+    near = np.zeros(wl.nx * wl.ny * wl.nz, bool)
+    b = np.floor(y_ref).astype(np.int64) - 1
+    for dz in range(4):
+        for dy in range(4):
+            for dx in range(4):
+                near[((b[:, 0] + dx) % wl.nx) + wl.nx * ((b[:, 1] + dy) + wl.ny * ((b[:, 2] + dz) % wl.nz))] = True
+    e_u = rel(u, u_ref)
+    e_near = rel(u.reshape(-1, 3)[near], u_ref.reshape(-1, 3)[near])
+    e_y = rel(y - x0, y_ref - x0)
+    print(f"{fmt}: velocity {e_u:.2e}, near the cell {e_near:.2e}, displacement {e_y:.2e}")
+    assert e_u <= tol_u
+    assert e_near <= tol_u
+    assert e_y <= tol_y
+
+
 def test_stochastic_rounding_keeps_small_increments(P):
     """A weak body force in a channel at rest: per step each population
     changes by far less than half an FP16 unit in the last place, so
