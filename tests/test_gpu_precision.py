@@ -201,12 +201,16 @@ def channel_oracle():
     return wl, sim.y.copy(), sim.fluid.u.copy()
 
 
-@pytest.mark.parametrize("fmt,tol_u,tol_y", [("f32", 1e-5, 1e-5), ("f16", 2e-2, 2e-2), ("f16sr", 2e-2, 2e-2),
-                                             ("bf16", 2e-1, 2e-1), ("bf16sr", 2e-1, 2e-1)])
+@pytest.mark.parametrize("fmt,tol_u,tol_y", [("f32", 1e-5, 1e-5), ("f16", 3e-3, 3e-3), ("f16sr", 6e-4, 1e-4),
+                                             ("bf16", 2e-2, 2e-2), ("bf16sr", 4e-3, 5e-4)])
 def test_precision_channel_full_size_by_format(P, channel_oracle, fmt, tol_u, tol_y):
     """Every storage format on the full-size precision workload against the
     FP64 oracle (not against FP32): velocity field, the velocity on the
-    nodes around the cell and the cell's displacement after 30 steps."""
+    nodes around the cell and the cell's displacement after 30 steps.
+    Measured on GB300 (field / near the cell / displacement): FP32 4.4e-7 /
+    2.7e-7 / 2.6e-7; FP16 6.9e-4 / 1.1e-3 / 9.8e-4; FP16-SR 2.1e-4 / 1.4e-4 /
+    2.0e-5; BF16 4.1e-3 / 7.3e-3 / 5.7e-3; BF16-SR 1.4e-3 / 7.9e-4 / 1.6e-4.
+    The 16-bit bounds are about three times those."""
     wl, y_ref, u_ref = channel_oracle
     ctx = P.cf_create(0)
     P.cf_set_population_format(ctx, fmt)
