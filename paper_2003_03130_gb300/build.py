@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcellfsi.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "-I", os.path.join(ROOT, "include")]
 
 
@@ -31,8 +31,9 @@ def nvcc() -> str:
 
 
 def _headers_mtime() -> float:
+    """Newest of the headers and of this file (its flags)."""
     hs = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
-          glob.glob(os.path.join(ROOT, "include", "*.h")))
+          glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)])
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
