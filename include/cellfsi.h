@@ -265,8 +265,9 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *          supports overlap a dozen-fold); 0 (default): one atomic per
  *          vertex and support node.
  * Block sizes are multiples of 32 in [32, 256].
- * No shape changes a computed value beyond the rounding order of the spread
- * (float atomics). cf_set_launch_shape applies from the next cf_step call;
+ * No shape changes a computed value beyond rounding: the order of the
+ * spread's float atomics (none with cf_set_spread(ctx, CF_SPREAD_FIXED)) and
+ * the force kernel's form [9]. cf_set_launch_shape applies from the next cf_step call;
  * CF_EINVAL for a value outside these sets. */
 #define CF_SHAPE_LEN 14
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
