@@ -1158,7 +1158,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (c->T > 0) {
         // one knob at a time, the others at their best so far; a candidate
-        // is judged by the time of whole pipelined steps, so that what the
+        // is rated by the time of whole pipelined steps, so that what the
         // far field overlaps counts as it does in cf_step
         struct Knob {
             int Shape::*field;
