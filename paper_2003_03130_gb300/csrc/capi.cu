@@ -176,7 +176,8 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     const MeshView m = view(c);
     const Shape &sh = c->shape;
     if (kind == Kind::Tail) {  // K5 of the last step (parity p0)
-        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sf, sh.interp_block));
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[p0], c->u[1 - p0], c->d_err, sf, sh.interp_block,
+                                         RegionSlot{nullptr}, sh.interp_form));
         return CF_OK;
     }
     if (kind == Kind::Fluid) {
@@ -206,7 +207,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         if (!(first && i == 0)) {  // K5 of the previous step (parity 1-p), with mark_k5 marking acc
             if (sh.mark_k5) CUDA_TRY(c, clear_slot(c, acc, sc));
             CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, sc, sh.interp_block,
-                                             sh.mark_k5 ? acc : none));
+                                             sh.mark_k5 ? acc : none, sh.interp_form));
         }
         if (!sh.mark_k5) CUDA_TRY(c, clear_slot(c, acc, sc));
         CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, sc));
@@ -217,7 +218,8 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
     }
     if (kind == Kind::Single) {  // K5 of the last step, after its near field in sc order
         const int pl = p0 ^ ((nsteps - 1) & 1);
-        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[pl], c->u[1 - pl], c->d_err, sc, sh.interp_block));
+        CUDA_TRY(c, launch_interp_advect(m, c->vel, c->lp, c->u[pl], c->u[1 - pl], c->d_err, sc, sh.interp_block,
+                                         RegionSlot{nullptr}, sh.interp_form));
         CUDA_TRY(c, cudaEventRecord(ev_near[nsteps - 1], sc));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(sf, ev_near[nsteps - 1], 0));
@@ -951,7 +953,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             cudaEventRecord(E[0], s);
             if (cells && t > 0 && e == cudaSuccess)
                 e = launch_interp_advect(m, c->vel, c->lp, c->u[1 - p], c->u[p], c->d_err, s, sh.interp_block,
-                                         sh.mark_k5 ? accm : none);
+                                         sh.mark_k5 ? accm : none, sh.interp_form);
             cudaEventRecord(E[1], s);
             if (cells && e == cudaSuccess) {
                 if (!sh.mark_k5) e = clear_slot(c, accm, s);
@@ -993,7 +995,8 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
     if (st == CF_OK && cells) {  // final K5
         const int p = c->cur ^ 1;
         cudaEventRecord(ev[NE * BATCH], s);
-        cudaError_t e = launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s, sh.interp_block);
+        cudaError_t e = launch_interp_advect(m, c->vel, c->lp, c->u[p], c->u[1 - p], c->d_err, s, sh.interp_block,
+                                             RegionSlot{nullptr}, sh.interp_form);
         cudaEventRecord(ev[NE * BATCH + 1], s);
         st = e == cudaSuccess ? wait_stream(c) : fail(c, CF_ECUDA, "launch failed: %s", cudaGetErrorString(e));
         float ms = 0.f;
@@ -1095,6 +1098,7 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[11] = sh.pop_pairs;
     shape[12] = sh.mark_k5;
     shape[13] = sh.staged;
+    shape[14] = sh.interp_form;
     return CF_OK;
 }
 
@@ -1132,6 +1136,8 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.mark_k5 = shape[12];
     if (shape[13] != 0 && shape[13] != 1) return fail(c, CF_EINVAL, "staged must be 0 or 1");
     sh.staged = shape[13];
+    if (shape[14] != 0 && shape[14] != 1) return fail(c, CF_EINVAL, "interp_form must be 0 or 1");
+    sh.interp_form = shape[14];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -1174,6 +1180,7 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::pop_pairs, {1, 0}},
             {&Shape::mark_k5, {0, 1}},
             {&Shape::staged, {0, 1}},
+            {&Shape::interp_form, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}},
             {&Shape::gather_block, {64, 128, 256}},
             {&Shape::interp_block, {64, 128, 256}},

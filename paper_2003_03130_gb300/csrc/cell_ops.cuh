@@ -65,6 +65,68 @@ __device__ __forceinline__ void mark_vertex(const MeshView &m, const float4 *__r
         mark_region<W>(s, lp, mark);
 }
 
+// ---- K5 in a fixed rounding order
+// The interpolation of u(t) at a vertex is split into eight partial sums:
+// for W = 2 partial k is the corner (dx, dy, dz) = (k & 1, (k >> 1) & 1,
+// k >> 2), for W = 4 the plane dz = k >> 1, rows dy = 2 (k & 1) + {0, 1},
+// x fastest. They meet in the tree ((p0 + p1) + (p2 + p3)) + ((p4 + p5) +
+// (p6 + p7)). Every product and sum is rounded explicitly (no contraction),
+// so the eight-thread form (one partial per thread, the tree by xor
+// shuffles) and the one-thread form give the same bits.
+__device__ __forceinline__ float3 add3_rn(float3 a, float3 b) {
+    return make_float3(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z));
+}
+
+template <int W>
+__device__ __forceinline__ float3 interp_partial(const Support &s, const float (&wx)[W], const float (&wy)[W],
+                                                 const float (&wz)[W], const float4 *__restrict__ vel,
+                                                 const LbmParams &p, int k) {
+    if constexpr (W == 2) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+        const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * wrapi(s.bz + dz, p.nz));
+        const float w = __fmul_rn(__fmul_rn(wx[dx], wy[dy]), wz[dz]);
+        const float4 q = __ldg(vel + n);
+        return make_float3(__fmul_rn(w, q.x), __fmul_rn(w, q.y), __fmul_rn(w, q.z));
+    } else {
+        const int dz = k >> 1, dy0 = 2 * (k & 1);
+        const int Z = wrapi(s.bz + dz, p.nz);
+        float3 a = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int dy = dy0 + j;
+            const int row = p.nx * (s.by + dy + p.ny * Z);
+            const float wyz = __fmul_rn(wy[dy], wz[dz]);
+#pragma unroll
+            for (int dx = 0; dx < W; ++dx) {
+                const float w = __fmul_rn(wx[dx], wyz);
+                const float4 q = __ldg(vel + wrapi(s.bx + dx, p.nx) + row);
+                a.x = __fmaf_rn(w, q.x, a.x);
+                a.y = __fmaf_rn(w, q.y, a.y);
+                a.z = __fmaf_rn(w, q.z, a.z);
+            }
+        }
+        return a;
+    }
+}
+
+// The interpolated u(t) at x + u_cur (d) in one thread; false if that
+// position's support is not valid.
+template <int W>
+__device__ __forceinline__ bool interp_vertex(const MeshView &m, const float4 *__restrict__ vel, const LbmParams &p,
+                                              float4 xr, float4 uc, Support &s, float3 &d) {
+    d = make_float3(0.f, 0.f, 0.f);
+    if (!support_of<W>(m.origin, xr, uc, p.ny, s)) return false;
+    float wx[W], wy[W], wz[W];
+    delta_weights<W>(s.fx, wx);
+    delta_weights<W>(s.fy, wy);
+    delta_weights<W>(s.fz, wz);
+    float3 a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = interp_partial<W>(s, wx, wy, wz, vel, p, k);
+    d = add3_rn(add3_rn(add3_rn(a[0], a[1]), add3_rn(a[2], a[3])), add3_rn(add3_rn(a[4], a[5]), add3_rn(a[6], a[7])));
+    return true;
+}
+
 // Corner-force load: from L2 (FC_L2) when the forces were written by other
 // blocks of the same launch, so that no stale L1 line is read.
 template <bool FC_L2>

@@ -45,6 +45,7 @@ struct Shape {
     int mark_k5 = 0;    // the interpolation (eight lanes per vertex) marks the region of the step after next,
                         // instead of the force launch (one thread per vertex) the next step's
     int staged = 0;     // the spread accumulates a block of vertices in shared memory before its global atomics
+    int interp_form = 0;  // interpolation + advection: eight threads per vertex (0) or one (1)
 };
 
 }  // namespace cf

@@ -14,16 +14,15 @@
 //         (dz, dy) takes the two nodes of its x row, for W = 4 lane dz the
 //         16 nodes of its z plane (float atomics: the spread field is exact
 //         up to the order of those additions).
-// K5 (k_interp_advect), eight threads per vertex:
+// K5 (k_interp_advect, eight threads per vertex, or k_interp_advect1, one):
 //   y^{t+1} = y^t + sum_x u(x) delta_h(x - y^t), with u(t) as stored by the
 //   near-field stream-collide on every node of the force region (which holds
-//   the support of y^t); each lane sums W^3 / 8 nodes in a fixed order (for
-//   W = 2 lane (dz, dy, dx) its node, for W = 4 lane (dz, j) the rows
-//   dy = 2j, 2j + 1 of plane dz = 0..3) and the eight partial sums meet in a
-//   fixed shuffle tree. The eight lanes then hold y^{t+1} and add the tiles
-//   of its support grown by one node to the force region of step t + 2 (a
-//   vertex moves less than a spacing per step, so that region holds the
-//   support of y^{t+2}), each lane taking its share of the tiles.
+//   the support of y^t), as eight partial sums of W^3 / 8 nodes each (for
+//   W = 2 one corner (dz, dy, dx), for W = 4 the rows dy = 2j, 2j + 1 of a
+//   plane dz) in a fixed tree, so both forms give the same bits. With
+//   marking, the new position's support grown by one node is added to the
+//   force region of step t + 2 (a vertex moves less than a spacing per step,
+//   so that region holds the support of y^{t+2}).
 #include <climits>
 
 #include "cell_ops.cuh"
@@ -183,10 +182,11 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, 
     return cudaGetLastError();
 }
 
-// Eight threads per vertex, each summing W^3 / 8 support nodes; the group of
-// eight combines its partial sums with shuffles. MARK: the lanes also mark the
-// region of the step after next (a separate instantiation, so that the form
-// without marking keeps its lower register count: 30 against 48).
+// Eight threads per vertex, each one of the eight partial sums of the
+// interpolation (interp_partial); the group of eight forms their tree by
+// shuffles. MARK: the lanes also mark the region of the step after next (a
+// separate instantiation, so that the form without marking keeps its lower
+// register count).
 template <int W, bool MARK>
 __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const float4 *__restrict__ vel, LbmParams p,
                                                        const float4 *__restrict__ u_cur, float4 *u_next,
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
     const int v = g >> 3, lane = g & 7;
     const bool live = v < m.V;
     float4 uc = make_float4(0.f, 0.f, 0.f, 0.f), xr = uc;
-    float vx = 0.f, vy = 0.f, vz = 0.f;
+    float3 a = make_float3(0.f, 0.f, 0.f);
     bool ok = false;
     if (live) {
         uc = __ldg(u_cur + v);
@@ -207,43 +207,18 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
             delta_weights<W>(s.fx, wx);
             delta_weights<W>(s.fy, wy);
             delta_weights<W>(s.fz, wz);
-            if constexpr (W == 2) {  // lane = corner (dx, dy, dz)
-                const int dx = lane & 1, dy = (lane >> 1) & 1, dz = lane >> 2;
-                const int n = wrapi(s.bx + dx, p.nx) + p.nx * (s.by + dy + p.ny * wrapi(s.bz + dz, p.nz));
-                const float w = wx[dx] * wy[dy] * wz[dz];
-                const float4 q = __ldg(vel + n);
-                vx = w * q.x;
-                vy = w * q.y;
-                vz = w * q.z;
-            } else {  // lane = (dz, row pair): plane dz = lane >> 1, rows dy = 2 (lane & 1) + {0, 1}
-                const int dz = lane >> 1, dy0 = 2 * (lane & 1);
-                const int Z = wrapi(s.bz + dz, p.nz);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int dy = dy0 + j;
-                    const int row = p.nx * (s.by + dy + p.ny * Z);
-                    const float wyz = wy[dy] * wz[dz];
-#pragma unroll
-                    for (int dx = 0; dx < W; ++dx) {
-                        const int n = wrapi(s.bx + dx, p.nx) + row;
-                        const float w = wx[dx] * wyz;
-                        const float4 q = __ldg(vel + n);
-                        vx = fmaf(w, q.x, vx);
-                        vy = fmaf(w, q.y, vy);
-                        vz = fmaf(w, q.z, vz);
-                    }
-                }
-            }
+            a = interp_partial<W>(s, wx, wy, wz, vel, p, lane);
         }
     }
+    // lane 0 ends with ((p0 + p1) + (p2 + p3)) + ((p4 + p5) + (p6 + p7))
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
-        vx += __shfl_xor_sync(0xffffffffu, vx, o);
-        vy += __shfl_xor_sync(0xffffffffu, vy, o);
-        vz += __shfl_xor_sync(0xffffffffu, vz, o);
+        a.x = __fadd_rn(a.x, __shfl_xor_sync(0xffffffffu, a.x, o));
+        a.y = __fadd_rn(a.y, __shfl_xor_sync(0xffffffffu, a.y, o));
+        a.z = __fadd_rn(a.z, __shfl_xor_sync(0xffffffffu, a.z, o));
     }
     if (!live) return;
-    const float4 un = make_float4(uc.x + vx, uc.y + vy, uc.z + vz, 0.f);
+    const float4 un = make_float4(__fadd_rn(uc.x, a.x), __fadd_rn(uc.y, a.y), __fadd_rn(uc.z, a.z), 0.f);
     if (MARK && ok) {  // the region of step t + 2 (an invalid support is K23's to report)
         Support s2;
         if (support_of<W>(m.origin, xr, un, p.ny, s2)) mark_region<W>(s2, p, mark, lane, 8);
@@ -257,27 +232,64 @@ __global__ void __launch_bounds__(256, 4) k_interp_advect(MeshView m, const floa
     if (!isfinite(un.x + un.y + un.z)) atomicOr(err, ERR_NONFINITE);
     // the next step's force region holds this step's support grown by one
     // node: a move of a spacing or more along an axis would leave it
-    if (!(fabsf(vx) < 1.f && fabsf(vy) < 1.f && fabsf(vz) < 1.f)) atomicOr(err, ERR_MOVED);
+    if (!(fabsf(a.x) < 1.f && fabsf(a.y) < 1.f && fabsf(a.z) < 1.f)) atomicOr(err, ERR_MOVED);
     u_next[v] = un;
 }
 
+// One thread per vertex: the same partial sums and tree in one thread
+// (fewer instructions per vertex than eight threads that each recompute the
+// support and the weights; less parallelism for small meshes).
+template <int W, bool MARK>
+__global__ void __launch_bounds__(256) k_interp_advect1(MeshView m, const float4 *__restrict__ vel, LbmParams p,
+                                                        const float4 *__restrict__ u_cur, float4 *u_next,
+                                                        unsigned *err, RegionSlot mark) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= m.V) return;
+    const float4 uc = __ldg(u_cur + v), xr = __ldg(m.xr + v);
+    Support s;
+    float3 d;
+    if (!interp_vertex<W>(m, vel, p, xr, uc, s, d)) {
+        atomicOr(err, ERR_DOMAIN);
+        u_next[v] = uc;
+        return;
+    }
+    const float4 un = make_float4(__fadd_rn(uc.x, d.x), __fadd_rn(uc.y, d.y), __fadd_rn(uc.z, d.z), 0.f);
+    if (MARK) {
+        Support s2;
+        if (support_of<W>(m.origin, xr, un, p.ny, s2)) mark_region<W>(s2, p, mark);
+    }
+    if (!isfinite(un.x + un.y + un.z)) atomicOr(err, ERR_NONFINITE);
+    if (!(fabsf(d.x) < 1.f && fabsf(d.y) < 1.f && fabsf(d.z) < 1.f)) atomicOr(err, ERR_MOVED);
+    u_next[v] = un;
+}
+
+template <int W, bool MARK>
+static void interp_t(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur, float4 *u_next,
+                     unsigned *err, cudaStream_t s, int bs, const RegionSlot &mark, int form) {
+    if (form == 1) {
+        k_interp_advect1<W, MARK><<<(m.V + bs - 1) / bs, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+    } else {
+        const long long threads = 8LL * m.V;
+        k_interp_advect<W, MARK><<<(int)((threads + bs - 1) / bs), bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+    }
+}
+
 cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
-                                 float4 *u_next, unsigned *err, cudaStream_t s, int block, const RegionSlot &mark) {
+                                 float4 *u_next, unsigned *err, cudaStream_t s, int block, const RegionSlot &mark,
+                                 int form) {
     if (m.V == 0) return cudaSuccess;
     const int bs = block > 0 ? block : 128;
-    const long long threads = 8LL * m.V;
-    const int blocks = (int)((threads + bs - 1) / bs);
     const bool mk = mark.bits != nullptr;
     if (p.dw == 4) {
         if (mk)
-            k_interp_advect<4, true><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+            interp_t<4, true>(m, vel, p, u_cur, u_next, err, s, bs, mark, form);
         else
-            k_interp_advect<4, false><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+            interp_t<4, false>(m, vel, p, u_cur, u_next, err, s, bs, mark, form);
     } else {
         if (mk)
-            k_interp_advect<2, true><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+            interp_t<2, true>(m, vel, p, u_cur, u_next, err, s, bs, mark, form);
         else
-            k_interp_advect<2, false><<<blocks, bs, 0, s>>>(m, vel, p, u_cur, u_next, err, mark);
+            interp_t<2, false>(m, vel, p, u_cur, u_next, err, s, bs, mark, form);
     }
     return cudaGetLastError();
 }

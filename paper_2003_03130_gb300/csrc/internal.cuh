@@ -149,13 +149,16 @@ __device__ __forceinline__ void delta_weights<2>(float f, float (&w)[2]) {
     w[0] = 1.f - f;
     w[1] = f;
 }
+// Every operation is rounded explicitly (no contraction), so the weights
+// are the same bits wherever they are inlined.
 template <>
 __device__ __forceinline__ void delta_weights<4>(float f, float (&w)[4]) {
-    const float q = sqrtf(fmaf(4.f * f, 1.f - f, 1.f));
-    w[0] = 0.125f * (3.f - 2.f * f - q);
-    w[1] = 0.125f * (3.f - 2.f * f + q);
-    w[2] = 0.125f * (1.f + 2.f * f + q);
-    w[3] = 0.125f * (1.f + 2.f * f - q);
+    const float q = __fsqrt_rn(__fmaf_rn(__fmul_rn(4.f, f), __fsub_rn(1.f, f), 1.f));
+    const float a = __fsub_rn(3.f, __fmul_rn(2.f, f)), b = __fadd_rn(1.f, __fmul_rn(2.f, f));
+    w[0] = __fmul_rn(0.125f, __fsub_rn(a, q));
+    w[1] = __fmul_rn(0.125f, __fadd_rn(a, q));
+    w[2] = __fmul_rn(0.125f, __fadd_rn(b, q));
+    w[3] = __fmul_rn(0.125f, __fsub_rn(b, q));
 }
 
 // ---------------------------------------------------------------- force field access
@@ -432,9 +435,13 @@ size_t pop_bytes(int fmt);
 // With mark.bits not null the same threads add the force region of the new
 // positions (the support of x + u_next grown by one node: the region of the
 // step after next) to `mark`, cleared by the caller.
+// form 0: eight threads per vertex (each a share of the support, the shares
+// summed by shuffles); 1: one thread per vertex. Both sum the same partial
+// sums in the same tree with every operation rounded explicitly: the same
+// bits.
 cudaError_t launch_interp_advect(const MeshView &m, const float4 *vel, const LbmParams &p, const float4 *u_cur,
                                  float4 *u_next, unsigned *err, cudaStream_t s, int block = 0,
-                                 const RegionSlot &mark = RegionSlot{nullptr});
+                                 const RegionSlot &mark = RegionSlot{nullptr}, int form = 0);
 // Compression between plates and the adjoint (csrc/adjoint.cu).
 // out = J_el v at displacements u (vertex sums of the corner tangents; uses m.fc).
 cudaError_t launch_force_jvp(const MeshView &m, const float4 *u, const float4 *v, float4 *out, unsigned *err,

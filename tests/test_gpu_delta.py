@@ -67,14 +67,18 @@ def test_small_shear_peskin(P, staged):
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
 
 
-@pytest.mark.parametrize("mode", ["single", "profiled"])
+@pytest.mark.parametrize("mode", ["single", "profiled", "interp1"])
 def test_peskin_every_launch_path(P, mode):
     """One-step graphs and plain launches clear and rebuild the 64-node
-    supports the same way as the pipelined graphs."""
+    supports the same way as the pipelined graphs; the 64-node
+    interpolation in one thread per vertex (interp1)."""
     wl = configs.small_shear()
     wl.delta = 4
     y0 = wl.cells[0].y0
-    ctx, sim, y, _ = pair(P, wl, 20, mode)
+    if mode == "interp1":
+        ctx, sim, y, _ = pair(P, wl, 20, "pipelined", shape={"interp_form": 1})
+    else:
+        ctx, sim, y, _ = pair(P, wl, 20, mode)
     assert rel(y - y0, sim.y - y0) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
 
