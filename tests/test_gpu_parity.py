@@ -623,16 +623,18 @@ def test_step_exchange_with_page_locked_buffers(P):
 def test_suspension_full_size(P):
     """The 400-cell suspension at full size (512 x 256 x 256 lattice,
     1.26 M vertices, 6.0 M tets) in the launch shape the autotuner picks for
-    it (32 x 2 x 4 tiles, near field in rows): every vertex displacement,
+    it (32 x 2 x 4 tiles, near field in rows, populations cached in L2, one
+    thread per vertex in the interpolation): every vertex displacement,
     every vertex force and the whole velocity field after 2 coupled steps
-    against the oracle. The cells start off their rest shape (seeded
-    perturbation of up to 0.08 lattice units per coordinate), so that the
-    forces are not rounding noise."""
+    against the oracle, and the velocity around the cells. The cells start
+    off their rest shape (seeded perturbation of up to 0.08 lattice units
+    per coordinate), so that the forces are not rounding noise."""
     wl = configs.batched_channel()
     for k, c in enumerate(wl.cells):
         c.y0 = perturb(c.x_ref, 0.08, 1000 + k)
     ctx = P.cf_create(0)
-    P.cf_set_launch_shape(ctx, {"tile_x": 32, "tile_y": 2, "tile_z": 4, "near_rows": 1})
+    P.cf_set_launch_shape(ctx, {"tile_x": 32, "tile_y": 2, "tile_z": 4, "near_rows": 1, "pop_l2": 1,
+                                "interp_form": 1})
     ids = P.load_workload(ctx, wl)
     P.cf_step(ctx, 2)
     y = P.cf_get_positions(ctx, P.CF_ALL_CELLS)
