@@ -270,18 +270,13 @@ cf_status cf_step_profiled(cf_ctx *ctx, int32_t n, double *kernel_ms, int64_t *n
  *          instructions per vertex, less parallelism). Both sum the same
  *          eight partial sums in the same tree with every operation rounded
  *          explicitly: the same positions, bit for bit ([5] gives the
- *          threads per block of either);
- *   [15]   form of the vertex sums + spread (unless [13] stages it): 0
- *          (default) four threads per vertex, each summing every fourth
- *          incidence entry and spreading onto a quarter of the support; 1
- *          one thread per vertex, the same four sums combined in the same
- *          order (the same bits; [4] gives the threads per block).
+ *          threads per block of either).
  * Block sizes are multiples of 32 in [32, 256].
  * No shape changes a computed value beyond rounding: the order of the
  * spread's float atomics (none with cf_set_spread(ctx, CF_SPREAD_FIXED)) and
  * the force kernel's form [9]. cf_set_launch_shape applies from the next cf_step call;
  * CF_EINVAL for a value outside these sets. */
-#define CF_SHAPE_LEN 16
+#define CF_SHAPE_LEN 15
 cf_status cf_get_launch_shape(cf_ctx *ctx, int32_t *shape);
 cf_status cf_set_launch_shape(cf_ctx *ctx, const int32_t *shape);
 
@@ -302,13 +297,12 @@ cf_status cf_set_chain_wait(cf_ctx *ctx, int64_t max_polls, int32_t extra_need);
  * context's own state. One knob at a time (tile shape, fused or separate
  * cell chain, near-field form, far-field load order, force-kernel form,
  * caching of FP32 populations, node pairs of 16-bit populations, where the
- * region is marked, staged spread, forms of the interpolation and of the
- * vertex sums, tet-force, spread and interpolation block sizes), every
- * candidate runs
+ * region is marked, staged spread, form of the interpolation, tet-force,
+ * spread and interpolation block sizes), every candidate runs
  * steps_per_candidate (>= 1) coupled steps exactly as cf_step runs them
  * (the same step graphs, far field and cell chain overlapping), timed as a
  * whole with CUDA events, and the fastest candidate is kept. The simulation
- * advances by those steps exactly as under cf_step (34 candidates in all). A fluid-only context has nothing to
+ * advances by those steps exactly as under cf_step (32 candidates in all). A fluid-only context has nothing to
  * tune and does not advance. shape_out (may be NULL) receives the chosen
  * shape (CF_SHAPE_LEN values). CF_ESTATE before cf_lbm_init; device errors
  * of the steps as cf_step. */

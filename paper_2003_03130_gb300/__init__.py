@@ -291,10 +291,9 @@ def cf_prepare_steps(ctx, n: int):
     _check(ctx, lib().cf_prepare_steps(ctx.handle, n))
 
 
-CF_SHAPE_LEN = 16
+CF_SHAPE_LEN = 15
 SHAPE_KEYS = ("tile_x", "tile_y", "tile_z", "tet_block", "gather_block", "interp_block", "fused", "near_rows",
-              "far_spec", "tet_form", "pop_l2", "pop_pairs", "mark_k5", "staged", "interp_form",
-              "gather_form")
+              "far_spec", "tet_form", "pop_l2", "pop_pairs", "mark_k5", "staged", "interp_form")
 
 
 def cf_get_launch_shape(ctx):
@@ -320,7 +319,7 @@ def cf_set_launch_shape(ctx, shape):
 def cf_autotune(ctx, steps_per_candidate=20):
     """Time the launch-shape candidates on the context's own state, each as
     steps_per_candidate whole coupled steps run like cf_step (the
-    simulation advances 34 x steps_per_candidate steps), and keep the
+    simulation advances 32 x steps_per_candidate steps), and keep the
     fastest; returns the chosen shape."""
     out = np.zeros(CF_SHAPE_LEN, np.int32)
     _check(ctx, lib().cf_autotune(ctx.handle, steps_per_candidate, _p(out, _i)))

@@ -139,7 +139,7 @@ cudaError_t launch_chain_step(cf_ctx *c, const MeshView &m, int p, const Shape &
     cudaError_t e = launch_tet_force(m, c->u[p], c->d_err, s, sh.tet_block, sh.tet_form, sh.mark_k5 ? nullptr : &c->lp,
                                      sh.mark_k5 ? nullptr : &acc);
     if (e != cudaSuccess) return e;
-    return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block, sh.staged, sh.gather_form);
+    return launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block, sh.staged);
 }
 
 // Tile fields of the lattice parameters for tile shape k.
@@ -964,8 +964,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             }
             cudaEventRecord(E[2], s);  // fused: the whole chain is timed as the tet-force slot
             if (cells && e == cudaSuccess && !sh.fused)
-                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block, sh.staged,
-                                         sh.gather_form);
+                e = launch_gather_spread(m, c->u[p], c->F, &c->lp, c->d_err, s, sh.gather_block, sh.staged);
             cudaEventRecord(E[3], s);
             if (e == cudaSuccess)
                 e = cells ? launch_lbm_far(c->f[p], c->f[1 - p], c->lp, use.bits, c->seed + p, sh.far_spec, s)
@@ -1100,7 +1099,6 @@ cf_status cf_get_launch_shape(cf_ctx *c, int32_t *shape) {
     shape[12] = sh.mark_k5;
     shape[13] = sh.staged;
     shape[14] = sh.interp_form;
-    shape[15] = sh.gather_form;
     return CF_OK;
 }
 
@@ -1140,8 +1138,6 @@ cf_status cf_set_launch_shape(cf_ctx *c, const int32_t *shape) {
     sh.staged = shape[13];
     if (shape[14] != 0 && shape[14] != 1) return fail(c, CF_EINVAL, "interp_form must be 0 or 1");
     sh.interp_form = shape[14];
-    if (shape[15] != 0 && shape[15] != 1) return fail(c, CF_EINVAL, "gather_form must be 0 or 1");
-    sh.gather_form = shape[15];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // no graph of the old shape in flight
     drop_graphs(c);
     c->shape = sh;
@@ -1185,7 +1181,6 @@ cf_status cf_autotune(cf_ctx *c, int32_t steps_per_candidate, int32_t *shape_out
             {&Shape::mark_k5, {0, 1}},
             {&Shape::staged, {0, 1}},
             {&Shape::interp_form, {0, 1}},
-            {&Shape::gather_form, {0, 1}},
             {&Shape::tet_block, {64, 128, 256}},
             {&Shape::gather_block, {64, 128, 256}},
             {&Shape::interp_block, {64, 128, 256}},

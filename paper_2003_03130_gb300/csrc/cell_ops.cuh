@@ -176,36 +176,6 @@ __device__ __forceinline__ void gather_vertex(const MeshView &m, int v, int lane
     }
 }
 
-// The vertex force of vertex v in one thread: the four lane sums of
-// gather_vertex (entries e0 + l, + 4, + 8, ... in ascending order) and their
-// tree (s0 + s1) + (s2 + s3), the order the four lanes' shuffles take, so
-// both forms give the same bits.
-template <bool FC_L2>
-__device__ __forceinline__ float3 gather_vertex1(const MeshView &m, int v) {
-    float3 p[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) p[k] = make_float3(0.f, 0.f, 0.f);
-    const int e0 = __ldg(m.csr_ptr + v), e1 = __ldg(m.csr_ptr + v + 1);
-    for (int e = e0; e < e1; e += 4) {
-        int id[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) id[k] = e + k < e1 ? __ldg(m.csr_idx + e + k) : -1;
-        float4 c[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            c[k] = id[k] >= 0 ? load_fc<FC_L2>(m.fc + (id[k] & 3) * m.T + (id[k] >> 2)) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (id[k] >= 0) {
-                p[k].x += c[k].x;
-                p[k].y += c[k].y;
-                p[k].z += c[k].z;
-            }
-    }
-    return make_float3((p[0].x + p[1].x) + (p[2].x + p[3].x), (p[0].y + p[1].y) + (p[2].y + p[3].y),
-                       (p[0].z + p[1].z) + (p[2].z + p[3].z));
-}
-
 // The spread of one vertex's force (fx, fy, fz) onto its support s, lane
 // `lane` of four taking its share of the support nodes: for W = 2 lane
 // (dz, dy) the two nodes of its x row, for W = 4 lane dz the W x W plane.
@@ -260,29 +230,6 @@ __device__ __forceinline__ void gather_spread_vertex(const MeshView &m, const fl
         const int n = wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz));
         force_add(F, p, n, w * fx, w * fy, w * fz);
     });
-}
-
-// gather_spread_vertex in one thread per vertex: the same vertex force
-// (gather_vertex1) and the same support nodes with the same weights.
-template <int W, bool FC_L2>
-__device__ __forceinline__ void gather_spread_vertex1(const MeshView &m, const float4 *__restrict__ u, float4 *F,
-                                                      const LbmParams &p, int do_spread, unsigned *err, int v) {
-    const float3 f = gather_vertex1<FC_L2>(m, v);
-    m.fv[v] = make_float4(f.x, f.y, f.z, 0.f);
-    if (!isfinite(f.x + f.y + f.z)) atomicOr(err, ERR_NONFINITE);
-    if (!do_spread) return;
-    Support s;
-    if (!support_of<W>(m.origin, __ldg(m.xr + v), __ldg(u + v), p.ny, s)) {
-        atomicOr(err, ERR_DOMAIN);
-        return;
-    }
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-#pragma unroll
-    for (int lane = 0; lane < 4; ++lane)
-        spread_vertex<W>(s, lane, [&](int X, int Y, int Z, float w) {
-            const int n = wrapi(X, nx) + nx * (Y + ny * wrapi(Z, nz));
-            force_add(F, p, n, w * f.x, w * f.y, w * f.z);
-        });
 }
 
 }  // namespace cf

@@ -46,7 +46,6 @@ struct Shape {
                         // instead of the force launch (one thread per vertex) the next step's
     int staged = 0;     // the spread accumulates a block of vertices in shared memory before its global atomics
     int interp_form = 0;  // interpolation + advection: eight threads per vertex (0) or one (1)
-    int gather_form = 0;  // vertex sums + spread: four threads per vertex (0) or one (1)
 };
 
 }  // namespace cf

@@ -148,16 +148,6 @@ __global__ void __launch_bounds__(256, 4) k_gather_spread(MeshView m, const floa
     gather_spread_vertex<W, false>(m, u, F, p, do_spread, err, v, g & 3, v < m.V);
 }
 
-// One thread per vertex (launch-shape form): the same sums in the same
-// order, the support and weights computed once instead of by four threads.
-template <int W>
-__global__ void __launch_bounds__(256) k_gather_spread1(MeshView m, const float4 *__restrict__ u, float4 *F,
-                                                        LbmParams p, int do_spread, unsigned *err) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= m.V) return;
-    gather_spread_vertex1<W, false>(m, u, F, p, do_spread, err, v);
-}
-
 // The staged spread's box takes more than the default 48 KB of dynamic
 // shared memory: opt in once per context, outside any stream capture.
 cudaError_t prepare_staged_spread() {
@@ -169,7 +159,7 @@ cudaError_t prepare_staged_spread() {
 }
 
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, int block, int staged, int form) {
+                                 cudaStream_t s, int block, int staged) {
     if (m.V == 0) return cudaSuccess;
     LbmParams p{};
     if (lp) p = *lp;
@@ -183,17 +173,8 @@ cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, 
         return cudaGetLastError();
     }
     const int bs = block > 0 ? block : 128;
-    const int spread = (F && lp) ? 1 : 0;
-    if (form == 1) {
-        const int blocks = (m.V + bs - 1) / bs;
-        if (p.dw == 4)
-            k_gather_spread1<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err);
-        else
-            k_gather_spread1<2><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err);
-        return cudaGetLastError();
-    }
     const long long threads = 4LL * m.V;
-    const int blocks = (int)((threads + bs - 1) / bs);
+    const int blocks = (int)((threads + bs - 1) / bs), spread = (F && lp) ? 1 : 0;
     if (p.dw == 4)
         k_gather_spread<4><<<blocks, bs, 0, s>>>(m, u, F, p, spread, err);
     else

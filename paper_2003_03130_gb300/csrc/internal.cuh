@@ -378,10 +378,9 @@ cudaError_t launch_taylor(const MeshView &m, const float4 *u, int t0, int t1, do
 // K2 (+K3): vertex force sums over the incidence rows; with F != null the
 // same threads spread their vertex force onto the lattice, directly with
 // global atomics or (staged) through a shared-memory box per block of
-// vertices. form (not staged) 0: four threads per vertex; 1: one thread per
-// vertex, the same sums in the same order (the same bits).
+// vertices.
 cudaError_t launch_gather_spread(const MeshView &m, const float4 *u, float4 *F, const LbmParams *lp, unsigned *err,
-                                 cudaStream_t s, int block = 0, int staged = 0, int form = 0);
+                                 cudaStream_t s, int block = 0, int staged = 0);
 // Shared-memory opt-in of the staged spread (once per context, before any
 // capture).
 cudaError_t prepare_staged_spread();

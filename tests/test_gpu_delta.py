@@ -71,13 +71,12 @@ def test_small_shear_peskin(P, staged):
 def test_peskin_every_launch_path(P, mode):
     """One-step graphs and plain launches clear and rebuild the 64-node
     supports the same way as the pipelined graphs; the 64-node
-    interpolation and the 64-node spread in one thread per vertex
-    (interp1)."""
+    interpolation in one thread per vertex (interp1)."""
     wl = configs.small_shear()
     wl.delta = 4
     y0 = wl.cells[0].y0
     if mode == "interp1":
-        ctx, sim, y, _ = pair(P, wl, 20, "pipelined", shape={"interp_form": 1, "gather_form": 1})
+        ctx, sim, y, _ = pair(P, wl, 20, "pipelined", shape={"interp_form": 1})
     else:
         ctx, sim, y, _ = pair(P, wl, 20, mode)
     assert rel(y - y0, sim.y - y0) <= TOL

@@ -5,8 +5,8 @@ spread's atomics no longer matters: the same workload must give bit-identical
 cell positions and fluid populations (compared through the density, which
 is read from the populations alone) whatever the launch shape (tile shape,
 block sizes, near-field form, where the region is marked, fused or separate
-cell chain, one thread or several per vertex in the interpolation and the
-vertex sums) and whatever the schedule (pipelined steps, one step per call,
+cell chain, eight threads or one per vertex in the interpolation) and
+whatever the schedule (pipelined steps, one step per call,
 the profiled path). The velocity readback takes u(t) from the near field on
 the last step's force region and from the populations elsewhere, two
 roundings of the same value, so where the regions differ it agrees to
@@ -57,8 +57,8 @@ SHAPES = [
      "interp_block": 256},
     {"tile_x": 8, "tile_y": 8, "tile_z": 4, "mark_k5": 1, "far_spec": 1, "pop_l2": 1},
     {"tile_x": 32, "tile_y": 4, "tile_z": 2, "fused": 1},
-    {"interp_form": 1, "interp_block": 64, "gather_form": 1},
-    {"interp_form": 1, "mark_k5": 1, "tile_x": 32, "tile_y": 2, "tile_z": 4, "gather_form": 1, "gather_block": 64},
+    {"interp_form": 1, "interp_block": 64},
+    {"interp_form": 1, "mark_k5": 1, "tile_x": 32, "tile_y": 2, "tile_z": 4},
 ]
 
 
