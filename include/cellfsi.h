@@ -117,7 +117,9 @@ cf_status cf_set_delta(cf_ctx *ctx, int32_t kernel);
  * y = -1/2 moving at (u_wall_lo_x, 0, 0) and y = ny-1/2 moving at
  * (u_wall_hi_x, 0, 0) (|u| < 0.1), and a uniform body-force density
  * body_force[3] (NULL = none), e.g. for a pressure-driven channel. The fluid
- * starts at rest with density 1. nx, ny, nz >= 1, nx*ny*nz*19 < 2^31.
+ * starts at rest with density 1. nx, ny, nz >= 1, ny, nz <= 65535,
+ * nx*ny*nz < 2^30 (node indices are 32-bit; 2^30 FP32 nodes take about
+ * 200 GB); CF_ENOMEM if the device cannot hold the lattice.
  * Re-initialises the fluid if called again. */
 cf_status cf_lbm_init(cf_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double tau,
                       double u_wall_lo_x, double u_wall_hi_x, const double *body_force);

@@ -451,7 +451,8 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     DeviceGuard dg(c->device);
     if (nx < 1 || ny < 1 || nz < 1) return fail(c, CF_EINVAL, "lattice extents must be >= 1");
     const long long N = (long long)nx * ny * nz;
-    if (N * 19 >= (1LL << 31)) return fail(c, CF_EINVAL, "lattice too large: 19 * nx*ny*nz must be < 2^31");
+    if (N >= (1LL << 30)) return fail(c, CF_EINVAL, "lattice too large: nx*ny*nz must be < 2^30");
+    if (ny > 65535 || nz > 65535) return fail(c, CF_EINVAL, "ny and nz must be <= 65535 (rows are grid dimensions)");
     if (!(tau > 0.5)) return fail(c, CF_EINVAL, "tau must be > 1/2");
     if (!(std::fabs(u_lo) < 0.1 && std::fabs(u_hi) < 0.1)) return fail(c, CF_EINVAL, "|u_wall| must be < 0.1");
     if (g && !(std::isfinite(g[0]) && std::isfinite(g[1]) && std::isfinite(g[2])))

@@ -245,7 +245,7 @@ __device__ __forceinline__ void lbm_node(const T *__restrict__ fin, T *__restric
                                          float4 *__restrict__ F, const LbmParams &p, int x, int y, int z,
                                          float4 *__restrict__ vel, unsigned seed, bool store = true) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int N = (int)p.N;
+    const long long N = p.N;  // 64-bit population offsets q * N + n
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const int n = x + nx * (y + ny * z);
@@ -463,7 +463,7 @@ __device__ __forceinline__ void lbm_pair(const T *__restrict__ fin, T *__restric
                                          const LbmParams &p, int x0, int y, int z, float4 *__restrict__ vel,
                                          unsigned seed) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int N = (int)p.N;
+    const long long N = p.N;  // 64-bit population offsets q * N + n
     const int xm = x0 == 0 ? nx - 2 : x0 - 2, xp = x0 + 2 == nx ? 0 : x0 + 2;  // neighbouring pairs
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const int n0 = x0 + nx * (y + ny * z);
@@ -733,7 +733,7 @@ template <class T>
 __global__ void k_macro(const T *__restrict__ f, const float4 *__restrict__ F, LbmParams p,
                         const unsigned *__restrict__ bits, const float4 *__restrict__ vel, double *rho, double *u) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = (int)p.N;
+    const long long N = p.N;  // 64-bit population offsets q * N + n
     if (n >= N) return;
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll

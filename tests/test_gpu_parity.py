@@ -386,7 +386,8 @@ def test_empty_and_limit_inputs(P):
 
     ctx = P.cf_create(0)
     rejects("CF_EINVAL", P.cf_lbm_init, ctx, 0, 8, 8, 1.0, 0.0, 0.0)
-    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 1024, 1024, 111, 1.0, 0.0, 0.0)  # 19 N >= 2^31
+    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 1024, 1024, 1024, 1.0, 0.0, 0.0)  # N >= 2^30
+    rejects("CF_EINVAL", P.cf_lbm_init, ctx, 2, 2, 70000, 1.0, 0.0, 0.0)  # nz beyond a grid dimension
     rejects("CF_EINVAL", P.cf_lbm_init, ctx, 8, 8, 8, 1.0, 0.1, 0.0)  # Mach guard
     rejects("CF_EINVAL", P.cf_lbm_init, ctx, 8, 8, 8, 1.0, 0.0, 0.0, (np.inf, 0.0, 0.0))
     cell = small_cell()
@@ -692,6 +693,32 @@ def test_multicell_shear_full_size(P):
     assert rel(f, sim.last_forces) <= TOL
     assert rel(P.cf_get_velocity(ctx), sim.fluid.u) <= TOL
     assert_local_parity(P.cf_get_velocity(ctx), sim.fluid.u, y, sim.y, y0, (wl.nx, wl.ny, wl.nz), wl.delta)
+
+
+def test_lattice_with_more_than_two_billion_population_values(P):
+    """64-bit population offsets: a 1024 x 128 x 1024 Couette start-up
+    (134 M nodes, 19 N = 2.55e9 > 2^31 population values, 20 GB of FP32
+    populations) against the same start-up on a 4 x 128 x 4 lattice. The
+    flow is uniform in x and z, so every node of a row of constant y does
+    the same arithmetic on the same values in both: the fields must agree bit
+    for bit at every node."""
+    big, small = (1024, 128, 1024), (4, 128, 4)
+    out = []
+    for nx, ny, nz in (big, small):
+        ctx = P.cf_create(0)
+        P.cf_lbm_init(ctx, nx, ny, nz, 1.0, -0.05, 0.05)
+        P.cf_step(ctx, 5)
+        out.append((P.cf_get_velocity(ctx), P.cf_get_density(ctx)))
+        P.cf_destroy(ctx)
+    (ub, rb), (us, rs) = out
+    assert ub.shape == (1024, 128, 1024, 3)
+    assert np.abs(us).max() > 1e-3  # the walls have moved the fluid
+    for z in (0, 511, 1023):  # rows of y at several (x, z), the highest offsets included
+        for x in (0, 700, 1023):
+            assert np.array_equal(ub[z, :, x], us[z % 4, :, x % 4])
+            assert np.array_equal(rb[z, :, x], rs[z % 4, :, x % 4])
+    # and everywhere: every (x, z) column equals the small lattice's
+    assert np.array_equal(ub, np.broadcast_to(us[:1, :, :1], ub.shape))
 
 
 def test_contexts_in_two_host_threads(P):
