@@ -213,7 +213,7 @@ cf_status enqueue_steps(cf_ctx *c, Kind kind, int p0, int s0, int nsteps, cudaSt
         CUDA_TRY(c, launch_chain_step(c, m, p, sh, acc, sc));
         if (i > 0) CUDA_TRY(c, cudaStreamWaitEvent(sc, ev_far[i - 1], 0));
         CUDA_TRY(c, launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, c->vel,
-                                    sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
+                                    sh.near_rows || !c->near_tiles_fit ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, sc));
         CUDA_TRY(c, cudaEventRecord(ev_near[i], sc));
     }
     if (kind == Kind::Single) {  // K5 of the last step, after its near field in sc order
@@ -490,7 +490,10 @@ cf_status cf_lbm_init(cf_ctx *c, int32_t nx, int32_t ny, int32_t nz, double tau,
     shape_to_lbm(p, c->shape);
     c->region_bits_max = (tmax + 31) / 32;
     c->region_stride = (c->region_bits_max + 31) / 32 * 32;
-    if (prepare_near_field((long long)c->region_bits_max) != cudaSuccess)
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    c->near_tiles_fit = sizeof(int) * (c->region_bits_max + 1) + 256 <= (size_t)smem_optin;  // + static
+    if (c->near_tiles_fit && prepare_near_field((long long)c->region_bits_max) != cudaSuccess)
         return fail(c, CF_ECUDA, "shared-memory opt-in of the near field failed");
     const size_t pop = pop_bytes(p.fmt) * 19 * (size_t)N;
     CUDA_TRY(c, cudaMalloc(&c->f[0], pop));
@@ -973,7 +976,7 @@ cf_status timed_steps(cf_ctx *c, int n, const Shape &sh, double acc[5]) {
             cudaEventRecord(E[4], s);
             if (cells && e == cudaSuccess)
                 e = launch_lbm_near(c->f[p], c->f[1 - p], c->F, c->lp, use.bits, c->vel,
-                                    sh.near_rows ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, s);
+                                    sh.near_rows || !c->near_tiles_fit ? 0 : near_grid(c), c->seed + p, c->seed + 1 - p, s);
             cudaEventRecord(E[5], s);
             c->cur ^= 1;
             c->tstep += 1;

@@ -115,6 +115,10 @@ struct cf_ctx {
     // with the most tiles)
     unsigned *region = nullptr;
     size_t region_stride = 0, region_bits_max = 0;
+    // the tile form of the near field keeps running counts of the region
+    // bitset in shared memory: false when they do not fit (lattices of more
+    // than ~470 M nodes), and the near field then runs in rows
+    bool near_tiles_fit = true;
     Shape shape;
     int sms = 152;  // multiprocessors of the device
 
