@@ -144,6 +144,21 @@ def test_fixed_spread_with_stochastic_rounding_is_bit_identical(P):
     same_state(a, b, utol=1e-4)
 
 
+def test_fixed_spread_full_size_long_run_repeats(P):
+    """The production shear at full size (128^3, R = 16 cell, Ca = 0.2) for
+    5,000 steps in two launch shapes (the default, and 32 x 2 x 4 tiles with
+    the near field in rows, L2-cached populations and the one-thread
+    interpolation): identical positions and populations after 5,000 steps,
+    where float atomics let runs drift apart."""
+    wl = configs.production_shear(ca=0.2, w=0.5)
+    a = run(P, wl, 5000)
+    b = run(P, wl, 5000, {"tile_x": 32, "tile_y": 2, "tile_z": 4, "near_rows": 1, "pop_l2": 1,
+                          "interp_form": 1})
+    same_state(a, b)
+    y0 = wl.cells[0].y0
+    assert np.abs(a[0] - y0).max() > 0.5  # the cell has moved and deformed
+
+
 def test_spread_mode_is_validated(P):
     ctx = P.cf_create(0)
     with pytest.raises(P.CellFSIError) as e:
