@@ -69,3 +69,30 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(P, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(ImportError):
         P.lib()
+
+
+def _gcc(args, tmp_path):
+    r = subprocess.run(["gcc", *args], capture_output=True, text=True, cwd=tmp_path)
+    assert r.returncode == 0, r.stderr
+
+
+def test_header_is_plain_c_and_every_symbol_links(libpath, tmp_path):
+    """The header compiles as strict C99 (no C++ in it), and a C program
+    that takes the address of every declared entry point links against the
+    library (run without a GPU: nothing is called)."""
+    names = declared()
+    src = tmp_path / "all.c"
+    src.write_text('#include "cellfsi.h"\ntypedef void (*fn)(void);\nfn table[] = {\n' +
+                   ",\n".join(f"    (fn){n}" for n in names) +
+                   "\n};\nint main(void) { return table[0] == 0; }\n")
+    libdir = os.path.dirname(libpath)
+    _gcc(["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+          str(src), "-L", libdir, "-lcellfsi", "-o", str(tmp_path / "all")], tmp_path)
+
+
+def test_c_driver_compiles_and_links(libpath, tmp_path):
+    """tests/c_abi_shear.c (the C program of the GPU test that drives a
+    coupled run through the ABI alone) builds warning-free as C99."""
+    _gcc(["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+          os.path.join(ROOT, "tests", "c_abi_shear.c"), "-L", os.path.dirname(libpath), "-lcellfsi",
+          "-o", str(tmp_path / "c_abi_shear")], tmp_path)

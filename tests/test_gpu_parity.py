@@ -6,6 +6,8 @@ Tolerances: norm-wise relative error ||x_gpu - x_oracle|| / ||x_oracle||
 FP64); bit-exact on tet orientation and incidence rows. Element-wise errors
 are not used because forces near the rest state are ~0.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -719,6 +721,50 @@ def test_lattice_with_more_than_two_billion_population_values(P):
             assert np.array_equal(rb[z, :, x], rs[z % 4, :, x % 4])
     # and everywhere: every (x, z) column equals the small lattice's
     assert np.array_equal(ub, np.broadcast_to(us[:1, :, :1], ub.shape))
+
+
+def test_c_program_through_the_abi_alone(P, tmp_path):
+    """A C program (tests/c_abi_shear.c) compiled with gcc against the
+    library drives a coupled shear run through the C ABI alone: its
+    positions and velocity field are the bits of the same run made through
+    the Python binding (both with the fixed-point spread) and match the
+    oracle at 1e-5."""
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib = os.path.join(root, "paper_2003_03130_gb300")
+    exe = str(tmp_path / "c_abi_shear")
+    r = subprocess.run(["gcc", "-std=c99", "-O2", "-I", os.path.join(root, "include"),
+                        os.path.join(root, "tests", "c_abi_shear.c"), "-L", lib, "-lcellfsi",
+                        "-Wl,-rpath," + lib, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    wl = configs.small_shear()
+    c = wl.cells[0]
+    steps = 30
+    with open(tmp_path / "in.bin", "wb") as f:
+        np.array([wl.nx, wl.ny, wl.nz], np.int32).tofile(f)
+        np.array([wl.tau, wl.u_wall_lo, wl.u_wall_hi, c.mu, c.kappa, c.w], np.float64).tofile(f)
+        np.array([len(c.x_ref), len(c.tets)], np.int32).tofile(f)
+        np.ascontiguousarray(c.x_ref, np.float64).tofile(f)
+        np.ascontiguousarray(c.y0, np.float64).tofile(f)
+        np.ascontiguousarray(c.tets, np.int32).tofile(f)
+    r = subprocess.run([exe, str(tmp_path / "in.bin"), str(tmp_path / "out.bin"), str(steps)], capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    out = np.fromfile(tmp_path / "out.bin", np.float64)
+    nv = len(c.x_ref)
+    y_c, u_c = out[:3 * nv].reshape(nv, 3), out[3 * nv:].reshape(wl.nz, wl.ny, wl.nx, 3)
+    ctx = P.cf_create(0)
+    P.cf_set_spread(ctx, "fixed")
+    (cid,) = P.load_workload(ctx, wl)
+    P.cf_step(ctx, steps)
+    assert np.array_equal(y_c, P.cf_get_positions(ctx, cid))
+    assert np.array_equal(u_c, P.cf_get_velocity(ctx))
+    P.cf_destroy(ctx)
+    sim = oracle.Coupled(wl)
+    sim.step(steps)
+    assert rel(y_c - c.y0, sim.y - c.y0) <= TOL
+    assert rel(u_c, sim.fluid.u) <= TOL
 
 
 def test_contexts_in_two_host_threads(P):
