@@ -351,6 +351,20 @@ def cpu_baseline(wl, seconds):
     return out
 
 
+def suspension_cpu_baseline():
+    """The oracle (FP64, as it stands, one thread) on the 400-cell suspension:
+    one untimed step, then whole steps for at least a second (one step takes
+    ~18 s there)."""
+    import oracle
+    from workloads import configs
+
+    oracle.build()
+    n, dt = _oracle_sample((configs.batched_channel(), 1.0))
+    return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} whole coupled step(s) of the 400-cell suspension (512x256x256, 6.0 M tets) after one "
+                      "untimed step, FP64, 1 thread"}
+
+
 def precision_block(P, torch, dev, steps):
     """FP32, FP16 and BF16 population storage (round to nearest, and
     stochastic rounding: f16sr, bf16sr) on the pressure-driven channel
@@ -660,6 +674,8 @@ def run_ours(args):
                      and args.spread == "float")
     if rank == 0 and world == 1 and default_shear and args.suspension_steps > 0:
         out["suspension"] = suspension_block(P, torch, dev, args.suspension_steps, peak)
+        if not args.no_cpu_baseline:
+            out["suspension"]["cpu_baseline"] = suspension_cpu_baseline()
     if rank == 0 and world == 1 and default_shear and args.compression_iters > 0:
         m = compression_measure(args.compression_iters)
         out["compression"] = {k: m[k] for k in ("steps_per_s", "steps", "config", "tet_forces_per_s", "adjoint",
