@@ -139,6 +139,9 @@ def parse():
                     help="shear workload: run the 9 (Ca, w) cases of the production shear for "
                          "--sweep-steps steps each and print the Taylor deformation, inclination and "
                          "cell strain every 100 steps")
+    ap.add_argument("--paper-sweep-steps", type=int, default=0,
+                    help="also run the paper's single-cell shear setup (160 x 240 x 80 box, R = 16, neo-Hookean "
+                         "w = 1) at Ca in {0.05, 0.1, 0.2, 0.3, 0.5} for this many steps each (0 = skip)")
     ap.add_argument("--sweep-steps", type=int, default=10000,
                     help="steps per (Ca, w) case of the production-shear sweep (0 = skip it in the "
                          "default run, which reports every 1,000th step)")
@@ -494,45 +497,50 @@ SWEEP_CA = (0.05, 0.2, 0.5)
 SWEEP_W = (0.0, 0.5, 1.0)
 
 
-def shear_sweep(P, torch, dev, steps, every):
+PAPER_SWEEP_CA = (0.05, 0.1, 0.2, 0.3, 0.5)
+
+
+def shear_sweep(P, torch, dev, steps, every, cases=None, make=None):
     """The production shear (128^3, R = 16, kappa = 50 mu) for every
-    (Ca, w) in {0.05, 0.2, 0.5} x {0, 0.5, 1}: `steps` coupled steps each,
-    with the Taylor deformation D, its printed-expression variant, the
-    inclination and the net cell strain (d_max - 2R) / 2R every `every`
-    steps, and the steps/s of each run."""
+    (Ca, w) in {0.05, 0.2, 0.5} x {0, 0.5, 1} (or the given cases and
+    workload maker): `steps` coupled steps each, with the Taylor deformation
+    D, its printed-expression variant, the inclination and the net cell
+    strain (d_max - 2R) / 2R every `every` steps, and the steps/s of each
+    run."""
     from workloads import configs
 
     out = []
     stream = torch.cuda.Stream(dev)
-    for ca in SWEEP_CA:
-        for w in SWEEP_W:
-            wl = configs.production_shear(ca=ca, w=w)
-            with torch.cuda.stream(stream):
-                ctx = P.cf_create(dev, stream.cuda_stream)
-                (cid,) = P.load_workload(ctx, wl)
-                P.cf_prepare_steps(ctx, every)
-                rows, t_dev, done, error = [], 0.0, 0, None
-                for k in range(0, steps, every):
-                    n = min(every, steps - k)
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    P.cf_step_async(ctx, n)
-                    e1.record(stream)
-                    try:
-                        P.cf_synchronize(ctx)
-                    except P.CellFSIError as e:  # e.g. a tet inverted: reported, the other cases still run
-                        error = f"{e.name} within steps {k + 1}-{k + n}: {e}"
-                        break
-                    t_dev += e0.elapsed_time(e1)
-                    done = k + n
-                    t = P.cf_get_taylor(ctx, cid)
-                    st = P.cf_get_cell_strain(ctx, cid, 2 * 16.0)
-                    rows.append([k + n, t["D"], t["D_literal"], t["inclination"], st["strain"]])
-                P.cf_destroy(ctx)
-            out.append({"ca": ca, "w": w, "mu": wl.cells[0].mu, "kappa": wl.cells[0].kappa,
-                        "steps_done": done, "error": error,
-                        "steps_per_s": done / (t_dev / 1e3) if t_dev > 0 else None,
-                        "columns": ["step", "D", "D_literal", "inclination_deg", "cell_strain"], "rows": rows})
+    cases = cases if cases is not None else [(ca, w) for ca in SWEEP_CA for w in SWEEP_W]
+    make = make or (lambda ca, w: configs.production_shear(ca=ca, w=w))
+    for ca, w in cases:
+        wl = make(ca, w)
+        with torch.cuda.stream(stream):
+            ctx = P.cf_create(dev, stream.cuda_stream)
+            (cid,) = P.load_workload(ctx, wl)
+            P.cf_prepare_steps(ctx, every)
+            rows, t_dev, done, error = [], 0.0, 0, None
+            for k in range(0, steps, every):
+                n = min(every, steps - k)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.cf_step_async(ctx, n)
+                e1.record(stream)
+                try:
+                    P.cf_synchronize(ctx)
+                except P.CellFSIError as e:  # e.g. a tet inverted: reported, the other cases still run
+                    error = f"{e.name} within steps {k + 1}-{k + n}: {e}"
+                    break
+                t_dev += e0.elapsed_time(e1)
+                done = k + n
+                t = P.cf_get_taylor(ctx, cid)
+                st = P.cf_get_cell_strain(ctx, cid, 2 * 16.0)
+                rows.append([k + n, t["D"], t["D_literal"], t["inclination"], st["strain"]])
+            P.cf_destroy(ctx)
+        out.append({"ca": ca, "w": w, "mu": wl.cells[0].mu, "kappa": wl.cells[0].kappa,
+                    "steps_done": done, "error": error,
+                    "steps_per_s": done / (t_dev / 1e3) if t_dev > 0 else None,
+                    "columns": ["step", "D", "D_literal", "inclination_deg", "cell_strain"], "rows": rows})
     return out
 
 
@@ -684,6 +692,14 @@ def run_ours(args):
         every = 100 if args.sweep else 1000
         sweep = shear_sweep(P, torch, dev, args.sweep_steps, every)
         out["shear_sweep"] = {"steps": args.sweep_steps, "every": every, "cases": sweep}
+    if rank == 0 and world == 1 and args.paper_sweep_steps > 0:
+        from workloads import configs
+
+        cases = [(ca, 1.0) for ca in PAPER_SWEEP_CA]
+        sweep = shear_sweep(P, torch, dev, args.paper_sweep_steps, 1000, cases,
+                            lambda ca, w: configs.paper_box_shear(ca=ca, w=w))
+        out["paper_box_sweep"] = {"workload": "paper_box_160x240x80_R16_neo-Hookean", "steps": args.paper_sweep_steps,
+                                  "every": 1000, "cases": sweep}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "shear":
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if world > 1:

@@ -88,6 +88,8 @@ def test_stream_collide_roofline_picks_the_longer_part_and_counts_its_bytes():
 
 def test_sweep_cases_cover_the_capillary_numbers_and_weights():
     assert bench.SWEEP_CA == (0.05, 0.2, 0.5) and bench.SWEEP_W == (0.0, 0.5, 1.0)
+    # the paper's own shear runs: neo-Hookean (w = 1) over a range of Ca
+    assert bench.PAPER_SWEEP_CA == (0.05, 0.1, 0.2, 0.3, 0.5)
 
 
 def test_step_roofline_adds_every_kernel_of_the_step():
