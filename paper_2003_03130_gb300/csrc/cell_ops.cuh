@@ -1,7 +1,7 @@
 // Per-element bodies of the cell kernels, shared by the separate launches
 // (csrc/tet_force.cu, csrc/ibm.cu) and the fused persistent chain
-// (csrc/chain.cu): tet corner forces, the per-vertex region marking, and the
-// vertex sum with its spread.
+// (csrc/chain.cu): tet corner forces, the per-vertex region marking, the
+// vertex sum with its spread, and the interpolation's partial sums.
 #pragma once
 
 #include "mr.cuh"
